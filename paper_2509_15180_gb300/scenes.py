@@ -1,0 +1,241 @@
+"""Seeded synthetic scenes shaped like the paper's workloads.
+
+This module holds input generation only: random designs and obstacle sets,
+no model arithmetic.  Both the CUDA path and the FP64 oracle consume its
+output, so that the two start from bit-identical float32 inputs.
+
+The paper's planning environments exist only as figures (Sec. 6.2), so
+seeded clutter stands in for them.  Every stream is numpy PCG64 with
+seed = 1000 * config + replicate; instances are drawn one after another
+from that stream, so the first k instances of a configuration do not depend
+on how many are drawn in total.
+
+Scene dictionary (CSR over instances; float32 unless noted):
+  n_links[int32 n]   target link count (one link grows per step)
+  l_seg, radius, pressure [n]      segment length (m), body radius (m), pressure (Pa)
+  base[n, 3]         base x, y (m) and heading (rad)
+  act_ptr[int32 n+1], act_begin, act_end (link units, begin < end),
+  act_side[int8] (+1 / -1), act_pressure (Pa), act_l0 (sPAM cell length, m)
+  obs_ptr[int32 n+1], obs_kind[uint8] (0 circle, 1 axis-aligned box),
+  obs_cx, obs_cy (m), obs_a (circle radius or box half-width), obs_b (box half-height)
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = ["config1", "config2", "config3", "config4", "make", "serve_requests", "robot_link_steps",
+           "concat", "subset"]
+
+
+def _rng(config: int, replicate: int = 0) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(1000 * config + replicate))
+
+
+def _cell_length(l_seg: float) -> float:
+    """sPAM cell length: the segment length on the 1 mm fabrication grid (Sec. 4.2)."""
+    return round(l_seg * 1000.0) / 1000.0
+
+
+def _obstacles(rng, n_circ, n_box, r_rng, half_rng, x0, S, keep_out):
+    """Obstacles with centres uniform in [x0, x0+S] x [-S/2, S/2]; an obstacle
+    whose bounding circle reaches into the keep-out disc around the base is
+    redrawn."""
+    kinds, cx, cy, a, b = [], [], [], [], []
+    for kind, count in ((0, n_circ), (1, n_box)):
+        for _ in range(count):
+            while True:
+                x = rng.uniform(x0, x0 + S)
+                y = rng.uniform(-0.5 * S, 0.5 * S)
+                if kind == 0:
+                    ra = rng.uniform(*r_rng)
+                    rb = 0.0
+                    reach = ra
+                else:
+                    ra = rng.uniform(*half_rng)
+                    rb = rng.uniform(*half_rng)
+                    reach = float(np.hypot(ra, rb))
+                if np.hypot(x, y) > reach + keep_out:
+                    break
+            kinds.append(kind); cx.append(x); cy.append(y); a.append(ra); b.append(rb)
+    return kinds, cx, cy, a, b
+
+
+def _actuators(rng, n_act, n_links, span_rng, p_rng):
+    out = []
+    for _ in range(n_act):
+        span = int(rng.integers(span_rng[0], span_rng[1] + 1))
+        span = min(span, n_links)
+        begin = int(rng.integers(0, n_links - span + 1))
+        side = 1 if rng.random() < 0.5 else -1
+        pa = rng.uniform(*p_rng)
+        out.append((float(begin), float(begin + span), side, pa))
+    return out
+
+
+def _pack(rows):
+    """rows: list of dicts with keys n_links, l_seg, radius, pressure, base, acts, obs."""
+    n = len(rows)
+    sc = {
+        "n_links": np.array([r["n_links"] for r in rows], np.int32),
+        "l_seg": np.array([r["l_seg"] for r in rows], np.float32),
+        "radius": np.array([r["radius"] for r in rows], np.float32),
+        "pressure": np.array([r["pressure"] for r in rows], np.float32),
+        "base": np.array([r["base"] for r in rows], np.float32).reshape(n, 3),
+    }
+    acts = [r["acts"] for r in rows]
+    sc["act_ptr"] = np.concatenate([[0], np.cumsum([len(a) for a in acts])]).astype(np.int32)
+    flat = [x for a in acts for x in a]
+    sc["act_begin"] = np.array([x[0] for x in flat], np.float32)
+    sc["act_end"] = np.array([x[1] for x in flat], np.float32)
+    sc["act_side"] = np.array([x[2] for x in flat], np.int8)
+    sc["act_pressure"] = np.array([x[3] for x in flat], np.float32)
+    sc["act_l0"] = np.array([_cell_length(r["l_seg"]) for r in rows for _ in r["acts"]], np.float32)
+    obs = [r["obs"] for r in rows]
+    sc["obs_ptr"] = np.concatenate([[0], np.cumsum([len(o[0]) for o in obs])]).astype(np.int32)
+    sc["obs_kind"] = np.array([k for o in obs for k in o[0]], np.uint8)
+    for key, idx in (("obs_cx", 1), ("obs_cy", 2), ("obs_a", 3), ("obs_b", 4)):
+        sc[key] = np.array([v for o in obs for v in o[idx]], np.float32)
+    return sc
+
+
+def config1(n_inst: int = 64, replicate: int = 0) -> dict:
+    """64 robots x 20 links of 2 cm, R 2.5 cm, P 5 kPa; with probability 1/2 one
+    actuator over 5 consecutive links at U[0, 10] kPa; 10 circles of radius
+    U[1, 3] cm in a 0.5 m box ahead of the base."""
+    rng = _rng(1, replicate)
+    rows = []
+    for _ in range(n_inst):
+        N, ls, R, P = 20, 0.02, 0.025, 5000.0
+        acts = _actuators(rng, 1, N, (5, 5), (0.0, 10000.0)) if rng.random() < 0.5 else []
+        obs = _obstacles(rng, 10, 0, (0.01, 0.03), None, 0.05, 0.5, R + ls)
+        rows.append(dict(n_links=N, l_seg=ls, radius=R, pressure=P, base=(0.0, 0.0, 0.0), acts=acts, obs=obs))
+    return _pack(rows)
+
+
+def config2(n_inst: int = 4096, replicate: int = 0) -> dict:
+    """4096 robots x 100 links of 1.5 cm, R U[2, 4] cm, P U[2, 10] kPa; 0-6
+    actuators over 3-15 links at U[0, 15] kPa; 20 circles (r U[1, 5] cm) and
+    20 boxes (sides U[2, 10] cm) in a 1.5 m box."""
+    rng = _rng(2, replicate)
+    rows = []
+    for _ in range(n_inst):
+        N, ls = 100, 0.015
+        R = rng.uniform(0.02, 0.04)
+        P = rng.uniform(2000.0, 10000.0)
+        acts = _actuators(rng, int(rng.integers(0, 7)), N, (3, 15), (0.0, 15000.0))
+        obs = _obstacles(rng, 20, 20, (0.01, 0.05), (0.01, 0.05), 0.05, 1.5, R + ls)
+        rows.append(dict(n_links=N, l_seg=ls, radius=R, pressure=P, base=(0.0, 0.0, 0.0), acts=acts, obs=obs))
+    return _pack(rows)
+
+
+def config3(n_inst: int = 16384, replicate: int = 0, n_range=(30, 300)) -> dict:
+    """Uneven batch: links U{30..300} of U[1, 3] cm, R and P as config 2, 0-8
+    actuators, 5-200 obstacles (half circles, half boxes) in a box whose side
+    is the robot's length."""
+    rng = _rng(3, replicate)
+    rows = []
+    for _ in range(n_inst):
+        N = int(rng.integers(n_range[0], n_range[1] + 1))
+        ls = rng.uniform(0.01, 0.03)
+        R = rng.uniform(0.02, 0.04)
+        P = rng.uniform(2000.0, 10000.0)
+        acts = _actuators(rng, int(rng.integers(0, 9)), N, (3, 15), (0.0, 15000.0))
+        n_obs = int(rng.integers(5, 201))
+        S = N * ls
+        obs = _obstacles(rng, n_obs // 2, n_obs - n_obs // 2, (0.01, 0.05), (0.01, 0.05), 0.05, S, R + ls)
+        rows.append(dict(n_links=N, l_seg=ls, radius=R, pressure=P, base=(0.0, 0.0, 0.0), acts=acts, obs=obs))
+    return _pack(rows)
+
+
+def config4(n_designs: int = 64, n_perturb: int = 1024, replicate: int = 0) -> tuple[dict, np.ndarray]:
+    """Robustness batch: designs as config 2 with 150 links and 60 obstacles in
+    a 2.25 m box, each perturbed n_perturb times (obstacle centres + N(0, 1 cm),
+    actuator endpoints + N(0, 0.5 link), pressures x U[0.95, 1.05]).  Returns
+    the scene and one goal point per instance (uniform in the far half of the
+    design's box)."""
+    rng = _rng(4, replicate)
+    rows, goals = [], []
+    for _ in range(n_designs):
+        N, ls = 150, 0.015
+        R = rng.uniform(0.02, 0.04)
+        P = rng.uniform(2000.0, 10000.0)
+        acts = _actuators(rng, int(rng.integers(0, 7)), N, (3, 15), (0.0, 15000.0))
+        S = 2.25
+        obs = _obstacles(rng, 30, 30, (0.01, 0.05), (0.01, 0.05), 0.05, S, R + ls)
+        goal = (rng.uniform(0.05 + 0.5 * S, 0.05 + S), rng.uniform(-0.5 * S, 0.5 * S))
+        for _ in range(n_perturb):
+            pk, pcx, pcy, pa, pb = obs
+            ncx = list(np.asarray(pcx) + rng.normal(0.0, 0.01, len(pcx)))
+            ncy = list(np.asarray(pcy) + rng.normal(0.0, 0.01, len(pcy)))
+            pacts = []
+            for (b0, e0, sd, pp) in acts:
+                b1 = float(np.clip(b0 + rng.normal(0.0, 0.5), 0.0, N - 0.5))
+                e1 = float(np.clip(e0 + rng.normal(0.0, 0.5), b1 + 0.5, N))
+                pacts.append((b1, e1, sd, pp * rng.uniform(0.95, 1.05)))
+            rows.append(dict(n_links=N, l_seg=ls, radius=R, pressure=P, base=(0.0, 0.0, 0.0), acts=pacts,
+                             obs=(pk, ncx, ncy, pa, pb)))
+            goals.append(goal)
+    return _pack(rows), np.array(goals, np.float32)
+
+
+def make(config: int, n_inst: int | None = None, replicate: int = 0) -> dict:
+    if config == 1:
+        return config1(64 if n_inst is None else n_inst, replicate)
+    if config == 2:
+        return config2(4096 if n_inst is None else n_inst, replicate)
+    if config == 3:
+        return config3(16384 if n_inst is None else n_inst, replicate)
+    raise ValueError("unknown configuration %r" % config)
+
+
+def serve_requests(n_req: int, rate_hz: float = 2000.0, replicate: int = 0, max_inst: int = 256):
+    """Poisson request stream for the serving loop: arrival times (s) and, per
+    request, a scene of U{1..max_inst} instances drawn as config 3 but with
+    links U{20..300}."""
+    rng = _rng(5, replicate)
+    t = np.cumsum(rng.exponential(1.0 / rate_hz, n_req))
+    sizes = rng.integers(1, max_inst + 1, n_req)
+    reqs = []
+    for k in range(n_req):
+        sub = config3(int(sizes[k]), replicate=5000 + 7919 * replicate + k, n_range=(20, 300))
+        reqs.append(sub)
+    return t, reqs
+
+
+def robot_link_steps(n_links) -> int:
+    """Sum over steps of the links present: N (N + 1) / 2 per instance grown from one link."""
+    n = np.asarray(n_links, dtype=np.int64)
+    return int((n * (n + 1) // 2).sum())
+
+
+def subset(scene: dict, idx) -> dict:
+    """Scene restricted to the instances idx (in that order)."""
+    idx = np.asarray(idx, dtype=np.int64)
+    out = {k: np.asarray(scene[k])[idx] for k in ("n_links", "l_seg", "radius", "pressure", "base")}
+    for pre, ptr in (("act", "act_ptr"), ("obs", "obs_ptr")):
+        p = np.asarray(scene[ptr])
+        cnt = p[idx + 1] - p[idx]
+        out[ptr] = np.concatenate([[0], np.cumsum(cnt)]).astype(np.int32)
+        sel = np.concatenate([np.arange(p[i], p[i + 1]) for i in idx]) if len(idx) else np.zeros(0, np.int64)
+        sel = sel.astype(np.int64)
+        for k in scene:
+            if k.startswith(pre + "_") and k != ptr:
+                out[k] = np.asarray(scene[k])[sel]
+    return out
+
+
+def concat(scenes) -> dict:
+    """Concatenate scenes instance-wise."""
+    out = {}
+    for k in ("n_links", "l_seg", "radius", "pressure", "base"):
+        out[k] = np.concatenate([s[k] for s in scenes])
+    for pre, ptr in (("act", "act_ptr"), ("obs", "obs_ptr")):
+        ptrs, base = [np.zeros(1, np.int32)], 0
+        for s in scenes:
+            ptrs.append(np.asarray(s[ptr][1:], np.int64) + base)
+            base += int(s[ptr][-1])
+        out[ptr] = np.concatenate(ptrs).astype(np.int32)
+        for k in scenes[0]:
+            if k.startswith(pre + "_") and k != ptr:
+                out[k] = np.concatenate([s[k] for s in scenes])
+    return out
