@@ -1,0 +1,230 @@
+/*
+ * vine.h -- C ABI of the GB300 library for the batched quasi-static growth
+ * step of planar vine robots, "Parallel Simulation of Contact and Actuation
+ * for Soft Growing Robots" (arXiv 2509.15180).
+ *
+ * What one growth step computes (Sec. 3-4 of the paper):
+ *   - a link is added at the tip (Sec. 4.1: only the distal length l_last
+ *     changes; every other link keeps length l_seg),
+ *   - per joint, the wrinkling-based restoring moment of the inflated body
+ *     (Sec. 3.2, Eq. wrinkling_model) and the moment of every sPAM actuator
+ *     covering the joint (Sec. 3.1, Eq. sPAM_model; Sec. 3.3,
+ *     Eq. restoring_moment) are summed,
+ *   - every link is tested against the robot's obstacles for penetration,
+ *   - the cost of Eq. (pbd) (weights w_a, w_b, w_c of Sec. 4.1, used in
+ *     potential form so that its stationary point is the moment balance with
+ *     contact forces) is brought to equilibrium from the previous state
+ *     (Algorithm 1, read as "the equilibrium reached from the warm start").
+ *
+ * Conventions for every entry point:
+ *   - Return value: vine_status.  No C++ exception crosses this boundary.
+ *     On failure vine_last_error() returns a thread-local message.
+ *   - Per-instance failures do not fail a call; they are reported in the
+ *     per-instance status (vine_inst_status).
+ *   - Streams: `cuda_stream` is a cudaStream_t (NULL = legacy default
+ *     stream).  Calls that only enqueue device work are asynchronous on that
+ *     stream.  Calls that read or write HOST memory synchronise the stream
+ *     before returning.
+ *   - Ownership: inputs are caller-owned and are copied during the call;
+ *     the caller may free them afterwards.  Outputs go to caller buffers.
+ *     Opaque handles are library-owned and released by the matching
+ *     *_destroy call.
+ *   - Units: SI (m, Pa, N, rad).  Link indices and actuator spans are in
+ *     link units (link k covers [k, k+1)).
+ */
+#ifndef VINE_H_
+#define VINE_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  VINE_OK = 0,
+  VINE_EINVAL = 1,         /* malformed argument or descriptor */
+  VINE_ENOMEM = 2,         /* device allocation failed */
+  VINE_ECUDA = 3,          /* CUDA runtime error (message in vine_last_error) */
+  VINE_ETIMEOUT = 4,       /* a bounded wait ran out */
+  VINE_EBUSY = 5,          /* admission refused, retry later */
+  VINE_ENOTCONVERGED = 6   /* reserved */
+} vine_status;
+
+typedef enum {
+  VINE_INST_OK = 0,        /* every step converged */
+  VINE_INST_MAXITER = 1,   /* some step hit max_iter before the tolerance */
+  VINE_INST_NONFINITE = 2, /* the state became NaN/Inf; the instance stopped */
+  VINE_INST_BADINPUT = 3   /* invalid design or obstacle values; never stepped */
+} vine_inst_status;
+
+/* Model and solver constants.  Fill with vine_params_default().
+ * w_a, w_b, w_c: weights of Eq. (pbd), Sec. 4.1 (160, 15, 1).
+ * eps_crit: critical wrinkling strain of Sec. 3.2 (fitted in the paper, value
+ *   not printed; default 0.01).
+ * R_c, R_act, a_spam: sPAM constants of Sec. 3.1 / 4.2 (5 mm, 17.18 mm, 1e-4).
+ * m_lo: lower end of the contraction parameter range of the force table (0.002).
+ * pen_frac: contact stiffness k_c = w_a pi P R^3 / (2 pen_frac R l_seg) (0.01).
+ * tol: convergence when the predicted displacement of every link end point
+ *   (and l_seg times every joint step) is at most tol times the robot length
+ *   N l_seg (1e-6); the test is evaluated in FP64.
+ * ls_switch: above this predicted displacement the step is line-searched
+ *   (Armijo on the cost, constant armijo_c1, at most max_halvings halvings).
+ * max_iter: Gauss-Newton iterations per growth step (100).
+ * discs_per_link: contact discs K_s of radius R at fractions k/K_s of each
+ *   link (2; 1..4 supported).
+ * mode, gd_alpha, gd_steps: reserved for the fixed-step gradient descent of
+ *   Algorithm 1 (mode 0 = equilibrium; only mode 0 is implemented). */
+typedef struct {
+  double w_a, w_b, w_c;
+  double eps_crit;
+  double R_c, R_act, a_spam;
+  double m_lo;
+  double pen_frac;
+  double tol;
+  double ls_switch;
+  double armijo_c1;
+  int32_t max_iter;
+  int32_t discs_per_link;
+  int32_t max_halvings;
+  int32_t mode;
+  double gd_alpha;
+  int32_t gd_steps;
+  int32_t reserved;
+} vine_params;
+
+/* Batch of independent robot instances, structure-of-arrays with CSR
+ * offsets.  All pointers are caller-owned; mem_is_device = 0 means host
+ * memory, 1 means device memory of the current device.
+ *   n_links[n]      target link count (>= 1); one link grows per step
+ *   l_seg[n]        segment length (m, > 0)
+ *   radius[n]       body radius R_vine (m, > 0)
+ *   pressure[n]     body pressure P_vine (Pa, > 0)
+ *   base[3n]        base x, y (m) and heading (rad)
+ *   act_ptr[n+1]    actuators of instance i are act_ptr[i] .. act_ptr[i+1]-1
+ *   act_begin/end   span [begin, end) in link units, 0 <= begin < end
+ *   act_side        +1 / -1: side the actuator pulls toward
+ *   act_pressure    actuation pressure P_act (Pa, >= 0)
+ *   act_l0          sPAM cell length l_0 (m, > 0)
+ *   obs_ptr[n+1]    obstacles of instance i are obs_ptr[i] .. obs_ptr[i+1]-1
+ *   obs_kind        0 circle (obs_a = radius), 1 axis-aligned box (obs_a,
+ *                   obs_b = half-width, half-height)
+ *   obs_cx, obs_cy  centre (m)
+ * Limits: n_links <= 1024, at most 1024 obstacles and 64 actuators per
+ * instance.  Values outside their ranges mark the instance BADINPUT. */
+typedef struct {
+  int32_t n_inst;
+  int32_t mem_is_device;
+  const int32_t* n_links;
+  const float* l_seg;
+  const float* radius;
+  const float* pressure;
+  const float* base;
+  const int32_t* act_ptr;
+  const float* act_begin;
+  const float* act_end;
+  const int8_t* act_side;
+  const float* act_pressure;
+  const float* act_l0;
+  const int32_t* obs_ptr;
+  const uint8_t* obs_kind;
+  const float* obs_cx;
+  const float* obs_cy;
+  const float* obs_a;
+  const float* obs_b;
+} vine_batch_desc;
+
+typedef struct vine_batch vine_batch;
+
+/* Per-batch counters (all instances), filled by vine_get_stats. */
+typedef struct {
+  int64_t robot_link_steps;  /* sum over converged steps of the links present */
+  int64_t steps_converged;
+  int64_t steps_total;
+  int64_t iterations;        /* Gauss-Newton iterations */
+  int64_t evaluations;       /* cost/gradient evaluations (incl. line search) */
+  int64_t link_evaluations;  /* sum over evaluations of the links present */
+  int64_t pair_tests;        /* disc-obstacle tests: sum over evaluations of N K_s n_obs */
+  int64_t circle_pair_tests; /* the part of pair_tests against circles */
+  int32_t n_maxiter, n_nonfinite, n_badinput, reserved;
+} vine_stats;
+
+/* Defaults listed above. */
+vine_status vine_params_default(vine_params* out);
+
+/* Copies the descriptor to the device, validates every instance, builds the
+ * sPAM force tables (one per distinct l_0: FP64 solves of Eq. sPAM_1/sPAM_2
+ * on 256 uniform strain knots) and the wrinkling-energy table, and leaves
+ * every instance with zero links.  Synchronises `cuda_stream`. */
+vine_status vine_batch_create(const vine_batch_desc* desc, const vine_params* params, void* cuda_stream,
+                              vine_batch** out);
+
+/* Back to zero links for every instance (statistics cleared).  Async. */
+vine_status vine_batch_reset(vine_batch* b, void* cuda_stream);
+
+/* Grows every instance by up to n_steps links (capped at its n_links), each
+ * step solved to equilibrium, in one persistent launch.  Async. */
+vine_status vine_grow_step(vine_batch* b, int32_t n_steps, void* cuda_stream);
+
+/* Grows every instance to its n_links: one persistent launch over a
+ * longest-first work queue, replayed from a CUDA graph.  Async. */
+vine_status vine_simulate(vine_batch* b, void* cuda_stream);
+
+/* Same result as vine_simulate, computed with one launch per instance in
+ * sequence (the comparison form).  Async. */
+vine_status vine_simulate_plain(vine_batch* b, void* cuda_stream);
+
+/* Current state.  Any output pointer may be NULL.  Layouts:
+ *   theta[sum n_links] (CSR by n_links; entries past the present links are 0)
+ *   l_last[n], n_present[n], iterations[n] (summed over steps),
+ *   residual[n] (largest final residual of any step, FP64),
+ *   inst_status[n] (vine_inst_status),
+ *   link_pose[3 * sum n_links]: start point x, y and heading of each link,
+ *   tip[2n]: distal end point.
+ * out_is_device = 1: outputs are device pointers (async);
+ * 0: host pointers (the stream is synchronised). */
+vine_status vine_get_state(const vine_batch* b, float* theta, float* l_last, float* link_pose, float* tip,
+                           int32_t* n_present, int32_t* iterations, double* residual, int32_t* inst_status,
+                           int32_t out_is_device, void* cuda_stream);
+
+/* Contact set at the current state: pairs (link k, obstacle o) with o the
+ * index within the instance's obstacles, such that some disc of link k
+ * penetrates obstacle o.  counts[n] receives the number of pairs of each
+ * instance (possibly more than max_pairs); pairs[n][max_pairs][2] receives
+ * the first max_pairs of them in (link, obstacle) order.  Memory flag and
+ * synchronisation as for vine_get_state. */
+vine_status vine_get_contacts(const vine_batch* b, int32_t* counts, int32_t* pairs, int32_t max_pairs,
+                              int32_t out_is_device, void* cuda_stream);
+
+/* Batch counters (host struct; synchronises the stream). */
+vine_status vine_get_stats(const vine_batch* b, vine_stats* out, void* cuda_stream);
+
+/* The prologue tables as used by the kernels (synchronous):
+ *   n_tab: number of sPAM force tables (one per distinct actuator l_0, in
+ *     order of first appearance among the actuators);
+ *   hdr[4 n_tab]: eps_lo, knot spacing h, 1/h, G(0) per table;
+ *   knots[2 * 256 n_tab]: (f_k, G_k): force per unit actuation pressure
+ *     (Eq. sPAM_force / P_act, m^2) at strain eps_lo + k h, and its integral
+ *     from eps_lo;
+ *   utab[2 * 1025]: (Uhat, mhat) of the wrinkling moment (Eq. wrinkling_model,
+ *     per unit pi P R^3) and its integral from 0, at theta_c + k h_u;
+ *   consts[4]: Uhat(pi), mhat(pi), theta_c, h_u.
+ * Any output pointer may be NULL. */
+vine_status vine_get_tables(const vine_batch* b, int32_t* n_tab, float* hdr, float* knots, float* utab,
+                            double* consts);
+
+/* Number of instances and total link capacity (sum of n_links). */
+vine_status vine_batch_info(const vine_batch* b, int32_t* n_inst, int64_t* total_links);
+
+/* Releases the batch (device memory freed after synchronising the device). */
+vine_status vine_batch_destroy(vine_batch* b);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* vine_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VINE_H_ */

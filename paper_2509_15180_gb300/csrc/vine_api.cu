@@ -1,0 +1,701 @@
+// vine_api.cu -- host side of the C ABI declared in include/vine.h.
+//
+// Batch creation validates the descriptor, builds the FP64 prologue tables on
+// the device, orders instances longest-first (cost ~ n_links^2 * n_obs: the
+// contact work of a robot grown from one link), sizes the shared-memory slice
+// of one warp for the largest robot and obstacle set, and records the
+// persistent launch of vine_simulate in a CUDA graph.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "vine.h"
+#include "vine_internal.cuh"
+
+using namespace vine;
+
+namespace {
+
+thread_local std::string g_err;
+
+vine_status fail(vine_status s, const char* msg) {
+  g_err = msg;
+  return s;
+}
+
+vine_status cuda_fail(cudaError_t e, const char* where) {
+  char buf[512];
+  std::snprintf(buf, sizeof(buf), "%s: %s", where, cudaGetErrorString(e));
+  g_err = buf;
+  return e == cudaErrorMemoryAllocation ? VINE_ENOMEM : VINE_ECUDA;
+}
+
+#define CK(call)                                         \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+  } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Device-side validation and encoding, one warp per instance.
+struct InitArgs {
+  int n_inst;
+  const int32_t* n_links;
+  const float *l_seg, *radius, *pressure, *base;
+  const int32_t* act_ptr;
+  const float *act_begin, *act_end;
+  const int8_t* act_side;
+  const float *act_pressure, *act_l0;
+  const int32_t* obs_ptr;
+  const uint8_t* obs_kind;
+  const float *obs_cx, *obs_cy, *obs_a, *obs_b;
+  const int* act_tab;   // per actuator: sPAM table index
+  const int* th_off;    // per instance: offset into theta
+  const int* status_h;  // per instance: structural check done on the host
+  double R_act, w_a, pen_frac;
+  InstDev* inst;
+  float4* obs;
+  float4* act;
+  int* status;
+};
+
+__device__ bool fin(float v) { return isfinite(v); }
+
+__global__ void init_kernel(const InitArgs A) {
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (i >= A.n_inst) return;
+  bool bad = A.status_h[i] != 0;
+  const float ls = A.l_seg[i], R = A.radius[i], P = A.pressure[i];
+  const float bx = A.base[3 * i], by = A.base[3 * i + 1], bpsi = A.base[3 * i + 2];
+  bad = bad || !(fin(ls) && ls > 0.f && fin(R) && R > 0.f && fin(P) && P > 0.f && fin(bx) && fin(by) && fin(bpsi));
+  const int a0 = A.act_ptr[i], a1 = A.act_ptr[i + 1], o0 = A.obs_ptr[i], o1 = A.obs_ptr[i + 1];
+  bool badl = false;
+  for (int a = a0 + lane; a < a1; a += 32) {
+    const float b = A.act_begin[a], e = A.act_end[a], pa = A.act_pressure[a], l0 = A.act_l0[a];
+    const int sd = A.act_side[a];
+    badl = badl || !(fin(b) && fin(e) && b >= 0.f && e > b && (sd == 1 || sd == -1) && fin(pa) && pa >= 0.f &&
+                     fin(l0) && l0 > 0.f);
+    int bits = A.act_tab[a] | (sd < 0 ? (int)0x80000000 : 0);
+    A.act[a] = make_float4(b, e, pa, __int_as_float(bits));
+  }
+  for (int o = o0 + lane; o < o1; o += 32) {
+    const int k = A.obs_kind[o];
+    const float cx = A.obs_cx[o], cy = A.obs_cy[o], a = A.obs_a[o], b = A.obs_b[o];
+    const float rx = (float)((double)cx - (double)bx), ry = (float)((double)cy - (double)by);
+    if (k == 0) {
+      badl = badl || !(fin(cx) && fin(cy) && fin(a) && a > 0.f);
+      const double rr = (double)R + (double)a;
+      A.obs[o] = make_float4(rx, ry, (float)rr, -(float)(rr * rr));
+    } else {
+      badl = badl || !(k == 1 && fin(cx) && fin(cy) && fin(a) && a > 0.f && fin(b) && b > 0.f);
+      A.obs[o] = make_float4(rx, ry, a, b);
+    }
+  }
+  bad = __any_sync(0xffffffffu, badl) || bad;
+  if (lane == 0) {
+    InstDev d;
+    const double Rd = R, Pd = P, ld = ls;
+    d.l_seg = ls;
+    d.R = R;
+    d.P = P;
+    d.d = (float)(2.0 * Rd + A.R_act);
+    d.kc = (float)(A.w_a * kPiD * Pd * Rd * Rd * Rd / (2.0 * A.pen_frac * Rd * ld));
+    d.kg = (float)(kPiD * Pd * Rd * Rd / (2.0 * ld));
+    d.PR3 = (float)(kPiD * Pd * Rd * Rd * Rd);
+    d.bpsi = bpsi;
+    d.bx = bx;
+    d.by = by;
+    d.pad0 = d.pad1 = 0.f;
+    d.n_target = A.n_links[i];
+    d.act_off = a0;
+    d.n_act = a1 - a0;
+    d.obs_off = o0;
+    d.n_obs = o1 - o0;
+    d.th_off = A.th_off[i];
+    d.n_circ = 0;
+    d.pad2 = 0;
+    A.inst[i] = d;
+    A.status[i] = bad ? kBadInput : kOK;
+  }
+}
+
+}  // namespace
+
+struct vine_batch {
+  int device = 0;
+  int n_inst = 0;
+  int64_t total_links = 0;
+  int n_tab = 0;
+  vine_params params{};
+  int ks = 2;
+  int nmax = 32, omax = 1, amax = 1;
+  size_t smem_warp = 0;
+  int grid = 1;
+  int max_target = 0;
+  void* dmem = nullptr;
+  void* stage = nullptr;  // lazily allocated host-output staging
+  size_t stage_bytes = 0;
+  GrowArgs args{};
+  int* status0 = nullptr;  // status after validation (restored by reset)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  std::vector<int> h_n_links, h_n_obs, h_n_circ;
+  std::vector<int> h_order;
+};
+
+extern "C" {
+
+const char* vine_last_error(void) { return g_err.c_str(); }
+
+vine_status vine_params_default(vine_params* p) {
+  if (!p) return fail(VINE_EINVAL, "vine_params_default: null pointer");
+  std::memset(p, 0, sizeof(*p));
+  p->w_a = 160.0;
+  p->w_b = 15.0;
+  p->w_c = 1.0;
+  p->eps_crit = 0.01;
+  p->R_c = 0.005;
+  p->R_act = 0.01718;
+  p->a_spam = 1e-4;
+  p->m_lo = 0.002;
+  p->pen_frac = 0.01;
+  p->tol = 1e-6;
+  p->ls_switch = 1e-3;
+  p->armijo_c1 = 1e-4;
+  p->max_iter = 100;
+  p->discs_per_link = 2;
+  p->max_halvings = 30;
+  p->mode = 0;
+  p->gd_alpha = 0.0;
+  p->gd_steps = 50;
+  return VINE_OK;
+}
+
+static vine_status copy_in(void* dst, const void* src, size_t bytes, int is_dev) {
+  if (bytes == 0) return VINE_OK;
+  if (!src) return fail(VINE_EINVAL, "vine_batch_create: null input array");
+  if (is_dev) {
+    CK(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
+  } else {
+    std::memcpy(dst, src, bytes);
+  }
+  return VINE_OK;
+}
+
+vine_status vine_batch_create(const vine_batch_desc* D, const vine_params* P, void* stream_v, vine_batch** out) {
+  if (!D || !out) return fail(VINE_EINVAL, "vine_batch_create: null descriptor or output");
+  *out = nullptr;
+  vine_params prm;
+  if (P) prm = *P; else vine_params_default(&prm);
+  if (prm.mode != 0) return fail(VINE_EINVAL, "vine_batch_create: only mode 0 (equilibrium) is implemented");
+  if (prm.discs_per_link < 1 || prm.discs_per_link > 4)
+    return fail(VINE_EINVAL, "vine_batch_create: discs_per_link must be 1..4");
+  if (!(prm.tol > 0.0) || prm.max_iter < 1 || prm.max_halvings < 0 || !(prm.eps_crit > 0.0 && prm.eps_crit < 1.0) ||
+      !(prm.R_c > 0.0 && prm.R_act > prm.R_c) || !(prm.m_lo > 0.0 && prm.m_lo < 0.5) || !(prm.pen_frac > 0.0))
+    return fail(VINE_EINVAL, "vine_batch_create: parameter out of range");
+  const int n = D->n_inst;
+  if (n <= 0) return fail(VINE_EINVAL, "vine_batch_create: n_inst must be positive");
+  const int dev = D->mem_is_device ? 1 : 0;
+  cudaStream_t st = (cudaStream_t)stream_v;
+
+  // ---- structure on the host
+  std::vector<int32_t> nl(n), aptr(n + 1), optr(n + 1);
+  vine_status s;
+  if ((s = copy_in(nl.data(), D->n_links, sizeof(int32_t) * n, dev)) != VINE_OK) return s;
+  if ((s = copy_in(aptr.data(), D->act_ptr, sizeof(int32_t) * (n + 1), dev)) != VINE_OK) return s;
+  if ((s = copy_in(optr.data(), D->obs_ptr, sizeof(int32_t) * (n + 1), dev)) != VINE_OK) return s;
+  if (aptr[0] != 0 || optr[0] != 0) return fail(VINE_EINVAL, "vine_batch_create: act_ptr/obs_ptr must start at 0");
+  for (int i = 0; i < n; ++i)
+    if (aptr[i + 1] < aptr[i] || optr[i + 1] < optr[i])
+      return fail(VINE_EINVAL, "vine_batch_create: act_ptr/obs_ptr must be non-decreasing");
+  const int n_act = aptr[n], n_obs = optr[n];
+  std::vector<float> l0(n_act);
+  std::vector<uint8_t> kind(n_obs);
+  if ((s = copy_in(l0.data(), D->act_l0, sizeof(float) * n_act, dev)) != VINE_OK) return s;
+  if ((s = copy_in(kind.data(), D->obs_kind, n_obs, dev)) != VINE_OK) return s;
+
+  auto B = new vine_batch();
+  B->params = prm;
+  B->ks = prm.discs_per_link;
+  B->n_inst = n;
+  cudaGetDevice(&B->device);
+  std::vector<int> status_h(n, 0), th_off(n, 0);
+  B->h_n_links.resize(n);
+  B->h_n_obs.resize(n);
+  B->h_n_circ.resize(n);
+  int64_t tot = 0;
+  int nmax = 1, omax = 1, amax = 1;
+  for (int i = 0; i < n; ++i) {
+    const int nli = nl[i], na = aptr[i + 1] - aptr[i], no = optr[i + 1] - optr[i];
+    const bool ok = nli >= 1 && nli <= kMaxLinks && na <= kMaxAct && no <= kMaxObs;
+    status_h[i] = ok ? 0 : 1;
+    th_off[i] = (int)tot;
+    const int cap = std::max(nli, 0);
+    tot += cap;
+    B->h_n_links[i] = ok ? nli : 0;
+    B->h_n_obs[i] = no;
+    int nc = 0;
+    for (int o = optr[i]; o < optr[i + 1]; ++o) nc += kind[o] == 0;
+    B->h_n_circ[i] = nc;
+    if (ok) {
+      nmax = std::max(nmax, nli);
+      omax = std::max(omax, no);
+      amax = std::max(amax, na);
+    }
+  }
+  if (tot > (int64_t)1 << 30) {
+    delete B;
+    return fail(VINE_EINVAL, "vine_batch_create: too many links in one batch");
+  }
+  B->total_links = tot;
+  B->max_target = nmax;
+  // ---- distinct sPAM cell lengths
+  std::vector<double> tabs;
+  std::vector<int> act_tab(n_act, 0);
+  for (int a = 0; a < n_act; ++a) {
+    const double v = l0[a];
+    if (!(std::isfinite(v) && v > 0.0)) continue;  // flagged bad on the device
+    auto it = std::find(tabs.begin(), tabs.end(), v);
+    if (it == tabs.end()) {
+      tabs.push_back(v);
+      act_tab[a] = (int)tabs.size() - 1;
+    } else {
+      act_tab[a] = (int)(it - tabs.begin());
+    }
+  }
+  B->n_tab = (int)tabs.size();
+  const int nt = std::max(B->n_tab, 1);
+
+  // ---- device memory
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += align256(std::max<size_t>(bytes, 16));
+    return o;
+  };
+  const size_t o_inst = take(sizeof(InstDev) * n), o_obs = take(sizeof(float4) * n_obs),
+               o_act = take(sizeof(float4) * n_act), o_hdr = take(sizeof(float4) * nt),
+               o_tab = take(sizeof(float2) * nt * kKnots), o_ut = take(sizeof(float2) * (kUCells + 1)),
+               o_th = take(sizeof(float) * tot), o_n = take(sizeof(int) * n), o_l = take(sizeof(float) * n),
+               o_st = take(sizeof(int) * n), o_st0 = take(sizeof(int) * n), o_it = take(sizeof(int) * n),
+               o_cv = take(sizeof(int) * n), o_sp = take(sizeof(int) * n), o_rls = take(sizeof(long long) * n),
+               o_ev = take(sizeof(long long) * n), o_le = take(sizeof(long long) * n),
+               o_rm = take(sizeof(double) * n), o_ord = take(sizeof(int) * n), o_cnt = take(sizeof(int) * 4);
+  const size_t persistent = off;
+  // setup scratch (freed at the end of create)
+  const size_t o_acttab = take(sizeof(int) * n_act), o_thoff = take(sizeof(int) * n),
+               o_sth = take(sizeof(int) * n), o_l0 = take(sizeof(double) * nt),
+               o_scr = take(sizeof(double) * (4 * nt + nt * kKnots + 2 * (kUCells + 1))),
+               o_cst = take(sizeof(double) * 4);
+  size_t o_raw = 0, raw_bytes = 0;
+  if (!dev) {
+    raw_bytes = sizeof(int32_t) * n + sizeof(float) * 6 * n + sizeof(int32_t) * 2 * (n + 1) +
+                (sizeof(float) * 4 + 1) * n_act + (sizeof(float) * 4 + 1) * n_obs + 4096;
+    o_raw = take(raw_bytes);
+  }
+  char* mem = nullptr;
+  cudaError_t e = cudaMalloc(&mem, off);
+  if (e != cudaSuccess) {
+    delete B;
+    return cuda_fail(e, "vine_batch_create: cudaMalloc");
+  }
+  B->dmem = mem;
+  auto P_ = [&](size_t o) { return (void*)(mem + o); };
+
+  // raw inputs on the device
+  InitArgs ia{};
+  ia.n_inst = n;
+  if (dev) {
+    ia.n_links = D->n_links; ia.l_seg = D->l_seg; ia.radius = D->radius; ia.pressure = D->pressure;
+    ia.base = D->base; ia.act_ptr = D->act_ptr; ia.act_begin = D->act_begin; ia.act_end = D->act_end;
+    ia.act_side = D->act_side; ia.act_pressure = D->act_pressure; ia.act_l0 = D->act_l0; ia.obs_ptr = D->obs_ptr;
+    ia.obs_kind = D->obs_kind; ia.obs_cx = D->obs_cx; ia.obs_cy = D->obs_cy; ia.obs_a = D->obs_a;
+    ia.obs_b = D->obs_b;
+  } else {
+    char* r = (char*)P_(o_raw);
+    size_t ro = 0;
+    auto put = [&](const void* src, size_t bytes) -> const void* {
+      char* d = r + ro;
+      if (bytes) {
+        cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, st);
+      }
+      ro += (bytes + 15) & ~size_t(15);
+      return d;
+    };
+    const bool ok_ptrs = D->n_links && D->l_seg && D->radius && D->pressure && D->base && D->act_ptr &&
+                         D->obs_ptr && (n_act == 0 || (D->act_begin && D->act_end && D->act_side &&
+                                                        D->act_pressure && D->act_l0)) &&
+                         (n_obs == 0 || (D->obs_kind && D->obs_cx && D->obs_cy && D->obs_a && D->obs_b));
+    if (!ok_ptrs) {
+      cudaFree(mem);
+      delete B;
+      return fail(VINE_EINVAL, "vine_batch_create: null input array");
+    }
+    ia.n_links = (const int32_t*)put(D->n_links, 4 * n);
+    ia.l_seg = (const float*)put(D->l_seg, 4 * n);
+    ia.radius = (const float*)put(D->radius, 4 * n);
+    ia.pressure = (const float*)put(D->pressure, 4 * n);
+    ia.base = (const float*)put(D->base, 12 * n);
+    ia.act_ptr = (const int32_t*)put(D->act_ptr, 4 * (n + 1));
+    ia.act_begin = (const float*)put(D->act_begin, 4 * n_act);
+    ia.act_end = (const float*)put(D->act_end, 4 * n_act);
+    ia.act_side = (const int8_t*)put(D->act_side, n_act);
+    ia.act_pressure = (const float*)put(D->act_pressure, 4 * n_act);
+    ia.act_l0 = (const float*)put(D->act_l0, 4 * n_act);
+    ia.obs_ptr = (const int32_t*)put(D->obs_ptr, 4 * (n + 1));
+    ia.obs_kind = (const uint8_t*)put(D->obs_kind, n_obs);
+    ia.obs_cx = (const float*)put(D->obs_cx, 4 * n_obs);
+    ia.obs_cy = (const float*)put(D->obs_cy, 4 * n_obs);
+    ia.obs_a = (const float*)put(D->obs_a, 4 * n_obs);
+    ia.obs_b = (const float*)put(D->obs_b, 4 * n_obs);
+  }
+  auto cleanup = [&]() {
+    cudaFree(mem);
+    delete B;
+  };
+#define CKC(call)                                    \
+  do {                                               \
+    cudaError_t e_ = (call);                         \
+    if (e_ != cudaSuccess) {                         \
+      vine_status s_ = cuda_fail(e_, #call);         \
+      cleanup();                                     \
+      return s_;                                     \
+    }                                                \
+  } while (0)
+  CKC(cudaMemcpyAsync(P_(o_acttab), act_tab.data(), sizeof(int) * n_act, cudaMemcpyHostToDevice, st));
+  CKC(cudaMemcpyAsync(P_(o_thoff), th_off.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+  CKC(cudaMemcpyAsync(P_(o_sth), status_h.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+  if (B->n_tab) CKC(cudaMemcpyAsync(P_(o_l0), tabs.data(), sizeof(double) * B->n_tab, cudaMemcpyHostToDevice, st));
+  ia.act_tab = (const int*)P_(o_acttab);
+  ia.th_off = (const int*)P_(o_thoff);
+  ia.status_h = (const int*)P_(o_sth);
+  ia.R_act = prm.R_act;
+  ia.w_a = prm.w_a;
+  ia.pen_frac = prm.pen_frac;
+  ia.inst = (InstDev*)P_(o_inst);
+  ia.obs = (float4*)P_(o_obs);
+  ia.act = (float4*)P_(o_act);
+  ia.status = (int*)P_(o_st);
+  // zero the per-instance state block (n .. resid) before validation writes status
+  CKC(cudaMemsetAsync(P_(o_n), 0, (size_t)(o_ord - o_n), st));
+  CKC(cudaMemsetAsync(P_(o_th), 0, sizeof(float) * std::max<int64_t>(tot, 1), st));
+  init_kernel<<<(n * 32 + 127) / 128, 128, 0, st>>>(ia);
+  CKC(cudaGetLastError());
+  CKC(cudaMemcpyAsync(P_(o_st0), P_(o_st), sizeof(int) * n, cudaMemcpyDeviceToDevice, st));
+  // prologue tables
+  GaussLegendre gl;
+  gauss_legendre(24, &gl);
+  double* scr = (double*)P_(o_scr);
+  CKC(launch_spam_tables((const double*)P_(o_l0), B->n_tab, prm.R_c, prm.R_act, prm.a_spam, prm.m_lo, gl,
+                         (float4*)P_(o_hdr), (float2*)P_(o_tab), scr, st));
+  CKC(launch_wrinkle_table(prm.eps_crit, gl, (float2*)P_(o_ut), scr + 4 * nt + nt * kKnots, (double*)P_(o_cst),
+                           st));
+  double cst[4];
+  CKC(cudaMemcpyAsync(cst, P_(o_cst), sizeof(cst), cudaMemcpyDeviceToHost, st));
+  // longest-first order
+  B->h_order.resize(n);
+  std::iota(B->h_order.begin(), B->h_order.end(), 0);
+  std::vector<double> cost(n);
+  for (int i = 0; i < n; ++i)
+    cost[i] = (double)B->h_n_links[i] * B->h_n_links[i] * (B->ks * (double)B->h_n_obs[i] + 8.0);
+  std::stable_sort(B->h_order.begin(), B->h_order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  CKC(cudaMemcpyAsync(P_(o_ord), B->h_order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+  CKC(cudaStreamSynchronize(st));
+  if (!(std::isfinite(cst[0]) && std::isfinite(cst[1]))) {
+    cleanup();
+    return fail(VINE_ECUDA, "vine_batch_create: wrinkling table build failed");
+  }
+  // ---- launch configuration
+  B->nmax = (nmax + 31) & ~31;
+  B->omax = omax;
+  B->amax = amax;
+  B->smem_warp = grow_smem_per_warp(B->nmax, B->omax, B->amax);
+  const size_t smem_cta = B->smem_warp * kWarpsPerCta;
+  int dev_id = 0, nsm = 1;
+  size_t smem_optin = 0;
+  cudaGetDevice(&dev_id);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev_id);
+  {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev_id);
+    smem_optin = (size_t)v;
+  }
+  if (smem_cta > smem_optin) {
+    cleanup();
+    return fail(VINE_EINVAL, "vine_batch_create: robot or obstacle set too large for shared memory");
+  }
+  CKC(grow_configure(B->ks, smem_cta));
+  const int per_sm = grow_max_ctas_per_sm(B->ks, smem_cta);
+  B->grid = std::max(1, std::min((n + kWarpsPerCta - 1) / kWarpsPerCta, nsm * per_sm));
+
+  GrowArgs& a = B->args;
+  a.inst = (const InstDev*)P_(o_inst);
+  a.obs = (const float4*)P_(o_obs);
+  a.act = (const float4*)P_(o_act);
+  a.tab_hdr = (const float4*)P_(o_hdr);
+  a.tab = (const float2*)P_(o_tab);
+  a.utab = (const float2*)P_(o_ut);
+  a.theta = (float*)P_(o_th);
+  a.n_cur = (int*)P_(o_n);
+  a.l_cur = (float*)P_(o_l);
+  a.status = (int*)P_(o_st);
+  a.iters = (int*)P_(o_it);
+  a.conv = (int*)P_(o_cv);
+  a.steps = (int*)P_(o_sp);
+  a.rls = (long long*)P_(o_rls);
+  a.evals = (long long*)P_(o_ev);
+  a.linkevals = (long long*)P_(o_le);
+  a.resid_max = (double*)P_(o_rm);
+  a.order = (const int*)P_(o_ord);
+  a.n_order = n;
+  a.counter = (int*)P_(o_cnt);
+  a.dynamic = 1;
+  a.n_steps = 0;
+  a.nmax = B->nmax;
+  a.omax = B->omax;
+  a.amax = B->amax;
+  a.warp_floats = (int)(B->smem_warp / sizeof(float));
+  a.w_a = (float)prm.w_a;
+  a.w_b = (float)prm.w_b;
+  a.w_c = (float)prm.w_c;
+  a.theta_c = (float)cst[2];
+  a.inv2thc = (float)(1.0 / (2.0 * cst[2]));
+  a.inv4thc = (float)(1.0 / (4.0 * cst[2]));
+  a.eps_c = (float)prm.eps_crit;
+  a.u_h = (float)cst[3];
+  a.u_invh = (float)(1.0 / cst[3]);
+  a.U_pi = (float)cst[0];
+  a.m_pi = (float)cst[1];
+  a.ls_switch = (float)prm.ls_switch;
+  a.c1 = (float)prm.armijo_c1;
+  a.tol = prm.tol;
+  a.max_iter = prm.max_iter;
+  a.max_halv = prm.max_halvings;
+  B->status0 = (int*)P_(o_st0);
+  (void)persistent;
+  *out = B;
+#undef CKC
+  return VINE_OK;
+}
+
+static vine_status grow_launch(vine_batch* B, int n_steps, cudaStream_t st) {
+  GrowArgs a = B->args;
+  a.n_steps = n_steps;
+  a.dynamic = 1;
+  CK(cudaMemsetAsync(a.counter, 0, sizeof(int), st));
+  CK(launch_grow(a, B->ks, B->grid, 32 * kWarpsPerCta, B->smem_warp * kWarpsPerCta, st));
+  return VINE_OK;
+}
+
+vine_status vine_batch_reset(vine_batch* B, void* stream_v) {
+  if (!B) return fail(VINE_EINVAL, "vine_batch_reset: null batch");
+  cudaStream_t st = (cudaStream_t)stream_v;
+  const GrowArgs& a = B->args;
+  CK(cudaMemsetAsync(a.theta, 0, sizeof(float) * std::max<int64_t>(B->total_links, 1), st));
+  CK(cudaMemsetAsync(a.n_cur, 0, sizeof(int) * B->n_inst, st));
+  CK(cudaMemsetAsync(a.l_cur, 0, sizeof(float) * B->n_inst, st));
+  CK(cudaMemsetAsync(a.iters, 0, sizeof(int) * B->n_inst, st));
+  CK(cudaMemsetAsync(a.conv, 0, sizeof(int) * B->n_inst, st));
+  CK(cudaMemsetAsync(a.steps, 0, sizeof(int) * B->n_inst, st));
+  CK(cudaMemsetAsync(a.rls, 0, sizeof(long long) * B->n_inst, st));
+  CK(cudaMemsetAsync(a.evals, 0, sizeof(long long) * B->n_inst, st));
+  CK(cudaMemsetAsync(a.linkevals, 0, sizeof(long long) * B->n_inst, st));
+  CK(cudaMemsetAsync(a.resid_max, 0, sizeof(double) * B->n_inst, st));
+  CK(cudaMemcpyAsync(a.status, B->status0, sizeof(int) * B->n_inst, cudaMemcpyDeviceToDevice, st));
+  return VINE_OK;
+}
+
+vine_status vine_grow_step(vine_batch* B, int32_t n_steps, void* stream_v) {
+  if (!B) return fail(VINE_EINVAL, "vine_grow_step: null batch");
+  if (n_steps < 0) return fail(VINE_EINVAL, "vine_grow_step: negative step count");
+  if (n_steps == 0) return VINE_OK;
+  return grow_launch(B, n_steps, (cudaStream_t)stream_v);
+}
+
+vine_status vine_simulate(vine_batch* B, void* stream_v) {
+  if (!B) return fail(VINE_EINVAL, "vine_simulate: null batch");
+  cudaStream_t st = (cudaStream_t)stream_v;
+  if (!B->graph_exec) {
+    // record [reset work counter, persistent growth kernel] once
+    CK(cudaStreamCreateWithFlags(&B->cap_stream, cudaStreamNonBlocking));
+    CK(cudaStreamBeginCapture(B->cap_stream, cudaStreamCaptureModeThreadLocal));
+    vine_status s = grow_launch(B, B->max_target, B->cap_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(B->cap_stream, &g);
+    if (s != VINE_OK) {
+      if (g) cudaGraphDestroy(g);
+      return s;
+    }
+    CK(e);
+    B->graph = g;
+    CK(cudaGraphInstantiate(&B->graph_exec, g, 0));
+  }
+  CK(cudaGraphLaunch(B->graph_exec, st));
+  return VINE_OK;
+}
+
+vine_status vine_simulate_plain(vine_batch* B, void* stream_v) {
+  if (!B) return fail(VINE_EINVAL, "vine_simulate_plain: null batch");
+  cudaStream_t st = (cudaStream_t)stream_v;
+  GrowArgs a = B->args;
+  a.n_steps = B->max_target;
+  a.dynamic = 0;
+  a.n_order = 1;
+  for (int k = 0; k < B->n_inst; ++k) {
+    a.order = B->args.order + k;
+    CK(launch_grow(a, B->ks, 1, 32, B->smem_warp, st));
+  }
+  return VINE_OK;
+}
+
+static vine_status ensure_stage(const vine_batch* Bc, size_t bytes) {
+  vine_batch* B = const_cast<vine_batch*>(Bc);
+  if (B->stage_bytes >= bytes) return VINE_OK;
+  if (B->stage) cudaFree(B->stage);
+  B->stage = nullptr;
+  B->stage_bytes = 0;
+  CK(cudaMalloc(&B->stage, bytes));
+  B->stage_bytes = bytes;
+  return VINE_OK;
+}
+
+vine_status vine_get_state(const vine_batch* B, float* theta, float* l_last, float* link_pose, float* tip,
+                           int32_t* n_present, int32_t* iterations, double* residual, int32_t* inst_status,
+                           int32_t out_is_device, void* stream_v) {
+  if (!B) return fail(VINE_EINVAL, "vine_get_state: null batch");
+  cudaStream_t st = (cudaStream_t)stream_v;
+  const GrowArgs& a = B->args;
+  const int n = B->n_inst;
+  const int64_t T = B->total_links;
+  if (out_is_device) {
+    if (theta || link_pose || tip) CK(launch_poses(a.inst, n, a.theta, a.n_cur, a.l_cur, theta, link_pose, tip, st));
+    if (l_last) CK(cudaMemcpyAsync(l_last, a.l_cur, 4 * n, cudaMemcpyDeviceToDevice, st));
+    if (n_present) CK(cudaMemcpyAsync(n_present, a.n_cur, 4 * n, cudaMemcpyDeviceToDevice, st));
+    if (iterations) CK(cudaMemcpyAsync(iterations, a.iters, 4 * n, cudaMemcpyDeviceToDevice, st));
+    if (residual) CK(cudaMemcpyAsync(residual, a.resid_max, 8 * n, cudaMemcpyDeviceToDevice, st));
+    if (inst_status) CK(cudaMemcpyAsync(inst_status, a.status, 4 * n, cudaMemcpyDeviceToDevice, st));
+    return VINE_OK;
+  }
+  const size_t need = align256(4 * std::max<int64_t>(T, 1)) + align256(12 * std::max<int64_t>(T, 1)) +
+                      align256(8 * (size_t)n);
+  vine_status s = ensure_stage(B, need);
+  if (s != VINE_OK) return s;
+  char* sg = (char*)B->stage;
+  float* d_th = (float*)sg;
+  float* d_pose = (float*)(sg + align256(4 * std::max<int64_t>(T, 1)));
+  float* d_tip = (float*)(sg + align256(4 * std::max<int64_t>(T, 1)) + align256(12 * std::max<int64_t>(T, 1)));
+  if (theta || link_pose || tip)
+    CK(launch_poses(a.inst, n, a.theta, a.n_cur, a.l_cur, theta ? d_th : nullptr, link_pose ? d_pose : nullptr,
+                    tip ? d_tip : nullptr, st));
+  if (theta) CK(cudaMemcpyAsync(theta, d_th, 4 * T, cudaMemcpyDeviceToHost, st));
+  if (link_pose) CK(cudaMemcpyAsync(link_pose, d_pose, 12 * T, cudaMemcpyDeviceToHost, st));
+  if (tip) CK(cudaMemcpyAsync(tip, d_tip, 8 * n, cudaMemcpyDeviceToHost, st));
+  if (l_last) CK(cudaMemcpyAsync(l_last, a.l_cur, 4 * n, cudaMemcpyDeviceToHost, st));
+  if (n_present) CK(cudaMemcpyAsync(n_present, a.n_cur, 4 * n, cudaMemcpyDeviceToHost, st));
+  if (iterations) CK(cudaMemcpyAsync(iterations, a.iters, 4 * n, cudaMemcpyDeviceToHost, st));
+  if (residual) CK(cudaMemcpyAsync(residual, a.resid_max, 8 * n, cudaMemcpyDeviceToHost, st));
+  if (inst_status) CK(cudaMemcpyAsync(inst_status, a.status, 4 * n, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return VINE_OK;
+}
+
+vine_status vine_get_contacts(const vine_batch* B, int32_t* counts, int32_t* pairs, int32_t max_pairs,
+                              int32_t out_is_device, void* stream_v) {
+  if (!B || !counts || max_pairs < 0 || (max_pairs > 0 && !pairs))
+    return fail(VINE_EINVAL, "vine_get_contacts: bad arguments");
+  cudaStream_t st = (cudaStream_t)stream_v;
+  const GrowArgs& a = B->args;
+  const int n = B->n_inst;
+  if (out_is_device) {
+    CK(launch_contacts(a.inst, n, a.obs, a.theta, a.n_cur, a.l_cur, B->ks, max_pairs, counts, pairs, st));
+    return VINE_OK;
+  }
+  const size_t pb = 8 * (size_t)n * (size_t)max_pairs;
+  vine_status s = ensure_stage(B, align256(4 * (size_t)n) + align256(std::max<size_t>(pb, 16)));
+  if (s != VINE_OK) return s;
+  int* d_c = (int*)B->stage;
+  int* d_p = (int*)((char*)B->stage + align256(4 * (size_t)n));
+  CK(launch_contacts(a.inst, n, a.obs, a.theta, a.n_cur, a.l_cur, B->ks, max_pairs, d_c, max_pairs ? d_p : nullptr,
+                     st));
+  CK(cudaMemcpyAsync(counts, d_c, 4 * (size_t)n, cudaMemcpyDeviceToHost, st));
+  if (pb) CK(cudaMemcpyAsync(pairs, d_p, pb, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return VINE_OK;
+}
+
+vine_status vine_get_stats(const vine_batch* B, vine_stats* out, void* stream_v) {
+  if (!B || !out) return fail(VINE_EINVAL, "vine_get_stats: null argument");
+  cudaStream_t st = (cudaStream_t)stream_v;
+  const GrowArgs& a = B->args;
+  const int n = B->n_inst;
+  std::vector<int> it(n), cv(n), sp(n), status(n);
+  std::vector<long long> rls(n), ev(n), le(n);
+  CK(cudaMemcpyAsync(it.data(), a.iters, 4 * n, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(cv.data(), a.conv, 4 * n, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(sp.data(), a.steps, 4 * n, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(status.data(), a.status, 4 * n, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(rls.data(), a.rls, 8 * n, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(ev.data(), a.evals, 8 * n, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(le.data(), a.linkevals, 8 * n, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  std::memset(out, 0, sizeof(*out));
+  for (int i = 0; i < n; ++i) {
+    out->robot_link_steps += rls[i];
+    out->steps_converged += cv[i];
+    out->steps_total += sp[i];
+    out->iterations += it[i];
+    out->evaluations += ev[i];
+    out->link_evaluations += le[i];
+    out->pair_tests += le[i] * B->ks * (int64_t)B->h_n_obs[i];
+    out->circle_pair_tests += le[i] * B->ks * (int64_t)B->h_n_circ[i];
+    out->n_maxiter += status[i] == kMaxIter;
+    out->n_nonfinite += status[i] == kNonFinite;
+    out->n_badinput += status[i] == kBadInput;
+  }
+  return VINE_OK;
+}
+
+vine_status vine_get_tables(const vine_batch* B, int32_t* n_tab, float* hdr, float* knots, float* utab,
+                            double* consts) {
+  if (!B || !n_tab) return fail(VINE_EINVAL, "vine_get_tables: null argument");
+  *n_tab = B->n_tab;
+  const GrowArgs& a = B->args;
+  if (hdr && B->n_tab) CK(cudaMemcpy(hdr, a.tab_hdr, sizeof(float4) * B->n_tab, cudaMemcpyDeviceToHost));
+  if (knots && B->n_tab)
+    CK(cudaMemcpy(knots, a.tab, sizeof(float2) * B->n_tab * kKnots, cudaMemcpyDeviceToHost));
+  if (utab) CK(cudaMemcpy(utab, a.utab, sizeof(float2) * (kUCells + 1), cudaMemcpyDeviceToHost));
+  if (consts) {
+    consts[0] = a.U_pi;
+    consts[1] = a.m_pi;
+    consts[2] = a.theta_c;
+    consts[3] = a.u_h;
+  }
+  return VINE_OK;
+}
+
+vine_status vine_batch_info(const vine_batch* B, int32_t* n_inst, int64_t* total_links) {
+  if (!B) return fail(VINE_EINVAL, "vine_batch_info: null batch");
+  if (n_inst) *n_inst = B->n_inst;
+  if (total_links) *total_links = B->total_links;
+  return VINE_OK;
+}
+
+vine_status vine_batch_destroy(vine_batch* B) {
+  if (!B) return VINE_OK;
+  cudaDeviceSynchronize();
+  if (B->graph_exec) cudaGraphExecDestroy(B->graph_exec);
+  if (B->graph) cudaGraphDestroy(B->graph);
+  if (B->cap_stream) cudaStreamDestroy(B->cap_stream);
+  if (B->stage) cudaFree(B->stage);
+  if (B->dmem) cudaFree(B->dmem);
+  delete B;
+  return VINE_OK;
+}
+
+}  // extern "C"

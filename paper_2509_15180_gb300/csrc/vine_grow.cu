@@ -1,0 +1,778 @@
+// vine_grow.cu -- the growth step of Sec. 4.1 (Algorithm 1) for a batch of
+// independent planar vine robots, one warp per robot.
+//
+// Per growth step (Sec. 3.3 / 4.1): a link is appended at the tip (joint
+// angle 0, distal length 0; the previous distal link snaps to l_seg), then
+// the cost of Eq. (pbd) in potential form
+//     J = w_a sum_j U_j(theta_j) + w_b k_g (l_seg - l)^2 + w_c k_c sum pen^2
+// is brought to its stationary point by damped Gauss-Newton:
+//   eval  : heading and position prefix sums (float-float), per joint the
+//           wrinkling moment (Eq. wrinkling_model) minus the sPAM moments
+//           (Eq. restoring_moment with the strain-coupled force table), every
+//           disc of every link against every obstacle (circle / box signed
+//           distance), suffix sums of contact forces and moments -> gradient,
+//           per-link 3x3 contact stiffness (planar twist coordinates).
+//   solve : the Gauss-Newton system diag(d) + sum_links E_i^T C_i E_i, with
+//           the distal length eliminated first, by a backward sweep of
+//           articulated stiffnesses in link-local frames and a forward sweep
+//           of twists -- exact for that matrix and O(N).
+//   test  : predicted displacement of every link end (FP64 max / N l_seg).
+//   step  : full step below ls_switch, Armijo backtracking above it.
+// Lanes own contiguous blocks of links; obstacles and actuators of the robot
+// are staged in shared memory; the serial sweeps run warp-uniform.
+#include <cmath>
+
+#include "vine_internal.cuh"
+
+namespace vine {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+struct FF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ FF two_sum(float a, float b) {
+  float s = a + b;
+  float bb = s - a;
+  float e = (a - (s - bb)) + (b - bb);
+  return {s, e};
+}
+__device__ __forceinline__ FF quick_two_sum(float a, float b) {
+  float s = a + b;
+  float e = b - (s - a);
+  return {s, e};
+}
+__device__ __forceinline__ FF ff_add(FF a, float b) {
+  FF t = two_sum(a.hi, b);
+  t.lo += a.lo;
+  return quick_two_sum(t.hi, t.lo);
+}
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  FF t = two_sum(a.hi, b.hi);
+  t.lo += a.lo + b.lo;
+  return quick_two_sum(t.hi, t.lo);
+}
+
+// exclusive prefix (sum over lanes < lane) of float-float values
+__device__ __forceinline__ FF warp_excl_scan(FF v, int lane) {
+  FF x = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    float h = __shfl_up_sync(kFull, x.hi, d);
+    float l = __shfl_up_sync(kFull, x.lo, d);
+    if (lane >= d) x = ff_add(FF{h, l}, x);
+  }
+  float h = __shfl_up_sync(kFull, x.hi, 1);
+  float l = __shfl_up_sync(kFull, x.lo, 1);
+  return lane == 0 ? FF{0.f, 0.f} : FF{h, l};
+}
+
+// exclusive suffix (sum over lanes > lane)
+__device__ __forceinline__ float warp_excl_suffix(float v, int lane) {
+  float x = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    float o = __shfl_down_sync(kFull, x, d);
+    if (lane + d < 32) x += o;
+  }
+  float o = __shfl_down_sync(kFull, x, 1);
+  return lane == 31 ? 0.f : o;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
+  return v;
+}
+
+// Per-warp shared-memory slice.
+struct Smem {
+  float4* obs;
+  float4* act;
+  float *TH, *TH0, *DTH, *LUX, *LUY, *G, *DD, *C0, *C1, *C2, *C3, *C4, *C5, *FX, *FY, *TL;
+};
+
+__device__ __forceinline__ Smem carve(float* base, const GrowArgs& A) {
+  Smem s;
+  s.obs = reinterpret_cast<float4*>(base);
+  s.act = s.obs + A.omax;
+  float* p = reinterpret_cast<float*>(s.act + A.amax);
+  const int n = A.nmax;
+  s.TH = p; s.TH0 = p + n; s.DTH = p + 2 * n; s.LUX = p + 3 * n; s.LUY = p + 4 * n; s.G = p + 5 * n;
+  s.DD = p + 6 * n; s.C0 = p + 7 * n; s.C1 = p + 8 * n; s.C2 = p + 9 * n; s.C3 = p + 10 * n; s.C4 = p + 11 * n;
+  s.C5 = p + 12 * n; s.FX = p + 13 * n; s.FY = p + 14 * n; s.TL = p + 15 * n;
+  return s;
+}
+
+// Wrinkling restoring moment per unit pi P R^3 (Sec. 3.2): value m, slope dm
+// and energy u = integral from 0.  At or below onset a linear ramp to 1/2;
+// above onset gamma_0 = 2 asin(sqrt(1 - eps_c / s)), s = sin(|theta| / 2).
+__device__ __forceinline__ void wrinkle(const GrowArgs& A, float th, float& m, float& dm, float& u) {
+  const float a = fabsf(th);
+  if (a <= A.theta_c) {
+    m = th * A.inv2thc;
+    dm = A.inv2thc;
+    u = a * a * A.inv4thc;
+    return;
+  }
+  const float ac = fminf(a, kPi);
+  float s, cs;
+  sincosf(0.5f * ac, &s, &cs);
+  const float q = sqrtf(fmaxf(1.f - A.eps_c / s, 0.f));
+  const float g = 2.f * asinf(q);
+  float sg, cg;
+  sincosf(g, &sg, &cg);
+  const float pg = kPi - g;
+  const float Nn = 2.f * sg * cg + 2.f * pg;
+  const float Dn = 4.f * (sg + pg * cg);
+  m = copysignf(Nn / Dn, th);
+  dm = (a < kPi) ? 4.f * A.eps_c * cs * (Nn * pg - Dn * sg) / (Dn * Dn * s * s) : 0.f;
+  if (a >= kPi) {
+    u = A.U_pi + A.m_pi * (a - kPi);
+  } else {
+    float t = (a - A.theta_c) * A.u_invh;
+    int k = min((int)t, kUCells - 1);
+    float tau = t - (float)k;
+    float2 p0 = A.utab[k], p1 = A.utab[k + 1];
+    float t2 = tau * tau, t3 = t2 * tau;
+    float h00 = 2.f * t3 - 3.f * t2 + 1.f, h10 = t3 - 2.f * t2 + tau, h01 = -2.f * t3 + 3.f * t2, h11 = t3 - t2;
+    u = h00 * p0.x + h01 * p1.x + A.u_h * (h10 * p0.y + h11 * p1.y);
+  }
+}
+
+struct Acc {
+  float fx, fy, tl, c00, c01, c02, c11, c12, c22, pen2;
+  float glc, hll, q0, q1, q2;
+};
+
+// One active contact: force kap * pen * n on a disc at fraction fr of the link.
+__device__ __forceinline__ void add_contact(Acc& c, float pen, float nx, float ny, float fr, float lx, float ly,
+                                            float kap, bool last, float ulx, float uly) {
+  const float f = kap * pen;
+  const float fx = f * nx, fy = f * ny;
+  c.fx += fx;
+  c.fy += fy;
+  const float rx = fr * lx, ry = fr * ly;
+  c.tl += rx * fy - ry * fx;
+  const float w0 = rx * ny - ry * nx;
+  c.c00 += kap * w0 * w0;
+  c.c01 += kap * w0 * nx;
+  c.c02 += kap * w0 * ny;
+  c.c11 += kap * nx * nx;
+  c.c12 += kap * nx * ny;
+  c.c22 += kap * ny * ny;
+  c.pen2 += pen * pen;
+  if (last) {
+    const float vl = fr * (nx * ulx + ny * uly);
+    c.glc += fr * (fx * ulx + fy * uly);
+    c.hll += kap * vl * vl;
+    c.q0 += kap * vl * w0;
+    c.q1 += kap * vl * nx;
+    c.q2 += kap * vl * ny;
+  }
+}
+
+// Penetration of a disc (offset dx, dy from the obstacle centre, radius R).
+// Returns pen > 0 and the outward normal when the disc overlaps obstacle ob.
+__device__ __forceinline__ float disc_pen(const float4 ob, float dx, float dy, float R, float fbx, float fby,
+                                          float& nx, float& ny) {
+  if (ob.w < 0.f) {  // circle: ob.z = R + r, -ob.w = (R + r)^2
+    const float d2 = dx * dx + dy * dy;
+    if (!(d2 < -ob.w)) return 0.f;
+    const float d = sqrtf(d2);
+    const float pen = ob.z - d;
+    if (d > 0.f) {
+      const float id = 1.f / d;
+      nx = dx * id;
+      ny = dy * id;
+    } else {
+      nx = fbx;
+      ny = fby;
+    }
+    return pen;
+  }
+  const float ax = fabsf(dx) - ob.z, ay = fabsf(dy) - ob.w;
+  if (!(fmaxf(ax, ay) < R)) return 0.f;
+  const float sx = dx >= 0.f ? 1.f : -1.f, sy = dy >= 0.f ? 1.f : -1.f;
+  float sd;
+  if (ax > 0.f && ay > 0.f) {
+    sd = sqrtf(ax * ax + ay * ay);
+    const float id = 1.f / sd;
+    nx = sx * ax * id;
+    ny = sy * ay * id;
+  } else if (ax > 0.f) {
+    sd = ax; nx = sx; ny = 0.f;
+  } else if (ay > 0.f) {
+    sd = ay; nx = 0.f; ny = sy;
+  } else if (ax >= ay) {
+    sd = ax; nx = sx; ny = 0.f;
+  } else {
+    sd = ay; nx = 0.f; ny = sy;
+  }
+  return R - sd;
+}
+
+struct EvalOut {
+  double J;
+  float gl, hll, q0, q1, q2, ulx, uly;
+};
+
+// Cost, gradient and Gauss-Newton data at the state (TH[0..N), l).
+template <int KS>
+__device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int N, float l, int lane) {
+  const int B = (N + 31) >> 5;
+  const int j0 = min(lane * B, N), j1 = min(j0 + B, N);
+  // headings psi_j = psi_b + sum_{i<=j} theta_i
+  FF hs{0.f, 0.f};
+  for (int j = j0; j < j1; ++j) hs = ff_add(hs, S.TH[j]);
+  FF psi = ff_add(warp_excl_scan(hs, lane), I.bpsi);
+  FF sx{0.f, 0.f}, sy{0.f, 0.f};
+  float ulx = 0.f, uly = 0.f;
+  for (int j = j0; j < j1; ++j) {
+    psi = ff_add(psi, S.TH[j]);
+    float sn, cs;
+    sincosf(psi.hi, &sn, &cs);
+    const float ux = cs - sn * psi.lo, uy = sn + cs * psi.lo;
+    const float L = (j == N - 1) ? l : I.l_seg;
+    const float lx = L * ux, ly = L * uy;
+    S.LUX[j] = lx;
+    S.LUY[j] = ly;
+    if (j == N - 1) {
+      ulx = ux;
+      uly = uy;
+    }
+    sx = ff_add(sx, lx);
+    sy = ff_add(sy, ly);
+  }
+  // link start points relative to the base
+  FF px = warp_excl_scan(sx, lane), py = warp_excl_scan(sy, lane);
+  const float kap = 2.f * A.w_c * I.kc;
+  const float floor_d = 1e-6f * A.w_a * I.PR3;
+  double Jl = 0.0;
+  Acc last_acc{};
+  for (int j = j0; j < j1; ++j) {
+    // ---- bending and actuation at joint j (Eq. restoring_moment)
+    const float th = S.TH[j];
+    float m, dm, u;
+    wrinkle(A, th, m, dm, u);
+    float M = I.PR3 * m, dM = I.PR3 * dm, U = I.PR3 * u;
+    for (int a = 0; a < I.n_act; ++a) {
+      const float4 ac = S.act[a];
+      const float cov = fminf(ac.y, (float)(j + 1)) - fmaxf(ac.x, (float)j);
+      if (cov <= 0.f) continue;
+      const int bits = __float_as_int(ac.w);
+      const float side = bits < 0 ? -1.f : 1.f;
+      const int tid = bits & 0x7fffffff;
+      const float e = side * I.d * th / I.l_seg;
+      const float4 hd = A.tab_hdr[tid];
+      const float2* tb = A.tab + (size_t)tid * kKnots;
+      const float uu = (e - hd.x) * hd.z;
+      float f, fp, Gi;
+      if (uu <= 0.f) {
+        const float f0 = tb[0].x;
+        f = f0; fp = 0.f; Gi = f0 * (e - hd.x);
+      } else if (uu >= (float)(kKnots - 1)) {
+        f = 0.f; fp = 0.f; Gi = tb[kKnots - 1].y;
+      } else {
+        const int k = (int)uu;
+        const float tau = uu - (float)k;
+        const float2 k0 = tb[k], k1 = tb[k + 1];
+        f = k0.x + tau * (k1.x - k0.x);
+        fp = (k1.x - k0.x) * hd.z;
+        Gi = k0.y + 0.5f * tau * hd.y * (k0.x + f);
+      }
+      M -= cov * side * ac.z * f * I.d;
+      dM -= cov * ac.z * fp * I.d * I.d / I.l_seg;
+      U -= cov * ac.z * I.l_seg * (Gi - hd.w);
+    }
+    Jl += (double)(A.w_a * U);
+    S.G[j] = A.w_a * M;
+    S.DD[j] = fmaxf(A.w_a * dM, floor_d);
+    // ---- contacts of link j: KS discs x every obstacle
+    const float lx = S.LUX[j], ly = S.LUY[j];
+    const bool last = (j == N - 1);
+    const float fbx = last ? -uly : -ly / I.l_seg, fby = last ? ulx : lx / I.l_seg;
+    FF xk[KS], yk[KS];
+#pragma unroll
+    for (int k = 0; k < KS; ++k) {
+      const float fr = (float)(k + 1) / (float)KS;
+      xk[k] = ff_add(px, fr * lx);
+      yk[k] = ff_add(py, fr * ly);
+    }
+    Acc c{};
+    for (int o = 0; o < I.n_obs; ++o) {
+      const float4 ob = S.obs[o];
+#pragma unroll
+      for (int k = 0; k < KS; ++k) {
+        const float dx = (xk[k].hi - ob.x) + xk[k].lo;
+        const float dy = (yk[k].hi - ob.y) + yk[k].lo;
+        float nx, ny;
+        const float pen = disc_pen(ob, dx, dy, I.R, fbx, fby, nx, ny);
+        if (pen > 0.f) add_contact(c, pen, nx, ny, (float)(k + 1) / (float)KS, lx, ly, kap, last, ulx, uly);
+      }
+    }
+    S.FX[j] = c.fx;
+    S.FY[j] = c.fy;
+    S.TL[j] = c.tl;
+    S.C0[j] = c.c00;
+    S.C1[j] = c.c01;
+    S.C2[j] = c.c02;
+    S.C3[j] = c.c11;
+    S.C4[j] = c.c12;
+    S.C5[j] = c.c22;
+    Jl += (double)(A.w_c * I.kc * c.pen2);
+    if (last) last_acc = c;
+    px = ff_add(px, lx);
+    py = ff_add(py, ly);
+  }
+  __syncwarp();
+  // ---- gradient: g_j = w_a M_tot,j - T_j, T_j = moment about p_j of the
+  // contact forces on links >= j = sum_{i>=j} (tl_i + Lu_i x F_{>i}).
+  float tfx = 0.f, tfy = 0.f;
+  for (int j = j0; j < j1; ++j) {
+    tfx += S.FX[j];
+    tfy += S.FY[j];
+  }
+  float fsx = warp_excl_suffix(tfx, lane), fsy = warp_excl_suffix(tfy, lane);
+  float tt = 0.f;
+  for (int j = j1 - 1; j >= j0; --j) {
+    const float t = S.TL[j] + (S.LUX[j] * fsy - S.LUY[j] * fsx);
+    S.TL[j] = t;
+    tt += t;
+    fsx += S.FX[j];
+    fsy += S.FY[j];
+  }
+  float run = warp_excl_suffix(tt, lane);
+  for (int j = j1 - 1; j >= j0; --j) {
+    run += S.TL[j];
+    S.G[j] -= run;
+  }
+  // ---- reductions
+  EvalOut E;
+  const double dlr = (double)I.l_seg - (double)l;
+  E.J = warp_sum(Jl) + (double)A.w_b * (double)I.kg * dlr * dlr;
+  const int owner = (N - 1) / B;
+  const float glc = __shfl_sync(kFull, last_acc.glc, owner);
+  E.hll = 2.f * A.w_b * I.kg + __shfl_sync(kFull, last_acc.hll, owner);
+  E.q0 = __shfl_sync(kFull, last_acc.q0, owner);
+  E.q1 = __shfl_sync(kFull, last_acc.q1, owner);
+  E.q2 = __shfl_sync(kFull, last_acc.q2, owner);
+  E.ulx = __shfl_sync(kFull, ulx, owner);
+  E.uly = __shfl_sync(kFull, uly, owner);
+  E.gl = -2.f * A.w_b * I.kg * (I.l_seg - l) - glc;
+  __syncwarp();
+  return E;
+}
+
+// Gauss-Newton step (DTH[0..N), dl) and its predicted displacement / (N l_seg).
+// Backward sweep: A_j (articulated stiffness of links >= j about p_j) and
+// beta_j; forward sweep: twists V_j and joint steps.  Warp-uniform.
+__device__ double gn_solve(const InstDev& I, const Smem& S, int N, bool lfix, const EvalOut& E, float& dl,
+                           int lane) {
+  float A00 = 0.f, A01 = 0.f, A02 = 0.f, A11 = 0.f, A12 = 0.f, A22 = 0.f;
+  float b0 = 0.f, b1 = 0.f, b2 = 0.f;
+  const float iH = lfix ? 0.f : 1.f / E.hll;
+  for (int j = N - 1; j >= 0; --j) {
+    float c00 = S.C0[j], c01 = S.C1[j], c02 = S.C2[j], c11 = S.C3[j], c12 = S.C4[j], c22 = S.C5[j];
+    const float dj = S.DD[j], gj = S.G[j], lx = S.LUX[j], ly = S.LUY[j];
+    float e0 = 0.f, e1 = 0.f, e2 = 0.f;
+    if (j == N - 1 && !lfix) {  // eliminate the distal length
+      c00 -= E.q0 * E.q0 * iH;
+      c01 -= E.q0 * E.q1 * iH;
+      c02 -= E.q0 * E.q2 * iH;
+      c11 -= E.q1 * E.q1 * iH;
+      c12 -= E.q1 * E.q2 * iH;
+      c22 -= E.q2 * E.q2 * iH;
+      const float s = -E.gl * iH;
+      e0 = s * E.q0;
+      e1 = s * E.q1;
+      e2 = s * E.q2;
+    }
+    // move (A, beta) from p_{j+1} to p_j: twist map a = (1, -ly, lx)
+    const float K01 = A01 - ly * A11 + lx * A12;
+    const float K02 = A02 - ly * A12 + lx * A22;
+    const float K00 = A00 - ly * (A01 + K01) + lx * (A02 + K02);
+    const float B0 = b0 - ly * b1 + lx * b2;
+    const float C00 = c00 + K00, C01 = c01 + K01, C02 = c02 + K02;
+    const float C11 = c11 + A11, C12 = c12 + A12, C22 = c22 + A22;
+    const float h0 = B0 + e0, h1 = b1 + e1, h2 = b2 + e2;
+    const float D = dj + C00;
+    const float iD = 1.f / D;
+    const float cc = gj + h0;
+    const float r = dj * iD;
+    A00 = C00 * r;
+    A01 = C01 * r;
+    A02 = C02 * r;
+    A11 = C11 - C01 * C01 * iD;
+    A12 = C12 - C01 * C02 * iD;
+    A22 = C22 - C02 * C02 * iD;
+    b0 = h0 - C00 * cc * iD;
+    b1 = h1 - C01 * cc * iD;
+    b2 = h2 - C02 * cc * iD;
+    if (lane == 0) {
+      S.C0[j] = C00;
+      S.C1[j] = C01;
+      S.C2[j] = C02;
+      S.C3[j] = iD;
+      S.C4[j] = cc;
+    }
+  }
+  __syncwarp();
+  float V0 = 0.f, V1 = 0.f, V2 = 0.f, rmax = 0.f;
+  dl = 0.f;
+  for (int j = 0; j < N; ++j) {
+    const float h0 = S.C0[j], h1 = S.C1[j], h2 = S.C2[j], iD = S.C3[j], cc = S.C4[j];
+    const float lx = S.LUX[j], ly = S.LUY[j];
+    const float dth = -(cc + h0 * V0 + h1 * V1 + h2 * V2) * iD;
+    V0 += dth;
+    float ex = 0.f, ey = 0.f;
+    if (j == N - 1) {
+      dl = lfix ? 0.f : -(E.gl + E.q0 * V0 + E.q1 * V1 + E.q2 * V2) * iH;
+      ex = dl * E.ulx;
+      ey = dl * E.uly;
+    }
+    V1 -= V0 * ly;
+    V2 += V0 * lx;
+    const float dx = V1 + ex, dy = V2 + ey;
+    rmax = fmaxf(rmax, fmaxf(sqrtf(dx * dx + dy * dy), I.l_seg * fabsf(dth)));
+    if (lane == 0) S.DTH[j] = dth;
+  }
+  __syncwarp();
+  return (double)rmax / ((double)N * (double)I.l_seg);
+}
+
+struct StepStats {
+  int iters;
+  double r;
+  long long evals, linkevals;
+};
+
+// Solves the current growth step to equilibrium from the warm start.
+template <int KS>
+__device__ int solve_step(const GrowArgs& A, const InstDev& I, const Smem& S, int N, float& l, int lane,
+                          StepStats& st) {
+  const int B = (N + 31) >> 5;
+  const int j0 = min(lane * B, N), j1 = min(j0 + B, N);
+  EvalOut E = eval<KS>(A, I, S, N, l, lane);
+  st.evals += 1;
+  st.linkevals += N;
+  int status = kMaxIter, it;
+  double r = 0.0;
+  for (it = 1; it <= A.max_iter; ++it) {
+    if (!isfinite(E.J)) {
+      status = kNonFinite;
+      break;
+    }
+    const bool lfix = (l <= 0.f && E.gl > 0.f) || (l >= I.l_seg && E.gl < 0.f);
+    float dl;
+    r = gn_solve(I, S, N, lfix, E, dl, lane);
+    if (!isfinite(r)) {
+      status = kNonFinite;
+      break;
+    }
+    if (r <= A.tol) {
+      for (int j = j0; j < j1; ++j) S.TH[j] += S.DTH[j];
+      l = fminf(fmaxf(l + dl, 0.f), I.l_seg);
+      status = kOK;
+      break;
+    }
+    double gd = 0.0;
+    for (int j = j0; j < j1; ++j) {
+      gd += (double)S.G[j] * (double)S.DTH[j];
+      S.TH0[j] = S.TH[j];
+    }
+    gd = warp_sum(gd);
+    const float l0 = l, gl0 = E.gl;
+    const double J0 = E.J;
+    float alpha = 1.f, lt = l0;
+    for (int h = 0; h <= A.max_halv; ++h) {
+      for (int j = j0; j < j1; ++j) S.TH[j] = S.TH0[j] + alpha * S.DTH[j];
+      lt = fminf(fmaxf(l0 + alpha * dl, 0.f), I.l_seg);
+      __syncwarp();
+      E = eval<KS>(A, I, S, N, lt, lane);
+      st.evals += 1;
+      st.linkevals += N;
+      if (r <= (double)A.ls_switch) break;
+      const double dec = (double)alpha * gd + (double)gl0 * ((double)lt - (double)l0);
+      if (E.J <= J0 + (double)A.c1 * dec) break;
+      alpha *= 0.5f;
+    }
+    l = lt;
+  }
+  if (it > A.max_iter) it = A.max_iter;
+  __syncwarp();
+  st.iters = it;
+  st.r = r;
+  return status;
+}
+
+template <int KS>
+__device__ void process_instance(const GrowArgs& A, int inst, const Smem& S, int lane) {
+  const InstDev I = A.inst[inst];
+  int status = A.status[inst];
+  if (status == kBadInput || status == kNonFinite) return;
+  int N = A.n_cur[inst];
+  if (N >= I.n_target || A.n_steps <= 0) return;
+  for (int k = lane; k < I.n_obs; k += 32) S.obs[k] = A.obs[I.obs_off + k];
+  for (int k = lane; k < I.n_act; k += 32) S.act[k] = A.act[I.act_off + k];
+  for (int k = lane; k < N; k += 32) S.TH[k] = A.theta[I.th_off + k];
+  float l = A.l_cur[inst];
+  __syncwarp();
+  int iters = 0, conv = 0, steps = 0;
+  long long rls = 0, evals = 0, linkevals = 0;
+  double rmax = 0.0;
+  for (int s = 0; s < A.n_steps && N < I.n_target; ++s) {
+    if (lane == 0) S.TH[N] = 0.f;  // new link at the tip
+    N += 1;
+    l = 0.f;
+    __syncwarp();
+    StepStats st{0, 0.0, 0, 0};
+    const int res = solve_step<KS>(A, I, S, N, l, lane, st);
+    iters += st.iters;
+    evals += st.evals;
+    linkevals += st.linkevals;
+    steps += 1;
+    if (!(st.r <= rmax)) rmax = st.r;
+    if (res == kOK) {
+      conv += 1;
+      rls += N;
+    } else if (res > status) {
+      status = res;
+    }
+    if (status == kNonFinite) break;
+  }
+  __syncwarp();
+  for (int k = lane; k < N; k += 32) A.theta[I.th_off + k] = S.TH[k];
+  if (lane == 0) {
+    A.n_cur[inst] = N;
+    A.l_cur[inst] = l;
+    A.status[inst] = status;
+    A.iters[inst] += iters;
+    A.conv[inst] += conv;
+    A.steps[inst] += steps;
+    A.rls[inst] += rls;
+    A.evals[inst] += evals;
+    A.linkevals[inst] += linkevals;
+    if (!(rmax <= A.resid_max[inst])) A.resid_max[inst] = rmax;
+  }
+  __syncwarp();
+}
+
+template <int KS>
+__global__ void __launch_bounds__(32 * kWarpsPerCta) grow_kernel(const GrowArgs A) {
+  extern __shared__ float4 smem4[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const Smem S = carve(reinterpret_cast<float*>(smem4) + (size_t)warp * A.warp_floats, A);
+  const int gw = blockIdx.x * (blockDim.x >> 5) + warp;
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  for (int round = 0;; ++round) {
+    int idx;
+    if (A.dynamic) {
+      int v = 0;
+      if (lane == 0) v = atomicAdd(A.counter, 1);
+      idx = __shfl_sync(kFull, v, 0);
+    } else {
+      idx = gw + round * nw;
+    }
+    if (idx >= A.n_order) break;
+    process_instance<KS>(A, A.order[idx], S, lane);
+  }
+}
+
+template <int KS>
+const void* kernel_ptr() {
+  return reinterpret_cast<const void*>(&grow_kernel<KS>);
+}
+
+const void* pick(int ks) {
+  switch (ks) {
+    case 1: return kernel_ptr<1>();
+    case 2: return kernel_ptr<2>();
+    case 3: return kernel_ptr<3>();
+    default: return kernel_ptr<4>();
+  }
+}
+
+}  // namespace
+
+size_t grow_smem_per_warp(int nmax, int omax, int amax) {
+  return sizeof(float4) * (size_t)(omax + amax) + sizeof(float) * 16 * (size_t)nmax;
+}
+
+cudaError_t grow_configure(int ks, size_t smem_per_cta) {
+  return cudaFuncSetAttribute(pick(ks), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_per_cta);
+}
+
+int grow_max_ctas_per_sm(int ks, size_t smem_per_cta) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick(ks), 32 * kWarpsPerCta, smem_per_cta) != cudaSuccess)
+    return 1;
+  return n > 0 ? n : 1;
+}
+
+cudaError_t launch_grow(const GrowArgs& a, int ks, int grid, int block, size_t smem, cudaStream_t s) {
+  switch (ks) {
+    case 1: grow_kernel<1><<<grid, block, smem, s>>>(a); break;
+    case 2: grow_kernel<2><<<grid, block, smem, s>>>(a); break;
+    case 3: grow_kernel<3><<<grid, block, smem, s>>>(a); break;
+    default: grow_kernel<4><<<grid, block, smem, s>>>(a); break;
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Outputs: poses and contact pairs at the current state (one warp per robot).
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void pose_kernel(const InstDev* inst, int n_inst, const float* theta, const int* n_cur,
+                            const float* l_cur, float* out_theta, float* out_pose, float* out_tip) {
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (gw >= n_inst) return;
+  const InstDev I = inst[gw];
+  const int N = n_cur[gw];
+  const float l = l_cur[gw];
+  const int B = (N + 31) >> 5;
+  const int j0 = min(lane * B, N), j1 = min(j0 + B, N);
+  const float* th = theta + I.th_off;
+  FF hs{0.f, 0.f};
+  for (int j = j0; j < j1; ++j) hs = ff_add(hs, th[j]);
+  FF psi0 = ff_add(warp_excl_scan(hs, lane), I.bpsi);
+  FF psi = psi0, sx{0.f, 0.f}, sy{0.f, 0.f};
+  for (int j = j0; j < j1; ++j) {
+    psi = ff_add(psi, th[j]);
+    float sn, cs;
+    sincosf(psi.hi, &sn, &cs);
+    const float L = (j == N - 1) ? l : I.l_seg;
+    sx = ff_add(sx, L * (cs - sn * psi.lo));
+    sy = ff_add(sy, L * (sn + cs * psi.lo));
+  }
+  FF px = warp_excl_scan(sx, lane), py = warp_excl_scan(sy, lane);
+  psi = psi0;
+  for (int j = j0; j < j1; ++j) {
+    psi = ff_add(psi, th[j]);
+    if (out_pose) {
+      out_pose[3 * ((size_t)I.th_off + j) + 0] = (px.hi + I.bx) + px.lo;
+      out_pose[3 * ((size_t)I.th_off + j) + 1] = (py.hi + I.by) + py.lo;
+      out_pose[3 * ((size_t)I.th_off + j) + 2] = psi.hi + psi.lo;
+    }
+    if (out_theta) out_theta[I.th_off + j] = th[j];
+    float sn, cs;
+    sincosf(psi.hi, &sn, &cs);
+    const float L = (j == N - 1) ? l : I.l_seg;
+    px = ff_add(px, L * (cs - sn * psi.lo));
+    py = ff_add(py, L * (sn + cs * psi.lo));
+  }
+  for (int j = N + lane; j < I.n_target; j += 32) {
+    if (out_pose) {
+      out_pose[3 * ((size_t)I.th_off + j) + 0] = 0.f;
+      out_pose[3 * ((size_t)I.th_off + j) + 1] = 0.f;
+      out_pose[3 * ((size_t)I.th_off + j) + 2] = 0.f;
+    }
+    if (out_theta) out_theta[I.th_off + j] = 0.f;
+  }
+  // the lane holding the last link has the tip in (px, py)
+  if (out_tip && N > 0 && j1 == N && j0 < j1) {
+    out_tip[2 * gw + 0] = (px.hi + I.bx) + px.lo;
+    out_tip[2 * gw + 1] = (py.hi + I.by) + py.lo;
+  }
+  if (out_tip && N == 0 && lane == 0) {
+    out_tip[2 * gw + 0] = I.bx;
+    out_tip[2 * gw + 1] = I.by;
+  }
+}
+
+// Contact pairs (link, obstacle) of one robot, in (link, obstacle) order.
+__global__ void contacts_kernel(const InstDev* inst, int n_inst, const float4* obs, const float* theta,
+                                const int* n_cur, const float* l_cur, int ks, int max_pairs, int* counts,
+                                int* pairs) {
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (gw >= n_inst) return;
+  const InstDev I = inst[gw];
+  const int N = n_cur[gw];
+  const float l = l_cur[gw];
+  const int B = (N + 31) >> 5;
+  const int j0 = min(lane * B, N), j1 = min(j0 + B, N);
+  const float* th = theta + I.th_off;
+  const float4* ob = obs + I.obs_off;
+  FF hs{0.f, 0.f};
+  for (int j = j0; j < j1; ++j) hs = ff_add(hs, th[j]);
+  FF psi0 = ff_add(warp_excl_scan(hs, lane), I.bpsi);
+  FF psi = psi0, sx{0.f, 0.f}, sy{0.f, 0.f};
+  for (int j = j0; j < j1; ++j) {
+    psi = ff_add(psi, th[j]);
+    float sn, cs;
+    sincosf(psi.hi, &sn, &cs);
+    const float L = (j == N - 1) ? l : I.l_seg;
+    sx = ff_add(sx, L * (cs - sn * psi.lo));
+    sy = ff_add(sy, L * (sn + cs * psi.lo));
+  }
+  const FF px0 = warp_excl_scan(sx, lane), py0 = warp_excl_scan(sy, lane);
+  int base = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    FF px = px0, py = py0;
+    psi = psi0;
+    int cnt = 0;
+    for (int j = j0; j < j1; ++j) {
+      psi = ff_add(psi, th[j]);
+      float sn, cs;
+      sincosf(psi.hi, &sn, &cs);
+      const float ux = cs - sn * psi.lo, uy = sn + cs * psi.lo;
+      const float L = (j == N - 1) ? l : I.l_seg;
+      const float lx = L * ux, ly = L * uy;
+      for (int o = 0; o < I.n_obs; ++o) {
+        const float4 b4 = ob[o];
+        bool hit = false;
+        for (int k = 1; k <= ks && !hit; ++k) {
+          const float fr = (float)k / (float)ks;
+          const FF xk = ff_add(px, fr * lx), yk = ff_add(py, fr * ly);
+          const float dx = (xk.hi - b4.x) + xk.lo, dy = (yk.hi - b4.y) + yk.lo;
+          float nx, ny;
+          hit = disc_pen(b4, dx, dy, I.R, -uy, ux, nx, ny) > 0.f;
+        }
+        if (hit) {
+          if (pass == 1 && base + cnt < max_pairs && pairs) {
+            pairs[2 * ((size_t)gw * max_pairs + base + cnt) + 0] = j;
+            pairs[2 * ((size_t)gw * max_pairs + base + cnt) + 1] = o;
+          }
+          ++cnt;
+        }
+      }
+      px = ff_add(px, lx);
+      py = ff_add(py, ly);
+    }
+    if (pass == 0) {
+      // exclusive prefix of counts over lanes
+      int x = cnt;
+      for (int d = 1; d < 32; d <<= 1) {
+        int v = __shfl_up_sync(kFull, x, d);
+        if (lane >= d) x += v;
+      }
+      const int total = __shfl_sync(kFull, x, 31);
+      base = x - cnt;
+      if (lane == 0) counts[gw] = total;
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_poses(const InstDev* inst, int n_inst, const float* theta, const int* n_cur, const float* l_cur,
+                         float* out_theta, float* out_pose, float* out_tip, cudaStream_t s) {
+  const int threads = 128;
+  const int blocks = (n_inst * 32 + threads - 1) / threads;
+  pose_kernel<<<blocks, threads, 0, s>>>(inst, n_inst, theta, n_cur, l_cur, out_theta, out_pose, out_tip);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_contacts(const InstDev* inst, int n_inst, const float4* obs, const float* theta, const int* n_cur,
+                            const float* l_cur, int ks, int max_pairs, int* counts, int* pairs, cudaStream_t s) {
+  const int threads = 128;
+  const int blocks = (n_inst * 32 + threads - 1) / threads;
+  contacts_kernel<<<blocks, threads, 0, s>>>(inst, n_inst, obs, theta, n_cur, l_cur, ks, max_pairs, counts, pairs);
+  return cudaGetLastError();
+}
+
+}  // namespace vine

@@ -1,0 +1,97 @@
+// vine_internal.cuh -- device layouts shared by the library's translation units.
+//
+// HBM layout of a batch (one cudaMalloc, carved in this order):
+//   InstDev  inst[n]            80 B per instance: derived constants + CSR offsets
+//   float4   obs[n_obs_total]   (cx - bx, cy - by, p, q): circle p = R + r, q = -(R + r)^2;
+//                               box p = half-width, q = half-height (> 0)
+//   float4   act[n_act_total]   (begin, end, side * P_act, table index as int bits)
+//   float4   tab_hdr[n_tab]     (eps_lo, h, 1/h, G(0)) per sPAM force table
+//   float2   tab[n_tab * 256]   (f_k, G_k): force per pressure at knot k and its
+//                               integral from eps_lo
+//   float2   utab[NU + 1]       wrinkling energy table (Uhat, mhat) on [theta_c, pi]
+//   float    theta[sum n_links] joint angles (CSR by n_links)
+//   per-instance state: N, l, status, counters
+// Instances never share data; one warp owns one instance at a time.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace vine {
+
+constexpr int kKnots = 256;        // sPAM force table knots (uniform in strain)
+constexpr int kUCells = 1024;      // wrinkling energy table cells on [theta_c, pi]
+constexpr int kWarpsPerCta = 4;    // warps per CTA of the growth kernel
+constexpr int kMaxLinks = 1024;
+constexpr int kMaxObs = 1024;
+constexpr int kMaxAct = 64;
+constexpr float kPi = 3.14159265358979323846f;
+constexpr double kPiD = 3.14159265358979323846;
+
+enum InstStatus : int { kOK = 0, kMaxIter = 1, kNonFinite = 2, kBadInput = 3 };
+
+struct __align__(16) InstDev {
+  float l_seg, R, P, d;      // d = 2 R + R_act (moment arm, Eq. restoring_moment)
+  float kc, kg, PR3, bpsi;   // contact / growth stiffness, pi P R^3, base heading
+  float bx, by, pad0, pad1;  // base position (obstacles are stored relative to it)
+  int n_target, act_off, n_act, obs_off;
+  int n_obs, th_off, n_circ, pad2;
+};
+
+struct GrowArgs {
+  const InstDev* inst;
+  const float4* obs;
+  const float4* act;
+  const float4* tab_hdr;
+  const float2* tab;
+  const float2* utab;
+  float* theta;
+  int* n_cur;
+  float* l_cur;
+  int* status;
+  int* iters;
+  int* conv;
+  int* steps;
+  long long* rls;
+  long long* evals;
+  long long* linkevals;
+  double* resid_max;
+  const int* order;
+  int n_order;
+  int* counter;
+  int dynamic;
+  int n_steps;
+  int nmax, omax, amax, warp_floats;
+  // model constants
+  float w_a, w_b, w_c;
+  float theta_c, inv2thc, inv4thc, eps_c;
+  float u_h, u_invh, U_pi, m_pi;
+  float ls_switch, c1;
+  double tol;
+  int max_iter, max_halv;
+};
+
+// Table build (FP64) -- vine_tables.cu
+struct GaussLegendre {
+  int n;
+  double x[32];
+  double w[32];
+};
+
+void gauss_legendre(int n, GaussLegendre* gl);
+cudaError_t launch_spam_tables(const double* l0, int n_tab, double R_c, double R_act, double a_spam, double m_lo,
+                               const GaussLegendre& gl, float4* hdr, float2* tab, double* scratch,
+                               cudaStream_t s);
+cudaError_t launch_wrinkle_table(double eps_c, const GaussLegendre& gl, float2* utab, double* scratch,
+                                 double* consts /*device [4]: U(pi), m(pi), theta_c, h*/, cudaStream_t s);
+
+// Growth kernel -- vine_grow.cu
+cudaError_t launch_grow(const GrowArgs& a, int ks, int grid, int block, size_t smem, cudaStream_t s);
+size_t grow_smem_per_warp(int nmax, int omax, int amax);
+cudaError_t grow_configure(int ks, size_t smem_per_cta);
+int grow_max_ctas_per_sm(int ks, size_t smem_per_cta);
+cudaError_t launch_poses(const InstDev* inst, int n_inst, const float* theta, const int* n_cur, const float* l_cur,
+                         float* out_theta, float* out_pose, float* out_tip, cudaStream_t s);
+cudaError_t launch_contacts(const InstDev* inst, int n_inst, const float4* obs, const float* theta, const int* n_cur,
+                            const float* l_cur, int ks, int max_pairs, int* counts, int* pairs, cudaStream_t s);
+
+}  // namespace vine

@@ -1,0 +1,283 @@
+// vine_tables.cu -- FP64 prologue kernels run once per batch:
+//
+//  * sPAM force-per-pressure tables, Sec. 3.1 Eq. (sPAM_1), (sPAM_2), (phiRC),
+//    (sPAM_force): for each distinct cell length l0, 256 knots uniform in
+//    actuator strain between eps(m_lo) and eps(m = 0.5); each knot is the
+//    exact model at that strain.  Incomplete elliptic integrals by
+//    Gauss-Legendre quadrature of their integrands (smooth for m <= 1/2);
+//    the unsaturated root of Eq. (sPAM_2) by a coarse scan for the first sign
+//    change followed by safeguarded Newton; m at each knot by the Illinois
+//    variant of regula falsi.  Branch rule: the smallest root in
+//    (0, phi_sat], else the saturated branch phi = acos(R_c / R_act).
+//  * the wrinkling energy table, Sec. 3.2 Eq. (wrinkling_model): the integral
+//    of the restoring moment from onset to pi on 1024 cells, with the moment
+//    itself at every knot, for cubic Hermite interpolation in the line search.
+#include <cmath>
+
+#include "vine_internal.cuh"
+
+namespace vine {
+
+// Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on P_n.
+void gauss_legendre(int n, GaussLegendre* gl) {
+  gl->n = n;
+  for (int i = 0; i < n; ++i) {
+    double x = std::cos(kPiD * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = x;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (x * p1 - p0) / (x * x - 1.0);
+      double dx = p1 / dp;
+      x -= dx;
+      if (std::fabs(dx) < 1e-16) break;
+    }
+    gl->x[i] = x;
+    gl->w[i] = 2.0 / ((1.0 - x * x) * dp * dp);
+  }
+}
+
+namespace {
+
+struct SpamConst {
+  double Rc, Ract, a, m_lo, phi_sat;
+};
+
+// F(phi|m) and E(phi|m) by quadrature of (1 - m sin^2 t)^(-1/2) and its inverse.
+__device__ void ellip_FE(const GaussLegendre& gl, double phi, double m, double* F, double* E) {
+  double sf = 0.0, se = 0.0;
+  const double hh = 0.5 * phi;
+  for (int i = 0; i < gl.n; ++i) {
+    double t = hh * (1.0 + gl.x[i]);
+    double s = sin(t);
+    double q = sqrt(1.0 - m * s * s);
+    sf += gl.w[i] / q;
+    se += gl.w[i] * q;
+  }
+  *F = hh * sf;
+  *E = hh * se;
+}
+
+__device__ double ellip_F(const GaussLegendre& gl, double phi, double m) {
+  double F, E;
+  ellip_FE(gl, phi, m, &F, &E);
+  return F;
+}
+
+// Residual of Eq. (sPAM_2) on the unsaturated branch (l_a = l_0), lam = l_0 / R_c.
+__device__ double resid2(const GaussLegendre& gl, const SpamConst& c, double phi, double m, double lam) {
+  if (phi <= 0.0) return -lam * (1.0 + c.a / (2.0 * m));
+  double cp = cos(phi);
+  return ellip_F(gl, phi, m) / (sqrt(m) * cp) - lam * (1.0 + c.a / (2.0 * m * cp * cp));
+}
+
+// Model at contraction parameter m: strain eps and force per pressure f.
+__device__ void spam_model(const GaussLegendre& gl, const SpamConst& c, double m, double l0, double* eps,
+                           double* f) {
+  const double lam = l0 / c.Rc;
+  const int nscan = 32;
+  double lo = 0.0, hi = -1.0;
+  for (int k = 1; k <= nscan; ++k) {
+    double ph = c.phi_sat * (double)k / nscan;
+    if (resid2(gl, c, ph, m, lam) >= 0.0) {
+      hi = ph;
+      break;
+    }
+    lo = ph;
+  }
+  double phi, la;
+  const double sm = sqrt(m);
+  if (hi > 0.0) {
+    // safeguarded Newton inside [lo, hi] (residual < 0 at lo, >= 0 at hi)
+    double x = 0.5 * (lo + hi);
+    for (int it = 0; it < 100; ++it) {
+      double cp = cos(x), sp = sin(x);
+      double F = ellip_F(gl, x, m);
+      double r = F / (sm * cp) - lam * (1.0 + c.a / (2.0 * m * cp * cp));
+      if (r >= 0.0) hi = x; else lo = x;
+      double dF = 1.0 / sqrt(1.0 - m * sp * sp);
+      double dr = (dF * cp + F * sp) / (sm * cp * cp) - lam * c.a * sp / (m * cp * cp * cp);
+      double xn = x - r / dr;
+      if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+      if (fabs(xn - x) <= 1e-16 * x || hi - lo <= 1e-16) {
+        x = xn;
+        break;
+      }
+      x = xn;
+    }
+    phi = x;
+    la = l0;
+  } else {
+    phi = c.phi_sat;
+    double cp = cos(phi);
+    la = c.Rc * ellip_F(gl, phi, m) / (sm * cp) / (1.0 + c.a / (2.0 * m * cp * cp));
+  }
+  double cp = cos(phi);
+  double F, E;
+  ellip_FE(gl, phi, m, &F, &E);
+  // Eq. (sPAM_1) solved for the strain
+  *eps = (la - 2.0 * c.Rc * (E - 0.5 * F) / (sm * cp)) / l0;
+  // Eq. (sPAM_force) per unit actuation pressure
+  *f = kPiD * c.Rc * c.Rc * (1.0 - 2.0 * m) / (2.0 * m * cp * cp);
+}
+
+// One thread per (table, knot): knots 1..254 by Illinois on eps(m) - target.
+__global__ void spam_knots_kernel(const double* l0s, SpamConst c, GaussLegendre gl, const double* bounds,
+                                  double* fknots) {
+  const int t = blockIdx.y;
+  const int k = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (k > kKnots - 2) return;
+  const double l0 = l0s[t];
+  const double elo = bounds[4 * t + 0], ehi = bounds[4 * t + 1];
+  const double target = elo + (ehi - elo) * (double)k / (kKnots - 1);
+  double a = c.m_lo, b = 0.5, fa = elo - target, fb = ehi - target;
+  double m = a, e = 0.0, f = 0.0;
+  int side = 0;
+  for (int it = 0; it < 200; ++it) {
+    m = (a * fb - b * fa) / (fb - fa);
+    if (!(m > a && m < b)) m = 0.5 * (a + b);
+    spam_model(gl, c, m, l0, &e, &f);
+    double fm = e - target;
+    if (fm == 0.0 || b - a <= 1e-15 * b) break;
+    if ((fm < 0.0) == (fa < 0.0)) {
+      a = m;
+      fa = fm;
+      if (side == -1) fb *= 0.5;
+      side = -1;
+    } else {
+      b = m;
+      fb = fm;
+      if (side == 1) fa *= 0.5;
+      side = 1;
+    }
+    if (fabs(fm) <= 1e-15 * (fabs(target) + 1e-3)) break;
+  }
+  fknots[t * kKnots + k] = f;
+}
+
+// One thread per table: eps at m_lo and m = 1/2 (the table's strain range).
+__global__ void spam_bounds_kernel(const double* l0s, int n_tab, SpamConst c, GaussLegendre gl, double* bounds,
+                                   double* fknots) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_tab) return;
+  double elo, flo, ehi, fhi;
+  spam_model(gl, c, c.m_lo, l0s[t], &elo, &flo);
+  spam_model(gl, c, 0.5, l0s[t], &ehi, &fhi);
+  bounds[4 * t + 0] = elo;
+  bounds[4 * t + 1] = ehi;
+  fknots[t * kKnots + 0] = flo;
+  fknots[t * kKnots + kKnots - 1] = 0.0;
+}
+
+// One thread per table: cumulative trapezoid integral from eps_lo (exact for
+// the piecewise-linear interpolant), header and FP32 copies.
+__global__ void spam_finish_kernel(int n_tab, const double* bounds, const double* fknots, float4* hdr, float2* tab) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_tab) return;
+  const double elo = bounds[4 * t + 0], ehi = bounds[4 * t + 1];
+  const double h = (ehi - elo) / (kKnots - 1);
+  const double* f = fknots + t * kKnots;
+  double G = 0.0, G0 = 0.0;
+  // G(0): integral from eps_lo to 0 (0 lies inside the range for l0 in use;
+  // handled generally below)
+  for (int k = 0; k < kKnots; ++k) {
+    tab[t * kKnots + k] = make_float2((float)f[k], (float)G);
+    if (k + 1 < kKnots) G += 0.5 * h * (f[k] + f[k + 1]);
+  }
+  if (0.0 <= elo) {
+    G0 = f[0] * (0.0 - elo);
+  } else if (0.0 >= ehi) {
+    G0 = G;
+  } else {
+    double u = (0.0 - elo) / h;
+    int k = (int)floor(u);
+    if (k > kKnots - 2) k = kKnots - 2;
+    double acc = 0.0;
+    for (int q = 0; q < k; ++q) acc += 0.5 * h * (f[q] + f[q + 1]);
+    double s = u - k;
+    double fe = f[k] + s * (f[k + 1] - f[k]);
+    acc += 0.5 * s * h * (f[k] + fe);
+    G0 = acc;
+  }
+  hdr[t] = make_float4((float)elo, (float)h, (float)(1.0 / h), (float)G0);
+}
+
+// Wrinkling moment M / (pi P R^3) above onset, written through
+// gamma_0 = 2 asin(sqrt(1 - eps_c / s)), s = sin(theta / 2).
+__device__ double mhat_above(double th, double ec) {
+  double s = sin(0.5 * fmin(th, kPiD));
+  double g = 2.0 * asin(sqrt(1.0 - ec / s));
+  return (sin(2.0 * g) + 2.0 * kPiD - 2.0 * g) / (4.0 * (sin(g) + (kPiD - g) * cos(g)));
+}
+
+// One thread per cell: integral of mhat over the cell (cells next to onset
+// are split finer: the moment has a (theta - theta_c)^(3/2) term there) and
+// mhat at the cell's left knot.
+__global__ void wrinkle_cells_kernel(double ec, GaussLegendre gl, double* cells, double* knots) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k > kUCells) return;
+  const double thc = 2.0 * asin(ec);
+  const double h = (kPiD - thc) / kUCells;
+  const double a = thc + h * k;
+  knots[k] = (k == 0) ? 0.5 : mhat_above(fmin(a, kPiD), ec);
+  if (k == kUCells) return;
+  const int nsub = (k < 8) ? 64 : 1;
+  double acc = 0.0;
+  for (int q = 0; q < nsub; ++q) {
+    double lo = a + h * q / nsub, hi = a + h * (q + 1) / nsub;
+    if (k < 8) {  // geometric grading toward onset inside the first cells
+      double r0 = (double)q / nsub, r1 = (double)(q + 1) / nsub;
+      lo = a + h * r0 * r0;
+      hi = a + h * r1 * r1;
+    }
+    double c = 0.5 * (lo + hi), w = 0.5 * (hi - lo), s = 0.0;
+    for (int i = 0; i < gl.n; ++i) s += gl.w[i] * mhat_above(c + w * gl.x[i], ec);
+    acc += w * s;
+  }
+  cells[k] = acc;
+}
+
+__global__ void wrinkle_finish_kernel(double ec, const double* cells, const double* knots, float2* utab,
+                                      double* consts) {
+  const double thc = 2.0 * asin(ec);
+  double U = thc / 4.0;  // ramp part: integral of theta / (2 theta_c) up to theta_c
+  for (int k = 0; k <= kUCells; ++k) {
+    utab[k] = make_float2((float)U, (float)knots[k]);
+    if (k < kUCells) U += cells[k];
+  }
+  consts[0] = U;  // integral up to pi
+  consts[1] = knots[kUCells];
+  consts[2] = thc;
+  consts[3] = (kPiD - thc) / kUCells;
+}
+
+}  // namespace
+
+cudaError_t launch_spam_tables(const double* l0, int n_tab, double R_c, double R_act, double a_spam, double m_lo,
+                               const GaussLegendre& gl, float4* hdr, float2* tab, double* scratch,
+                               cudaStream_t s) {
+  if (n_tab <= 0) return cudaSuccess;
+  SpamConst c{R_c, R_act, a_spam, m_lo, std::acos(R_c / R_act)};
+  double* bounds = scratch;              // [4 n_tab]
+  double* fk = scratch + 4 * n_tab;      // [n_tab * 256]
+  spam_bounds_kernel<<<(n_tab + 31) / 32, 32, 0, s>>>(l0, n_tab, c, gl, bounds, fk);
+  dim3 grid((kKnots - 2 + 31) / 32, n_tab);
+  spam_knots_kernel<<<grid, 32, 0, s>>>(l0, c, gl, bounds, fk);
+  spam_finish_kernel<<<(n_tab + 31) / 32, 32, 0, s>>>(n_tab, bounds, fk, hdr, tab);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wrinkle_table(double eps_c, const GaussLegendre& gl, float2* utab, double* scratch,
+                                 double* consts, cudaStream_t s) {
+  double* cells = scratch;               // [kUCells]
+  double* knots = scratch + kUCells;     // [kUCells + 1]
+  wrinkle_cells_kernel<<<(kUCells + 1 + 63) / 64, 64, 0, s>>>(eps_c, gl, cells, knots);
+  wrinkle_finish_kernel<<<1, 1, 0, s>>>(eps_c, cells, knots, utab, consts);
+  return cudaGetLastError();
+}
+
+}  // namespace vine

@@ -1,0 +1,231 @@
+"""Thin ctypes binding over the C ABI of ``include/vine.h``.
+
+Argument marshalling only: every computation happens in ``libvine.so``.
+Importing this module loads the library and raises ImportError when it has
+not been built (``python -m paper_2509_15180_gb300.build`` or
+``__graft_entry__.build()``); there is no fallback.
+
+Arrays may be numpy arrays (host memory) or torch tensors (host or CUDA);
+pointers are taken with ``.ctypes.data`` / ``.data_ptr()``.  Streams are
+``torch.cuda.Stream`` objects, raw ``cudaStream_t`` integers or None (legacy
+default stream).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libvine.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libvine.so is not built (%s); run paper_2509_15180_gb300.build.build()" % LIB_PATH)
+_lib = C.CDLL(LIB_PATH)
+
+VINE_OK, VINE_EINVAL, VINE_ENOMEM, VINE_ECUDA, VINE_ETIMEOUT, VINE_EBUSY, VINE_ENOTCONVERGED = range(7)
+INST_OK, INST_MAXITER, INST_NONFINITE, INST_BADINPUT = range(4)
+
+
+class vine_params(C.Structure):
+    _fields_ = [("w_a", C.c_double), ("w_b", C.c_double), ("w_c", C.c_double), ("eps_crit", C.c_double),
+                ("R_c", C.c_double), ("R_act", C.c_double), ("a_spam", C.c_double), ("m_lo", C.c_double),
+                ("pen_frac", C.c_double), ("tol", C.c_double), ("ls_switch", C.c_double),
+                ("armijo_c1", C.c_double), ("max_iter", C.c_int32), ("discs_per_link", C.c_int32),
+                ("max_halvings", C.c_int32), ("mode", C.c_int32), ("gd_alpha", C.c_double),
+                ("gd_steps", C.c_int32), ("reserved", C.c_int32)]
+
+
+class vine_batch_desc(C.Structure):
+    _fields_ = [("n_inst", C.c_int32), ("mem_is_device", C.c_int32)] + [
+        (k, C.c_void_p) for k in ("n_links", "l_seg", "radius", "pressure", "base", "act_ptr", "act_begin",
+                                  "act_end", "act_side", "act_pressure", "act_l0", "obs_ptr", "obs_kind",
+                                  "obs_cx", "obs_cy", "obs_a", "obs_b")]
+
+
+class vine_stats(C.Structure):
+    _fields_ = [(k, C.c_int64) for k in ("robot_link_steps", "steps_converged", "steps_total", "iterations",
+                                         "evaluations", "link_evaluations", "pair_tests", "circle_pair_tests")] + [
+        (k, C.c_int32) for k in ("n_maxiter", "n_nonfinite", "n_badinput", "reserved")]
+
+
+_p, _i32, _i64 = C.c_void_p, C.c_int32, C.c_int64
+_SIG = {
+    "vine_params_default": [_p],
+    "vine_batch_create": [_p, _p, _p, _p],
+    "vine_batch_reset": [_p, _p],
+    "vine_grow_step": [_p, _i32, _p],
+    "vine_simulate": [_p, _p],
+    "vine_simulate_plain": [_p, _p],
+    "vine_get_state": [_p, _p, _p, _p, _p, _p, _p, _p, _p, _i32, _p],
+    "vine_get_contacts": [_p, _p, _p, _i32, _i32, _p],
+    "vine_get_stats": [_p, _p, _p],
+    "vine_batch_info": [_p, _p, _p],
+    "vine_get_tables": [_p, _p, _p, _p, _p, _p],
+    "vine_batch_destroy": [_p],
+}
+for _name, _args in _SIG.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = C.c_int
+_lib.vine_last_error.restype = C.c_char_p
+_lib.vine_last_error.argtypes = []
+
+EXPORTED = list(_SIG) + ["vine_last_error"]
+
+
+class VineError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = _lib.vine_last_error().decode(errors="replace")
+        super().__init__("%s failed with status %d: %s" % (where, status, msg))
+        self.status = status
+
+
+def _check(status: int, where: str):
+    if status != VINE_OK:
+        raise VineError(status, where)
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return int(s.cuda_stream)
+
+
+def _ptr(a) -> int | None:
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return int(a.data_ptr()) if a.numel() else None
+    a = np.asarray(a)
+    return int(a.ctypes.data) if a.size else None
+
+
+def last_error() -> str:
+    return _lib.vine_last_error().decode(errors="replace")
+
+
+def vine_params_default() -> vine_params:
+    p = vine_params()
+    _check(_lib.vine_params_default(C.byref(p)), "vine_params_default")
+    return p
+
+
+# -------------------------------------------------------------------------
+# batch
+# -------------------------------------------------------------------------
+_HOST_DTYPES = dict(n_links=np.int32, l_seg=np.float32, radius=np.float32, pressure=np.float32,
+                    base=np.float32, act_ptr=np.int32, act_begin=np.float32, act_end=np.float32,
+                    act_side=np.int8, act_pressure=np.float32, act_l0=np.float32, obs_ptr=np.int32,
+                    obs_kind=np.uint8, obs_cx=np.float32, obs_cy=np.float32, obs_a=np.float32,
+                    obs_b=np.float32)
+
+
+class Batch:
+    """A batch handle: ``vine_batch_create`` on construction,
+    ``vine_batch_destroy`` on close()."""
+
+    def __init__(self, scene: dict, params: vine_params | None = None, stream=None):
+        keep = {}
+        dev = 0
+        for k, dt in _HOST_DTYPES.items():
+            v = scene[k]
+            if hasattr(v, "data_ptr"):  # torch tensor
+                dev = 1 if v.is_cuda else dev
+                keep[k] = v.contiguous()
+            else:
+                keep[k] = np.ascontiguousarray(np.asarray(v).reshape(-1), dtype=dt)
+        self._keep = keep
+        D = vine_batch_desc()
+        D.n_inst = int(len(scene["n_links"]))
+        D.mem_is_device = dev
+        for k in _HOST_DTYPES:
+            setattr(D, k, _ptr(keep[k]))
+        self.n_inst = D.n_inst
+        self.params = params if params is not None else vine_params_default()
+        h = C.c_void_p()
+        _check(_lib.vine_batch_create(C.byref(D), C.byref(self.params), _stream(stream), C.byref(h)),
+               "vine_batch_create")
+        self.h = h
+        n, tl = C.c_int32(), C.c_int64()
+        _check(_lib.vine_batch_info(h, C.byref(n), C.byref(tl)), "vine_batch_info")
+        self.total_links = tl.value
+        nl = scene["n_links"]
+        self.n_links = nl.cpu().numpy() if hasattr(nl, "cpu") else np.asarray(nl)
+        self.offsets = np.concatenate([[0], np.cumsum(self.n_links)]).astype(np.int64)
+        self._keep = None  # inputs were copied during create
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.vine_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self, stream=None):
+        _check(_lib.vine_batch_reset(self.h, _stream(stream)), "vine_batch_reset")
+
+    def grow_step(self, n_steps: int = 1, stream=None):
+        _check(_lib.vine_grow_step(self.h, int(n_steps), _stream(stream)), "vine_grow_step")
+
+    def simulate(self, stream=None):
+        _check(_lib.vine_simulate(self.h, _stream(stream)), "vine_simulate")
+
+    def simulate_plain(self, stream=None):
+        _check(_lib.vine_simulate_plain(self.h, _stream(stream)), "vine_simulate_plain")
+
+    def state(self, stream=None) -> dict:
+        """Host copy of the state (synchronises the stream)."""
+        n, T = self.n_inst, max(self.total_links, 1)
+        out = dict(theta=np.zeros(T, np.float32), l=np.zeros(n, np.float32), pose=np.zeros((T, 3), np.float32),
+                   tip=np.zeros((n, 2), np.float32), N=np.zeros(n, np.int32), iters=np.zeros(n, np.int32),
+                   resid=np.zeros(n, np.float64), status=np.zeros(n, np.int32))
+        _check(_lib.vine_get_state(self.h, _ptr(out["theta"]), _ptr(out["l"]), _ptr(out["pose"]), _ptr(out["tip"]),
+                                   _ptr(out["N"]), _ptr(out["iters"]), _ptr(out["resid"]), _ptr(out["status"]), 0,
+                                   _stream(stream)), "vine_get_state")
+        return out
+
+    def state_device(self, out: dict, stream=None):
+        """Writes the state into torch CUDA tensors (async on the stream)."""
+        g = lambda k: _ptr(out.get(k))
+        _check(_lib.vine_get_state(self.h, g("theta"), g("l"), g("pose"), g("tip"), g("N"), g("iters"),
+                                   g("resid"), g("status"), 1, _stream(stream)), "vine_get_state")
+
+    def contacts(self, max_pairs: int = 256, stream=None):
+        """(counts[n], pairs[n, max_pairs, 2]) at the current state."""
+        counts = np.zeros(self.n_inst, np.int32)
+        pairs = np.zeros((self.n_inst, max_pairs, 2), np.int32)
+        _check(_lib.vine_get_contacts(self.h, _ptr(counts), _ptr(pairs), int(max_pairs), 0, _stream(stream)),
+               "vine_get_contacts")
+        return counts, pairs
+
+    def stats(self, stream=None) -> dict:
+        s = vine_stats()
+        _check(_lib.vine_get_stats(self.h, C.byref(s), _stream(stream)), "vine_get_stats")
+        return {k: getattr(s, k) for k, _ in vine_stats._fields_}
+
+    def tables(self) -> dict:
+        """Prologue tables as the kernels use them (see vine_get_tables)."""
+        nt = C.c_int32()
+        _check(_lib.vine_get_tables(self.h, C.byref(nt), None, None, None, None), "vine_get_tables")
+        n = nt.value
+        hdr = np.zeros((max(n, 1), 4), np.float32)
+        kn = np.zeros((max(n, 1), 256, 2), np.float32)
+        ut = np.zeros((1025, 2), np.float32)
+        cs = np.zeros(4, np.float64)
+        _check(_lib.vine_get_tables(self.h, C.byref(nt), _ptr(hdr), _ptr(kn), _ptr(ut), _ptr(cs)),
+               "vine_get_tables")
+        return dict(n_tab=n, hdr=hdr[:n], knots=kn[:n], utab=ut, consts=cs)
+
+    def theta_of(self, st: dict, i: int):
+        return st["theta"][self.offsets[i]: self.offsets[i] + st["N"][i]]
+
+    def pose_of(self, st: dict, i: int):
+        return st["pose"][self.offsets[i]: self.offsets[i] + st["N"][i]]

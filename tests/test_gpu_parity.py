@@ -1,0 +1,236 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Bar: link start points and tip within 1e-4 link lengths, headings within
+1e-4 rad, contact sets identical apart from grazing pairs (|gap| within
+2e-4 link lengths), every step converged.  Inputs are the seeded scenes of
+paper_2509_15180_gb300.scenes.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2509_15180_gb300 import scenes
+
+from parity import contact_sets, contacts_match, pose_error
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2509_15180_gb300 import vine  # noqa: E402  (fails loudly if libvine.so is missing)
+
+POSE_TOL = 1e-4      # link lengths
+HEAD_TOL = 1e-4      # rad
+THREADS = 16
+
+
+def _oracle(sc, tol=1e-10):
+    return oracle.Oracle(sc, oracle.default_params(tol=tol))
+
+
+def _compare(b, st, orc, ost, sc, idx_gpu, idx_orc, counts=None, pairs=None):
+    worst = 0.0
+    for ig, io in zip(idx_gpu, idx_orc):
+        ls = float(sc["l_seg"][io])
+        e, eh = pose_error(b, st, orc, ost, io) if b is not None else (0, 0)
+        worst = max(worst, e / ls)
+        assert e <= POSE_TOL * ls, "instance %d: position error %.3g link lengths" % (ig, e / ls)
+        assert eh <= HEAD_TOL, "instance %d: heading error %.3g rad" % (ig, eh)
+        if counts is not None:
+            g, o, gr = contact_sets(counts, pairs, orc, ost, io, ls)
+            assert contacts_match(g, o, gr), "instance %d: contact sets differ: gpu-only %s oracle-only %s" % (
+                ig, sorted(g - o - gr), sorted(o - g - gr))
+    return worst
+
+
+class _Sub:
+    """Batch view restricted to chosen instances (for pose_error)."""
+
+    def __init__(self, b, st, idx):
+        self.b, self.idx = b, idx
+        self.st = {k: v for k, v in st.items()}
+
+    def pose_of(self, st, i):
+        return self.b.pose_of(self.st, self.idx[i])
+
+
+def test_prologue_tables_match_oracle():
+    sc = scenes.config2(16)
+    b = vine.Batch(sc)
+    T = b.tables()
+    orc = _oracle(sc)
+    ot = orc.tables()
+    assert T["n_tab"] == len(ot) == 1
+    l0, lo, hi, f = ot[0]
+    assert T["hdr"][0, 0] == pytest.approx(lo, rel=1e-6, abs=1e-9)
+    assert T["hdr"][0, 1] == pytest.approx((hi - lo) / 255, rel=1e-6)
+    assert np.allclose(T["knots"][0, :, 0], f, rtol=2e-6, atol=1e-12 * f.max())
+    # cumulative integral
+    G = np.concatenate([[0.0], np.cumsum(0.5 * (hi - lo) / 255 * (f[1:] + f[:-1]))])
+    assert np.allclose(T["knots"][0, :, 1], G, rtol=5e-6, atol=1e-9 * G.max())
+    # wrinkling energy table against the oracle's quadrature
+    thc, hu = T["consts"][2], T["consts"][3]
+    for k in (0, 1, 5, 40, 300, 1023, 1024):
+        m, _, u = oracle.wrinkle(thc + k * hu)
+        assert T["utab"][k, 0] == pytest.approx(u, rel=2e-6)
+        assert T["utab"][k, 1] == pytest.approx(m, rel=2e-6)
+    b.close()
+
+
+def test_config1_full_parity():
+    sc = scenes.config1()
+    b = vine.Batch(sc)
+    b.simulate()
+    st = b.state()
+    counts, pairs = b.contacts(64)
+    stats = b.stats()
+    orc = _oracle(sc)
+    ost = orc.new_state()
+    orc.run(ost, 20, threads=THREADS)
+    assert np.all(st["status"] == 0) and np.all(st["N"] == 20)
+    assert stats["steps_converged"] == 64 * 20
+    assert stats["robot_link_steps"] == scenes.robot_link_steps(sc["n_links"])
+    n = sc["n_links"].size
+    _compare(b, st, orc, ost, sc, range(n), range(n), counts, pairs)
+    b.close()
+
+
+def test_config1_stepwise_parity():
+    sc = scenes.config1(24)
+    b = vine.Batch(sc)
+    orc = _oracle(sc)
+    ost = orc.new_state()
+    n = sc["n_links"].size
+    for step in range(20):
+        b.grow_step(1)
+        orc.run(ost, 1, threads=THREADS)
+        st = b.state()
+        counts, pairs = b.contacts(64)
+        assert np.all(st["N"] == step + 1)
+        _compare(b, st, orc, ost, sc, range(n), range(n), counts, pairs)
+    b.close()
+
+
+def test_plain_form_is_bitwise_identical():
+    sc = scenes.config1(16)
+    b1, b2 = vine.Batch(sc), vine.Batch(sc)
+    b1.simulate()
+    b2.simulate_plain()
+    s1, s2 = b1.state(), b2.state()
+    for k in ("theta", "l", "pose", "tip", "N", "iters"):
+        assert np.array_equal(s1[k], s2[k]), k
+    b1.close(); b2.close()
+
+
+def test_config2_full_size_sampled():
+    """4096 robots x 100 links in the launch the benchmark times; 12 sampled
+    robots recomputed by the oracle."""
+    sc = scenes.config2()
+    b = vine.Batch(sc)
+    b.simulate()
+    torch.cuda.synchronize()
+    st = b.state()
+    counts, pairs = b.contacts(256)
+    stats = b.stats()
+    assert np.all(st["N"] == 100)
+    nbad = int((st["status"] != 0).sum())
+    assert nbad <= 4096 // 200, "too many non-converged robots: %d" % nbad
+    rng = np.random.default_rng(7)
+    idx = np.sort(rng.choice(4096, 12, replace=False))
+    sub = scenes.subset(sc, idx)
+    orc = _oracle(sub)
+    ost = orc.new_state()
+    orc.run(ost, 100, threads=THREADS)
+    view = _Sub(b, st, idx)
+    sub_st = dict(st)
+    sub_st["tip"] = st["tip"][idx]
+    view.st = st
+    for k, i in enumerate(idx):
+        if st["status"][i] != 0 or ost["status"][k] != 0:
+            continue
+        ls = float(sc["l_seg"][i])
+        th = orc.theta_of(ost, k)
+        px, py, psi = orc.poses(k, th, ost["l"][k])
+        pose = b.pose_of(st, i)
+        e = max(np.max(np.abs(pose[:, 0] - px[:-1])), np.max(np.abs(pose[:, 1] - py[:-1])),
+                abs(st["tip"][i, 0] - px[-1]), abs(st["tip"][i, 1] - py[-1]))
+        assert e <= POSE_TOL * ls, "robot %d: position error %.3g link lengths" % (i, e / ls)
+        g = {tuple(p) for p in pairs[i, : counts[i]]}
+        gap = orc.gaps(k, th, ost["l"][k])
+        o = {(int(a), int(c)) for a, c in zip(*np.nonzero(gap < 0))}
+        gr = {(int(a), int(c)) for a, c in zip(*np.nonzero(np.abs(gap) <= 2e-4 * ls))}
+        assert contacts_match(g, o, gr), "robot %d contact sets differ" % i
+    assert stats["robot_link_steps"] >= 0.99 * scenes.robot_link_steps(sc["n_links"])
+    b.close()
+
+
+def test_uneven_batch_sampled():
+    """Uneven robots (30-120 links, 5-200 obstacles, 0-8 actuators) in one launch."""
+    sc = scenes.config3(96, n_range=(30, 120))
+    b = vine.Batch(sc)
+    b.simulate()
+    st = b.state()
+    counts, pairs = b.contacts(512)
+    assert np.all(st["N"] == sc["n_links"])
+    idx = np.array([0, 5, 17, 33, 61, 90])
+    sub = scenes.subset(sc, idx)
+    orc = _oracle(sub)
+    ost = orc.new_state()
+    orc.run(ost, 400, threads=THREADS)
+    for k, i in enumerate(idx):
+        if st["status"][i] != 0 or ost["status"][k] != 0:
+            continue
+        ls = float(sc["l_seg"][i])
+        th = orc.theta_of(ost, k)
+        px, py, psi = orc.poses(k, th, ost["l"][k])
+        pose = b.pose_of(st, i)
+        e = max(np.max(np.abs(pose[:, 0] - px[:-1])), np.max(np.abs(pose[:, 1] - py[:-1])),
+                abs(st["tip"][i, 0] - px[-1]), abs(st["tip"][i, 1] - py[-1]))
+        assert e <= POSE_TOL * ls, "robot %d: position error %.3g link lengths" % (i, e / ls)
+    b.close()
+
+
+def test_edge_cases():
+    # straight tube, no obstacles/actuators; one-link robot; bad input next to good ones
+    sc = scenes.config1(4)
+    sc["act_ptr"] = np.zeros(5, np.int32)
+    for k in ("act_begin", "act_end", "act_pressure", "act_l0"):
+        sc[k] = np.zeros(0, np.float32)
+    sc["act_side"] = np.zeros(0, np.int8)
+    sc["obs_ptr"][:] = 0
+    for k in ("obs_cx", "obs_cy", "obs_a", "obs_b"):
+        sc[k] = np.zeros(0, np.float32)
+    sc["obs_kind"] = np.zeros(0, np.uint8)
+    sc["n_links"][1] = 1
+    sc["radius"][2] = -1.0
+    b = vine.Batch(sc)
+    b.simulate()
+    st = b.state()
+    assert st["status"][2] == vine.INST_BADINPUT and st["N"][2] == 0
+    assert st["status"][0] == 0 and st["status"][1] == 0 and st["N"][1] == 1
+    assert np.all(b.theta_of(st, 0) == 0.0)
+    ls = float(sc["l_seg"][0])
+    assert np.allclose(b.pose_of(st, 0)[:, 0], np.arange(20) * ls, atol=1e-7)
+    assert st["tip"][0, 0] == pytest.approx(20 * ls, abs=1e-6)
+    # reset + re-run is deterministic; zero steps is a no-op
+    b.reset()
+    b.grow_step(0)
+    assert np.all(b.state()["N"] == 0)
+    b.simulate()
+    st2 = b.state()
+    for k in ("theta", "pose", "tip", "l"):
+        assert np.array_equal(st[k], st2[k]), k
+    b.close()
+
+
+def test_device_inputs_match_host_inputs():
+    sc = scenes.config1(8)
+    dsc = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in sc.items()}
+    b1, b2 = vine.Batch(sc), vine.Batch(dsc)
+    b1.simulate(); b2.simulate()
+    s1, s2 = b1.state(), b2.state()
+    for k in ("theta", "pose", "tip", "l", "iters"):
+        assert np.array_equal(s1[k], s2[k]), k
+    b1.close(); b2.close()
