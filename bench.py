@@ -1,0 +1,288 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched growth step (robot-link-steps per second).
+
+Workload: 4096 robots x 100 links of 1.5 cm, radius U[2, 4] cm, pressure
+U[2, 10] kPa, 0-6 sPAM actuators, 20 circles + 20 boxes each in a 1.5 m box
+(seeded synthetic scenes), every robot grown from one link to 100 links with
+every step solved to the equilibrium tolerance 1e-6.  One bench step = one
+vine_simulate call over the whole batch (a robot-link-step is one link
+present during one growth step: 100*101/2 per robot).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle on the
+host cores (a bounded sample of the same workload per step).  Under torchrun
+each rank grows its own replica of the workload (weak scaling, no
+collective on the data path); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "robot-link-steps/s at equilibrium tol 1e-6 on 1 GB300 (batched/served vs plain); p50/p99 latency"
+UNIT = "robot-link-steps/s"
+WORKLOAD = "design-optimisation batch: 4096 robots x 100 links (1.5 cm), 20 circles + 20 boxes, 0-6 sPAM actuators"
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, throttle reasons)."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index, self.samples, self.proc = index, [], None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+        rows = [r for r in self.samples if len(r) >= 8]
+        if rows:
+            sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+            mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+            out["sm_mhz"] = float(np.median(sm)) if sm else None
+            out["sm_max_mhz"] = max(mx) if mx else None
+            names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+            out["reasons"] = sorted({n for r in rows for n, v in zip(names, r[4:8]) if v.lower() == "active"})
+            out["samples"] = len(rows)
+        return out
+
+
+def run_gpu(args):
+    import torch
+
+    from paper_2509_15180_gb300 import scenes, vine
+
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    sc = scenes.config2(4096, replicate=rank)
+    rls_per_step = scenes.robot_link_steps(sc["n_links"])
+    stream = torch.cuda.current_stream()
+    dsc = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in sc.items()}
+    b = vine.Batch(dsc, stream=stream)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def one_step():
+        b.reset(stream)
+        b.simulate(stream)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    stats = b.stats(stream)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    conv_rls = 0
+    for k in range(args.steps):
+        flush.zero_()  # L2 flush outside the timed interval
+        b.reset(stream)
+        starts[k].record(stream)
+        b.simulate(stream)
+        ends[k].record(stream)
+        torch.cuda.synchronize()
+        conv_rls += b.stats(stream)["robot_link_steps"]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    step_ms = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
+    total_s = float(step_ms.sum()) / 1e3
+    if ws > 1:
+        t = torch.tensor([total_s, conv_rls], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+        total_s, conv_all = float(tmax[0]), float(t[1])
+    else:
+        conv_all = float(conv_rls)
+    value = conv_all / total_s
+    st_last = b.stats(stream)
+
+    # --- end to end through the C ABI with host buffers (create/copy in, grow, read back)
+    e2e_steps = max(2, min(args.steps, 5))
+    host = {k: np.ascontiguousarray(v) for k, v in sc.items()}
+    h2d = int(sum(v.nbytes for v in host.values()))
+    T = int(sc["n_links"].sum())
+    n = len(sc["n_links"])
+    d2h = T * 4 + T * 12 + n * (8 + 4 + 4 + 4 + 8 + 4)
+    bw = vine.Batch(host, stream=stream)  # warm (tables, graph) once
+    bw.simulate(stream)
+    bw.state(stream)
+    bw.close()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_rls = 0
+    for _ in range(e2e_steps):
+        be = vine.Batch(host, stream=stream)
+        be.simulate(stream)
+        out = be.state(stream)
+        e2e_rls += int(be.stats(stream)["robot_link_steps"])
+        be.close()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": e2e_rls / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+           "ms_per_step": 1e3 * e2e_s / e2e_steps}
+
+    # --- plain form: one launch per robot, same kernel (subset of the batch)
+    n_plain = args.plain_robots
+    sub = scenes.subset(sc, np.arange(n_plain))
+    bp = vine.Batch(sub, stream=stream)
+    bp.simulate_plain(stream)
+    torch.cuda.synchronize()
+    bp.reset(stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    bp.simulate_plain(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_s = e0.elapsed_time(e1) / 1e3
+    plain = {"value": bp.stats(stream)["robot_link_steps"] / plain_s, "unit": UNIT, "robots": n_plain,
+             "launches": n_plain, "note": "one launch per robot, sequential; the first %d robots" % n_plain}
+    bp.close()
+
+    # --- roofline of the growth kernel: algorithmic FP32 flops per launch
+    flops = (40.0 * st_last["link_evaluations"] + 10.0 * st_last["circle_pair_tests"] +
+             14.0 * (st_last["pair_tests"] - st_last["circle_pair_tests"]))
+    launch_s = float(np.mean(step_ms)) / 1e3
+    achieved = flops / launch_s / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": args.traffic,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived; MEASURED_PEAKS has no FP32 figure)",
+                "flops_per_launch": flops}
+
+    result = None
+    if rank == 0:
+        cpu = cpu_baseline(args, sc) if ws == 1 and not args.no_cpu else None
+        lat = {"p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+               "what": "latency of one whole-batch simulate call"}
+        result = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 residual test)", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "robots_per_gpu": n, "links": 100,
+                       "robot_link_steps_per_step": rls_per_step, "l2": "flushed between timed steps (512 MiB write)",
+                       "tol": 1e-6},
+            "e2e": e2e, "plain": plain, "latency": lat, "roofline": roofline, "cpu_baseline": cpu,
+            "clocks": ck, "gpu_launches": args.steps,
+            "solver": {"iters_per_step": st_last["iterations"] / max(st_last["steps_total"], 1),
+                       "evals_per_step": st_last["evaluations"] / max(st_last["steps_total"], 1),
+                       "steps_converged": st_last["steps_converged"], "steps_total": st_last["steps_total"],
+                       "robots_maxiter": st_last["n_maxiter"]},
+        }
+    b.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return result
+
+
+def cpu_baseline(args, sc, robots=None):
+    """The FP64 oracle as it stands, OpenMP over robots on all host cores, on a
+    bounded sample of the workload (the first `robots` robots)."""
+    import oracle
+    from paper_2509_15180_gb300 import scenes
+
+    robots = robots or args.cpu_robots
+    sub = scenes.subset(sc, np.arange(robots))
+    orc = oracle.Oracle(sub)
+    st = orc.new_state()
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    orc.run(st, 100, threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": float(st["rls"].sum()) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "first %d robots of the workload, all 100 growth steps (%.1f s)" % (robots, dt)}
+
+
+def run_reference(args):
+    """Reference arm: the oracle on the host cores, same metric and workload."""
+    from paper_2509_15180_gb300 import scenes
+
+    ws, rank = _dist()
+    if rank != 0:
+        return None
+    sc = scenes.config2(4096)
+    vals, times = [], []
+    for _ in range(args.warmup):
+        cpu_baseline(args, sc, robots=8)
+    for _ in range(args.steps):
+        r = cpu_baseline(args, sc, robots=args.ref_robots)
+        vals.append(r["value"])
+        times.append(scenes.robot_link_steps(sc["n_links"][: args.ref_robots]) / r["value"])
+    v = float(np.mean(vals))
+    cores = os.cpu_count() or 1
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "robots_per_step": args.ref_robots},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "first %d robots of the workload per step" % args.ref_robots},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--plain-robots", type=int, default=64)
+    ap.add_argument("--cpu-robots", type=int, default=96)
+    ap.add_argument("--ref-robots", type=int, default=48)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None)
+    args = ap.parse_args()
+    res = run_reference(args) if args.impl == "reference" else run_gpu(args)
+    if res is not None:
+        print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

@@ -69,8 +69,9 @@ typedef enum {
  * tol: convergence when the predicted displacement of every link end point
  *   (and l_seg times every joint step) is at most tol times the robot length
  *   N l_seg (1e-6); the test is evaluated in FP64.
- * ls_switch: above this predicted displacement the step is line-searched
- *   (Armijo on the cost, constant armijo_c1, at most max_halvings halvings).
+ * ls_switch: above this predicted displacement (same units as tol) the step
+ *   is line-searched (Armijo on the cost, constant armijo_c1, at most
+ *   max_halvings halvings); at or below it the full step is taken (1e-5).
  * max_iter: Gauss-Newton iterations per growth step (100).
  * discs_per_link: contact discs K_s of radius R at fractions k/K_s of each
  *   link (2; 1..4 supported).

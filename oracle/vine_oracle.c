@@ -33,6 +33,7 @@
  * Gauss-Kronrod (7,15) quadrature (Kronrod 1965 nodes and weights).
  */
 #include <math.h>
+#include <stdio.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -69,7 +70,7 @@ void orc_params_default(orc_params* p) {
   p->m_lo = 0.002;
   p->pen_frac = 0.01;
   p->tol = 1e-6;
-  p->ls_switch = 1e-3;
+  p->ls_switch = 1e-5;
   p->armijo_c1 = 1e-4;
   p->max_iter = 100;
   p->discs_per_link = 2;
@@ -661,6 +662,10 @@ static double step_residual(const inst_t* I, int N, const double* dx, const geo_
 
 enum { ORC_OK = 0, ORC_MAXITER = 1, ORC_NONFINITE = 2, ORC_BADINPUT = 3 };
 
+/* Diagnostic trace of the solver iterations to stderr (off by default). */
+static int g_trace = 0;
+void orc_set_trace(int on) { g_trace = on; }
+
 /* Equilibrium of the current chain from the warm start (theta, l): damped
  * Gauss-Newton with the bound 0 <= l <= l_seg handled as an active set,
  * Armijo backtracking on J while the predicted displacement exceeds
@@ -701,7 +706,8 @@ static int solve_step(const inst_t* I, int N, double* th, double* l, int* iters_
     double gd = 0.0;
     for (int k = 0; k < N; ++k) gd += g[k] * dx[k];
     double alpha = 1.0, Jt = J, lt = *l;
-    for (int h = 0; h <= p->max_halvings; ++h) {
+    int hcount = 0;
+    for (int h = 0; h <= p->max_halvings; ++h, ++hcount) {
       for (int k = 0; k < N; ++k) tt[k] = th[k] + alpha * dx[k];
       lt = fmin(fmax(*l + alpha * dx[N], 0.0), I->l_seg);
       Jt = energy(I, N, tt, lt, NULL, NULL, &G);
@@ -711,6 +717,9 @@ static int solve_step(const inst_t* I, int N, double* th, double* l, int* iters_
       if (Jt <= J + p->armijo_c1 * dec) break;
       alpha *= 0.5;
     }
+    if (g_trace)
+      fprintf(stderr, "it %3d r %.3e J %.9e alpha %.3g halvings %d l %.5f lfix %d gd %.3e\n", it, r, J, alpha,
+              hcount, *l, lfix, gd);
     for (int k = 0; k < N; ++k) th[k] = tt[k];
     *l = lt;
     J = energy(I, N, th, *l, g, H, &G);

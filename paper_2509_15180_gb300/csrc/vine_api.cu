@@ -166,7 +166,7 @@ vine_status vine_params_default(vine_params* p) {
   p->m_lo = 0.002;
   p->pen_frac = 0.01;
   p->tol = 1e-6;
-  p->ls_switch = 1e-3;
+  p->ls_switch = 1e-5;
   p->armijo_c1 = 1e-4;
   p->max_iter = 100;
   p->discs_per_link = 2;
