@@ -215,6 +215,17 @@ vine_status vine_get_stats(const vine_batch* b, vine_stats* out, void* cuda_stre
 vine_status vine_get_tables(const vine_batch* b, int32_t* n_tab, float* hdr, float* knots, float* utab,
                             double* consts);
 
+/* Introspection of one robot at a caller-given state (synchronous; host
+ * buffers; allocates a small device buffer): with n_links links present,
+ * joint angles theta[n_links] and distal length l_last, returns the cost of
+ * Eq. (pbd) in potential form (FP64 sum of FP32 terms), its gradient
+ * grad[n_links + 1] (the last entry is d/d l_last), the Gauss-Newton step
+ * step[n_links + 1] the solver would take there (the last entry is 0 when
+ * the bound on l_last is active, reported in *l_fixed), and that step's
+ * predicted-displacement residual.  Does not change the batch state. */
+vine_status vine_probe_state(const vine_batch* b, int32_t inst, int32_t n_links, const float* theta, float l_last,
+                             double* cost, float* grad, float* step, double* residual, int32_t* l_fixed);
+
 /* Number of instances and total link capacity (sum of n_links). */
 vine_status vine_batch_info(const vine_batch* b, int32_t* n_inst, int64_t* total_links);
 

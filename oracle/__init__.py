@@ -87,6 +87,9 @@ def lib():
         L.orc_gaps.argtypes = [p, p, p, i, i, p, d, p]
         L.orc_sdf.restype = d
         L.orc_sdf.argtypes = [p, i, d, d, p, p]
+        L.orc_gn_step.restype = i
+        L.orc_gn_step.argtypes = [p, p, p, i, i, p, d, p, p, p, p]
+        L.orc_set_trace.argtypes = [i]
         L.orc_run.restype = i
         L.orc_run.argtypes = [p, p, p, i, p, p, p, p, p, p, p, p, p, i]
         _lib = L
@@ -218,6 +221,18 @@ class Oracle:
         st = lib().orc_solve(C.byref(self.P), C.byref(self.B), self.T, int(i), th.size, _ptr(th), C.byref(lv),
                              C.byref(it), C.byref(r))
         return th, lv.value, it.value, r.value, st
+
+    def gn_step(self, i: int, theta, l: float):
+        """(dx[N+1], residual, J, lfix): one Gauss-Newton step at a fixed state."""
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        N = th.size
+        dx = np.zeros(N + 1)
+        r, J, lf = C.c_double(), C.c_double(), C.c_int()
+        rc = lib().orc_gn_step(C.byref(self.P), C.byref(self.B), self.T, int(i), N, _ptr(th), float(l), _ptr(dx),
+                               C.byref(r), C.byref(J), C.byref(lf))
+        if rc != 0:
+            raise ValueError("Gauss-Newton matrix not positive definite")
+        return dx, r.value, J.value, bool(lf.value)
 
     def poses(self, i: int, theta, l: float):
         th = np.ascontiguousarray(theta, dtype=np.float64)

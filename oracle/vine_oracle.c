@@ -754,6 +754,32 @@ int orc_solve(const orc_params* p, const orc_batch* b, const orc_tables* T, int 
   return solve_step(&I, N, th, l, iters, resid, NULL);
 }
 
+/* One Gauss-Newton step at the state (theta, l) without moving it: the step
+ * dx[0..N] (dx[N] for l; 0 when the bound on l is active), its predicted
+ * displacement residual, and the cost.  Returns 0 on success. */
+int orc_gn_step(const orc_params* p, const orc_batch* b, const orc_tables* T, int i, int N, const double* th,
+                double l, double* dx, double* resid, double* J, int* lfix_out) {
+  inst_t I;
+  inst_init(&I, p, b, T, i);
+  const int n = N + 1;
+  geo_t G;
+  geo_alloc(&G, N);
+  double* g = (double*)malloc(sizeof(double) * n);
+  double* H = (double*)malloc(sizeof(double) * n * n);
+  double* rhs = (double*)malloc(sizeof(double) * n);
+  *J = energy(&I, N, th, l, g, H, &G);
+  int lfix = (l <= 0.0 && g[N] > 0.0) || (l >= I.l_seg && g[N] < 0.0);
+  int m = lfix ? N : n;
+  for (int k = 0; k < m; ++k) rhs[k] = -g[k];
+  int rc = chol_solve(H, n, m, rhs, dx);
+  if (lfix) dx[N] = 0.0;
+  *resid = rc == 0 ? step_residual(&I, N, dx, &G) : NAN;
+  *lfix_out = lfix;
+  free(g); free(H); free(rhs);
+  geo_free(&G);
+  return rc;
+}
+
 /* Link start points p_0..p_N and headings psi_0..psi_{N-1}. */
 void orc_poses(const orc_params* p, const orc_batch* b, const orc_tables* T, int i, int N, const double* th,
                double l, double* px, double* py, double* psi) {

@@ -679,6 +679,37 @@ vine_status vine_get_tables(const vine_batch* B, int32_t* n_tab, float* hdr, flo
   return VINE_OK;
 }
 
+vine_status vine_probe_state(const vine_batch* B, int32_t inst, int32_t n_links, const float* theta, float l_last,
+                             double* cost, float* grad, float* step, double* residual, int32_t* l_fixed) {
+  if (!B || !theta || !cost || !grad || !step || !residual) return fail(VINE_EINVAL, "vine_probe_state: null argument");
+  if (inst < 0 || inst >= B->n_inst || n_links < 1 || n_links > B->h_n_links[inst])
+    return fail(VINE_EINVAL, "vine_probe_state: instance or link count out of range");
+  const size_t n = (size_t)n_links;
+  char* d = nullptr;
+  const size_t bytes = 256 + 4 * n + 4 * (n + 1) * 2 + 64;
+  CK(cudaMalloc(&d, bytes));
+  float* d_th = (float*)(d + 64);
+  float* d_g = d_th + n;
+  float* d_dx = d_g + n + 1;
+  double* d_J = (double*)d;
+  double* d_r = d_J + 1;
+  int* d_lf = (int*)(d_J + 2);
+  cudaError_t e = cudaMemcpy(d_th, theta, 4 * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_probe(B->args, B->ks, inst, n_links, d_th, l_last, d_J, d_g, d_dx, d_r, d_lf,
+                                         B->smem_warp, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  int lf = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(cost, d_J, 8, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(residual, d_r, 8, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&lf, d_lf, 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(grad, d_g, 4 * (n + 1), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(step, d_dx, 4 * (n + 1), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(e, "vine_probe_state");
+  if (l_fixed) *l_fixed = lf;
+  return VINE_OK;
+}
+
 vine_status vine_batch_info(const vine_batch* B, int32_t* n_inst, int64_t* total_links) {
   if (!B) return fail(VINE_EINVAL, "vine_batch_info: null batch");
   if (n_inst) *n_inst = B->n_inst;

@@ -581,6 +581,36 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) grow_kernel(const GrowArgs 
   }
 }
 
+// Cost, gradient and one Gauss-Newton step at a caller-given state of one
+// robot (introspection for tests; one warp).
+template <int KS>
+__global__ void __launch_bounds__(32) probe_kernel(const GrowArgs A, int inst, int N, const float* theta, float l,
+                                                   double* outJ, float* out_g, float* out_dx, double* out_r,
+                                                   int* out_lfix) {
+  extern __shared__ float4 smem4[];
+  const int lane = threadIdx.x & 31;
+  const Smem S = carve(reinterpret_cast<float*>(smem4), A);
+  const InstDev I = A.inst[inst];
+  for (int k = lane; k < I.n_obs; k += 32) S.obs[k] = A.obs[I.obs_off + k];
+  for (int k = lane; k < I.n_act; k += 32) S.act[k] = A.act[I.act_off + k];
+  for (int k = lane; k < N; k += 32) S.TH[k] = theta[k];
+  __syncwarp();
+  const EvalOut E = eval<KS>(A, I, S, N, l, lane);
+  for (int k = lane; k < N; k += 32) out_g[k] = S.G[k];
+  __syncwarp();
+  const bool lfix = (l <= 0.f && E.gl > 0.f) || (l >= I.l_seg && E.gl < 0.f);
+  float dl;
+  const double r = gn_solve(I, S, N, lfix, E, dl, lane);
+  for (int k = lane; k < N; k += 32) out_dx[k] = S.DTH[k];
+  if (lane == 0) {
+    out_g[N] = E.gl;
+    out_dx[N] = dl;
+    *outJ = E.J;
+    *out_r = r;
+    *out_lfix = lfix ? 1 : 0;
+  }
+}
+
 template <int KS>
 const void* kernel_ptr() {
   return reinterpret_cast<const void*>(&grow_kernel<KS>);
@@ -618,6 +648,17 @@ cudaError_t launch_grow(const GrowArgs& a, int ks, int grid, int block, size_t s
     case 2: grow_kernel<2><<<grid, block, smem, s>>>(a); break;
     case 3: grow_kernel<3><<<grid, block, smem, s>>>(a); break;
     default: grow_kernel<4><<<grid, block, smem, s>>>(a); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_probe(const GrowArgs& a, int ks, int inst, int N, const float* theta, float l, double* J,
+                         float* g, float* dx, double* r, int* lfix, size_t smem, cudaStream_t s) {
+  switch (ks) {
+    case 1: probe_kernel<1><<<1, 32, smem, s>>>(a, inst, N, theta, l, J, g, dx, r, lfix); break;
+    case 2: probe_kernel<2><<<1, 32, smem, s>>>(a, inst, N, theta, l, J, g, dx, r, lfix); break;
+    case 3: probe_kernel<3><<<1, 32, smem, s>>>(a, inst, N, theta, l, J, g, dx, r, lfix); break;
+    default: probe_kernel<4><<<1, 32, smem, s>>>(a, inst, N, theta, l, J, g, dx, r, lfix); break;
   }
   return cudaGetLastError();
 }

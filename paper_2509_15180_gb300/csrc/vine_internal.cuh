@@ -89,6 +89,8 @@ cudaError_t launch_grow(const GrowArgs& a, int ks, int grid, int block, size_t s
 size_t grow_smem_per_warp(int nmax, int omax, int amax);
 cudaError_t grow_configure(int ks, size_t smem_per_cta);
 int grow_max_ctas_per_sm(int ks, size_t smem_per_cta);
+cudaError_t launch_probe(const GrowArgs& a, int ks, int inst, int N, const float* theta, float l, double* J,
+                         float* g, float* dx, double* r, int* lfix, size_t smem, cudaStream_t s);
 cudaError_t launch_poses(const InstDev* inst, int n_inst, const float* theta, const int* n_cur, const float* l_cur,
                          float* out_theta, float* out_pose, float* out_tip, cudaStream_t s);
 cudaError_t launch_contacts(const InstDev* inst, int n_inst, const float4* obs, const float* theta, const int* n_cur,

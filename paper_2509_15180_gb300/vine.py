@@ -63,6 +63,7 @@ _SIG = {
     "vine_get_stats": [_p, _p, _p],
     "vine_batch_info": [_p, _p, _p],
     "vine_get_tables": [_p, _p, _p, _p, _p, _p],
+    "vine_probe_state": [_p, _i32, _i32, _p, C.c_float, _p, _p, _p, _p, _p],
     "vine_batch_destroy": [_p],
 }
 for _name, _args in _SIG.items():
@@ -223,6 +224,17 @@ class Batch:
         _check(_lib.vine_get_tables(self.h, C.byref(nt), _ptr(hdr), _ptr(kn), _ptr(ut), _ptr(cs)),
                "vine_get_tables")
         return dict(n_tab=n, hdr=hdr[:n], knots=kn[:n], utab=ut, consts=cs)
+
+    def probe(self, i: int, theta, l: float):
+        """(cost, grad[N+1], step[N+1], residual, l_fixed) at a given state (vine_probe_state)."""
+        th = np.ascontiguousarray(theta, dtype=np.float32)
+        N = th.size
+        J, r, lf = C.c_double(), C.c_double(), C.c_int32()
+        g = np.zeros(N + 1, np.float32)
+        dx = np.zeros(N + 1, np.float32)
+        _check(_lib.vine_probe_state(self.h, int(i), N, _ptr(th), float(l), C.byref(J), _ptr(g), _ptr(dx),
+                                     C.byref(r), C.byref(lf)), "vine_probe_state")
+        return J.value, g, dx, r.value, bool(lf.value)
 
     def theta_of(self, st: dict, i: int):
         return st["theta"][self.offsets[i]: self.offsets[i] + st["N"][i]]

@@ -1,0 +1,56 @@
+"""GPU parity of one evaluation: at fixed states taken from the oracle's own
+trajectories (rounded to float32), the CUDA cost, gradient, Gauss-Newton step
+and its residual against the FP64 oracle's."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2509_15180_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2509_15180_gb300 import vine  # noqa: E402
+
+
+def _states(sc, steps, every):
+    orc = oracle.Oracle(sc, oracle.default_params(tol=1e-10))
+    st = orc.new_state()
+    out = []
+    for s in range(steps):
+        orc.run(st, 1, threads=8)
+        if (s + 1) % every == 0:
+            for i in range(sc["n_links"].size):
+                out.append((i, orc.theta_of(st, i).astype(np.float32), np.float32(st["l"][i])))
+    return orc, out
+
+
+@pytest.mark.parametrize("cfg", [1, 2])
+def test_probe_matches_oracle(cfg):
+    sc = scenes.config1(16) if cfg == 1 else scenes.config2(8)
+    steps, every = (20, 5) if cfg == 1 else (60, 15)
+    orc, states = _states(sc, steps, every)
+    b = vine.Batch(sc)
+    worst = dict(J=0.0, g=0.0, dx=0.0, r=0.0)
+    for (i, th, l) in states:
+        th64 = th.astype(np.float64)
+        # perturb off the equilibrium so the gradient and step are not ~0
+        pert = th64 + 1e-3 * np.sin(np.arange(th.size) * 1.7 + i)
+        for thv, lv in ((th64, float(l)), (pert, float(l) * 0.7)):
+            th32 = thv.astype(np.float32)
+            Jg, gg, dg, rg, lfg = b.probe(i, th32, lv)
+            dxo, ro, Jo, lfo = orc.gn_step(i, th32.astype(np.float64), float(np.float32(lv)))
+            _, go, _ = orc.energy(i, th32.astype(np.float64), float(np.float32(lv)), hessian=False)
+            assert lfg == lfo
+            worst["J"] = max(worst["J"], abs(Jg - Jo) / max(abs(Jo), 1e-12))
+            worst["g"] = max(worst["g"], np.max(np.abs(gg - go)) / max(np.max(np.abs(go)), 1e-12))
+            worst["dx"] = max(worst["dx"], np.max(np.abs(dg - dxo)) / max(np.max(np.abs(dxo)), 1e-12))
+            worst["r"] = max(worst["r"], abs(rg - ro) / max(ro, 1e-30))
+    print("probe cfg %d worst relative errors: %s" % (cfg, worst))
+    assert worst["J"] < 1e-5
+    assert worst["g"] < 1e-3
+    assert worst["dx"] < 1e-2
+    assert worst["r"] < 1e-2
+    b.close()
