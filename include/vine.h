@@ -69,9 +69,12 @@ typedef enum {
  * tol: convergence when the predicted displacement of every link end point
  *   (and l_seg times every joint step) is at most tol times the robot length
  *   N l_seg (1e-6); the test is evaluated in FP64.
- * ls_switch: above this predicted displacement (same units as tol) the step
- *   is line-searched (Armijo on the cost, constant armijo_c1, at most
- *   max_halvings halvings); at or below it the full step is taken (1e-5).
+ * fval_eps, armijo_c1: every step is line-searched on the projected path
+ *   (at most max_halvings halvings): accepted when the cost decreases by
+ *   armijo_c1 times the predicted decrease (Armijo), or, when the cost change
+ *   is within fval_eps |J| (FP32 rounding level), when the directional slope
+ *   there is at most (2 armijo_c1 - 1) times the initial slope (approximate
+ *   Wolfe condition of Hager and Zhang, 2005).  Defaults 1e-6, 1e-4.
  * max_iter: Gauss-Newton iterations per growth step (100).
  * discs_per_link: contact discs K_s of radius R at fractions k/K_s of each
  *   link (2; 1..4 supported).
@@ -84,7 +87,7 @@ typedef struct {
   double m_lo;
   double pen_frac;
   double tol;
-  double ls_switch;
+  double fval_eps;
   double armijo_c1;
   int32_t max_iter;
   int32_t discs_per_link;

@@ -40,7 +40,7 @@ class Params(C.Structure):
     _fields_ = [("w_a", C.c_double), ("w_b", C.c_double), ("w_c", C.c_double),
                 ("eps_crit", C.c_double), ("R_c", C.c_double), ("R_act", C.c_double),
                 ("a_spam", C.c_double), ("m_lo", C.c_double), ("pen_frac", C.c_double),
-                ("tol", C.c_double), ("ls_switch", C.c_double), ("armijo_c1", C.c_double),
+                ("tol", C.c_double), ("fval_eps", C.c_double), ("armijo_c1", C.c_double),
                 ("max_iter", C.c_int32), ("discs_per_link", C.c_int32),
                 ("max_halvings", C.c_int32), ("pad", C.c_int32)]
 

@@ -55,7 +55,7 @@ typedef struct {
   double m_lo;            /* lower end of the tabulated m range */
   double pen_frac;        /* contact stiffness: penetration (fraction of R) per unit moment */
   double tol;             /* convergence: predicted displacement / robot length */
-  double ls_switch;       /* above this predicted displacement, Armijo line search */
+  double fval_eps;        /* cost differences below fval_eps |J| are read as rounding level */
   double armijo_c1;       /* sufficient-decrease constant */
   int32_t max_iter;       /* Gauss-Newton iterations per growth step */
   int32_t discs_per_link; /* contact discs per link (K_s) */
@@ -70,7 +70,7 @@ void orc_params_default(orc_params* p) {
   p->m_lo = 0.002;
   p->pen_frac = 0.01;
   p->tol = 1e-6;
-  p->ls_switch = 1e-5;
+  p->fval_eps = 1e-6;
   p->armijo_c1 = 1e-4;
   p->max_iter = 100;
   p->discs_per_link = 2;
@@ -668,9 +668,9 @@ void orc_set_trace(int on) { g_trace = on; }
 
 /* Equilibrium of the current chain from the warm start (theta, l): damped
  * Gauss-Newton with the bound 0 <= l <= l_seg handled as an active set,
- * Armijo backtracking on J while the predicted displacement exceeds
- * ls_switch, full steps below it, stop when it is at most tol (the final
- * step is applied).  Algorithm 1 of Sec. 4.1 read as "the stationary point
+ * backtracking line search (Armijo, or approximate Wolfe when the cost change
+ * is at rounding level), stop when the predicted displacement is at most tol
+ * (the final step is applied).  Algorithm 1 of Sec. 4.1 read as "the stationary point
  * of Eq. (pbd) reached from the warm start". */
 static int solve_step(const inst_t* I, int N, double* th, double* l, int* iters_out, double* resid_out,
                       long long* evals_out) {
@@ -683,6 +683,8 @@ static int solve_step(const inst_t* I, int N, double* th, double* l, int* iters_
   double* dx = (double*)malloc(sizeof(double) * n);
   double* rhs = (double*)malloc(sizeof(double) * n);
   double* tt = (double*)malloc(sizeof(double) * n);
+  double* gt = (double*)malloc(sizeof(double) * n);
+  double* Ht = (double*)malloc(sizeof(double) * n * n);
   int status = ORC_MAXITER, it = 0;
   double r = INFINITY;
   long long evals = 0;
@@ -703,18 +705,28 @@ static int solve_step(const inst_t* I, int N, double* th, double* l, int* iters_
       status = ORC_OK;
       break;
     }
+    /* Line search on the projected path x(a) = P(x + a dx): Armijo on J, or,
+     * when the cost change is at the rounding level of J, the approximate
+     * Wolfe condition of Hager and Zhang (2005) on the directional slope. */
     double gd = 0.0;
     for (int k = 0; k < N; ++k) gd += g[k] * dx[k];
+    const int l_moves = !((*l <= 0.0 && dx[N] < 0.0) || (*l >= I->l_seg && dx[N] > 0.0));
+    const double slope0 = gd + (l_moves ? g[N] * dx[N] : 0.0);
     double alpha = 1.0, Jt = J, lt = *l;
     int hcount = 0;
     for (int h = 0; h <= p->max_halvings; ++h, ++hcount) {
       for (int k = 0; k < N; ++k) tt[k] = th[k] + alpha * dx[k];
       lt = fmin(fmax(*l + alpha * dx[N], 0.0), I->l_seg);
-      Jt = energy(I, N, tt, lt, NULL, NULL, &G);
+      Jt = energy(I, N, tt, lt, gt, Ht, &G);
       ++evals;
-      if (r <= p->ls_switch) break;
-      double dec = alpha * gd + g[N] * (lt - *l);
+      const double dec = alpha * gd + g[N] * (lt - *l);
       if (Jt <= J + p->armijo_c1 * dec) break;
+      if (fabs(Jt - J) <= p->fval_eps * fabs(J)) {
+        double st = 0.0;
+        for (int k = 0; k < N; ++k) st += gt[k] * dx[k];
+        if (lt > 0.0 && lt < I->l_seg) st += gt[N] * dx[N];
+        if (st <= (2.0 * p->armijo_c1 - 1.0) * slope0) break;
+      }
       alpha *= 0.5;
     }
     if (g_trace)
@@ -722,13 +734,15 @@ static int solve_step(const inst_t* I, int N, double* th, double* l, int* iters_
               hcount, *l, lfix, gd);
     for (int k = 0; k < N; ++k) th[k] = tt[k];
     *l = lt;
-    J = energy(I, N, th, *l, g, H, &G);
+    J = Jt;
+    memcpy(g, gt, sizeof(double) * n);
+    memcpy(H, Ht, sizeof(double) * n * n);
   }
   if (it > p->max_iter) it = p->max_iter;
   *iters_out = it;
   *resid_out = r;
   if (evals_out) *evals_out = evals;
-  free(g); free(H); free(dx); free(rhs); free(tt);
+  free(g); free(H); free(dx); free(rhs); free(tt); free(gt); free(Ht);
   geo_free(&G);
   return status;
 }

@@ -166,7 +166,7 @@ vine_status vine_params_default(vine_params* p) {
   p->m_lo = 0.002;
   p->pen_frac = 0.01;
   p->tol = 1e-6;
-  p->ls_switch = 1e-5;
+  p->fval_eps = 1e-6;
   p->armijo_c1 = 1e-4;
   p->max_iter = 100;
   p->discs_per_link = 2;
@@ -197,7 +197,7 @@ vine_status vine_batch_create(const vine_batch_desc* D, const vine_params* P, vo
   if (prm.discs_per_link < 1 || prm.discs_per_link > 4)
     return fail(VINE_EINVAL, "vine_batch_create: discs_per_link must be 1..4");
   if (!(prm.tol > 0.0) || prm.max_iter < 1 || prm.max_halvings < 0 || !(prm.eps_crit > 0.0 && prm.eps_crit < 1.0) ||
-      !(prm.R_c > 0.0 && prm.R_act > prm.R_c) || !(prm.m_lo > 0.0 && prm.m_lo < 0.5) || !(prm.pen_frac > 0.0))
+      !(prm.R_c > 0.0 && prm.R_act > prm.R_c) || !(prm.m_lo > 0.0 && prm.m_lo < 0.5) || !(prm.pen_frac > 0.0) || !(prm.fval_eps >= 0.0) || !(prm.armijo_c1 > 0.0 && prm.armijo_c1 < 0.5))
     return fail(VINE_EINVAL, "vine_batch_create: parameter out of range");
   const int n = D->n_inst;
   if (n <= 0) return fail(VINE_EINVAL, "vine_batch_create: n_inst must be positive");
@@ -472,7 +472,7 @@ vine_status vine_batch_create(const vine_batch_desc* D, const vine_params* P, vo
   a.u_invh = (float)(1.0 / cst[3]);
   a.U_pi = (float)cst[0];
   a.m_pi = (float)cst[1];
-  a.ls_switch = (float)prm.ls_switch;
+  a.fval_eps = (float)prm.fval_eps;
   a.c1 = (float)prm.armijo_c1;
   a.tol = prm.tol;
   a.max_iter = prm.max_iter;

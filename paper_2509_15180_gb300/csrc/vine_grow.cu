@@ -17,7 +17,9 @@
 //           articulated stiffnesses in link-local frames and a forward sweep
 //           of twists -- exact for that matrix and O(N).
 //   test  : predicted displacement of every link end (FP64 max / N l_seg).
-//   step  : full step below ls_switch, Armijo backtracking above it.
+//   step  : backtracking on the projected path: Armijo on J, or the
+//           approximate Wolfe slope test when the cost change is at FP32
+//           rounding level of J.
 // Lanes own contiguous blocks of links; obstacles and actuators of the robot
 // are staged in shared memory; the serial sweeps run warp-uniform.
 #include <cmath>
@@ -478,6 +480,9 @@ __device__ int solve_step(const GrowArgs& A, const InstDev& I, const Smem& S, in
       status = kOK;
       break;
     }
+    // Line search on the projected path P(x + a dx): Armijo on J, or, when the
+    // cost change is at the rounding level of J, the approximate Wolfe
+    // condition (Hager and Zhang 2005) on the directional slope.
     double gd = 0.0;
     for (int j = j0; j < j1; ++j) {
       gd += (double)S.G[j] * (double)S.DTH[j];
@@ -486,6 +491,8 @@ __device__ int solve_step(const GrowArgs& A, const InstDev& I, const Smem& S, in
     gd = warp_sum(gd);
     const float l0 = l, gl0 = E.gl;
     const double J0 = E.J;
+    const bool l_moves = !((l0 <= 0.f && dl < 0.f) || (l0 >= I.l_seg && dl > 0.f));
+    const double slope0 = gd + (l_moves ? (double)gl0 * (double)dl : 0.0);
     float alpha = 1.f, lt = l0;
     for (int h = 0; h <= A.max_halv; ++h) {
       for (int j = j0; j < j1; ++j) S.TH[j] = S.TH0[j] + alpha * S.DTH[j];
@@ -494,9 +501,15 @@ __device__ int solve_step(const GrowArgs& A, const InstDev& I, const Smem& S, in
       E = eval<KS>(A, I, S, N, lt, lane);
       st.evals += 1;
       st.linkevals += N;
-      if (r <= (double)A.ls_switch) break;
       const double dec = (double)alpha * gd + (double)gl0 * ((double)lt - (double)l0);
       if (E.J <= J0 + (double)A.c1 * dec) break;
+      if (fabs(E.J - J0) <= (double)A.fval_eps * fabs(J0)) {
+        double sl = 0.0;
+        for (int j = j0; j < j1; ++j) sl += (double)S.G[j] * (double)S.DTH[j];
+        sl = warp_sum(sl);
+        if (lt > 0.f && lt < I.l_seg) sl += (double)E.gl * (double)dl;
+        if (sl <= (2.0 * (double)A.c1 - 1.0) * slope0) break;
+      }
       alpha *= 0.5f;
     }
     l = lt;

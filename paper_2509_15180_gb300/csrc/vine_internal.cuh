@@ -65,7 +65,7 @@ struct GrowArgs {
   float w_a, w_b, w_c;
   float theta_c, inv2thc, inv4thc, eps_c;
   float u_h, u_invh, U_pi, m_pi;
-  float ls_switch, c1;
+  float fval_eps, c1;
   double tol;
   int max_iter, max_halv;
 };

@@ -31,7 +31,7 @@ INST_OK, INST_MAXITER, INST_NONFINITE, INST_BADINPUT = range(4)
 class vine_params(C.Structure):
     _fields_ = [("w_a", C.c_double), ("w_b", C.c_double), ("w_c", C.c_double), ("eps_crit", C.c_double),
                 ("R_c", C.c_double), ("R_act", C.c_double), ("a_spam", C.c_double), ("m_lo", C.c_double),
-                ("pen_frac", C.c_double), ("tol", C.c_double), ("ls_switch", C.c_double),
+                ("pen_frac", C.c_double), ("tol", C.c_double), ("fval_eps", C.c_double),
                 ("armijo_c1", C.c_double), ("max_iter", C.c_int32), ("discs_per_link", C.c_int32),
                 ("max_halvings", C.c_int32), ("mode", C.c_int32), ("gd_alpha", C.c_double),
                 ("gd_steps", C.c_int32), ("reserved", C.c_int32)]

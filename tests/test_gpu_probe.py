@@ -49,7 +49,9 @@ def test_probe_matches_oracle(cfg):
             worst["dx"] = max(worst["dx"], np.max(np.abs(dg - dxo)) / max(np.max(np.abs(dxo)), 1e-12))
             worst["r"] = max(worst["r"], abs(rg - ro) / max(ro, 1e-30))
     print("probe cfg %d worst relative errors: %s" % (cfg, worst))
-    assert worst["J"] < 1e-5
+    # the contact energy w_c k_c pen^2 carries the FP32 penetration error
+    # (~1e-8 m against pen ~1e-4 m), so the cost agrees to ~1e-4 relative
+    assert worst["J"] < 1e-3
     assert worst["g"] < 1e-3
     assert worst["dx"] < 1e-2
     assert worst["r"] < 1e-2
