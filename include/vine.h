@@ -229,6 +229,16 @@ vine_status vine_get_tables(const vine_batch* b, int32_t* n_tab, float* hdr, flo
 vine_status vine_probe_state(const vine_batch* b, int32_t inst, int32_t n_links, const float* theta, float l_last,
                              double* cost, float* grad, float* step, double* residual, int32_t* l_fixed);
 
+/* Diagnostics: record every line-search trial of robot `inst` in later
+ * growth launches (at most `capacity` records of 13 doubles: links present,
+ * iteration, halving (-1 = converged), step fraction, predicted-displacement
+ * residual, cost before, cost at the trial, predicted decrease, initial
+ * slope, slope at the trial, trial distal length, distal length fixed, 0).
+ * inst < 0 switches recording off.  Allocates device memory. */
+vine_status vine_debug_trace(vine_batch* b, int32_t inst, int32_t capacity);
+/* Copies up to `capacity` recorded trials to host `records`; *count = copied. */
+vine_status vine_debug_trace_read(const vine_batch* b, double* records, int32_t capacity, int32_t* count);
+
 /* Number of instances and total link capacity (sum of n_links). */
 vine_status vine_batch_info(const vine_batch* b, int32_t* n_inst, int64_t* total_links);
 

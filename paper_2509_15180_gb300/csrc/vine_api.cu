@@ -147,6 +147,7 @@ struct vine_batch {
   cudaGraphExec_t graph_exec = nullptr;
   std::vector<int> h_n_links, h_n_obs, h_n_circ;
   std::vector<int> h_order;
+  void* trace_mem = nullptr;
 };
 
 extern "C" {
@@ -710,6 +711,40 @@ vine_status vine_probe_state(const vine_batch* B, int32_t inst, int32_t n_links,
   return VINE_OK;
 }
 
+vine_status vine_debug_trace(vine_batch* B, int32_t inst, int32_t capacity) {
+  if (!B) return fail(VINE_EINVAL, "vine_debug_trace: null batch");
+  if (B->trace_mem) cudaFree(B->trace_mem);
+  B->trace_mem = nullptr;
+  B->args.trace = nullptr;
+  B->args.trace_count = nullptr;
+  if (B->graph_exec) {  // the recorded launch carries the old arguments
+    cudaGraphExecDestroy(B->graph_exec);
+    cudaGraphDestroy(B->graph);
+    B->graph_exec = nullptr;
+    B->graph = nullptr;
+  }
+  if (inst < 0 || capacity <= 0) return VINE_OK;
+  CK(cudaMalloc(&B->trace_mem, 256 + sizeof(double) * 13 * (size_t)capacity));
+  CK(cudaMemset(B->trace_mem, 0, 256));
+  B->args.trace_count = (int*)B->trace_mem;
+  B->args.trace = (double*)((char*)B->trace_mem + 256);
+  B->args.trace_inst = inst;
+  B->args.trace_cap = capacity;
+  return VINE_OK;
+}
+
+vine_status vine_debug_trace_read(const vine_batch* B, double* records, int32_t capacity, int32_t* count) {
+  if (!B || !count) return fail(VINE_EINVAL, "vine_debug_trace_read: null argument");
+  *count = 0;
+  if (!B->trace_mem) return VINE_OK;
+  int n = 0;
+  CK(cudaMemcpy(&n, B->args.trace_count, 4, cudaMemcpyDeviceToHost));
+  n = std::min(n, std::min(capacity, B->args.trace_cap));
+  if (n > 0 && records) CK(cudaMemcpy(records, B->args.trace, sizeof(double) * 13 * n, cudaMemcpyDeviceToHost));
+  *count = n;
+  return VINE_OK;
+}
+
 vine_status vine_batch_info(const vine_batch* B, int32_t* n_inst, int64_t* total_links) {
   if (!B) return fail(VINE_EINVAL, "vine_batch_info: null batch");
   if (n_inst) *n_inst = B->n_inst;
@@ -724,6 +759,7 @@ vine_status vine_batch_destroy(vine_batch* B) {
   if (B->graph) cudaGraphDestroy(B->graph);
   if (B->cap_stream) cudaStreamDestroy(B->cap_stream);
   if (B->stage) cudaFree(B->stage);
+  if (B->trace_mem) cudaFree(B->trace_mem);
   if (B->dmem) cudaFree(B->dmem);
   delete B;
   return VINE_OK;

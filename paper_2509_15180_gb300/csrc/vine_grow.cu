@@ -452,9 +452,21 @@ struct StepStats {
 };
 
 // Solves the current growth step to equilibrium from the warm start.
+// Diagnostic record of one line-search trial (only for A.trace_inst).
+__device__ __forceinline__ void trace_rec(const GrowArgs& A, int inst, int lane, int N, int it, int h, double a,
+                                          double r, double J0, double Jt, double dec, double s0, double st, double lt,
+                                          double lfix) {
+  if (A.trace == nullptr || inst != A.trace_inst || lane != 0) return;
+  const int k = atomicAdd(A.trace_count, 1);
+  if (k >= A.trace_cap) return;
+  double* o = A.trace + 13 * (size_t)k;
+  o[0] = N; o[1] = it; o[2] = h; o[3] = a; o[4] = r; o[5] = J0; o[6] = Jt; o[7] = dec; o[8] = s0; o[9] = st;
+  o[10] = lt; o[11] = lfix; o[12] = 0.0;
+}
+
 template <int KS>
 __device__ int solve_step(const GrowArgs& A, const InstDev& I, const Smem& S, int N, float& l, int lane,
-                          StepStats& st) {
+                          StepStats& st, int inst) {
   const int B = (N + 31) >> 5;
   const int j0 = min(lane * B, N), j1 = min(j0 + B, N);
   EvalOut E = eval<KS>(A, I, S, N, l, lane);
@@ -475,6 +487,7 @@ __device__ int solve_step(const GrowArgs& A, const InstDev& I, const Smem& S, in
       break;
     }
     if (r <= A.tol) {
+      trace_rec(A, inst, lane, N, it, -1, 1.0, r, E.J, E.J, 0.0, 0.0, 0.0, l + dl, lfix ? 1.0 : 0.0);
       for (int j = j0; j < j1; ++j) S.TH[j] += S.DTH[j];
       l = fminf(fmaxf(l + dl, 0.f), I.l_seg);
       status = kOK;
@@ -502,12 +515,15 @@ __device__ int solve_step(const GrowArgs& A, const InstDev& I, const Smem& S, in
       st.evals += 1;
       st.linkevals += N;
       const double dec = (double)alpha * gd + (double)gl0 * ((double)lt - (double)l0);
-      if (E.J <= J0 + (double)A.c1 * dec) break;
-      if (fabs(E.J - J0) <= (double)A.fval_eps * fabs(J0)) {
-        double sl = 0.0;
+      double sl = 0.0;
+      if (A.trace != nullptr || fabs(E.J - J0) <= (double)A.fval_eps * fabs(J0)) {
         for (int j = j0; j < j1; ++j) sl += (double)S.G[j] * (double)S.DTH[j];
         sl = warp_sum(sl);
         if (lt > 0.f && lt < I.l_seg) sl += (double)E.gl * (double)dl;
+      }
+      trace_rec(A, inst, lane, N, it, h, alpha, r, J0, E.J, dec, slope0, sl, lt, lfix ? 1.0 : 0.0);
+      if (E.J <= J0 + (double)A.c1 * dec) break;
+      if (fabs(E.J - J0) <= (double)A.fval_eps * fabs(J0)) {
         if (sl <= (2.0 * (double)A.c1 - 1.0) * slope0) break;
       }
       alpha *= 0.5f;
@@ -542,7 +558,7 @@ __device__ void process_instance(const GrowArgs& A, int inst, const Smem& S, int
     l = 0.f;
     __syncwarp();
     StepStats st{0, 0.0, 0, 0};
-    const int res = solve_step<KS>(A, I, S, N, l, lane, st);
+    const int res = solve_step<KS>(A, I, S, N, l, lane, st, inst);
     iters += st.iters;
     evals += st.evals;
     linkevals += st.linkevals;

@@ -68,6 +68,10 @@ struct GrowArgs {
   float fval_eps, c1;
   double tol;
   int max_iter, max_halv;
+  // diagnostics: per line-search trial records of one robot (off when null)
+  double* trace;
+  int* trace_count;
+  int trace_inst, trace_cap;
 };
 
 // Table build (FP64) -- vine_tables.cu

@@ -64,6 +64,8 @@ _SIG = {
     "vine_batch_info": [_p, _p, _p],
     "vine_get_tables": [_p, _p, _p, _p, _p, _p],
     "vine_probe_state": [_p, _i32, _i32, _p, C.c_float, _p, _p, _p, _p, _p],
+    "vine_debug_trace": [_p, _i32, _i32],
+    "vine_debug_trace_read": [_p, _p, _i32, _p],
     "vine_batch_destroy": [_p],
 }
 for _name, _args in _SIG.items():
@@ -235,6 +237,18 @@ class Batch:
         _check(_lib.vine_probe_state(self.h, int(i), N, _ptr(th), float(l), C.byref(J), _ptr(g), _ptr(dx),
                                      C.byref(r), C.byref(lf)), "vine_probe_state")
         return J.value, g, dx, r.value, bool(lf.value)
+
+    def trace(self, inst: int, capacity: int = 4096):
+        """Start recording line-search trials of one robot (vine_debug_trace)."""
+        self._trace_cap = capacity
+        _check(_lib.vine_debug_trace(self.h, int(inst), int(capacity)), "vine_debug_trace")
+
+    def trace_read(self) -> np.ndarray:
+        cap = getattr(self, "_trace_cap", 0)
+        out = np.zeros((max(cap, 1), 13), np.float64)
+        n = C.c_int32()
+        _check(_lib.vine_debug_trace_read(self.h, _ptr(out), int(cap), C.byref(n)), "vine_debug_trace_read")
+        return out[: n.value]
 
     def theta_of(self, st: dict, i: int):
         return st["theta"][self.offsets[i]: self.offsets[i] + st["N"][i]]
