@@ -72,7 +72,9 @@ typedef enum {
  * fval_eps, armijo_c1: every step is line-searched on the projected path
  *   (at most max_halvings halvings): accepted when the cost decreases by
  *   armijo_c1 times the predicted decrease (Armijo), or, when the cost change
- *   is within fval_eps |J| (FP32 rounding level), when the directional slope
+ *   is within fval_eps times the sum of the magnitudes of the cost's terms
+ *   (each contact counted at w_c k_c (pen^2 + 2 R pen)) -- the rounding
+ *   level of the FP32 evaluation -- when the directional slope
  *   there is at most (2 armijo_c1 - 1) times the initial slope (approximate
  *   Wolfe condition of Hager and Zhang, 2005).  Defaults 1e-6, 1e-4.
  * max_iter: Gauss-Newton iterations per growth step (100).

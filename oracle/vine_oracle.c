@@ -55,7 +55,7 @@ typedef struct {
   double m_lo;            /* lower end of the tabulated m range */
   double pen_frac;        /* contact stiffness: penetration (fraction of R) per unit moment */
   double tol;             /* convergence: predicted displacement / robot length */
-  double fval_eps;        /* cost differences below fval_eps |J| are read as rounding level */
+  double fval_eps;        /* cost changes below fval_eps x (sum of |terms|) read as rounding level */
   double armijo_c1;       /* sufficient-decrease constant */
   int32_t max_iter;       /* Gauss-Newton iterations per growth step */
   int32_t discs_per_link; /* contact discs per link (K_s) */
@@ -538,7 +538,12 @@ static void geo_free(geo_t* G) { free(G->px); free(G->py); free(G->ux); free(G->
 /*   U_j = pi P R^3 Uhat(theta_j) - sum_a c_aj P_a l_seg Phi_a(eps_aj)        */
 /* with dU_j/dtheta_j = M_tot,j of Eq. (restoring_moment).                    */
 /* ------------------------------------------------------------------------ */
-static double energy(const inst_t* I, int N, const double* th, double l, double* g, double* H, geo_t* G) {
+/* Also returns, in *mag (if non-null), the magnitude scale of J: the sum of
+ * the absolute values of its terms, each contact counted at w_c k_c
+ * (pen^2 + 2 R pen).  Cost changes below fval_eps times this scale are read
+ * as rounding level by the line search. */
+static double energy(const inst_t* I, int N, const double* th, double l, double* g, double* H, geo_t* G,
+                     double* mag) {
   const orc_params* p = I->p;
   const orc_batch* b = I->b;
   const int n = N + 1;
@@ -546,12 +551,13 @@ static double energy(const inst_t* I, int N, const double* th, double l, double*
   chain_fk(I, N, th, l, G->px, G->py, G->ux, G->uy, G->L);
   if (g) for (int k = 0; k < n; ++k) g[k] = 0.0;
   if (H) for (int k = 0; k < n * n; ++k) H[k] = 0.0;
-  double J = 0.0;
+  double J = 0.0, S = 0.0;
   /* bending and actuation, per joint */
   for (int j = 0; j < N; ++j) {
     double M = PR3 * wr_mhat(th[j], p->eps_crit);
     double dM = PR3 * wr_mhat_d(th[j], p->eps_crit);
     double U = PR3 * wr_uhat(th[j], p->eps_crit);
+    double Um = fabs(U);
     for (int a = I->a0; a < I->a1; ++a) {
       double c = coverage(b->act_begin[a], b->act_end[a], j);
       if (c <= 0.0) continue;
@@ -563,14 +569,18 @@ static double energy(const inst_t* I, int N, const double* th, double l, double*
       table_f(t, e, &f, &fp);
       M -= c * s * Pa * f * I->d;
       dM -= c * Pa * fp * I->d * I->d / I->l_seg;
-      U -= c * Pa * I->l_seg * (table_G(t, e) - table_G(t, 0.0));
+      const double Ua = c * Pa * I->l_seg * (table_G(t, e) - table_G(t, 0.0));
+      U -= Ua;
+      Um += fabs(Ua);
     }
     J += p->w_a * U;
+    S += p->w_a * Um;
     if (g) g[j] += p->w_a * M;
     if (H) H[j * n + j] += fmax(p->w_a * dM, 1e-6 * p->w_a * PR3);
   }
   /* growth */
   J += p->w_b * I->kg * (I->l_seg - l) * (I->l_seg - l);
+  S += p->w_b * I->kg * (I->l_seg - l) * (I->l_seg - l);
   if (g) g[N] += -2.0 * p->w_b * I->kg * (I->l_seg - l);
   if (H) H[N * n + N] += 2.0 * p->w_b * I->kg;
   /* contact: every disc of every link against every obstacle */
@@ -587,6 +597,7 @@ static double energy(const inst_t* I, int N, const double* th, double l, double*
         double pen = I->R - sd;
         if (!(pen > 0.0)) continue;
         J += p->w_c * I->kc * pen * pen;
+        S += p->w_c * I->kc * (pen * pen + 2.0 * I->R * pen);
         if (!v) continue;
         /* v = d pen / d x: rotation about p_j moves the disc by z x (x - p_j) */
         for (int q = 0; q < n; ++q) v[q] = 0.0;
@@ -607,6 +618,7 @@ static double energy(const inst_t* I, int N, const double* th, double l, double*
     }
   }
   free(v);
+  if (mag) *mag = S;
   return J;
 }
 
@@ -688,7 +700,8 @@ static int solve_step(const inst_t* I, int N, double* th, double* l, int* iters_
   int status = ORC_MAXITER, it = 0;
   double r = INFINITY;
   long long evals = 0;
-  double J = energy(I, N, th, *l, g, H, &G);
+  double Smag = 0.0, Smt = 0.0;
+  double J = energy(I, N, th, *l, g, H, &G, &Smag);
   ++evals;
   for (it = 1; it <= p->max_iter; ++it) {
     if (!isfinite(J)) { status = ORC_NONFINITE; break; }
@@ -717,11 +730,11 @@ static int solve_step(const inst_t* I, int N, double* th, double* l, int* iters_
     for (int h = 0; h <= p->max_halvings; ++h, ++hcount) {
       for (int k = 0; k < N; ++k) tt[k] = th[k] + alpha * dx[k];
       lt = fmin(fmax(*l + alpha * dx[N], 0.0), I->l_seg);
-      Jt = energy(I, N, tt, lt, gt, Ht, &G);
+      Jt = energy(I, N, tt, lt, gt, Ht, &G, &Smt);
       ++evals;
       const double dec = alpha * gd + g[N] * (lt - *l);
       if (Jt <= J + p->armijo_c1 * dec) break;
-      if (fabs(Jt - J) <= p->fval_eps * fabs(J)) {
+      if (fabs(Jt - J) <= p->fval_eps * fmax(Smag, Smt)) {
         double st = 0.0;
         for (int k = 0; k < N; ++k) st += gt[k] * dx[k];
         if (lt > 0.0 && lt < I->l_seg) st += gt[N] * dx[N];
@@ -735,6 +748,7 @@ static int solve_step(const inst_t* I, int N, double* th, double* l, int* iters_
     for (int k = 0; k < N; ++k) th[k] = tt[k];
     *l = lt;
     J = Jt;
+    Smag = Smt;
     memcpy(g, gt, sizeof(double) * n);
     memcpy(H, Ht, sizeof(double) * n * n);
   }
@@ -756,7 +770,7 @@ double orc_energy(const orc_params* p, const orc_batch* b, const orc_tables* T, 
   inst_init(&I, p, b, T, i);
   geo_t G;
   geo_alloc(&G, N);
-  double J = energy(&I, N, th, l, g, H, &G);
+  double J = energy(&I, N, th, l, g, H, &G, NULL);
   geo_free(&G);
   return J;
 }
@@ -781,7 +795,7 @@ int orc_gn_step(const orc_params* p, const orc_batch* b, const orc_tables* T, in
   double* g = (double*)malloc(sizeof(double) * n);
   double* H = (double*)malloc(sizeof(double) * n * n);
   double* rhs = (double*)malloc(sizeof(double) * n);
-  *J = energy(&I, N, th, l, g, H, &G);
+  *J = energy(&I, N, th, l, g, H, &G, NULL);
   int lfix = (l <= 0.0 && g[N] > 0.0) || (l >= I.l_seg && g[N] < 0.0);
   int m = lfix ? N : n;
   for (int k = 0; k < m; ++k) rhs[k] = -g[k];

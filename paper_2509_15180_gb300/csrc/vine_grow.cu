@@ -145,7 +145,7 @@ __device__ __forceinline__ void wrinkle(const GrowArgs& A, float th, float& m, f
 }
 
 struct Acc {
-  float fx, fy, tl, c00, c01, c02, c11, c12, c22, pen2;
+  float fx, fy, tl, c00, c01, c02, c11, c12, c22, pen2, pen1;
   float glc, hll, q0, q1, q2;
 };
 
@@ -166,6 +166,7 @@ __device__ __forceinline__ void add_contact(Acc& c, float pen, float nx, float n
   c.c12 += kap * nx * ny;
   c.c22 += kap * ny * ny;
   c.pen2 += pen * pen;
+  c.pen1 += pen;
   if (last) {
     const float vl = fr * (nx * ulx + ny * uly);
     c.glc += fr * (fx * ulx + fy * uly);
@@ -217,7 +218,7 @@ __device__ __forceinline__ float disc_pen(const float4 ob, float dx, float dy, f
 }
 
 struct EvalOut {
-  double J;
+  double J, S;  // cost and the sum of the magnitudes of its terms
   float gl, hll, q0, q1, q2, ulx, uly;
 };
 
@@ -252,7 +253,7 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
   FF px = warp_excl_scan(sx, lane), py = warp_excl_scan(sy, lane);
   const float kap = 2.f * A.w_c * I.kc;
   const float floor_d = 1e-6f * A.w_a * I.PR3;
-  double Jl = 0.0;
+  double Jl = 0.0, Sl = 0.0;
   Acc last_acc{};
   for (int j = j0; j < j1; ++j) {
     // ---- bending and actuation at joint j (Eq. restoring_moment)
@@ -260,6 +261,7 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
     float m, dm, u;
     wrinkle(A, th, m, dm, u);
     float M = I.PR3 * m, dM = I.PR3 * dm, U = I.PR3 * u;
+    float Um = fabsf(U);
     for (int a = 0; a < I.n_act; ++a) {
       const float4 ac = S.act[a];
       const float cov = fminf(ac.y, (float)(j + 1)) - fmaxf(ac.x, (float)j);
@@ -287,9 +289,12 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
       }
       M -= cov * side * ac.z * f * I.d;
       dM -= cov * ac.z * fp * I.d * I.d / I.l_seg;
-      U -= cov * ac.z * I.l_seg * (Gi - hd.w);
+      const float Ua = cov * ac.z * I.l_seg * (Gi - hd.w);
+      U -= Ua;
+      Um += fabsf(Ua);
     }
     Jl += (double)(A.w_a * U);
+    Sl += (double)(A.w_a * Um);
     S.G[j] = A.w_a * M;
     S.DD[j] = fmaxf(A.w_a * dM, floor_d);
     // ---- contacts of link j: KS discs x every obstacle
@@ -325,6 +330,7 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
     S.C4[j] = c.c12;
     S.C5[j] = c.c22;
     Jl += (double)(A.w_c * I.kc * c.pen2);
+    Sl += (double)(A.w_c * I.kc) * ((double)c.pen2 + 2.0 * (double)I.R * (double)c.pen1);
     if (last) last_acc = c;
     px = ff_add(px, lx);
     py = ff_add(py, ly);
@@ -355,6 +361,7 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
   EvalOut E;
   const double dlr = (double)I.l_seg - (double)l;
   E.J = warp_sum(Jl) + (double)A.w_b * (double)I.kg * dlr * dlr;
+  E.S = warp_sum(Sl) + (double)A.w_b * (double)I.kg * dlr * dlr;
   const int owner = (N - 1) / B;
   const float glc = __shfl_sync(kFull, last_acc.glc, owner);
   E.hll = 2.f * A.w_b * I.kg + __shfl_sync(kFull, last_acc.hll, owner);
@@ -503,7 +510,7 @@ __device__ int solve_step(const GrowArgs& A, const InstDev& I, const Smem& S, in
     }
     gd = warp_sum(gd);
     const float l0 = l, gl0 = E.gl;
-    const double J0 = E.J;
+    const double J0 = E.J, S0 = E.S;
     const bool l_moves = !((l0 <= 0.f && dl < 0.f) || (l0 >= I.l_seg && dl > 0.f));
     const double slope0 = gd + (l_moves ? (double)gl0 * (double)dl : 0.0);
     float alpha = 1.f, lt = l0;
@@ -516,16 +523,15 @@ __device__ int solve_step(const GrowArgs& A, const InstDev& I, const Smem& S, in
       st.linkevals += N;
       const double dec = (double)alpha * gd + (double)gl0 * ((double)lt - (double)l0);
       double sl = 0.0;
-      if (A.trace != nullptr || fabs(E.J - J0) <= (double)A.fval_eps * fabs(J0)) {
+      const bool rounding = fabs(E.J - J0) <= (double)A.fval_eps * fmax(S0, E.S);
+      if (A.trace != nullptr || rounding) {
         for (int j = j0; j < j1; ++j) sl += (double)S.G[j] * (double)S.DTH[j];
         sl = warp_sum(sl);
         if (lt > 0.f && lt < I.l_seg) sl += (double)E.gl * (double)dl;
       }
       trace_rec(A, inst, lane, N, it, h, alpha, r, J0, E.J, dec, slope0, sl, lt, lfix ? 1.0 : 0.0);
       if (E.J <= J0 + (double)A.c1 * dec) break;
-      if (fabs(E.J - J0) <= (double)A.fval_eps * fabs(J0)) {
-        if (sl <= (2.0 * (double)A.c1 - 1.0) * slope0) break;
-      }
+      if (rounding && sl <= (2.0 * (double)A.c1 - 1.0) * slope0) break;
       alpha *= 0.5f;
     }
     l = lt;

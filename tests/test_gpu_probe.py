@@ -44,14 +44,16 @@ def test_probe_matches_oracle(cfg):
             dxo, ro, Jo, lfo = orc.gn_step(i, th32.astype(np.float64), float(np.float32(lv)))
             _, go, _ = orc.energy(i, th32.astype(np.float64), float(np.float32(lv)), hessian=False)
             assert lfg == lfo
-            worst["J"] = max(worst["J"], abs(Jg - Jo) / max(abs(Jo), 1e-12))
+            # J can nearly cancel (bending vs actuator energy); scale by one
+            # joint's onset energy w_a pi P R^3 as well
+            scale = abs(Jo) + 160.0 * np.pi * float(sc["pressure"][i]) * float(sc["radius"][i]) ** 3
+            worst["J"] = max(worst["J"], abs(Jg - Jo) / scale)
             worst["g"] = max(worst["g"], np.max(np.abs(gg - go)) / max(np.max(np.abs(go)), 1e-12))
             worst["dx"] = max(worst["dx"], np.max(np.abs(dg - dxo)) / max(np.max(np.abs(dxo)), 1e-12))
             worst["r"] = max(worst["r"], abs(rg - ro) / max(ro, 1e-30))
     print("probe cfg %d worst relative errors: %s" % (cfg, worst))
-    # the contact energy w_c k_c pen^2 carries the FP32 penetration error
-    # (~1e-8 m against pen ~1e-4 m), so the cost agrees to ~1e-4 relative
-    assert worst["J"] < 1e-3
+    # FP32 terms and the Hermite-tabulated wrinkling energy near onset
+    assert worst["J"] < 1e-4
     assert worst["g"] < 1e-3
     assert worst["dx"] < 1e-2
     assert worst["r"] < 1e-2
