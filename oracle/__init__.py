@@ -42,7 +42,7 @@ class Params(C.Structure):
                 ("a_spam", C.c_double), ("m_lo", C.c_double), ("pen_frac", C.c_double),
                 ("tol", C.c_double), ("fval_eps", C.c_double), ("armijo_c1", C.c_double),
                 ("max_iter", C.c_int32), ("discs_per_link", C.c_int32),
-                ("max_halvings", C.c_int32), ("pad", C.c_int32)]
+                ("max_halvings", C.c_int32), ("exact_hessian", C.c_int32)]
 
 
 class _Batch(C.Structure):
@@ -81,6 +81,8 @@ def lib():
         L.orc_tables_get.argtypes = [p, i, p, p, p, p]
         L.orc_energy.restype = d
         L.orc_energy.argtypes = [p, p, p, i, i, p, d, p, p]
+        L.orc_energy_exact.restype = d
+        L.orc_energy_exact.argtypes = [p, p, p, i, i, p, d, p, p]
         L.orc_solve.restype = i
         L.orc_solve.argtypes = [p, p, p, i, i, p, p, p, p]
         L.orc_poses.argtypes = [p, p, p, i, i, p, d, p, p, p]
@@ -214,6 +216,16 @@ class Oracle:
                              _ptr(H) if hessian else None)
         return J, g, (H.reshape(N + 1, N + 1) if hessian else None)
 
+    def hessian_exact(self, i: int, theta, l: float):
+        """Exact Hessian of J (contact curvature and load terms included)."""
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        N = th.size
+        g = np.zeros(N + 1)
+        H = np.zeros((N + 1) * (N + 1))
+        lib().orc_energy_exact(C.byref(self.P), C.byref(self.B), self.T, int(i), N, _ptr(th), float(l), _ptr(g),
+                               _ptr(H))
+        return H.reshape(N + 1, N + 1)
+
     def solve(self, i: int, theta, l: float):
         th = np.array(theta, dtype=np.float64)
         lv = C.c_double(float(l))
@@ -223,7 +235,8 @@ class Oracle:
         return th, lv.value, it.value, r.value, st
 
     def gn_step(self, i: int, theta, l: float):
-        """(dx[N+1], residual, J, lfix): one Gauss-Newton step at a fixed state."""
+        """(dx[N+1], residual, J, lfix): the solver's Newton step at a fixed state
+        (exact Hessian when positive definite, else Gauss-Newton)."""
         th = np.ascontiguousarray(theta, dtype=np.float64)
         N = th.size
         dx = np.zeros(N + 1)

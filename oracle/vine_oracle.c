@@ -57,10 +57,10 @@ typedef struct {
   double tol;             /* convergence: predicted displacement / robot length */
   double fval_eps;        /* cost changes below fval_eps x (sum of |terms|) read as rounding level */
   double armijo_c1;       /* sufficient-decrease constant */
-  int32_t max_iter;       /* Gauss-Newton iterations per growth step */
+  int32_t max_iter;       /* Newton iterations per growth step */
   int32_t discs_per_link; /* contact discs per link (K_s) */
   int32_t max_halvings;   /* line-search halvings */
-  int32_t pad;
+  int32_t exact_hessian;  /* 1: exact Hessian of J when positive definite, else Gauss-Newton; 0: Gauss-Newton */
 } orc_params;
 
 void orc_params_default(orc_params* p) {
@@ -75,7 +75,7 @@ void orc_params_default(orc_params* p) {
   p->max_iter = 100;
   p->discs_per_link = 2;
   p->max_halvings = 30;
-  p->pad = 0;
+  p->exact_hessian = 1;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -489,12 +489,13 @@ static void chain_fk(const inst_t* I, int N, const double* th, double l, double*
  * Circle: |x - c| - r.  Box: distance to an axis-aligned rectangle with
  * half-sizes (a, b), negative inside (nearest face; ties go to the x face).
  * A point exactly at a circle's centre takes the normal (tx, ty). */
-static double obs_sdf(const orc_batch* b, int o, double x, double y, double tx, double ty, double* nx,
-                      double* ny) {
+static double obs_sdf_k(const orc_batch* b, int o, double x, double y, double tx, double ty, double* nx,
+                        double* ny, double* kappa) {
   double dx = x - b->obs_cx[o], dy = y - b->obs_cy[o];
+  *kappa = 0.0;
   if (b->obs_kind[o] == 0) {
     double dist = sqrt(dx * dx + dy * dy);
-    if (dist > 0.0) { *nx = dx / dist; *ny = dy / dist; }
+    if (dist > 0.0) { *nx = dx / dist; *ny = dy / dist; *kappa = 1.0 / dist; }
     else { *nx = tx; *ny = ty; }
     return dist - b->obs_a[o];
   }
@@ -503,12 +504,22 @@ static double obs_sdf(const orc_batch* b, int o, double x, double y, double tx, 
   if (qx > 0.0 && qy > 0.0) {
     double dist = sqrt(qx * qx + qy * qy);
     *nx = sx * qx / dist; *ny = sy * qy / dist;
+    *kappa = 1.0 / dist;
     return dist;
   }
   if (qx > 0.0) { *nx = sx; *ny = 0.0; return qx; }
   if (qy > 0.0) { *nx = 0.0; *ny = sy; return qy; }
   if (qx >= qy) { *nx = sx; *ny = 0.0; return qx; }
   *nx = 0.0; *ny = sy; return qy;
+}
+
+/* Signed distance, outward normal n, and kappa: the Hessian of the signed
+ * distance is kappa (I - n n^T) (1/distance to the centre or corner; 0 on a
+ * box face and inside a box). */
+static double obs_sdf(const orc_batch* b, int o, double x, double y, double tx, double ty, double* nx,
+                      double* ny) {
+  double k;
+  return obs_sdf_k(b, o, x, y, tx, ty, nx, ny, &k);
 }
 
 /* Coverage of joint/link j by actuator span [b, e) (link units). */
@@ -542,8 +553,8 @@ static void geo_free(geo_t* G) { free(G->px); free(G->py); free(G->ux); free(G->
  * the absolute values of its terms, each contact counted at w_c k_c
  * (pen^2 + 2 R pen).  Cost changes below fval_eps times this scale are read
  * as rounding level by the line search. */
-static double energy(const inst_t* I, int N, const double* th, double l, double* g, double* H, geo_t* G,
-                     double* mag) {
+static double energy_h(const inst_t* I, int N, const double* th, double l, double* g, double* H, geo_t* G,
+                       double* mag, int exact) {
   const orc_params* p = I->p;
   const orc_batch* b = I->b;
   const int n = N + 1;
@@ -592,8 +603,8 @@ static double energy(const inst_t* I, int N, const double* th, double l, double*
       double x = G->px[i] + fr * G->L[i] * G->ux[i];
       double y = G->py[i] + fr * G->L[i] * G->uy[i];
       for (int o = I->o0; o < I->o1; ++o) {
-        double nx, ny;
-        double sd = obs_sdf(b, o, x, y, -G->uy[i], G->ux[i], &nx, &ny);
+        double nx, ny, kap_sd;
+        double sd = obs_sdf_k(b, o, x, y, -G->uy[i], G->ux[i], &nx, &ny, &kap_sd);
         double pen = I->R - sd;
         if (!(pen > 0.0)) continue;
         J += p->w_c * I->kc * pen * pen;
@@ -613,6 +624,39 @@ static double energy(const inst_t* I, int N, const double* th, double l, double*
             if (v[r] == 0.0) continue;
             for (int c2 = 0; c2 < n; ++c2) H[r * n + c2] += kap * v[r] * v[c2];
           }
+          if (exact) {
+            /* pen times the second derivatives of pen:
+             *   d2/dth_j dth_m = -t_j^T Hsd t_m + n.(x - p_max(j,m)),
+             *   d2/dl dth_j    = -fr t_j^T Hsd u - fr n.(z x u),
+             *   d2/dl^2        = -fr^2 u^T Hsd u,
+             * with t_j = z x (x - p_j) and Hsd = kappa (I - n n^T). */
+            const double ux = G->ux[i], uy = G->uy[i];
+            const int last = (i == N - 1);
+            for (int j = 0; j <= i; ++j) {
+              double tjx = -(y - G->py[j]), tjy = x - G->px[j];
+              double tjn = tjx * nx + tjy * ny;
+              for (int m = 0; m <= i; ++m) {
+                double tmx = -(y - G->py[m]), tmy = x - G->px[m];
+                double tmn = tmx * nx + tmy * ny;
+                double curv = kap_sd * ((tjx * tmx + tjy * tmy) - tjn * tmn);
+                int q = j > m ? j : m;
+                double geo = nx * (x - G->px[q]) + ny * (y - G->py[q]);
+                H[j * n + m] += kap * pen * (-curv + geo);
+              }
+              if (last) {
+                double un = ux * nx + uy * ny;
+                double curv = kap_sd * ((tjx * ux + tjy * uy) - tjn * un);
+                double zu_n = -uy * nx + ux * ny;
+                double val = kap * pen * (-fr * curv - fr * zu_n);
+                H[j * n + N] += val;
+                H[N * n + j] += val;
+              }
+            }
+            if (last) {
+              double un = ux * nx + uy * ny;
+              H[N * n + N] += kap * pen * (-fr * fr * kap_sd * (1.0 - un * un));
+            }
+          }
         }
       }
     }
@@ -620,6 +664,12 @@ static double energy(const inst_t* I, int N, const double* th, double l, double*
   free(v);
   if (mag) *mag = S;
   return J;
+}
+
+/* Energy with the Gauss-Newton matrix (contact second derivatives dropped). */
+static double energy(const inst_t* I, int N, const double* th, double l, double* g, double* H, geo_t* G,
+                     double* mag) {
+  return energy_h(I, N, th, l, g, H, G, mag, 0);
 }
 
 /* Cholesky solve of the leading m x m block of H (row stride n). */
@@ -678,8 +728,9 @@ enum { ORC_OK = 0, ORC_MAXITER = 1, ORC_NONFINITE = 2, ORC_BADINPUT = 3 };
 static int g_trace = 0;
 void orc_set_trace(int on) { g_trace = on; }
 
-/* Equilibrium of the current chain from the warm start (theta, l): damped
- * Gauss-Newton with the bound 0 <= l <= l_seg handled as an active set,
+/* Equilibrium of the current chain from the warm start (theta, l): Newton
+ * steps (exact Hessian of J when positive definite, else the Gauss-Newton
+ * matrix), the bound 0 <= l <= l_seg handled as an active set,
  * backtracking line search (Armijo, or approximate Wolfe when the cost change
  * is at rounding level), stop when the predicted displacement is at most tol
  * (the final step is applied).  Algorithm 1 of Sec. 4.1 read as "the stationary point
@@ -697,6 +748,7 @@ static int solve_step(const inst_t* I, int N, double* th, double* l, int* iters_
   double* tt = (double*)malloc(sizeof(double) * n);
   double* gt = (double*)malloc(sizeof(double) * n);
   double* Ht = (double*)malloc(sizeof(double) * n * n);
+  double* Hs = (double*)malloc(sizeof(double) * n * n);
   int status = ORC_MAXITER, it = 0;
   double r = INFINITY;
   long long evals = 0;
@@ -708,7 +760,15 @@ static int solve_step(const inst_t* I, int N, double* th, double* l, int* iters_
     int lfix = (*l <= 0.0 && g[N] > 0.0) || (*l >= I->l_seg && g[N] < 0.0);
     int m = lfix ? N : n;
     for (int k = 0; k < m; ++k) rhs[k] = -g[k];
-    if (chol_solve(H, n, m, rhs, dx) != 0) { status = ORC_NONFINITE; break; }
+    /* Newton step with the exact Hessian of J when it is positive definite,
+     * else with the Gauss-Newton matrix (always positive definite). */
+    int solved = 0;
+    if (p->exact_hessian) {
+      energy_h(I, N, th, *l, NULL, Hs, &G, NULL, 1);
+      solved = chol_solve(Hs, n, m, rhs, dx) == 0;
+      chain_fk(I, N, th, *l, G.px, G.py, G.ux, G.uy, G.L);
+    }
+    if (!solved && chol_solve(H, n, m, rhs, dx) != 0) { status = ORC_NONFINITE; break; }
     if (lfix) dx[N] = 0.0;
     r = step_residual(I, N, dx, &G);
     if (!isfinite(r)) { status = ORC_NONFINITE; break; }
@@ -756,7 +816,7 @@ static int solve_step(const inst_t* I, int N, double* th, double* l, int* iters_
   *iters_out = it;
   *resid_out = r;
   if (evals_out) *evals_out = evals;
-  free(g); free(H); free(dx); free(rhs); free(tt); free(gt); free(Ht);
+  free(g); free(H); free(dx); free(rhs); free(tt); free(gt); free(Ht); free(Hs);
   geo_free(&G);
   return status;
 }
@@ -775,6 +835,18 @@ double orc_energy(const orc_params* p, const orc_batch* b, const orc_tables* T, 
   return J;
 }
 
+/* Cost, gradient and the exact Hessian of J (contact second derivatives included). */
+double orc_energy_exact(const orc_params* p, const orc_batch* b, const orc_tables* T, int i, int N,
+                        const double* th, double l, double* g, double* H) {
+  inst_t I;
+  inst_init(&I, p, b, T, i);
+  geo_t G;
+  geo_alloc(&G, N);
+  double J = energy_h(&I, N, th, l, g, H, &G, NULL, 1);
+  geo_free(&G);
+  return J;
+}
+
 int orc_solve(const orc_params* p, const orc_batch* b, const orc_tables* T, int i, int N, double* th, double* l,
               int* iters, double* resid) {
   inst_t I;
@@ -782,7 +854,7 @@ int orc_solve(const orc_params* p, const orc_batch* b, const orc_tables* T, int 
   return solve_step(&I, N, th, l, iters, resid, NULL);
 }
 
-/* One Gauss-Newton step at the state (theta, l) without moving it: the step
+/* The solver's Newton step at the state (theta, l) without moving it: the step
  * dx[0..N] (dx[N] for l; 0 when the bound on l is active), its predicted
  * displacement residual, and the cost.  Returns 0 on success. */
 int orc_gn_step(const orc_params* p, const orc_batch* b, const orc_tables* T, int i, int N, const double* th,
@@ -799,7 +871,15 @@ int orc_gn_step(const orc_params* p, const orc_batch* b, const orc_tables* T, in
   int lfix = (l <= 0.0 && g[N] > 0.0) || (l >= I.l_seg && g[N] < 0.0);
   int m = lfix ? N : n;
   for (int k = 0; k < m; ++k) rhs[k] = -g[k];
-  int rc = chol_solve(H, n, m, rhs, dx);
+  int rc = 1;
+  if (p->exact_hessian) {
+    double* He = (double*)malloc(sizeof(double) * n * n);
+    energy_h(&I, N, th, l, NULL, He, &G, NULL, 1);
+    rc = chol_solve(He, n, m, rhs, dx);
+    free(He);
+    chain_fk(&I, N, th, l, G.px, G.py, G.ux, G.uy, G.L);
+  }
+  if (rc != 0) rc = chol_solve(H, n, m, rhs, dx);
   if (lfix) dx[N] = 0.0;
   *resid = rc == 0 ? step_residual(&I, N, dx, &G) : NAN;
   *lfix_out = lfix;

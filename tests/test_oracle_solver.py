@@ -199,6 +199,29 @@ def test_gauss_newton_contact_rows():
     assert np.allclose(H, ref, rtol=1e-6, atol=1e-6 * np.abs(H).max())
 
 
+@pytest.mark.parametrize("ks", [1, 2])
+def test_exact_hessian_matches_finite_differences(ks):
+    """The exact Hessian (obstacle curvature and load-stiffness terms of the
+    contact penalty included) equals central differences of the gradient."""
+    sc, rng = contact_scene()
+    o = oracle.Oracle(sc, oracle.default_params(discs_per_link=ks))
+    for _ in range(6):
+        th = rng.normal(0, 0.08, 6)
+        l = rng.uniform(0.002, 0.019)
+        H = o.hessian_exact(0, th, l)
+        h = 1e-7
+        Hf = np.zeros((7, 7))
+        for k in range(7):
+            tp, tm = th.copy(), th.copy()
+            lp, lm = l, l
+            if k < 6:
+                tp[k] += h; tm[k] -= h
+            else:
+                lp += h; lm -= h
+            Hf[:, k] = (o.energy(0, tp, lp, False)[1] - o.energy(0, tm, lm, False)[1]) / (2 * h)
+        assert np.max(np.abs(H - Hf)) <= 1e-7 * np.max(np.abs(Hf))
+
+
 # ------------------------------------------------------------------ P2 / P3 free space
 def _free_joint_balance(o, sc, i, j, lo, hi):
     """Scalar FP64 bisection of M(theta) = sum_a tau_a(theta) at joint j."""
