@@ -81,7 +81,10 @@ typedef enum {
  * discs_per_link: contact discs K_s of radius R at fractions k/K_s of each
  *   link (2; 1..4 supported).
  * mode, gd_alpha, gd_steps: reserved for the fixed-step gradient descent of
- *   Algorithm 1 (mode 0 = equilibrium; only mode 0 is implemented). */
+ *   Algorithm 1 (mode 0 = equilibrium; only mode 0 is implemented).
+ * exact_hessian: 1 = Newton steps with the exact Hessian of the cost when it
+ *   is positive definite, else with the Gauss-Newton matrix (contact second
+ *   derivatives dropped); 0 = always Gauss-Newton (default 1). */
 typedef struct {
   double w_a, w_b, w_c;
   double eps_crit;
@@ -97,7 +100,7 @@ typedef struct {
   int32_t mode;
   double gd_alpha;
   int32_t gd_steps;
-  int32_t reserved;
+  int32_t exact_hessian;
 } vine_params;
 
 /* Batch of independent robot instances, structure-of-arrays with CSR
@@ -153,6 +156,7 @@ typedef struct {
   int64_t link_evaluations;  /* sum over evaluations of the links present */
   int64_t pair_tests;        /* disc-obstacle tests: sum over evaluations of N K_s n_obs */
   int64_t circle_pair_tests; /* the part of pair_tests against circles */
+  int64_t gn_fallbacks;      /* Newton steps that used the Gauss-Newton matrix */
   int32_t n_maxiter, n_nonfinite, n_badinput, reserved;
 } vine_stats;
 

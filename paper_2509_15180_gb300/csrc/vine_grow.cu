@@ -149,9 +149,17 @@ struct Acc {
   float glc, hll, q0, q1, q2;
 };
 
-// One active contact: force kap * pen * n on a disc at fraction fr of the link.
-__device__ __forceinline__ void add_contact(Acc& c, float pen, float nx, float ny, float fr, float lx, float ly,
-                                            float kap, bool last, float ulx, float uly) {
+// One active contact: force kap * pen * n on a disc at fraction fr of the
+// link.  Gauss-Newton part kap w w^T of the link's 3x3 stiffness in twist
+// coordinates about the link start, w = ((x - p) x n, n_x, n_y).  With EXACT
+// also pen times the second derivatives of pen: obstacle curvature
+// -(kap pen kinv) s s^T, s = (n.(x - p), -n_y, n_x) (kinv = 1/distance to the
+// circle centre or box corner, 0 on a box face), and the local part of the
+// load stiffness fr Lu.F on the rotational entry; for the distal link the
+// couplings with its length l.
+template <bool EXACT>
+__device__ __forceinline__ void add_contact(Acc& c, float pen, float nx, float ny, float kinv, float fr, float lx,
+                                            float ly, float kap, bool last, float ulx, float uly) {
   const float f = kap * pen;
   const float fx = f * nx, fy = f * ny;
   c.fx += fx;
@@ -167,6 +175,17 @@ __device__ __forceinline__ void add_contact(Acc& c, float pen, float nx, float n
   c.c22 += kap * ny * ny;
   c.pen2 += pen * pen;
   c.pen1 += pen;
+  float s0 = 0.f, cc = 0.f;
+  if (EXACT) {
+    s0 = nx * rx + ny * ry;
+    cc = f * kinv;
+    c.c00 -= cc * s0 * s0 - (rx * fx + ry * fy);
+    c.c01 += cc * s0 * ny;
+    c.c02 -= cc * s0 * nx;
+    c.c11 -= cc * ny * ny;
+    c.c12 += cc * ny * nx;
+    c.c22 -= cc * nx * nx;
+  }
   if (last) {
     const float vl = fr * (nx * ulx + ny * uly);
     c.glc += fr * (fx * ulx + fy * uly);
@@ -174,13 +193,21 @@ __device__ __forceinline__ void add_contact(Acc& c, float pen, float nx, float n
     c.q0 += kap * vl * w0;
     c.q1 += kap * vl * nx;
     c.q2 += kap * vl * ny;
+    if (EXACT) {
+      const float tu = nx * uly - ny * ulx;  // tangent (-n_y, n_x) . u
+      c.hll -= cc * fr * fr * tu * tu;
+      c.q0 -= cc * fr * tu * s0 + fr * (fy * ulx - fx * uly);
+      c.q1 += cc * fr * tu * ny;
+      c.q2 -= cc * fr * tu * nx;
+    }
   }
 }
 
 // Penetration of a disc (offset dx, dy from the obstacle centre, radius R).
-// Returns pen > 0 and the outward normal when the disc overlaps obstacle ob.
+// Returns pen > 0, the outward normal and the curvature kinv of the signed
+// distance when the disc overlaps obstacle ob.
 __device__ __forceinline__ float disc_pen(const float4 ob, float dx, float dy, float R, float fbx, float fby,
-                                          float& nx, float& ny) {
+                                          float& nx, float& ny, float& kinv) {
   if (ob.w < 0.f) {  // circle: ob.z = R + r, -ob.w = (R + r)^2
     const float d2 = dx * dx + dy * dy;
     if (!(d2 < -ob.w)) return 0.f;
@@ -190,9 +217,11 @@ __device__ __forceinline__ float disc_pen(const float4 ob, float dx, float dy, f
       const float id = 1.f / d;
       nx = dx * id;
       ny = dy * id;
+      kinv = id;
     } else {
       nx = fbx;
       ny = fby;
+      kinv = 0.f;
     }
     return pen;
   }
@@ -200,11 +229,13 @@ __device__ __forceinline__ float disc_pen(const float4 ob, float dx, float dy, f
   if (!(fmaxf(ax, ay) < R)) return 0.f;
   const float sx = dx >= 0.f ? 1.f : -1.f, sy = dy >= 0.f ? 1.f : -1.f;
   float sd;
+  kinv = 0.f;
   if (ax > 0.f && ay > 0.f) {
     sd = sqrtf(ax * ax + ay * ay);
     const float id = 1.f / sd;
     nx = sx * ax * id;
     ny = sy * ay * id;
+    kinv = id;
   } else if (ax > 0.f) {
     sd = ax; nx = sx; ny = 0.f;
   } else if (ay > 0.f) {
@@ -222,9 +253,11 @@ struct EvalOut {
   float gl, hll, q0, q1, q2, ulx, uly;
 };
 
-// Cost, gradient and Gauss-Newton data at the state (TH[0..N), l).
+// Cost, gradient and the Newton data at the state (TH[0..N), l): the exact
+// Hessian when `exact`, else the Gauss-Newton matrix.
 template <int KS>
-__device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int N, float l, int lane) {
+__device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int N, float l, int lane,
+                        bool exact) {
   const int B = (N + 31) >> 5;
   const int j0 = min(lane * B, N), j1 = min(j0 + B, N);
   // headings psi_j = psi_b + sum_{i<=j} theta_i
@@ -315,9 +348,13 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
       for (int k = 0; k < KS; ++k) {
         const float dx = (xk[k].hi - ob.x) + xk[k].lo;
         const float dy = (yk[k].hi - ob.y) + yk[k].lo;
-        float nx, ny;
-        const float pen = disc_pen(ob, dx, dy, I.R, fbx, fby, nx, ny);
-        if (pen > 0.f) add_contact(c, pen, nx, ny, (float)(k + 1) / (float)KS, lx, ly, kap, last, ulx, uly);
+        float nx, ny, kinv;
+        const float pen = disc_pen(ob, dx, dy, I.R, fbx, fby, nx, ny, kinv);
+        if (pen > 0.f) {
+          const float fr = (float)(k + 1) / (float)KS;
+          if (exact) add_contact<true>(c, pen, nx, ny, kinv, fr, lx, ly, kap, last, ulx, uly);
+          else add_contact<false>(c, pen, nx, ny, kinv, fr, lx, ly, kap, last, ulx, uly);
+        }
       }
     }
     S.FX[j] = c.fx;
@@ -348,6 +385,8 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
   for (int j = j1 - 1; j >= j0; --j) {
     const float t = S.TL[j] + (S.LUX[j] * fsy - S.LUY[j] * fsx);
     S.TL[j] = t;
+    // load stiffness: forces on the links beyond j, times their lever along Lu_j
+    if (exact) S.C0[j] += S.LUX[j] * fsx + S.LUY[j] * fsy;
     tt += t;
     fsx += S.FX[j];
     fsy += S.FY[j];
@@ -378,11 +417,15 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
 // Gauss-Newton step (DTH[0..N), dl) and its predicted displacement / (N l_seg).
 // Backward sweep: A_j (articulated stiffness of links >= j about p_j) and
 // beta_j; forward sweep: twists V_j and joint steps.  Warp-uniform.
+// Returns a negative value when a pivot is not positive (the matrix is not
+// positive definite); the step is then not formed.
 __device__ double gn_solve(const InstDev& I, const Smem& S, int N, bool lfix, const EvalOut& E, float& dl,
                            int lane) {
   float A00 = 0.f, A01 = 0.f, A02 = 0.f, A11 = 0.f, A12 = 0.f, A22 = 0.f;
   float b0 = 0.f, b1 = 0.f, b2 = 0.f;
+  if (!lfix && !(E.hll > 0.f)) return -1.0;
   const float iH = lfix ? 0.f : 1.f / E.hll;
+  bool pd = true;
   for (int j = N - 1; j >= 0; --j) {
     float c00 = S.C0[j], c01 = S.C1[j], c02 = S.C2[j], c11 = S.C3[j], c12 = S.C4[j], c22 = S.C5[j];
     const float dj = S.DD[j], gj = S.G[j], lx = S.LUX[j], ly = S.LUY[j];
@@ -408,6 +451,7 @@ __device__ double gn_solve(const InstDev& I, const Smem& S, int N, bool lfix, co
     const float C11 = c11 + A11, C12 = c12 + A12, C22 = c22 + A22;
     const float h0 = B0 + e0, h1 = b1 + e1, h2 = b2 + e2;
     const float D = dj + C00;
+    pd = pd && (D > 0.f);
     const float iD = 1.f / D;
     const float cc = gj + h0;
     const float r = dj * iD;
@@ -429,6 +473,7 @@ __device__ double gn_solve(const InstDev& I, const Smem& S, int N, bool lfix, co
     }
   }
   __syncwarp();
+  if (!pd) return -1.0;
   float V0 = 0.f, V1 = 0.f, V2 = 0.f, rmax = 0.f;
   dl = 0.f;
   for (int j = 0; j < N; ++j) {
@@ -456,6 +501,7 @@ struct StepStats {
   int iters;
   double r;
   long long evals, linkevals;
+  int fallbacks;
 };
 
 // Solves the current growth step to equilibrium from the warm start.
@@ -476,7 +522,8 @@ __device__ int solve_step(const GrowArgs& A, const InstDev& I, const Smem& S, in
                           StepStats& st, int inst) {
   const int B = (N + 31) >> 5;
   const int j0 = min(lane * B, N), j1 = min(j0 + B, N);
-  EvalOut E = eval<KS>(A, I, S, N, l, lane);
+  const bool exact = A.exact != 0;
+  EvalOut E = eval<KS>(A, I, S, N, l, lane, exact);
   st.evals += 1;
   st.linkevals += N;
   int status = kMaxIter, it;
@@ -489,7 +536,15 @@ __device__ int solve_step(const GrowArgs& A, const InstDev& I, const Smem& S, in
     const bool lfix = (l <= 0.f && E.gl > 0.f) || (l >= I.l_seg && E.gl < 0.f);
     float dl;
     r = gn_solve(I, S, N, lfix, E, dl, lane);
-    if (!isfinite(r)) {
+    if (exact && r < 0.0) {
+      // exact Hessian not positive definite here: Gauss-Newton matrix instead
+      E = eval<KS>(A, I, S, N, l, lane, false);
+      st.evals += 1;
+      st.linkevals += N;
+      st.fallbacks += 1;
+      r = gn_solve(I, S, N, lfix, E, dl, lane);
+    }
+    if (!isfinite(r) || r < 0.0) {
       status = kNonFinite;
       break;
     }
@@ -518,7 +573,7 @@ __device__ int solve_step(const GrowArgs& A, const InstDev& I, const Smem& S, in
       for (int j = j0; j < j1; ++j) S.TH[j] = S.TH0[j] + alpha * S.DTH[j];
       lt = fminf(fmaxf(l0 + alpha * dl, 0.f), I.l_seg);
       __syncwarp();
-      E = eval<KS>(A, I, S, N, lt, lane);
+      E = eval<KS>(A, I, S, N, lt, lane, exact);
       st.evals += 1;
       st.linkevals += N;
       const double dec = (double)alpha * gd + (double)gl0 * ((double)lt - (double)l0);
@@ -556,18 +611,19 @@ __device__ void process_instance(const GrowArgs& A, int inst, const Smem& S, int
   float l = A.l_cur[inst];
   __syncwarp();
   int iters = 0, conv = 0, steps = 0;
-  long long rls = 0, evals = 0, linkevals = 0;
+  long long rls = 0, evals = 0, linkevals = 0, fallbacks = 0;
   double rmax = 0.0;
   for (int s = 0; s < A.n_steps && N < I.n_target; ++s) {
     if (lane == 0) S.TH[N] = 0.f;  // new link at the tip
     N += 1;
     l = 0.f;
     __syncwarp();
-    StepStats st{0, 0.0, 0, 0};
+    StepStats st{0, 0.0, 0, 0, 0};
     const int res = solve_step<KS>(A, I, S, N, l, lane, st, inst);
     iters += st.iters;
     evals += st.evals;
     linkevals += st.linkevals;
+    fallbacks += st.fallbacks;
     steps += 1;
     if (!(st.r <= rmax)) rmax = st.r;
     if (res == kOK) {
@@ -590,6 +646,7 @@ __device__ void process_instance(const GrowArgs& A, int inst, const Smem& S, int
     A.rls[inst] += rls;
     A.evals[inst] += evals;
     A.linkevals[inst] += linkevals;
+    A.fallbacks[inst] += fallbacks;
     if (!(rmax <= A.resid_max[inst])) A.resid_max[inst] = rmax;
   }
   __syncwarp();
@@ -630,12 +687,16 @@ __global__ void __launch_bounds__(32) probe_kernel(const GrowArgs A, int inst, i
   for (int k = lane; k < I.n_act; k += 32) S.act[k] = A.act[I.act_off + k];
   for (int k = lane; k < N; k += 32) S.TH[k] = theta[k];
   __syncwarp();
-  const EvalOut E = eval<KS>(A, I, S, N, l, lane);
+  EvalOut E = eval<KS>(A, I, S, N, l, lane, A.exact != 0);
   for (int k = lane; k < N; k += 32) out_g[k] = S.G[k];
   __syncwarp();
   const bool lfix = (l <= 0.f && E.gl > 0.f) || (l >= I.l_seg && E.gl < 0.f);
   float dl;
-  const double r = gn_solve(I, S, N, lfix, E, dl, lane);
+  double r = gn_solve(I, S, N, lfix, E, dl, lane);
+  if (A.exact != 0 && r < 0.0) {
+    E = eval<KS>(A, I, S, N, l, lane, false);
+    r = gn_solve(I, S, N, lfix, E, dl, lane);
+  }
   for (int k = lane; k < N; k += 32) out_dx[k] = S.DTH[k];
   if (lane == 0) {
     out_g[N] = E.gl;
@@ -805,8 +866,8 @@ __global__ void contacts_kernel(const InstDev* inst, int n_inst, const float4* o
           const float fr = (float)k / (float)ks;
           const FF xk = ff_add(px, fr * lx), yk = ff_add(py, fr * ly);
           const float dx = (xk.hi - b4.x) + xk.lo, dy = (yk.hi - b4.y) + yk.lo;
-          float nx, ny;
-          hit = disc_pen(b4, dx, dy, I.R, -uy, ux, nx, ny) > 0.f;
+          float nx, ny, kinv;
+          hit = disc_pen(b4, dx, dy, I.R, -uy, ux, nx, ny, kinv) > 0.f;
         }
         if (hit) {
           if (pass == 1 && base + cnt < max_pairs && pairs) {

@@ -54,6 +54,7 @@ struct GrowArgs {
   long long* rls;
   long long* evals;
   long long* linkevals;
+  long long* fallbacks;  // Newton steps that fell back to the Gauss-Newton matrix
   double* resid_max;
   const int* order;
   int n_order;
@@ -68,6 +69,7 @@ struct GrowArgs {
   float fval_eps, c1;
   double tol;
   int max_iter, max_halv;
+  int exact;  // exact Hessian when positive definite (else Gauss-Newton)
   // diagnostics: per line-search trial records of one robot (off when null)
   double* trace;
   int* trace_count;

@@ -48,9 +48,11 @@ def test_probe_matches_oracle(cfg):
             # joint's onset energy w_a pi P R^3 as well
             scale = abs(Jo) + 160.0 * np.pi * float(sc["pressure"][i]) * float(sc["radius"][i]) ** 3
             worst["J"] = max(worst["J"], abs(Jg - Jo) / scale)
-            worst["g"] = max(worst["g"], np.max(np.abs(gg - go)) / max(np.max(np.abs(go)), 1e-12))
-            worst["dx"] = max(worst["dx"], np.max(np.abs(dg - dxo)) / max(np.max(np.abs(dxo)), 1e-12))
-            worst["r"] = max(worst["r"], abs(rg - ro) / max(ro, 1e-30))
+            # at equilibrium states the gradient and step are ~0: compare
+            # against the joint moment scale and a 1e-4 rad step scale too
+            worst["g"] = max(worst["g"], np.max(np.abs(gg - go)) / (np.max(np.abs(go)) + scale))
+            worst["dx"] = max(worst["dx"], np.max(np.abs(dg - dxo)) / (np.max(np.abs(dxo)) + 1e-4))
+            worst["r"] = max(worst["r"], abs(rg - ro) / (ro + 1e-6))
     print("probe cfg %d worst relative errors: %s" % (cfg, worst))
     # FP32 terms and the Hermite-tabulated wrinkling energy near onset
     assert worst["J"] < 1e-4
