@@ -98,7 +98,7 @@ def run_gpu(args):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    sc = scenes.config2(4096, replicate=rank)
+    sc = scenes.config2(args.robots, replicate=rank)
     rls_per_step = scenes.robot_link_steps(sc["n_links"])
     stream = torch.cuda.current_stream()
     dsc = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in sc.items()}
@@ -148,16 +148,17 @@ def run_gpu(args):
     st_last = b.stats(stream)
 
     # --- end to end through the C ABI with host buffers (create/copy in, grow, read back)
-    e2e_steps = max(2, min(args.steps, 5))
+    e2e_steps = 0 if args.no_e2e else max(2, min(args.steps, 5))
     host = {k: np.ascontiguousarray(v) for k, v in sc.items()}
     h2d = int(sum(v.nbytes for v in host.values()))
     T = int(sc["n_links"].sum())
     n = len(sc["n_links"])
     d2h = T * 4 + T * 12 + n * (8 + 4 + 4 + 4 + 8 + 4)
-    bw = vine.Batch(host, stream=stream)  # warm (tables, graph) once
-    bw.simulate(stream)
-    bw.state(stream)
-    bw.close()
+    if e2e_steps:
+        bw = vine.Batch(host, stream=stream)  # warm (tables, graph) once
+        bw.simulate(stream)
+        bw.state(stream)
+        bw.close()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e2e_rls = 0
@@ -168,25 +169,15 @@ def run_gpu(args):
         e2e_rls += int(be.stats(stream)["robot_link_steps"])
         be.close()
     e2e_s = time.perf_counter() - t0
-    e2e = {"value": e2e_rls / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-           "ms_per_step": 1e3 * e2e_s / e2e_steps}
+    e2e = None if not e2e_steps else {
+        "value": e2e_rls / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+        "ms_per_step": 1e3 * e2e_s / e2e_steps}
 
     # --- plain form: one launch per robot, same kernel (subset of the batch)
     n_plain = args.plain_robots
-    sub = scenes.subset(sc, np.arange(n_plain))
-    bp = vine.Batch(sub, stream=stream)
-    bp.simulate_plain(stream)
-    torch.cuda.synchronize()
-    bp.reset(stream)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    bp.simulate_plain(stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    plain_s = e0.elapsed_time(e1) / 1e3
-    plain = {"value": bp.stats(stream)["robot_link_steps"] / plain_s, "unit": UNIT, "robots": n_plain,
-             "launches": n_plain, "note": "one launch per robot, sequential; the first %d robots" % n_plain}
-    bp.close()
+    plain = None
+    if n_plain > 0:
+        plain = _plain(scenes, vine, torch, sc, stream, n_plain)
 
     # --- roofline of the growth kernel: algorithmic FP32 flops per launch
     flops = (40.0 * st_last["link_evaluations"] + 10.0 * st_last["circle_pair_tests"] +
@@ -207,7 +198,8 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 residual test)", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "robots_per_gpu": n, "links": 100,
+            "config": {"workload": WORKLOAD if n == 4096 else WORKLOAD.replace("4096", str(n)),
+                       "robots_per_gpu": n, "links": 100,
                        "robot_link_steps_per_step": rls_per_step, "l2": "flushed between timed steps (512 MiB write)",
                        "tol": 1e-6},
             "e2e": e2e, "plain": plain, "latency": lat, "roofline": roofline, "cpu_baseline": cpu,
@@ -215,12 +207,32 @@ def run_gpu(args):
             "solver": {"iters_per_step": st_last["iterations"] / max(st_last["steps_total"], 1),
                        "evals_per_step": st_last["evaluations"] / max(st_last["steps_total"], 1),
                        "steps_converged": st_last["steps_converged"], "steps_total": st_last["steps_total"],
-                       "robots_maxiter": st_last["n_maxiter"]},
+                       "robots_maxiter": st_last["n_maxiter"], "robots_nonfinite": st_last["n_nonfinite"],
+                       "gn_fallbacks_per_step": st_last["gn_fallbacks"] / max(st_last["steps_total"], 1)},
         }
     b.close()
     if ws > 1:
         dist.destroy_process_group()
     return result
+
+
+def _plain(scenes, vine, torch, sc, stream, n_plain):
+    """Plain form: one launch per robot, same kernel, on the first robots."""
+    sub = scenes.subset(sc, np.arange(n_plain))
+    bp = vine.Batch(sub, stream=stream)
+    bp.simulate_plain(stream)
+    torch.cuda.synchronize()
+    bp.reset(stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    bp.simulate_plain(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_s = e0.elapsed_time(e1) / 1e3
+    out = {"value": bp.stats(stream)["robot_link_steps"] / plain_s, "unit": UNIT, "robots": n_plain,
+           "launches": n_plain, "note": "one launch per robot, sequential; the first %d robots" % n_plain}
+    bp.close()
+    return out
 
 
 def cpu_baseline(args, sc, robots=None):
@@ -273,7 +285,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--robots", type=int, default=4096, help="robots per GPU (the workload has 4096)")
     ap.add_argument("--plain-robots", type=int, default=64)
+    ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-robots", type=int, default=96)
     ap.add_argument("--ref-robots", type=int, default=48)
     ap.add_argument("--no-cpu", action="store_true")
