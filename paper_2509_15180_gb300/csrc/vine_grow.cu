@@ -251,6 +251,7 @@ __device__ __forceinline__ float disc_pen(const float4 ob, float dx, float dy, f
 struct EvalOut {
   double J, S;  // cost and the sum of the magnitudes of its terms
   float gl, hll, q0, q1, q2, ulx, uly;
+  float kg_wb;  // growth stiffness w_b k_g (scale of the distal-length pivot)
 };
 
 // Cost, gradient and the Newton data at the state (TH[0..N), l): the exact
@@ -410,6 +411,7 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
   E.ulx = __shfl_sync(kFull, ulx, owner);
   E.uly = __shfl_sync(kFull, uly, owner);
   E.gl = -2.f * A.w_b * I.kg * (I.l_seg - l) - glc;
+  E.kg_wb = A.w_b * I.kg;
   __syncwarp();
   return E;
 }
@@ -423,10 +425,10 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
 // pivot lost to FP32 rounding (distal-length Schur complement of a buckled
 // joint) is raised to a small positive floor instead.
 __device__ double gn_solve(const InstDev& I, const Smem& S, int N, bool lfix, const EvalOut& E, float& dl,
-                           int lane, bool strict) {
+                           int lane, bool strict, float& max_dth) {
   float A00 = 0.f, A01 = 0.f, A02 = 0.f, A11 = 0.f, A12 = 0.f, A22 = 0.f;
   float b0 = 0.f, b1 = 0.f, b2 = 0.f;
-  if (!lfix && !(E.hll > 0.f)) return -1.0;
+  if (strict && !lfix && !(E.hll > 1e-3f * 2.f * E.kg_wb)) return -1.0;
   const float iH = lfix ? 0.f : 1.f / E.hll;
   bool pd = true;
   for (int j = N - 1; j >= 0; --j) {
@@ -454,9 +456,10 @@ __device__ double gn_solve(const InstDev& I, const Smem& S, int N, bool lfix, co
     const float C11 = c11 + A11, C12 = c12 + A12, C22 = c22 + A22;
     const float h0 = B0 + e0, h1 = b1 + e1, h2 = b2 + e2;
     float D = dj + C00;
-    if (!(D > 0.f)) {
+    const float Dmin = 1e-6f * (dj + fabsf(c00) + fabsf(K00));
+    if (!(D > Dmin)) {
       if (strict) pd = false;
-      else D = 1e-6f * (dj + fabsf(c00) + fabsf(K00)) + 1e-30f;
+      else D = Dmin;
     }
     const float iD = 1.f / D;
     const float cc = gj + h0;
@@ -480,7 +483,7 @@ __device__ double gn_solve(const InstDev& I, const Smem& S, int N, bool lfix, co
   }
   __syncwarp();
   if (!pd) return -1.0;
-  float V0 = 0.f, V1 = 0.f, V2 = 0.f, rmax = 0.f;
+  float V0 = 0.f, V1 = 0.f, V2 = 0.f, rmax = 0.f, dmax = 0.f;
   dl = 0.f;
   for (int j = 0; j < N; ++j) {
     const float h0 = S.C0[j], h1 = S.C1[j], h2 = S.C2[j], iD = S.C3[j], cc = S.C4[j];
@@ -496,10 +499,13 @@ __device__ double gn_solve(const InstDev& I, const Smem& S, int N, bool lfix, co
     V1 -= V0 * ly;
     V2 += V0 * lx;
     const float dx = V1 + ex, dy = V2 + ey;
-    rmax = fmaxf(rmax, fmaxf(sqrtf(dx * dx + dy * dy), I.l_seg * fabsf(dth)));
+    const float v = fmaxf(sqrtf(dx * dx + dy * dy), I.l_seg * fabsf(dth));
+    if (!(v <= rmax)) rmax = v;  // keeps NaN
+    if (!(fabsf(dth) <= dmax)) dmax = fabsf(dth);
     if (lane == 0) S.DTH[j] = dth;
   }
   __syncwarp();
+  max_dth = dmax;
   return (double)rmax / ((double)N * (double)I.l_seg);
 }
 
@@ -541,14 +547,15 @@ __device__ int solve_step(const GrowArgs& A, const InstDev& I, const Smem& S, in
     }
     const bool lfix = (l <= 0.f && E.gl > 0.f) || (l >= I.l_seg && E.gl < 0.f);
     float dl;
-    r = gn_solve(I, S, N, lfix, E, dl, lane, exact);
-    if (exact && r < 0.0) {
+    float mdth;
+    r = gn_solve(I, S, N, lfix, E, dl, lane, exact, mdth);
+    if (exact && !(r >= 0.0 && isfinite(r))) {
       // exact Hessian not positive definite here: Gauss-Newton matrix instead
       E = eval<KS>(A, I, S, N, l, lane, false);
       st.evals += 1;
       st.linkevals += N;
       st.fallbacks += 1;
-      r = gn_solve(I, S, N, lfix, E, dl, lane, false);
+      r = gn_solve(I, S, N, lfix, E, dl, lane, false, mdth);
     }
     if (!isfinite(r) || r < 0.0) {
       status = kNonFinite;
@@ -698,10 +705,11 @@ __global__ void __launch_bounds__(32) probe_kernel(const GrowArgs A, int inst, i
   __syncwarp();
   const bool lfix = (l <= 0.f && E.gl > 0.f) || (l >= I.l_seg && E.gl < 0.f);
   float dl;
-  double r = gn_solve(I, S, N, lfix, E, dl, lane, A.exact != 0);
-  if (A.exact != 0 && r < 0.0) {
+  float mdth;
+  double r = gn_solve(I, S, N, lfix, E, dl, lane, A.exact != 0, mdth);
+  if (A.exact != 0 && !(r >= 0.0 && isfinite(r))) {
     E = eval<KS>(A, I, S, N, l, lane, false);
-    r = gn_solve(I, S, N, lfix, E, dl, lane, false);
+    r = gn_solve(I, S, N, lfix, E, dl, lane, false, mdth);
   }
   for (int k = lane; k < N; k += 32) out_dx[k] = S.DTH[k];
   if (lane == 0) {

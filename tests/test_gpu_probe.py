@@ -15,6 +15,19 @@ if not torch.cuda.is_available():
 from paper_2509_15180_gb300 import vine  # noqa: E402
 
 
+def _displacements(orc, i, th, l, dx):
+    """Displacement of every link end predicted by the step dx (joint angles, then l)."""
+    px, py, psi = orc.poses(i, th, l)
+    N = th.size
+    out = np.zeros((N, 2))
+    for k in range(N):
+        rx, ry = px[k + 1] - px[: k + 1], py[k + 1] - py[: k + 1]
+        out[k, 0] = np.sum(-dx[: k + 1] * ry)
+        out[k, 1] = np.sum(dx[: k + 1] * rx)
+    out[N - 1] += dx[N] * np.array([np.cos(psi[N - 1]), np.sin(psi[N - 1])])
+    return out
+
+
 def _states(sc, steps, every):
     orc = oracle.Oracle(sc, oracle.default_params(tol=1e-10))
     st = orc.new_state()
@@ -60,7 +73,14 @@ def test_probe_matches_oracle(cfg, exact):
             # at equilibrium states the gradient and step are ~0: compare
             # against the joint moment scale and a 1e-4 rad step scale too
             worst["g"] = max(worst["g"], np.max(np.abs(gg - go)) / (np.max(np.abs(go)) + scale))
-            worst["dx"] = max(worst["dx"], np.max(np.abs(dg - dxo)) / (np.max(np.abs(dxo)) + 1e-4))
+            # compare the steps as the link-end displacements they predict (the
+            # soft directions of an ill-conditioned matrix are resolved only
+            # to FP32 accuracy in joint-angle terms)
+            th_o = th32.astype(np.float64)
+            dg_p = _displacements(orc, i, th_o, float(np.float32(lv)), dg.astype(np.float64))
+            do_p = _displacements(orc, i, th_o, float(np.float32(lv)), dxo)
+            L = th.size * float(sc["l_seg"][i])
+            worst["dx"] = max(worst["dx"], np.max(np.abs(dg_p - do_p)) / (np.max(np.abs(do_p)) + 1e-6 * L))
             worst["r"] = max(worst["r"], abs(rg - ro) / (ro + 1e-6))
     print("probe cfg %d exact %d worst relative errors: %s" % (cfg, exact, worst))
     # FP32 terms and the Hermite-tabulated wrinkling energy near onset
