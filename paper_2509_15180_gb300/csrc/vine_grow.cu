@@ -551,6 +551,7 @@ __device__ int solve_step(const GrowArgs& A, const InstDev& I, const Smem& S, in
     r = gn_solve(I, S, N, lfix, E, dl, lane, exact, mdth);
     if (exact && !(r >= 0.0 && isfinite(r))) {
       // exact Hessian not positive definite here: Gauss-Newton matrix instead
+      trace_rec(A, inst, lane, N, it, -2, 0.0, r, E.J, E.J, 0.0, 0.0, (double)E.hll, l, lfix ? 1.0 : 0.0);
       E = eval<KS>(A, I, S, N, l, lane, false);
       st.evals += 1;
       st.linkevals += N;
@@ -558,6 +559,8 @@ __device__ int solve_step(const GrowArgs& A, const InstDev& I, const Smem& S, in
       r = gn_solve(I, S, N, lfix, E, dl, lane, false, mdth);
     }
     if (!isfinite(r) || r < 0.0) {
+      trace_rec(A, inst, lane, N, it, -3, 0.0, r, E.J, E.S, (double)E.gl, (double)mdth, (double)E.hll, l,
+                lfix ? 1.0 : 0.0);
       status = kNonFinite;
       break;
     }
