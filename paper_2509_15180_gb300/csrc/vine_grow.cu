@@ -456,10 +456,10 @@ __device__ double gn_solve(const InstDev& I, const Smem& S, int N, bool lfix, co
     const float C11 = c11 + A11, C12 = c12 + A12, C22 = c22 + A22;
     const float h0 = B0 + e0, h1 = b1 + e1, h2 = b2 + e2;
     float D = dj + C00;
-    const float Dmin = 1e-6f * (dj + fabsf(c00) + fabsf(K00));
-    if (!(D > Dmin)) {
+    const float Dscale = dj + fabsf(c00) + fabsf(K00);
+    if (!(D > 1e-6f * Dscale)) {
       if (strict) pd = false;
-      else D = Dmin;
+      else D = 1e-3f * Dscale;
     }
     const float iD = 1.f / D;
     const float cc = gj + h0;
@@ -558,11 +558,28 @@ __device__ int solve_step(const GrowArgs& A, const InstDev& I, const Smem& S, in
       st.fallbacks += 1;
       r = gn_solve(I, S, N, lfix, E, dl, lane, false, mdth);
     }
-    if (!isfinite(r) || r < 0.0) {
-      trace_rec(A, inst, lane, N, it, -3, 0.0, r, E.J, E.S, (double)E.gl, (double)mdth, (double)E.hll, l,
-                lfix ? 1.0 : 0.0);
+    if (!isfinite(E.J)) {
       status = kNonFinite;
       break;
+    }
+    if (!isfinite(r) || r < 0.0) {
+      // the Gauss-Newton sweep lost its pivots to FP32 range (bending floor
+      // against contact stiffness): steepest descent, at most 0.05 rad per joint
+      trace_rec(A, inst, lane, N, it, -3, 0.0, r, E.J, E.S, (double)E.gl, (double)mdth, (double)E.hll, l,
+                lfix ? 1.0 : 0.0);
+      float gm = 0.f;
+      for (int j = j0; j < j1; ++j) gm = fmaxf(gm, fabsf(S.G[j]));
+      for (int d = 16; d > 0; d >>= 1) gm = fmaxf(gm, __shfl_xor_sync(kFull, gm, d));
+      const float sc = gm > 0.f ? 0.05f / gm : 0.f;
+      for (int j = j0; j < j1; ++j) S.DTH[j] = -S.G[j] * sc;
+      dl = lfix ? 0.f : -E.gl * sc * I.l_seg * I.l_seg;
+      if (!(sc > 0.f) || !isfinite(dl)) {
+        status = kNonFinite;
+        break;
+      }
+      r = 1.0;  // not a Newton step: never taken as converged
+      st.fallbacks += 1;
+      __syncwarp();
     }
     if (r <= A.tol) {
       trace_rec(A, inst, lane, N, it, -1, 1.0, r, E.J, E.J, 0.0, 0.0, 0.0, l + dl, lfix ? 1.0 : 0.0);
