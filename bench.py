@@ -146,6 +146,12 @@ def run_gpu(args):
         conv_all = float(conv_rls)
     value = conv_all / total_s
     st_last = b.stats(stream)
+    rc = b.robot_counters(stream)
+    cyc_ms = rc["cycles"] / 2.07e6  # at the maximum SM clock
+    robots = {"mean_ms": float(cyc_ms.mean()), "p99_ms": float(np.percentile(cyc_ms, 99)),
+              "max_ms": float(cyc_ms.max()), "evals_mean": float(rc["evals"].mean()),
+              "evals_max": int(rc["evals"].max()),
+              "what": "per-robot time its warp spent (clock64 at 2.07 GHz) in the last timed step"}
 
     # --- end to end through the C ABI with host buffers (create/copy in, grow, read back)
     e2e_steps = 0 if args.no_e2e else max(2, min(args.steps, 5))
@@ -203,7 +209,7 @@ def run_gpu(args):
                        "robot_link_steps_per_step": rls_per_step, "l2": "flushed between timed steps (512 MiB write)",
                        "tol": 1e-6},
             "e2e": e2e, "plain": plain, "latency": lat, "roofline": roofline, "cpu_baseline": cpu,
-            "clocks": ck, "gpu_launches": args.steps,
+            "clocks": ck, "gpu_launches": args.steps, "robots": robots,
             "solver": {"iters_per_step": st_last["iterations"] / max(st_last["steps_total"], 1),
                        "evals_per_step": st_last["evaluations"] / max(st_last["steps_total"], 1),
                        "steps_converged": st_last["steps_converged"], "steps_total": st_last["steps_total"],

@@ -245,6 +245,12 @@ vine_status vine_debug_trace(vine_batch* b, int32_t inst, int32_t capacity);
 /* Copies up to `capacity` recorded trials to host `records`; *count = copied. */
 vine_status vine_debug_trace_read(const vine_batch* b, double* records, int32_t capacity, int32_t* count);
 
+/* Per-robot counters since the last reset (host arrays of n; any may be
+ * NULL; synchronises the stream): converged growth steps, cost
+ * evaluations, and SM clock cycles its warp spent on it. */
+vine_status vine_get_robot_counters(const vine_batch* b, int32_t* steps_converged, int64_t* evaluations,
+                                    int64_t* cycles, void* cuda_stream);
+
 /* Number of instances and total link capacity (sum of n_links). */
 vine_status vine_batch_info(const vine_batch* b, int32_t* n_inst, int64_t* total_links);
 

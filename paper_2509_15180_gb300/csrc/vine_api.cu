@@ -288,7 +288,7 @@ vine_status vine_batch_create(const vine_batch_desc* D, const vine_params* P, vo
                o_st = take(sizeof(int) * n), o_st0 = take(sizeof(int) * n), o_it = take(sizeof(int) * n),
                o_cv = take(sizeof(int) * n), o_sp = take(sizeof(int) * n), o_rls = take(sizeof(long long) * n),
                o_ev = take(sizeof(long long) * n), o_le = take(sizeof(long long) * n),
-               o_fb = take(sizeof(long long) * n),
+               o_fb = take(sizeof(long long) * n), o_cy = take(sizeof(long long) * n),
                o_rm = take(sizeof(double) * n), o_ord = take(sizeof(int) * n), o_cnt = take(sizeof(int) * 4);
   const size_t persistent = off;
   // setup scratch (freed at the end of create)
@@ -455,6 +455,7 @@ vine_status vine_batch_create(const vine_batch_desc* D, const vine_params* P, vo
   a.evals = (long long*)P_(o_ev);
   a.linkevals = (long long*)P_(o_le);
   a.fallbacks = (long long*)P_(o_fb);
+  a.cycles = (long long*)P_(o_cy);
   a.resid_max = (double*)P_(o_rm);
   a.order = (const int*)P_(o_ord);
   a.n_order = n;
@@ -512,6 +513,7 @@ vine_status vine_batch_reset(vine_batch* B, void* stream_v) {
   CK(cudaMemsetAsync(a.evals, 0, sizeof(long long) * B->n_inst, st));
   CK(cudaMemsetAsync(a.linkevals, 0, sizeof(long long) * B->n_inst, st));
   CK(cudaMemsetAsync(a.fallbacks, 0, sizeof(long long) * B->n_inst, st));
+  CK(cudaMemsetAsync(a.cycles, 0, sizeof(long long) * B->n_inst, st));
   CK(cudaMemsetAsync(a.resid_max, 0, sizeof(double) * B->n_inst, st));
   CK(cudaMemcpyAsync(a.status, B->status0, sizeof(int) * B->n_inst, cudaMemcpyDeviceToDevice, st));
   return VINE_OK;
@@ -749,6 +751,19 @@ vine_status vine_debug_trace_read(const vine_batch* B, double* records, int32_t 
   n = std::min(n, std::min(capacity, B->args.trace_cap));
   if (n > 0 && records) CK(cudaMemcpy(records, B->args.trace, sizeof(double) * 13 * n, cudaMemcpyDeviceToHost));
   *count = n;
+  return VINE_OK;
+}
+
+vine_status vine_get_robot_counters(const vine_batch* B, int32_t* steps_converged, int64_t* evaluations,
+                                    int64_t* cycles, void* stream_v) {
+  if (!B) return fail(VINE_EINVAL, "vine_get_robot_counters: null batch");
+  cudaStream_t st = (cudaStream_t)stream_v;
+  const GrowArgs& a = B->args;
+  const int n = B->n_inst;
+  if (steps_converged) CK(cudaMemcpyAsync(steps_converged, a.conv, 4 * n, cudaMemcpyDeviceToHost, st));
+  if (evaluations) CK(cudaMemcpyAsync(evaluations, a.evals, 8 * n, cudaMemcpyDeviceToHost, st));
+  if (cycles) CK(cudaMemcpyAsync(cycles, a.cycles, 8 * n, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
   return VINE_OK;
 }
 

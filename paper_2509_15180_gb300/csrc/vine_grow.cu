@@ -94,6 +94,7 @@ struct Smem {
   float4* obs;
   float4* act;
   float *TH, *TH0, *DTH, *LUX, *LUY, *G, *DD, *C0, *C1, *C2, *C3, *C4, *C5, *FX, *FY, *TL;
+  float* LX;  // distal-link couplings: g_l contact part, h_ll, q0, q1, q2
 };
 
 __device__ __forceinline__ Smem carve(float* base, const GrowArgs& A) {
@@ -105,6 +106,7 @@ __device__ __forceinline__ Smem carve(float* base, const GrowArgs& A) {
   s.TH = p; s.TH0 = p + n; s.DTH = p + 2 * n; s.LUX = p + 3 * n; s.LUY = p + 4 * n; s.G = p + 5 * n;
   s.DD = p + 6 * n; s.C0 = p + 7 * n; s.C1 = p + 8 * n; s.C2 = p + 9 * n; s.C3 = p + 10 * n; s.C4 = p + 11 * n;
   s.C5 = p + 12 * n; s.FX = p + 13 * n; s.FY = p + 14 * n; s.TL = p + 15 * n;
+  s.LX = p + 16 * n;
   return s;
 }
 
@@ -144,13 +146,10 @@ __device__ __forceinline__ void wrinkle(const GrowArgs& A, float th, float& m, f
   }
 }
 
-struct Acc {
-  float fx, fy, tl, c00, c01, c02, c11, c12, c22, pen2, pen1;
-  float glc, hll, q0, q1, q2;
-};
-
-// One active contact: force kap * pen * n on a disc at fraction fr of the
-// link.  Gauss-Newton part kap w w^T of the link's 3x3 stiffness in twist
+// One active contact: force kap * pen * n on a disc at fraction fr of link j,
+// accumulated into the link's shared-memory arrays (the link belongs to the
+// calling lane; contacts are rare, so the accumulators need no registers).
+// Gauss-Newton part kap w w^T of the link's 3x3 stiffness in twist
 // coordinates about the link start, w = ((x - p) x n, n_x, n_y).  With EXACT
 // also pen times the second derivatives of pen: obstacle curvature
 // -(kap pen kinv) s s^T, s = (n.(x - p), -n_y, n_x) (kinv = 1/distance to the
@@ -158,48 +157,51 @@ struct Acc {
 // load stiffness fr Lu.F on the rotational entry; for the distal link the
 // couplings with its length l.
 template <bool EXACT>
-__device__ __forceinline__ void add_contact(Acc& c, float pen, float nx, float ny, float kinv, float fr, float lx,
-                                            float ly, float kap, bool last, float ulx, float uly) {
+__device__ __forceinline__ void add_contact(const Smem& S, int j, float pen, float nx, float ny, float kinv,
+                                            float fr, float lx, float ly, float kap, bool last, float ulx,
+                                            float uly) {
   const float f = kap * pen;
   const float fx = f * nx, fy = f * ny;
-  c.fx += fx;
-  c.fy += fy;
+  S.FX[j] += fx;
+  S.FY[j] += fy;
   const float rx = fr * lx, ry = fr * ly;
-  c.tl += rx * fy - ry * fx;
+  S.TL[j] += rx * fy - ry * fx;
   const float w0 = rx * ny - ry * nx;
-  c.c00 += kap * w0 * w0;
-  c.c01 += kap * w0 * nx;
-  c.c02 += kap * w0 * ny;
-  c.c11 += kap * nx * nx;
-  c.c12 += kap * nx * ny;
-  c.c22 += kap * ny * ny;
-  c.pen2 += pen * pen;
-  c.pen1 += pen;
+  float c00 = kap * w0 * w0, c01 = kap * w0 * nx, c02 = kap * w0 * ny;
+  float c11 = kap * nx * nx, c12 = kap * nx * ny, c22 = kap * ny * ny;
   float s0 = 0.f, cc = 0.f;
   if (EXACT) {
     s0 = nx * rx + ny * ry;
     cc = f * kinv;
-    c.c00 -= cc * s0 * s0 - (rx * fx + ry * fy);
-    c.c01 += cc * s0 * ny;
-    c.c02 -= cc * s0 * nx;
-    c.c11 -= cc * ny * ny;
-    c.c12 += cc * ny * nx;
-    c.c22 -= cc * nx * nx;
+    c00 -= cc * s0 * s0 - (rx * fx + ry * fy);
+    c01 += cc * s0 * ny;
+    c02 -= cc * s0 * nx;
+    c11 -= cc * ny * ny;
+    c12 += cc * ny * nx;
+    c22 -= cc * nx * nx;
   }
+  S.C0[j] += c00;
+  S.C1[j] += c01;
+  S.C2[j] += c02;
+  S.C3[j] += c11;
+  S.C4[j] += c12;
+  S.C5[j] += c22;
   if (last) {
     const float vl = fr * (nx * ulx + ny * uly);
-    c.glc += fr * (fx * ulx + fy * uly);
-    c.hll += kap * vl * vl;
-    c.q0 += kap * vl * w0;
-    c.q1 += kap * vl * nx;
-    c.q2 += kap * vl * ny;
+    float glc = fr * (fx * ulx + fy * uly), hll = kap * vl * vl;
+    float q0 = kap * vl * w0, q1 = kap * vl * nx, q2 = kap * vl * ny;
     if (EXACT) {
       const float tu = nx * uly - ny * ulx;  // tangent (-n_y, n_x) . u
-      c.hll -= cc * fr * fr * tu * tu;
-      c.q0 -= cc * fr * tu * s0 + fr * (fy * ulx - fx * uly);
-      c.q1 += cc * fr * tu * ny;
-      c.q2 -= cc * fr * tu * nx;
+      hll -= cc * fr * fr * tu * tu;
+      q0 -= cc * fr * tu * s0 + fr * (fy * ulx - fx * uly);
+      q1 += cc * fr * tu * ny;
+      q2 -= cc * fr * tu * nx;
     }
+    S.LX[0] += glc;
+    S.LX[1] += hll;
+    S.LX[2] += q0;
+    S.LX[3] += q1;
+    S.LX[4] += q2;
   }
 }
 
@@ -288,7 +290,6 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
   const float kap = 2.f * A.w_c * I.kc;
   const float floor_d = 1e-6f * A.w_a * I.PR3;
   double Jl = 0.0, Sl = 0.0;
-  Acc last_acc{};
   for (int j = j0; j < j1; ++j) {
     // ---- bending and actuation at joint j (Eq. restoring_moment)
     const float th = S.TH[j];
@@ -342,7 +343,20 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
       xk[k] = ff_add(px, fr * lx);
       yk[k] = ff_add(py, fr * ly);
     }
-    Acc c{};
+    S.FX[j] = 0.f;
+    S.FY[j] = 0.f;
+    S.TL[j] = 0.f;
+    S.C0[j] = 0.f;
+    S.C1[j] = 0.f;
+    S.C2[j] = 0.f;
+    S.C3[j] = 0.f;
+    S.C4[j] = 0.f;
+    S.C5[j] = 0.f;
+    if (last) {
+#pragma unroll
+      for (int q = 0; q < 5; ++q) S.LX[q] = 0.f;
+    }
+    float pen2 = 0.f, pen1 = 0.f;
     for (int o = 0; o < I.n_obs; ++o) {
       const float4 ob = S.obs[o];
 #pragma unroll
@@ -353,23 +367,15 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
         const float pen = disc_pen(ob, dx, dy, I.R, fbx, fby, nx, ny, kinv);
         if (pen > 0.f) {
           const float fr = (float)(k + 1) / (float)KS;
-          if (exact) add_contact<true>(c, pen, nx, ny, kinv, fr, lx, ly, kap, last, ulx, uly);
-          else add_contact<false>(c, pen, nx, ny, kinv, fr, lx, ly, kap, last, ulx, uly);
+          pen2 += pen * pen;
+          pen1 += pen;
+          if (exact) add_contact<true>(S, j, pen, nx, ny, kinv, fr, lx, ly, kap, last, ulx, uly);
+          else add_contact<false>(S, j, pen, nx, ny, kinv, fr, lx, ly, kap, last, ulx, uly);
         }
       }
     }
-    S.FX[j] = c.fx;
-    S.FY[j] = c.fy;
-    S.TL[j] = c.tl;
-    S.C0[j] = c.c00;
-    S.C1[j] = c.c01;
-    S.C2[j] = c.c02;
-    S.C3[j] = c.c11;
-    S.C4[j] = c.c12;
-    S.C5[j] = c.c22;
-    Jl += (double)(A.w_c * I.kc * c.pen2);
-    Sl += (double)(A.w_c * I.kc) * ((double)c.pen2 + 2.0 * (double)I.R * (double)c.pen1);
-    if (last) last_acc = c;
+    Jl += (double)(A.w_c * I.kc * pen2);
+    Sl += (double)(A.w_c * I.kc) * ((double)pen2 + 2.0 * (double)I.R * (double)pen1);
     px = ff_add(px, lx);
     py = ff_add(py, ly);
   }
@@ -403,11 +409,11 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
   E.J = warp_sum(Jl) + (double)A.w_b * (double)I.kg * dlr * dlr;
   E.S = warp_sum(Sl) + (double)A.w_b * (double)I.kg * dlr * dlr;
   const int owner = (N - 1) / B;
-  const float glc = __shfl_sync(kFull, last_acc.glc, owner);
-  E.hll = 2.f * A.w_b * I.kg + __shfl_sync(kFull, last_acc.hll, owner);
-  E.q0 = __shfl_sync(kFull, last_acc.q0, owner);
-  E.q1 = __shfl_sync(kFull, last_acc.q1, owner);
-  E.q2 = __shfl_sync(kFull, last_acc.q2, owner);
+  const float glc = S.LX[0];  // written by the owner lane before the __syncwarp above
+  E.hll = 2.f * A.w_b * I.kg + S.LX[1];
+  E.q0 = S.LX[2];
+  E.q1 = S.LX[3];
+  E.q2 = S.LX[4];
   E.ulx = __shfl_sync(kFull, ulx, owner);
   E.uly = __shfl_sync(kFull, uly, owner);
   E.gl = -2.f * A.w_b * I.kg * (I.l_seg - l) - glc;
@@ -633,6 +639,7 @@ __device__ int solve_step(const GrowArgs& A, const InstDev& I, const Smem& S, in
 
 template <int KS>
 __device__ void process_instance(const GrowArgs& A, int inst, const Smem& S, int lane) {
+  const long long t_start = clock64();
   const InstDev I = A.inst[inst];
   int status = A.status[inst];
   if (status == kBadInput || status == kNonFinite) return;
@@ -680,13 +687,14 @@ __device__ void process_instance(const GrowArgs& A, int inst, const Smem& S, int
     A.evals[inst] += evals;
     A.linkevals[inst] += linkevals;
     A.fallbacks[inst] += fallbacks;
+    A.cycles[inst] += clock64() - t_start;
     if (!(rmax <= A.resid_max[inst])) A.resid_max[inst] = rmax;
   }
   __syncwarp();
 }
 
 template <int KS>
-__global__ void __launch_bounds__(32 * kWarpsPerCta) grow_kernel(const GrowArgs A) {
+__global__ void __launch_bounds__(32 * kWarpsPerCta, 4) grow_kernel(const GrowArgs A) {
   extern __shared__ float4 smem4[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const Smem S = carve(reinterpret_cast<float*>(smem4) + (size_t)warp * A.warp_floats, A);
@@ -758,7 +766,7 @@ const void* pick(int ks) {
 }  // namespace
 
 size_t grow_smem_per_warp(int nmax, int omax, int amax) {
-  return sizeof(float4) * (size_t)(omax + amax) + sizeof(float) * 16 * (size_t)nmax;
+  return sizeof(float4) * (size_t)(omax + amax) + sizeof(float) * (16 * (size_t)nmax + 8);
 }
 
 cudaError_t grow_configure(int ks, size_t smem_per_cta) {

@@ -55,6 +55,7 @@ struct GrowArgs {
   long long* evals;
   long long* linkevals;
   long long* fallbacks;  // Newton steps that fell back to the Gauss-Newton matrix
+  long long* cycles;     // SM clock cycles the owning warp spent on the robot
   double* resid_max;
   const int* order;
   int n_order;

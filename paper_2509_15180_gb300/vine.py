@@ -66,6 +66,7 @@ _SIG = {
     "vine_get_tables": [_p, _p, _p, _p, _p, _p],
     "vine_probe_state": [_p, _i32, _i32, _p, C.c_float, _p, _p, _p, _p, _p],
     "vine_debug_trace": [_p, _i32, _i32],
+    "vine_get_robot_counters": [_p, _p, _p, _p, _p],
     "vine_debug_trace_read": [_p, _p, _i32, _p],
     "vine_batch_destroy": [_p],
 }
@@ -238,6 +239,14 @@ class Batch:
         _check(_lib.vine_probe_state(self.h, int(i), N, _ptr(th), float(l), C.byref(J), _ptr(g), _ptr(dx),
                                      C.byref(r), C.byref(lf)), "vine_probe_state")
         return J.value, g, dx, r.value, bool(lf.value)
+
+    def robot_counters(self, stream=None) -> dict:
+        """Per-robot converged steps, evaluations and SM cycles (vine_get_robot_counters)."""
+        n = self.n_inst
+        out = dict(conv=np.zeros(n, np.int32), evals=np.zeros(n, np.int64), cycles=np.zeros(n, np.int64))
+        _check(_lib.vine_get_robot_counters(self.h, _ptr(out["conv"]), _ptr(out["evals"]), _ptr(out["cycles"]),
+                                            _stream(stream)), "vine_get_robot_counters")
+        return out
 
     def trace(self, inst: int, capacity: int = 4096):
         """Start recording line-search trials of one robot (vine_debug_trace)."""
