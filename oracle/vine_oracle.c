@@ -732,7 +732,8 @@ void orc_set_trace(int on) { g_trace = on; }
  * steps (exact Hessian of J when positive definite, else the Gauss-Newton
  * matrix), the bound 0 <= l <= l_seg handled as an active set,
  * backtracking line search (Armijo, or approximate Wolfe when the cost change
- * is at rounding level), stop when the predicted displacement is at most tol
+ * is at rounding level; a search with no acceptable trial ends the step as
+ * not converged), stop when the predicted displacement is at most tol
  * (the final step is applied).  Algorithm 1 of Sec. 4.1 read as "the stationary point
  * of Eq. (pbd) reached from the warm start". */
 static int solve_step(const inst_t* I, int N, double* th, double* l, int* iters_out, double* resid_out,
@@ -786,22 +787,24 @@ static int solve_step(const inst_t* I, int N, double* th, double* l, int* iters_
     const int l_moves = !((*l <= 0.0 && dx[N] < 0.0) || (*l >= I->l_seg && dx[N] > 0.0));
     const double slope0 = gd + (l_moves ? g[N] * dx[N] : 0.0);
     double alpha = 1.0, Jt = J, lt = *l;
-    int hcount = 0;
+    int hcount = 0, accepted = 0;
     for (int h = 0; h <= p->max_halvings; ++h, ++hcount) {
       for (int k = 0; k < N; ++k) tt[k] = th[k] + alpha * dx[k];
       lt = fmin(fmax(*l + alpha * dx[N], 0.0), I->l_seg);
       Jt = energy(I, N, tt, lt, gt, Ht, &G, &Smt);
       ++evals;
       const double dec = alpha * gd + g[N] * (lt - *l);
-      if (Jt <= J + p->armijo_c1 * dec) break;
+      if (Jt <= J + p->armijo_c1 * dec) { accepted = 1; break; }
       if (fabs(Jt - J) <= p->fval_eps * fmax(Smag, Smt)) {
         double st = 0.0;
         for (int k = 0; k < N; ++k) st += gt[k] * dx[k];
         if (lt > 0.0 && lt < I->l_seg) st += gt[N] * dx[N];
-        if (st <= (2.0 * p->armijo_c1 - 1.0) * slope0) break;
+        if (st <= (2.0 * p->armijo_c1 - 1.0) * slope0) { accepted = 1; break; }
       }
       alpha *= 0.5;
     }
+    /* no acceptable trial: the step ends here, not converged */
+    if (!accepted) { status = ORC_MAXITER; break; }
     if (g_trace)
       fprintf(stderr, "it %3d r %.3e J %.9e alpha %.3g halvings %d l %.5f lfix %d gd %.3e\n", it, r, J, alpha,
               hcount, *l, lfix, gd);

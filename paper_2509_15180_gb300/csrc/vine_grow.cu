@@ -19,7 +19,7 @@
 //   test  : predicted displacement of every link end (FP64 max / N l_seg).
 //   step  : backtracking on the projected path: Armijo on J, or the
 //           approximate Wolfe slope test when the cost change is at FP32
-//           rounding level of J.
+//           rounding level of J; no acceptable trial ends the step.
 // Lanes own contiguous blocks of links; obstacles and actuators of the robot
 // are staged in shared memory; the serial sweeps run warp-uniform.
 #include <cmath>
@@ -608,6 +608,7 @@ __device__ int solve_step(const GrowArgs& A, const InstDev& I, const Smem& S, in
     const bool l_moves = !((l0 <= 0.f && dl < 0.f) || (l0 >= I.l_seg && dl > 0.f));
     const double slope0 = gd + (l_moves ? (double)gl0 * (double)dl : 0.0);
     float alpha = 1.f, lt = l0;
+    bool accepted = false;
     for (int h = 0; h <= A.max_halv; ++h) {
       for (int j = j0; j < j1; ++j) S.TH[j] = S.TH0[j] + alpha * S.DTH[j];
       lt = fminf(fmaxf(l0 + alpha * dl, 0.f), I.l_seg);
@@ -624,9 +625,21 @@ __device__ int solve_step(const GrowArgs& A, const InstDev& I, const Smem& S, in
         if (lt > 0.f && lt < I.l_seg) sl += (double)E.gl * (double)dl;
       }
       trace_rec(A, inst, lane, N, it, h, alpha, r, J0, E.J, dec, slope0, sl, lt, lfix ? 1.0 : 0.0);
-      if (E.J <= J0 + (double)A.c1 * dec) break;
-      if (rounding && sl <= (2.0 * (double)A.c1 - 1.0) * slope0) break;
+      if (E.J <= J0 + (double)A.c1 * dec) {
+        accepted = true;
+        break;
+      }
+      if (rounding && sl <= (2.0 * (double)A.c1 - 1.0) * slope0) {
+        accepted = true;
+        break;
+      }
       alpha *= 0.5f;
+    }
+    if (!accepted) {  // no acceptable trial: the step ends at the last accepted iterate
+      for (int j = j0; j < j1; ++j) S.TH[j] = S.TH0[j];
+      l = l0;
+      __syncwarp();
+      break;
     }
     l = lt;
   }
