@@ -80,7 +80,9 @@ def test_probe_matches_oracle(cfg, exact):
             dg_p = _displacements(orc, i, th_o, float(np.float32(lv)), dg.astype(np.float64))
             do_p = _displacements(orc, i, th_o, float(np.float32(lv)), dxo)
             L = th.size * float(sc["l_seg"][i])
-            e = np.max(np.abs(dg_p - do_p)) / (np.max(np.abs(do_p)) + 1e-6 * L)
+            # floor at 5x the convergence scale: at an equilibrium state both
+            # steps are FP32/FP64 noise of about the tolerance
+            e = np.max(np.abs(dg_p - do_p)) / (np.max(np.abs(do_p)) + 5e-6 * L)
             key = "dx" if thv is th64 else "dx_off"
             worst[key] = max(worst.get(key, 0.0), e)
             worst["r"] = max(worst["r"], abs(rg - ro) / (ro + 1e-6))
