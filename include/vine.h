@@ -257,6 +257,35 @@ vine_status vine_batch_info(const vine_batch* b, int32_t* n_inst, int64_t* total
 /* Releases the batch (device memory freed after synchronising the device). */
 vine_status vine_batch_destroy(vine_batch* b);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free table build.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc -- for example a
+ * process whose device memory is entirely handed to another framework's
+ * pool, or a latency-critical loop in which the device synchronisation that
+ * cudaMalloc/cudaFree imply is not acceptable.
+ *
+ * Builds the sPAM force-per-pressure tables (the same kernels and results as
+ * the tables vine_batch_create builds and vine_get_tables returns) for n_tab
+ * cell lengths l0[n_tab] (device, metres), writing hdr[4 n_tab] (device,
+ * 16-byte aligned) and knots[2 * 256 n_tab] (device, 8-byte aligned) in the
+ * vine_get_tables layout.  Only R_c, R_act, a_spam and m_lo of *params are
+ * used.  Asynchronous on cuda_stream.
+ *
+ * The FP64 working space is a file-scope device array sized for
+ * VINE_NOALLOC_MAX_TABLES tables (133 KB), held by every GPU that loads the
+ * library until the process exits.  n_tab beyond that maximum is rejected
+ * with VINE_EINVAL and nothing is launched.  The call allocates no memory
+ * (no cudaMalloc, cudaFree or allocating library routine).  Its first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.
+ * Every call shares the one array: calls whose work overlaps on the GPU
+ * (other streams, or other host threads on the same device) race on it and
+ * must be serialised by the caller.  No entry of the array needs to start at
+ * zero: each entry a call reads is written earlier by that call. */
+#define VINE_NOALLOC_MAX_TABLES 64
+vine_status vine_spam_tables_noalloc(const double* l0, int32_t n_tab, const vine_params* params, float* hdr,
+                                     float* knots, void* cuda_stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* vine_last_error(void);
 

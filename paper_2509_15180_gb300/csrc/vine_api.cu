@@ -18,19 +18,22 @@
 
 using namespace vine;
 
+namespace vine {
+void set_last_error(const char* msg, const char* detail);
+}
+
 namespace {
 
-thread_local std::string g_err;
+// fixed storage: setting the message never allocates
+thread_local char g_err[512];
 
 vine_status fail(vine_status s, const char* msg) {
-  g_err = msg;
+  std::snprintf(g_err, sizeof(g_err), "%s", msg);
   return s;
 }
 
 vine_status cuda_fail(cudaError_t e, const char* where) {
-  char buf[512];
-  std::snprintf(buf, sizeof(buf), "%s: %s", where, cudaGetErrorString(e));
-  g_err = buf;
+  std::snprintf(g_err, sizeof(g_err), "%s: %s", where, cudaGetErrorString(e));
   return e == cudaErrorMemoryAllocation ? VINE_ENOMEM : VINE_ECUDA;
 }
 
@@ -126,6 +129,10 @@ __global__ void init_kernel(const InitArgs A) {
 
 }  // namespace
 
+void vine::set_last_error(const char* msg, const char* detail) {
+  std::snprintf(g_err, sizeof(g_err), "%s%s", msg, detail ? detail : "");
+}
+
 struct vine_batch {
   int device = 0;
   int n_inst = 0;
@@ -152,7 +159,7 @@ struct vine_batch {
 
 extern "C" {
 
-const char* vine_last_error(void) { return g_err.c_str(); }
+const char* vine_last_error(void) { return g_err; }
 
 vine_status vine_params_default(vine_params* p) {
   if (!p) return fail(VINE_EINVAL, "vine_params_default: null pointer");

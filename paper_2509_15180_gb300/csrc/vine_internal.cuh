@@ -91,6 +91,9 @@ cudaError_t launch_spam_tables(const double* l0, int n_tab, double R_c, double R
 cudaError_t launch_wrinkle_table(double eps_c, const GaussLegendre& gl, float2* utab, double* scratch,
                                  double* consts /*device [4]: U(pi), m(pi), theta_c, h*/, cudaStream_t s);
 
+// Thread-local message returned by vine_last_error (fixed storage; vine_api.cu).
+void set_last_error(const char* msg, const char* detail = nullptr);
+
 // Growth kernel -- vine_grow.cu
 cudaError_t launch_grow(const GrowArgs& a, int ks, int grid, int block, size_t smem, cudaStream_t s);
 size_t grow_smem_per_warp(int nmax, int omax, int amax);

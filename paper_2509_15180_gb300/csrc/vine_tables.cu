@@ -281,3 +281,81 @@ cudaError_t launch_wrinkle_table(double eps_c, const GaussLegendre& gl, float2* 
 }
 
 }  // namespace vine
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the sPAM table build.  The FP64 scratch lives in
+// a file-scope device array; host code never uses the array's name as an
+// address (it is a host-side stand-in), only the pointer that
+// cudaGetSymbolAddress returns for the current device, fetched once per
+// device on that device's first call.
+// ---------------------------------------------------------------------------
+#include <cstdint>
+#include <mutex>
+
+#include "vine.h"
+
+namespace {
+
+constexpr int kNoallocScratchDoubles = VINE_NOALLOC_MAX_TABLES * (4 + vine::kKnots);
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) double g_table_scratch[kNoallocScratchDoubles];
+
+std::mutex g_scratch_mu;
+double* g_scratch_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array for the current device (set-up on the
+// first call per device).  Returns cudaSuccess or the runtime's error.
+cudaError_t scratch_for_current_device(double** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_table_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_scratch_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" vine_status vine_spam_tables_noalloc(const double* l0, int32_t n_tab, const vine_params* params,
+                                                float* hdr, float* knots, void* cuda_stream) {
+  if (!l0 || !params || !hdr || !knots) {
+    vine::set_last_error("vine_spam_tables_noalloc: null argument");
+    return VINE_EINVAL;
+  }
+  if (n_tab < 1 || n_tab > VINE_NOALLOC_MAX_TABLES) {
+    vine::set_last_error("vine_spam_tables_noalloc: n_tab must be 1..VINE_NOALLOC_MAX_TABLES (64)");
+    return VINE_EINVAL;
+  }
+  if ((reinterpret_cast<uintptr_t>(hdr) & 15) != 0 || (reinterpret_cast<uintptr_t>(knots) & 7) != 0) {
+    vine::set_last_error("vine_spam_tables_noalloc: hdr must be 16-byte and knots 8-byte aligned");
+    return VINE_EINVAL;
+  }
+  const vine_params& p = *params;
+  if (!(p.R_c > 0.0 && p.R_act > p.R_c) || !(p.m_lo > 0.0 && p.m_lo < 0.5) || !(p.a_spam >= 0.0)) {
+    vine::set_last_error("vine_spam_tables_noalloc: parameter out of range");
+    return VINE_EINVAL;
+  }
+  double* scratch = nullptr;
+  cudaError_t e = scratch_for_current_device(&scratch);
+  if (e == cudaSuccess) {
+    vine::GaussLegendre gl;
+    vine::gauss_legendre(24, &gl);
+    // every scratch entry the kernels read is written earlier in the same
+    // call, so nothing needs clearing between calls
+    e = vine::launch_spam_tables(l0, n_tab, p.R_c, p.R_act, p.a_spam, p.m_lo, gl, reinterpret_cast<float4*>(hdr),
+                                 reinterpret_cast<float2*>(knots), scratch, static_cast<cudaStream_t>(cuda_stream));
+  }
+  if (e != cudaSuccess) {
+    vine::set_last_error("vine_spam_tables_noalloc: ", cudaGetErrorString(e));
+    return VINE_ECUDA;
+  }
+  return VINE_OK;
+}

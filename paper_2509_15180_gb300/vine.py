@@ -67,6 +67,7 @@ _SIG = {
     "vine_probe_state": [_p, _i32, _i32, _p, C.c_float, _p, _p, _p, _p, _p],
     "vine_debug_trace": [_p, _i32, _i32],
     "vine_get_robot_counters": [_p, _p, _p, _p, _p],
+    "vine_spam_tables_noalloc": [_p, _i32, _p, _p, _p, _p],
     "vine_debug_trace_read": [_p, _p, _i32, _p],
     "vine_batch_destroy": [_p],
 }
@@ -117,6 +118,18 @@ def vine_params_default() -> vine_params:
     p = vine_params()
     _check(_lib.vine_params_default(C.byref(p)), "vine_params_default")
     return p
+
+
+NOALLOC_MAX_TABLES = 64
+
+
+def vine_spam_tables_noalloc(l0, hdr, knots, params: vine_params | None = None, stream=None):
+    """Allocation-free sPAM table build (vine_spam_tables_noalloc).  l0: CUDA
+    float64 tensor [n_tab]; hdr: CUDA float32 [n_tab, 4]; knots: CUDA float32
+    [n_tab, 256, 2] -- all allocated by the caller."""
+    prm = params if params is not None else vine_params_default()
+    _check(_lib.vine_spam_tables_noalloc(_ptr(l0), int(l0.numel()), C.byref(prm), _ptr(hdr), _ptr(knots),
+                                         _stream(stream)), "vine_spam_tables_noalloc")
 
 
 # -------------------------------------------------------------------------
