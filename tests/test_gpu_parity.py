@@ -193,13 +193,15 @@ def test_uneven_batch_sampled():
     st = b.state()
     counts, pairs = b.contacts(512)
     assert np.all((st["N"] == sc["n_links"]) | (st["status"] == vine.INST_NONFINITE))
-    idx = np.array([0, 5, 17, 33, 61, 90])
+    idx = np.arange(0, 96, 6)
     sub = scenes.subset(sc, idx)
     orc = _oracle(sub)
     ost = orc.new_state()
     orc.run(ost, 400, threads=THREADS)
     cls = _classify(b, st, orc, ost, sub, counts, pairs, idx_gpu=idx)
-    assert cls.count("match") >= 4
+    print("uneven sample: %d match, %d basin switches, %d flagged" % (cls.count("match"), cls.count("switch"),
+                                                                     cls.count("flagged")))
+    assert cls.count("match") >= len(idx) // 2
     b.close()
 
 
