@@ -91,6 +91,8 @@ def lib():
         L.orc_sdf.argtypes = [p, i, d, d, p, p]
         L.orc_gn_step.restype = i
         L.orc_gn_step.argtypes = [p, p, p, i, i, p, d, p, p, p, p]
+        L.orc_grad.restype = i
+        L.orc_grad.argtypes = [p, p, p, i, i, p, d, d, d, p, p, p, p]
         L.orc_set_trace.argtypes = [i]
         L.orc_run.restype = i
         L.orc_run.argtypes = [p, p, p, i, p, p, p, p, p, p, p, p, p, i]
@@ -246,6 +248,19 @@ class Oracle:
         if rc != 0:
             raise ValueError("Gauss-Newton matrix not positive definite")
         return dx, r.value, J.value, bool(lf.value)
+
+    def grad(self, i: int, theta, l: float, goal):
+        """Tip-distance cost |p_N - goal| at the equilibrium (theta, l) and its
+        adjoint derivatives with respect to each actuator's pressure (per Pa),
+        begin and end (per link unit).  Returns (cost, dP, dB, dE, status);
+        status 1 = exact Hessian not positive definite (NaN derivatives)."""
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        na = int(self._keep["act_ptr"][i + 1] - self._keep["act_ptr"][i])
+        dP, dB, dE = np.zeros(max(na, 1)), np.zeros(max(na, 1)), np.zeros(max(na, 1))
+        c = C.c_double()
+        rc = lib().orc_grad(C.byref(self.P), C.byref(self.B), self.T, int(i), th.size, _ptr(th), float(l),
+                            float(goal[0]), float(goal[1]), C.byref(c), _ptr(dP), _ptr(dB), _ptr(dE))
+        return c.value, dP[:na], dB[:na], dE[:na], rc
 
     def poses(self, i: int, theta, l: float):
         th = np.ascontiguousarray(theta, dtype=np.float64)

@@ -891,6 +891,69 @@ int orc_gn_step(const orc_params* p, const orc_batch* b, const orc_tables* T, in
   return rc;
 }
 
+/* Adjoint of the tip-distance cost at an equilibrium of the last growth
+ * step (implicit differentiation, for the design optimisation of Sec. 5).
+ * At the state x* = (theta, l) with grad J(x*) = 0:
+ *   cost c = |p_N - goal|, p_N the distal end point;
+ *   lambda solves H lambda = dc/dx on the free unknowns, H the exact Hessian
+ *     of J, with l dropped when its bound is active (the solver's rule);
+ *   dc/dq = -lambda . d(grad J)/dq for the pressure q = P_a and the span ends
+ *     q = b_a, e_a of each actuator of the instance.
+ * grad J depends on P_a and the span only through the actuator moment
+ * c_aj s_a P_a f_a(eps_aj) d of Eq. (restoring_moment): linearly in P_a,
+ * and through the coverage c_aj = |[j, j+1) n [b_a, e_a)| in the ends, whose
+ * (right) derivatives are -1 on link floor(b_a) and +1 on link floor(e_a)
+ * (links that exist only).  The earlier growth steps do not enter: every
+ * link but the distal one has its fixed length l_seg, so J at the last step
+ * depends on the design only through the terms above.
+ * Outputs dP, dB, dE have one entry per actuator of instance i.  Returns 0,
+ * or 1 when the exact Hessian is not positive definite at x* (no gradient;
+ * outputs NaN). */
+int orc_grad(const orc_params* p, const orc_batch* b, const orc_tables* T, int i, int N, const double* th,
+             double l, double gx, double gy, double* cost, double* dP, double* dB, double* dE) {
+  inst_t I;
+  inst_init(&I, p, b, T, i);
+  const int n = N + 1, na = I.a1 - I.a0;
+  geo_t G;
+  geo_alloc(&G, N);
+  double* g = (double*)malloc(sizeof(double) * n);
+  double* H = (double*)malloc(sizeof(double) * n * n);
+  double* rhs = (double*)malloc(sizeof(double) * n);
+  double* lam = (double*)malloc(sizeof(double) * n);
+  energy_h(&I, N, th, l, g, H, &G, NULL, 1);
+  const double ex = G.px[N] - gx, ey = G.py[N] - gy;
+  const double c = sqrt(ex * ex + ey * ey);
+  *cost = c;
+  const double sx = c > 0.0 ? ex / c : 0.0, sy = c > 0.0 ? ey / c : 0.0;
+  /* dc/dtheta_j = s . (z x (p_N - p_j)), dc/dl = s . u_{N-1} */
+  for (int j = 0; j < N; ++j) rhs[j] = -sx * (G.py[N] - G.py[j]) + sy * (G.px[N] - G.px[j]);
+  rhs[N] = N > 0 ? sx * G.ux[N - 1] + sy * G.uy[N - 1] : 0.0;
+  const int lfix = (l <= 0.0 && g[N] > 0.0) || (l >= I.l_seg && g[N] < 0.0);
+  const int m = lfix ? N : n;
+  int rc = N > 0 ? chol_solve(H, n, m, rhs, lam) : 0;
+  if (lfix) lam[N] = 0.0;
+  for (int a = 0; a < na; ++a) {
+    dP[a] = dB[a] = dE[a] = rc ? NAN : 0.0;
+    if (rc) continue;
+    const int ga = I.a0 + a;
+    const double bg = b->act_begin[ga], en = b->act_end[ga];
+    const double s = (double)b->act_side[ga], Pa = b->act_pressure[ga];
+    const orc_table* t = &T->tab[T->act_tab[ga]];
+    const double jb = floor(bg), je = floor(en);
+    for (int j = 0; j < N; ++j) {
+      double f, fp;
+      table_f(t, s * I.d * th[j] / I.l_seg, &f, &fp);
+      /* d g_j / d P_a = -w_a c_aj s f d */
+      dP[a] += lam[j] * p->w_a * coverage(bg, en, j) * s * f * I.d;
+      if (bg < en && (double)j == jb) dB[a] -= lam[j] * p->w_a * s * Pa * f * I.d;
+      if (bg < en && (double)j == je) dE[a] += lam[j] * p->w_a * s * Pa * f * I.d;
+    }
+  }
+  free(g); free(H); free(rhs); free(lam);
+  geo_free(&G);
+  return rc ? 1 : 0;
+}
+
 /* Link start points p_0..p_N and headings psi_0..psi_{N-1}. */
 void orc_poses(const orc_params* p, const orc_batch* b, const orc_tables* T, int i, int N, const double* th,
                double l, double* px, double* py, double* psi) {

@@ -147,21 +147,22 @@ def config3(n_inst: int = 16384, replicate: int = 0, n_range=(30, 300)) -> dict:
     return _pack(rows)
 
 
-def config4(n_designs: int = 64, n_perturb: int = 1024, replicate: int = 0) -> tuple[dict, np.ndarray]:
+def config4(n_designs: int = 64, n_perturb: int = 1024, replicate: int = 0, n_links: int = 150,
+            box: float = 2.25, n_circ: int = 30, n_box: int = 30) -> tuple[dict, np.ndarray]:
     """Robustness batch: designs as config 2 with 150 links and 60 obstacles in
     a 2.25 m box, each perturbed n_perturb times (obstacle centres + N(0, 1 cm),
     actuator endpoints + N(0, 0.5 link), pressures x U[0.95, 1.05]).  Returns
     the scene and one goal point per instance (uniform in the far half of the
-    design's box)."""
+    design's box).  The keyword sizes give smaller variants for tests."""
     rng = _rng(4, replicate)
     rows, goals = [], []
     for _ in range(n_designs):
-        N, ls = 150, 0.015
+        N, ls = n_links, 0.015
         R = rng.uniform(0.02, 0.04)
         P = rng.uniform(2000.0, 10000.0)
         acts = _actuators(rng, int(rng.integers(0, 7)), N, (3, 15), (0.0, 15000.0))
-        S = 2.25
-        obs = _obstacles(rng, 30, 30, (0.01, 0.05), (0.01, 0.05), 0.05, S, R + ls)
+        S = box
+        obs = _obstacles(rng, n_circ, n_box, (0.01, 0.05), (0.01, 0.05), 0.05, S, R + ls)
         goal = (rng.uniform(0.05 + 0.5 * S, 0.05 + S), rng.uniform(-0.5 * S, 0.5 * S))
         for _ in range(n_perturb):
             pk, pcx, pcy, pa, pb = obs

@@ -79,7 +79,6 @@ def test_probe_matches_oracle(cfg, exact):
             th_o = th32.astype(np.float64)
             dg_p = _displacements(orc, i, th_o, float(np.float32(lv)), dg.astype(np.float64))
             do_p = _displacements(orc, i, th_o, float(np.float32(lv)), dxo)
-            L = th.size * float(sc["l_seg"][i])
             # in link lengths: at an equilibrium state both steps are FP32/FP64
             # noise, so the bar is the pose tolerance (1e-4 link lengths) plus
             # 1% of the step
@@ -87,14 +86,15 @@ def test_probe_matches_oracle(cfg, exact):
             e = np.max(np.abs(dg_p - do_p)) / (1e-4 * ls + 1e-2 * np.max(np.abs(do_p)))
             key = "dx" if thv is th64 else "dx_off"
             worst[key] = max(worst.get(key, 0.0), e)
-            worst["r"] = max(worst["r"], abs(rg - ro) / (ro + 1e-6))
+            # the residual is relative to the robot length and tested against
+            # tol = 1e-6: at equilibrium both sides read FP32/FP64 noise of
+            # about that size, so the bar is tol plus 2% of the residual
+            worst["r"] = max(worst["r"], abs(rg - ro) / (1e-6 + 2e-2 * ro))
     print("probe cfg %d exact %d worst relative errors: %s" % (cfg, exact, worst))
     # FP32 terms and the Hermite-tabulated wrinkling energy near onset
     assert worst["J"] < 1e-4
     assert worst["g"] < 5e-3  # FP32 contact forces: ~1e-8 m penetration error x stiffness x lever
     assert worst["dx"] < 1.0
-    # off equilibrium (deep contacts) the FP32 contact forces carry ~1e-3
-    # relative error which the soft bending modes amplify: a looser bar
-    assert worst.get("dx_off", 0.0) < 50.0
-    assert worst["r"] < 1e-2
+    assert worst.get("dx_off", 0.0) < 1.0
+    assert worst["r"] < 1.0
     b.close()
