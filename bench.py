@@ -35,6 +35,10 @@ UNIT = "robot-link-steps/s"
 WORKLOAD = "design-optimisation batch: 4096 robots x 100 links (1.5 cm), 20 circles + 20 boxes, 0-6 sPAM actuators"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
 L2_FLUSH_BYTES = 512 << 20
+# DRAM bytes (read + write) of one growth launch per robot, from an ncu
+# capture of one launch over 1024 robots x 100 links of this workload:
+# designs and obstacles are read once per robot, so traffic scales with robots.
+GROW_DRAM_BYTES_PER_ROBOT = (1.558784e6 + 2.816e3) / 1024
 
 
 def _dist():
@@ -190,8 +194,11 @@ def run_gpu(args):
              14.0 * (st_last["pair_tests"] - st_last["circle_pair_tests"]))
     launch_s = float(np.mean(step_ms)) / 1e3
     achieved = flops / launch_s / 1e12
+    traffic = args.traffic if args.traffic is not None else GROW_DRAM_BYTES_PER_ROBOT * n
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": args.traffic,
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of a 1024-robot launch, "
+                                  "scaled by robots",
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived; MEASURED_PEAKS has no FP32 figure)",
                 "flops_per_launch": flops}
 
