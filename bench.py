@@ -157,6 +157,21 @@ def run_gpu(args):
               "evals_max": int(rc["evals"].max()),
               "what": "per-robot time its warp spent (clock64 at 2.07 GHz) in the last timed step"}
 
+    # --- adjoint (vine_grad) at the final equilibria of the last timed step
+    goals = torch.from_numpy(scenes.goal_points(len(sc["n_links"]), 1.5, replicate=rank)).cuda()
+    b.grad(goals, stream)
+    torch.cuda.synchronize()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    gout = b.grad(goals, stream)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    gstat = gout["status"].cpu().numpy()
+    adjoint = {"ms": a0.elapsed_time(a1), "robots": int(gstat.size), "ok": int((gstat == 0).sum()),
+               "not_pd": int((gstat == 1).sum()), "no_state": int((gstat == 2).sum()),
+               "what": "one vine_grad launch: tip-distance cost and its derivatives w.r.t. every actuator's "
+                       "pressure and span at every robot's final equilibrium"}
+
     # --- end to end through the C ABI with host buffers (create/copy in, grow, read back)
     e2e_steps = 0 if args.no_e2e else max(2, min(args.steps, 5))
     host = {k: np.ascontiguousarray(v) for k, v in sc.items()}
@@ -216,6 +231,7 @@ def run_gpu(args):
                        "robot_link_steps_per_step": rls_per_step, "l2": "flushed between timed steps (512 MiB write)",
                        "tol": 1e-6},
             "e2e": e2e, "plain": plain, "latency": lat, "roofline": roofline, "cpu_baseline": cpu,
+            "adjoint": adjoint,
             "clocks": ck, "gpu_launches": args.steps, "robots": robots,
             "solver": {"iters_per_step": st_last["iterations"] / max(st_last["steps_total"], 1),
                        "evals_per_step": st_last["evaluations"] / max(st_last["steps_total"], 1),

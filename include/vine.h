@@ -207,6 +207,39 @@ vine_status vine_get_state(const vine_batch* b, float* theta, float* l_last, flo
 vine_status vine_get_contacts(const vine_batch* b, int32_t* counts, int32_t* pairs, int32_t max_pairs,
                               int32_t out_is_device, void* cuda_stream);
 
+/* Replaces every actuator's pressure and span (arrays [sum n_act] in the
+ * descriptor's actuator order; Pa and link units), keeping its side and cell
+ * length, for the next growth from reset: the design update of an
+ * optimisation loop without rebuilding the batch or its tables.  Values that
+ * fail the create-time checks (finite, 0 <= begin < end, pressure >= 0) mark
+ * the instance VINE_INST_BADINPUT until the batch is recreated.
+ * ptrs_are_device as for vine_grad (host pointers: the stream is
+ * synchronised; device pointers: async). */
+vine_status vine_set_actuators(vine_batch* b, const float* pressure, const float* begin, const float* end,
+                               int32_t ptrs_are_device, void* cuda_stream);
+
+/* Adjoint of the equilibrium (implicit differentiation; the gradient a
+ * design optimisation over the models of Sec. 3 needs).  For every instance,
+ * at its current state taken as the equilibrium of its last growth step:
+ *   cost[n] = |p_tip - goal|, goal_xy[2n] absolute goal points (m);
+ *   d_pressure, d_begin, d_end [sum n_act] (CSR by act_ptr, the descriptor's
+ *     actuator order): d cost / d P_a (per Pa), d cost / d b_a and
+ *     d cost / d e_a (per link unit; right derivatives at integer ends);
+ *   grad_status[n]: 0 ok; 1 the exact Hessian of the cost of Eq. (pbd) is
+ *     not positive definite at the state (derivatives NaN); 2 the instance
+ *     has no valid state (bad input or non-finite; cost and derivatives NaN).
+ * lambda = H^-1 d cost / d x (x = joint angles and the distal length, the
+ * distal length dropped when its bound is active, as in the solver), then
+ * d cost / d q = -lambda . d(grad J)/dq: grad J depends on an actuator's
+ * pressure and span only through its moment c_aj s_a P_a f_a(eps_aj) d
+ * (Eq. restoring_moment).  An instance with no links has cost |base - goal|
+ * and zero derivatives.
+ * ptrs_are_device = 1: every pointer is a device pointer (async on
+ * cuda_stream); 0: host pointers (staged through a library-owned device
+ * buffer; the stream is synchronised).  The batch state is not changed. */
+vine_status vine_grad(const vine_batch* b, const float* goal_xy, double* cost, double* d_pressure, double* d_begin,
+                      double* d_end, int32_t* grad_status, int32_t ptrs_are_device, void* cuda_stream);
+
 /* Batch counters (host struct; synchronises the stream). */
 vine_status vine_get_stats(const vine_batch* b, vine_stats* out, void* cuda_stream);
 

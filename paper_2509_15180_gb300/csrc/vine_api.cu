@@ -127,6 +127,27 @@ __global__ void init_kernel(const InitArgs A) {
   }
 }
 
+// New actuator pressures and spans for every instance (one warp per
+// instance); the side and table index are kept.  Invalid values mark the
+// instance BADINPUT, in the validated status too (so reset keeps it).
+__global__ void actuator_update_kernel(const InstDev* inst, int n_inst, const float* pressure, const float* begin,
+                                       const float* end, float4* act, int* status0, int* status) {
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (i >= n_inst) return;
+  const InstDev I = inst[i];
+  bool badl = false;
+  for (int k = lane; k < I.n_act; k += 32) {
+    const int a = I.act_off + k;
+    const float b = begin[a], e = end[a], pa = pressure[a];
+    badl = badl || !(fin(b) && fin(e) && b >= 0.f && e > b && fin(pa) && pa >= 0.f);
+    act[a] = make_float4(b, e, pa, act[a].w);
+  }
+  if (__any_sync(0xffffffffu, badl) && lane == 0) {
+    status0[i] = kBadInput;
+    status[i] = kBadInput;
+  }
+}
+
 }  // namespace
 
 void vine::set_last_error(const char* msg, const char* detail) {
@@ -137,6 +158,7 @@ struct vine_batch {
   int device = 0;
   int n_inst = 0;
   int64_t total_links = 0;
+  int n_act = 0;
   int n_tab = 0;
   vine_params params{};
   int ks = 2;
@@ -279,6 +301,7 @@ vine_status vine_batch_create(const vine_batch_desc* D, const vine_params* P, vo
     }
   }
   B->n_tab = (int)tabs.size();
+  B->n_act = n_act;
   const int nt = std::max(B->n_tab, 1);
 
   // ---- device memory
@@ -640,6 +663,79 @@ vine_status vine_get_contacts(const vine_batch* B, int32_t* counts, int32_t* pai
                      st));
   CK(cudaMemcpyAsync(counts, d_c, 4 * (size_t)n, cudaMemcpyDeviceToHost, st));
   if (pb) CK(cudaMemcpyAsync(pairs, d_p, pb, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return VINE_OK;
+}
+
+vine_status vine_set_actuators(vine_batch* B, const float* pressure, const float* begin, const float* end,
+                               int32_t ptrs_are_device, void* stream_v) {
+  if (!B) return fail(VINE_EINVAL, "vine_set_actuators: null batch");
+  const size_t na = (size_t)B->n_act;
+  if (na == 0) return VINE_OK;
+  if (!pressure || !begin || !end) return fail(VINE_EINVAL, "vine_set_actuators: null argument");
+  cudaStream_t st = (cudaStream_t)stream_v;
+  const float *dp = pressure, *db = begin, *de = end;
+  if (!ptrs_are_device) {
+    vine_status s = ensure_stage(B, 3 * align256(4 * na));
+    if (s != VINE_OK) return s;
+    char* sg = (char*)B->stage;
+    CK(cudaMemcpyAsync(sg, pressure, 4 * na, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(sg + align256(4 * na), begin, 4 * na, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(sg + 2 * align256(4 * na), end, 4 * na, cudaMemcpyHostToDevice, st));
+    dp = (const float*)sg;
+    db = (const float*)(sg + align256(4 * na));
+    de = (const float*)(sg + 2 * align256(4 * na));
+  }
+  const GrowArgs& a = B->args;
+  const int threads = 128, blocks = (B->n_inst * 32 + threads - 1) / threads;
+  actuator_update_kernel<<<blocks, threads, 0, st>>>(a.inst, B->n_inst, dp, db, de, const_cast<float4*>(a.act),
+                                                     B->status0, a.status);
+  CK(cudaGetLastError());
+  if (!ptrs_are_device) CK(cudaStreamSynchronize(st));
+  return VINE_OK;
+}
+
+vine_status vine_grad(const vine_batch* B, const float* goal_xy, double* cost, double* d_pressure, double* d_begin,
+                      double* d_end, int32_t* grad_status, int32_t ptrs_are_device, void* stream_v) {
+  if (!B || !goal_xy || !cost || !grad_status || (B->n_act > 0 && (!d_pressure || !d_begin || !d_end)))
+    return fail(VINE_EINVAL, "vine_grad: null argument");
+  cudaStream_t st = (cudaStream_t)stream_v;
+  const int n = B->n_inst;
+  const size_t na = (size_t)B->n_act;
+  // one warp per CTA, several CTAs per SM; the robots come longest first
+  const int grid = std::max(1, std::min(n, B->grid * kWarpsPerCta));
+  GradArgs g{};
+  if (ptrs_are_device) {
+    g.goal = goal_xy;
+    g.cost = cost;
+    g.dP = d_pressure;
+    g.dB = d_begin;
+    g.dE = d_end;
+    g.gstat = grad_status;
+    CK(launch_grad(B->args, g, B->ks, grid, B->smem_warp, st));
+    return VINE_OK;
+  }
+  const size_t o_goal = 0, o_cost = align256(8 * (size_t)n), o_stat = o_cost + align256(8 * (size_t)n),
+               o_dp = o_stat + align256(4 * (size_t)n), o_db = o_dp + align256(8 * std::max<size_t>(na, 1)),
+               o_de = o_db + align256(8 * std::max<size_t>(na, 1)), total = o_de + align256(8 * std::max<size_t>(na, 1));
+  vine_status s = ensure_stage(B, total);
+  if (s != VINE_OK) return s;
+  char* sg = (char*)B->stage;
+  g.goal = (const float*)(sg + o_goal);
+  g.cost = (double*)(sg + o_cost);
+  g.gstat = (int*)(sg + o_stat);
+  g.dP = (double*)(sg + o_dp);
+  g.dB = (double*)(sg + o_db);
+  g.dE = (double*)(sg + o_de);
+  CK(cudaMemcpyAsync(sg + o_goal, goal_xy, 8 * (size_t)n, cudaMemcpyHostToDevice, st));
+  CK(launch_grad(B->args, g, B->ks, grid, B->smem_warp, st));
+  CK(cudaMemcpyAsync(cost, g.cost, 8 * (size_t)n, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(grad_status, g.gstat, 4 * (size_t)n, cudaMemcpyDeviceToHost, st));
+  if (na) {
+    CK(cudaMemcpyAsync(d_pressure, g.dP, 8 * na, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(d_begin, g.dB, 8 * na, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(d_end, g.dE, 8 * na, cudaMemcpyDeviceToHost, st));
+  }
   CK(cudaStreamSynchronize(st));
   return VINE_OK;
 }

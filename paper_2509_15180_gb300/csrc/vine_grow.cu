@@ -762,6 +762,123 @@ __global__ void __launch_bounds__(32) probe_kernel(const GrowArgs A, int inst, i
   }
 }
 
+// Force per unit pressure of sPAM table `tid` at strain e (the piecewise-
+// linear table of Sec. 3.1; held below its first knot, zero beyond its last).
+__device__ __forceinline__ float spam_force(const GrowArgs& A, int tid, float e) {
+  const float4 hd = A.tab_hdr[tid];
+  const float2* tb = A.tab + (size_t)tid * kKnots;
+  const float uu = (e - hd.x) * hd.z;
+  if (uu <= 0.f) return tb[0].x;
+  if (uu >= (float)(kKnots - 1)) return 0.f;
+  const int k = (int)uu;
+  const float tau = uu - (float)k;
+  return tb[k].x + tau * (tb[k + 1].x - tb[k].x);
+}
+
+// Adjoint of the tip-distance cost c = |p_N - goal| at one robot's current
+// state, taken as the equilibrium of its last growth step (implicit
+// differentiation): lambda = H^-1 dc/dx with H the exact Hessian of the cost
+// of Eq. (pbd) (the articulated sweep of gn_solve with the right-hand side
+// replaced), then dc/dq = -lambda . d(grad J)/dq.  grad J depends on an
+// actuator's pressure P_a and span [b_a, e_a) only through its moment
+// c_aj s_a P_a f_a(eps_aj) d (Eq. restoring_moment): linearly in P_a, and
+// through the coverage c_aj, whose right derivatives are -1 on link
+// floor(b_a) and +1 on link floor(e_a).  Status: 0 ok, 1 the exact Hessian is
+// not positive definite there (derivatives NaN), 2 the robot has no valid
+// state (bad input or non-finite; cost and derivatives NaN).
+template <int KS>
+__device__ void grad_instance(const GrowArgs& A, const GradArgs& G, int inst, const Smem& S, int lane) {
+  const InstDev I = A.inst[inst];
+  const int N = A.n_cur[inst];
+  const int st = A.status[inst];
+  const float gx = G.goal[2 * inst] - I.bx, gy = G.goal[2 * inst + 1] - I.by;
+  const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+  if (st == kBadInput || st == kNonFinite || N <= 0) {
+    const bool ok = (N <= 0 && st != kBadInput && st != kNonFinite);
+    for (int a = lane; a < I.n_act; a += 32) {
+      G.dP[I.act_off + a] = ok ? 0.0 : qnan;
+      G.dB[I.act_off + a] = ok ? 0.0 : qnan;
+      G.dE[I.act_off + a] = ok ? 0.0 : qnan;
+    }
+    if (lane == 0) {
+      G.cost[inst] = ok ? sqrt((double)gx * gx + (double)gy * gy) : qnan;
+      G.gstat[inst] = ok ? 0 : 2;
+    }
+    return;
+  }
+  for (int k = lane; k < I.n_obs; k += 32) S.obs[k] = A.obs[I.obs_off + k];
+  for (int k = lane; k < I.n_act; k += 32) S.act[k] = A.act[I.act_off + k];
+  for (int k = lane; k < N; k += 32) S.TH[k] = A.theta[I.th_off + k];
+  const float l = A.l_cur[inst];
+  __syncwarp();
+  EvalOut E = eval<KS>(A, I, S, N, l, lane, true);
+  const bool lfix = (l <= 0.f && E.gl > 0.f) || (l >= I.l_seg && E.gl < 0.f);
+  // tip relative to the base, and dc/dtheta_j = s . (z x (p_N - p_j))
+  const int B = (N + 31) >> 5;
+  const int j0 = min(lane * B, N), j1 = min(j0 + B, N);
+  float sx = 0.f, sy = 0.f;
+  for (int j = j0; j < j1; ++j) {
+    sx += S.LUX[j];
+    sy += S.LUY[j];
+  }
+  float rx = warp_excl_suffix(sx, lane), ry = warp_excl_suffix(sy, lane);
+  const float tx = __shfl_sync(kFull, rx + sx, 0), ty = __shfl_sync(kFull, ry + sy, 0);
+  const double ex = (double)tx - (double)gx, ey = (double)ty - (double)gy;
+  const double c = sqrt(ex * ex + ey * ey);
+  const float ux = c > 0.0 ? (float)(ex / c) : 0.f, uy = c > 0.0 ? (float)(ey / c) : 0.f;
+  for (int j = j1 - 1; j >= j0; --j) {
+    rx += S.LUX[j];
+    ry += S.LUY[j];
+    S.G[j] = ux * ry - uy * rx;  // minus dc/dtheta_j: the sweep solves H x = -G
+  }
+  E.gl = -(ux * E.ulx + uy * E.uly);
+  __syncwarp();
+  float dl, mdth;
+  const double r = gn_solve(I, S, N, lfix, E, dl, lane, true, mdth);
+  const bool ok = r >= 0.0 && isfinite(r);
+  for (int a = 0; a < I.n_act; ++a) {
+    const float4 ac = S.act[a];
+    const int bits = __float_as_int(ac.w);
+    const float side = bits < 0 ? -1.f : 1.f;
+    const int tid = bits & 0x7fffffff;
+    const float jb = floorf(ac.x), je = floorf(ac.y);
+    const bool span = ac.x < ac.y;
+    double sP = 0.0, sB = 0.0, sE = 0.0;
+    for (int j = j0; j < j1; ++j) {
+      const float cov = fminf(ac.y, (float)(j + 1)) - fmaxf(ac.x, (float)j);
+      const bool isb = span && (float)j == jb, ise = span && (float)j == je;
+      if (!(cov > 0.f) && !isb && !ise) continue;
+      const float f = spam_force(A, tid, side * I.d * S.TH[j] / I.l_seg);
+      const double m = (double)A.w_a * side * f * I.d * (double)S.DTH[j];  // -lambda_j d g_j / d(c_aj P_a)
+      if (cov > 0.f) sP += m * cov;
+      if (isb) sB -= m * ac.z;
+      if (ise) sE += m * ac.z;
+    }
+    sP = warp_sum(sP);
+    sB = warp_sum(sB);
+    sE = warp_sum(sE);
+    if (lane == 0) {
+      G.dP[I.act_off + a] = ok ? sP : qnan;
+      G.dB[I.act_off + a] = ok ? sB : qnan;
+      G.dE[I.act_off + a] = ok ? sE : qnan;
+    }
+  }
+  if (lane == 0) {
+    G.cost[inst] = c;
+    G.gstat[inst] = ok ? 0 : 1;
+  }
+  __syncwarp();
+}
+
+// One warp per robot, longest robots first.
+template <int KS>
+__global__ void __launch_bounds__(32) grad_kernel(const GrowArgs A, const GradArgs G) {
+  extern __shared__ float4 smem4[];
+  const int lane = threadIdx.x & 31;
+  const Smem S = carve(reinterpret_cast<float*>(smem4), A);
+  for (int idx = blockIdx.x; idx < A.n_order; idx += gridDim.x) grad_instance<KS>(A, G, A.order[idx], S, lane);
+}
+
 template <int KS>
 const void* kernel_ptr() {
   return reinterpret_cast<const void*>(&grow_kernel<KS>);
@@ -799,6 +916,25 @@ cudaError_t launch_grow(const GrowArgs& a, int ks, int grid, int block, size_t s
     case 2: grow_kernel<2><<<grid, block, smem, s>>>(a); break;
     case 3: grow_kernel<3><<<grid, block, smem, s>>>(a); break;
     default: grow_kernel<4><<<grid, block, smem, s>>>(a); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad(const GrowArgs& a, const GradArgs& g, int ks, int grid, size_t smem, cudaStream_t s) {
+  const void* fn;
+  switch (ks) {
+    case 1: fn = reinterpret_cast<const void*>(&grad_kernel<1>); break;
+    case 2: fn = reinterpret_cast<const void*>(&grad_kernel<2>); break;
+    case 3: fn = reinterpret_cast<const void*>(&grad_kernel<3>); break;
+    default: fn = reinterpret_cast<const void*>(&grad_kernel<4>); break;
+  }
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  switch (ks) {
+    case 1: grad_kernel<1><<<grid, 32, smem, s>>>(a, g); break;
+    case 2: grad_kernel<2><<<grid, 32, smem, s>>>(a, g); break;
+    case 3: grad_kernel<3><<<grid, 32, smem, s>>>(a, g); break;
+    default: grad_kernel<4><<<grid, 32, smem, s>>>(a, g); break;
   }
   return cudaGetLastError();
 }

@@ -4,7 +4,7 @@
 //   InstDev  inst[n]            80 B per instance: derived constants + CSR offsets
 //   float4   obs[n_obs_total]   (cx - bx, cy - by, p, q): circle p = R + r, q = -(R + r)^2;
 //                               box p = half-width, q = half-height (> 0)
-//   float4   act[n_act_total]   (begin, end, side * P_act, table index as int bits)
+//   float4   act[n_act_total]   (begin, end, P_act, table index as int bits, side in the sign bit)
 //   float4   tab_hdr[n_tab]     (eps_lo, h, 1/h, G(0)) per sPAM force table
 //   float2   tab[n_tab * 256]   (f_k, G_k): force per pressure at knot k and its
 //                               integral from eps_lo
@@ -77,6 +77,16 @@ struct GrowArgs {
   int trace_inst, trace_cap;
 };
 
+// Adjoint outputs (vine_grad): device pointers.
+struct GradArgs {
+  const float* goal;  // [2 n] goal points (absolute)
+  double* cost;       // [n]
+  double* dP;         // [n_act_total] d cost / d actuator pressure (per Pa)
+  double* dB;         // [n_act_total] d cost / d actuator begin (per link)
+  double* dE;         // [n_act_total] d cost / d actuator end (per link)
+  int* gstat;         // [n] 0 ok, 1 exact Hessian not positive definite, 2 no valid state
+};
+
 // Table build (FP64) -- vine_tables.cu
 struct GaussLegendre {
   int n;
@@ -101,6 +111,7 @@ cudaError_t grow_configure(int ks, size_t smem_per_cta);
 int grow_max_ctas_per_sm(int ks, size_t smem_per_cta);
 cudaError_t launch_probe(const GrowArgs& a, int ks, int inst, int N, const float* theta, float l, double* J,
                          float* g, float* dx, double* r, int* lfix, size_t smem, cudaStream_t s);
+cudaError_t launch_grad(const GrowArgs& a, const GradArgs& g, int ks, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_poses(const InstDev* inst, int n_inst, const float* theta, const int* n_cur, const float* l_cur,
                          float* out_theta, float* out_pose, float* out_tip, cudaStream_t s);
 cudaError_t launch_contacts(const InstDev* inst, int n_inst, const float4* obs, const float* theta, const int* n_cur,

@@ -23,7 +23,7 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["config1", "config2", "config3", "config4", "make", "serve_requests", "robot_link_steps",
+__all__ = ["config1", "config2", "config3", "config4", "goal_points", "make", "serve_requests", "robot_link_steps",
            "concat", "subset"]
 
 
@@ -177,6 +177,15 @@ def config4(n_designs: int = 64, n_perturb: int = 1024, replicate: int = 0, n_li
                              obs=(pk, ncx, ncy, pa, pb)))
             goals.append(goal)
     return _pack(rows), np.array(goals, np.float32)
+
+
+def goal_points(n_inst: int, box: float, replicate: int = 0) -> np.ndarray:
+    """One goal point per instance, uniform in the far half of a box of side
+    `box` ahead of the base (as the robustness batch draws them)."""
+    rng = _rng(6, replicate)
+    gx = rng.uniform(0.05 + 0.5 * box, 0.05 + box, n_inst)
+    gy = rng.uniform(-0.5 * box, 0.5 * box, n_inst)
+    return np.stack([gx, gy], axis=1).astype(np.float32)
 
 
 def make(config: int, n_inst: int | None = None, replicate: int = 0) -> dict:

@@ -69,6 +69,8 @@ _SIG = {
     "vine_get_robot_counters": [_p, _p, _p, _p, _p],
     "vine_spam_tables_noalloc": [_p, _i32, _p, _p, _p, _p],
     "vine_debug_trace_read": [_p, _p, _i32, _p],
+    "vine_set_actuators": [_p, _p, _p, _p, _i32, _p],
+    "vine_grad": [_p, _p, _p, _p, _p, _p, _p, _i32, _p],
     "vine_batch_destroy": [_p],
 }
 for _name, _args in _SIG.items():
@@ -173,6 +175,9 @@ class Batch:
         self.total_links = tl.value
         nl = scene["n_links"]
         self.n_links = nl.cpu().numpy() if hasattr(nl, "cpu") else np.asarray(nl)
+        ap = scene["act_ptr"]
+        self.act_ptr = (ap.cpu().numpy() if hasattr(ap, "cpu") else np.asarray(ap)).astype(np.int64)
+        self.n_act = int(self.act_ptr[-1])
         self.offsets = np.concatenate([[0], np.cumsum(self.n_links)]).astype(np.int64)
         self._keep = None  # inputs were copied during create
 
@@ -198,6 +203,47 @@ class Batch:
 
     def simulate_plain(self, stream=None):
         _check(_lib.vine_simulate_plain(self.h, _stream(stream)), "vine_simulate_plain")
+
+    def set_actuators(self, pressure, begin, end, stream=None):
+        """New actuator pressures (Pa) and spans (link units), [n_act] each:
+        numpy arrays (synchronous) or CUDA float32 tensors (async)."""
+        dev = int(hasattr(pressure, "is_cuda") and pressure.is_cuda)
+        if dev:
+            args = [x.contiguous() for x in (pressure, begin, end)]
+        else:
+            args = [np.ascontiguousarray(np.asarray(x).reshape(-1), np.float32) for x in (pressure, begin, end)]
+        for x in args:
+            if (x.numel() if dev else x.size) != self.n_act:
+                raise ValueError("set_actuators: expected %d values per array" % self.n_act)
+        _check(_lib.vine_set_actuators(self.h, _ptr(args[0]), _ptr(args[1]), _ptr(args[2]), dev, _stream(stream)),
+               "vine_set_actuators")
+        self._act_keep = args  # alive until the async copy has run
+
+    def grad(self, goal, stream=None) -> dict:
+        """Tip-distance cost |p_tip - goal| and its adjoint derivatives at the
+        current state (vine_grad).  goal: [n, 2] numpy (host path, returns
+        numpy) or CUDA float32 tensor (device path, returns CUDA tensors,
+        async)."""
+        n, na = self.n_inst, self.n_act
+        if hasattr(goal, "is_cuda") and goal.is_cuda:
+            import torch
+            g = goal.contiguous()
+            out = dict(cost=torch.empty(n, dtype=torch.float64, device=g.device),
+                       dP=torch.empty(max(na, 1), dtype=torch.float64, device=g.device),
+                       dB=torch.empty(max(na, 1), dtype=torch.float64, device=g.device),
+                       dE=torch.empty(max(na, 1), dtype=torch.float64, device=g.device),
+                       status=torch.empty(n, dtype=torch.int32, device=g.device))
+            dev = 1
+        else:
+            g = np.ascontiguousarray(np.asarray(goal, np.float32).reshape(n, 2))
+            out = dict(cost=np.zeros(n), dP=np.zeros(max(na, 1)), dB=np.zeros(max(na, 1)), dE=np.zeros(max(na, 1)),
+                       status=np.zeros(n, np.int32))
+            dev = 0
+        _check(_lib.vine_grad(self.h, _ptr(g), _ptr(out["cost"]), _ptr(out["dP"]), _ptr(out["dB"]), _ptr(out["dE"]),
+                              _ptr(out["status"]), dev, _stream(stream)), "vine_grad")
+        for k in ("dP", "dB", "dE"):
+            out[k] = out[k][:na]
+        return out
 
     def state(self, stream=None) -> dict:
         """Host copy of the state (synchronises the stream)."""

@@ -14,7 +14,8 @@ def _declared():
 
 def test_header_declares_entry_points():
     names = _declared()
-    for n in ("vine_batch_create", "vine_grow_step", "vine_simulate", "vine_get_state", "vine_batch_destroy"):
+    for n in ("vine_batch_create", "vine_grow_step", "vine_simulate", "vine_get_state", "vine_grad",
+              "vine_set_actuators", "vine_batch_destroy"):
         assert n in names
 
 

@@ -1,0 +1,152 @@
+"""GPU adjoint (vine_grad) against the FP64 oracle's adjoint at the same
+state, the actuator update path, and the torch.autograd.Function."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2509_15180_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2509_15180_gb300 import vine  # noqa: E402
+from paper_2509_15180_gb300.autograd import VineSim  # noqa: E402
+
+
+def _scene(n_designs=6, n_perturb=2, n_links=30):
+    return scenes.config4(n_designs=n_designs, n_perturb=n_perturb, n_links=n_links, box=0.015 * n_links,
+                          n_circ=8, n_box=8)
+
+
+def _compare(sc, goals, b, st, g, min_checked):
+    """Oracle adjoint at the GPU's own final state (float32 angles widened)."""
+    orc = oracle.Oracle(sc)
+    rows = []
+    skipped = 0
+    for i in range(sc["n_links"].size):
+        a0, a1 = int(sc["act_ptr"][i]), int(sc["act_ptr"][i + 1])
+        if st["status"][i] != 0 or g["status"][i] != 0:
+            skipped += 1
+            continue
+        th = b.theta_of(st, i).astype(np.float64)
+        c, dP, dB, dE, rc = orc.grad(i, th, float(st["l"][i]), goals[i].astype(np.float64))
+        if rc != 0:
+            skipped += 1
+            continue
+        assert abs(g["cost"][i] - c) <= 1e-6 * max(c, 1e-3), (i, g["cost"][i], c)
+        for k, v in (("dP", dP), ("dB", dB), ("dE", dE)):
+            for a in range(a1 - a0):
+                rows.append((k, i, a, g[k][a0 + a], v[a]))
+    worst = {}
+    for k in ("dP", "dB", "dE"):
+        sel = [r for r in rows if r[0] == k]
+        if not sel:
+            continue
+        scale = max(abs(r[4]) for r in sel)
+        errs = [abs(r[3] - r[4]) / scale for r in sel]
+        worst[k] = max(errs)
+        # FP32 Hessian and gradient: ~1e-3 of the largest derivative of its kind
+        assert worst[k] < 2e-2, (k, worst[k], sel[int(np.argmax(errs))])
+    print("adjoint parity: %d derivatives, %d robots skipped, worst per kind %s" % (len(rows), skipped, worst))
+    assert len(rows) >= min_checked
+    return worst
+
+
+def test_grad_matches_oracle_adjoint_small():
+    sc, goals = _scene()
+    b = vine.Batch(sc)
+    b.simulate()
+    st = b.state()
+    g = b.grad(goals)
+    _compare(sc, goals, b, st, g, 40)
+    b.close()
+
+
+def test_grad_device_path_equals_host_path():
+    sc, goals = _scene(4, 2)
+    b = vine.Batch(sc)
+    b.simulate()
+    gh = b.grad(goals)
+    gd = b.grad(torch.from_numpy(goals).cuda())
+    torch.cuda.synchronize()
+    for k in ("cost", "dP", "dB", "dE", "status"):
+        assert np.array_equal(gd[k].cpu().numpy(), gh[k], equal_nan=True), k
+    b.close()
+
+
+def test_grad_full_length_robustness_designs_sampled():
+    """Config-4 shaped designs (150 links, 60 obstacles, 2.25 m box), 8 designs
+    x 16 perturbations, one launch; 24 robots checked against the oracle."""
+    sc, goals = scenes.config4(n_designs=8, n_perturb=16)
+    b = vine.Batch(sc)
+    b.simulate()
+    st = b.state()
+    g = b.grad(goals)
+    ok = (g["status"] == 0) & (st["status"] == 0)
+    print("robots with a gradient: %d of %d (status %s)" % (ok.sum(), ok.size, np.bincount(g["status"])))
+    assert ok.mean() >= 0.8
+    idx = np.sort(np.random.default_rng(3).choice(len(goals), 24, replace=False))
+    sub = scenes.subset(sc, idx)
+    stsub = {k: v[idx] for k, v in st.items() if k in ("status", "l", "N")}
+    thetas = [b.theta_of(st, i) for i in idx]
+
+    class _View:
+        def theta_of(self, s, j):
+            return thetas[j]
+
+    asub = np.concatenate([np.arange(sc["act_ptr"][i], sc["act_ptr"][i + 1]) for i in idx]).astype(np.int64)
+    gsub = dict(cost=g["cost"][idx], status=g["status"][idx], dP=g["dP"][asub], dB=g["dB"][asub], dE=g["dE"][asub])
+    _compare(sub, goals[idx], _View(), stsub, gsub, 30)
+    b.close()
+
+
+def test_set_actuators_equals_fresh_batch():
+    sc, goals = _scene(4, 2)
+    rng = np.random.default_rng(11)
+    p2 = (sc["act_pressure"] * rng.uniform(0.8, 1.2, sc["act_pressure"].size)).astype(np.float32)
+    b2 = (sc["act_begin"] + rng.uniform(-0.3, 0.3, sc["act_begin"].size)).clip(0.0).astype(np.float32)
+    e2 = np.maximum(sc["act_end"] + rng.uniform(-0.3, 0.3, sc["act_end"].size), b2 + 0.5).astype(np.float32)
+    ref = dict(sc, act_pressure=p2, act_begin=b2, act_end=e2)
+    b = vine.Batch(sc)
+    b.set_actuators(p2, b2, e2)
+    b.reset()
+    b.simulate()
+    fresh = vine.Batch(ref)
+    fresh.simulate()
+    s1, s2 = b.state(), fresh.state()
+    for k in ("theta", "l", "N", "status", "iters"):
+        assert np.array_equal(s1[k], s2[k]), k
+    # an invalid span marks only its robot
+    bad_e = e2.copy()
+    bad_e[0] = b2[0] - 1.0
+    b.set_actuators(p2, b2, bad_e)
+    b.reset()
+    st = b.state()
+    owner = int(np.searchsorted(sc["act_ptr"], 0, side="right") - 1)
+    assert st["status"][owner] == vine.INST_BADINPUT
+    assert np.all(np.delete(st["status"], owner) == 0)
+    b.close(); fresh.close()
+
+
+def test_autograd_function_chain_rule():
+    sc, goals = _scene(4, 2)
+    b = vine.Batch(sc)
+    dev = torch.device("cuda")
+    P = torch.tensor(sc["act_pressure"], device=dev, requires_grad=True)
+    B = torch.tensor(sc["act_begin"], device=dev, requires_grad=True)
+    E = torch.tensor(sc["act_end"], device=dev, requires_grad=True)
+    goal = torch.tensor(goals, device=dev)
+    cost = VineSim.apply(P, B, E, b, goal)
+    w = torch.linspace(0.5, 2.0, cost.numel(), device=dev, dtype=torch.float64)
+    (cost * w).sum().backward()
+    g = b.grad(goals)
+    owner = np.repeat(np.arange(len(goals)), np.diff(sc["act_ptr"]))
+    wn = w.cpu().numpy()[owner]
+    ok = ~np.isnan(g["dP"])
+    assert np.allclose(P.grad.cpu().numpy()[ok], (wn * g["dP"])[ok].astype(np.float32), rtol=1e-6, atol=0)
+    assert np.allclose(B.grad.cpu().numpy()[ok], (wn * g["dB"])[ok].astype(np.float32), rtol=1e-6, atol=0)
+    assert np.allclose(E.grad.cpu().numpy()[ok], (wn * g["dE"])[ok].astype(np.float32), rtol=1e-6, atol=0)
+    assert np.allclose(cost.detach().cpu().numpy(), g["cost"], rtol=0, atol=0)
+    b.close()
