@@ -319,6 +319,91 @@ vine_status vine_batch_destroy(vine_batch* b);
 vine_status vine_spam_tables_noalloc(const double* l0, int32_t n_tab, const vine_params* params, float* hdr,
                                      float* knots, void* cuda_stream);
 
+/* ---------------------------------------------------------------------------
+ * Serving loop: continuous batching of growth requests on one GPU.  The
+ * paper's planners (Sec. 5) issue many small simulation requests; a server
+ * keeps every admitted robot's state on the device between growth launches
+ * and mixes robots of different requests in each launch.
+ *
+ * A server owns a fixed arena of robot slots (design, obstacles, joint
+ * angles and counters of one robot each, capacities below), the sPAM force
+ * tables of every cell length seen so far and the wrinkling-energy table, and
+ * one worker thread that owns its CUDA stream.  Each worker tick admits the
+ * waiting requests into free slots (copy in, validate, encode, build missing
+ * tables), grows every active robot by up to steps_per_tick links in one
+ * persistent launch (largest remaining work first), reads back the links
+ * present and status of the active robots, and retires the requests whose
+ * robots are all done (reached n_links, or stopped non-finite / bad input).
+ * A robot's result does not depend on the requests it shared launches with.
+ * ------------------------------------------------------------------------- */
+typedef struct vine_server vine_server;
+
+typedef struct {
+  size_t device_mem_budget; /* bytes the server may hold on the device (0: 1 GiB) */
+  int32_t max_slots;        /* robot slots (0: as many as the budget holds) */
+  int32_t max_links;        /* per slot: links (0: 320) */
+  int32_t max_obs;          /* per slot: obstacles (0: 256) */
+  int32_t max_act;          /* per slot: actuators (0: 16) */
+  int32_t max_request;      /* robots per request (0: 256) */
+  int32_t steps_per_tick;   /* growth steps per robot per launch (0: 8) */
+  int32_t max_tables;       /* distinct sPAM cell lengths held (0: 256) */
+} vine_server_config;
+
+typedef struct {
+  int32_t n_inst;             /* robots of the request */
+  int32_t reserved;
+  int64_t total_links;        /* sum of n_links */
+  int64_t robot_link_steps;   /* links present summed over converged steps */
+  double t_submit, t_admit, t_done; /* vine_serve_clock seconds */
+} vine_request_info;
+
+typedef struct {
+  int64_t ticks;              /* growth launches */
+  int64_t requests_done;
+  int64_t robot_link_steps;   /* of retired requests */
+  int32_t active_robots, waiting_requests;
+  int32_t free_slots, max_slots;
+  double busy_s;              /* wall time of ticks with active robots */
+} vine_server_stats;
+
+/* Zeroes in every field: the defaults listed above. */
+vine_status vine_server_config_default(vine_server_config* out);
+
+/* Allocates the slot arena and tables (one cudaMalloc within the budget),
+ * builds the wrinkling table and starts the worker on the current device.
+ * VINE_EINVAL when the budget cannot hold one slot per robot of a maximal
+ * request or the slot does not fit in shared memory. */
+vine_status vine_server_create(const vine_params* params, const vine_server_config* config, vine_server** out);
+
+/* Copies a request (host memory: desc->mem_is_device must be 0) and queues
+ * it; *request_id identifies it.  VINE_EBUSY when the free slots (less those
+ * promised to requests still waiting) cannot hold its robots: nothing is
+ * kept and the client retries later.  VINE_EINVAL for a malformed request,
+ * more robots than max_request, a robot beyond the slot capacities, or more
+ * distinct cell lengths than the table capacity.  Thread-safe. */
+vine_status vine_serve_submit(vine_server* s, const vine_batch_desc* desc, uint64_t* request_id);
+
+/* Waits up to timeout_us (0: do not wait) for request_id to finish.  Done:
+ * fills *info (may be NULL) and the host outputs (any may be NULL), in the
+ * layouts of vine_get_state -- theta[sum n_links], l_last[n], tip[2n],
+ * n_present[n], inst_status[n], iterations[n] -- and releases the request
+ * (its id is then unknown).  Not done: VINE_ETIMEOUT (info filled with the
+ * request's size and submit time).  Unknown id: VINE_EINVAL.  A worker
+ * failure: VINE_ECUDA.  Thread-safe. */
+vine_status vine_serve_poll(vine_server* s, uint64_t request_id, int32_t timeout_us, vine_request_info* info,
+                            float* theta, float* l_last, float* tip, int32_t* n_present, int32_t* inst_status,
+                            int32_t* iterations);
+
+/* Counters of the server (host struct). */
+vine_status vine_server_get_stats(vine_server* s, vine_server_stats* out);
+
+/* The clock of t_submit / t_admit / t_done (seconds, monotonic). */
+vine_status vine_serve_clock(double* seconds);
+
+/* Stops the worker after its current tick, drops unfinished and unpolled
+ * requests and frees the server. */
+vine_status vine_server_destroy(vine_server* s);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* vine_last_error(void);
 

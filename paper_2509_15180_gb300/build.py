@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libvine.so")
-SOURCES = ["vine_tables.cu", "vine_grow.cu", "vine_api.cu"]
+SOURCES = ["vine_tables.cu", "vine_grow.cu", "vine_api.cu", "vine_serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
@@ -60,7 +60,7 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
             if r.returncode != 0:
                 raise RuntimeError("nvcc failed: " + " ".join(cmd))
     if _stale(LIB, objs):
-        cmd = [nvcc, "-shared", "-o", LIB] + objs + ARCH
+        cmd = [nvcc, "-shared", "-o", LIB] + objs + ARCH + ["-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             sys.stdout.write(r.stdout + r.stderr)

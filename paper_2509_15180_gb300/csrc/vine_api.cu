@@ -45,38 +45,23 @@ vine_status cuda_fail(cudaError_t e, const char* where) {
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// Device-side validation and encoding, one warp per instance.
-struct InitArgs {
-  int n_inst;
-  const int32_t* n_links;
-  const float *l_seg, *radius, *pressure, *base;
-  const int32_t* act_ptr;
-  const float *act_begin, *act_end;
-  const int8_t* act_side;
-  const float *act_pressure, *act_l0;
-  const int32_t* obs_ptr;
-  const uint8_t* obs_kind;
-  const float *obs_cx, *obs_cy, *obs_a, *obs_b;
-  const int* act_tab;   // per actuator: sPAM table index
-  const int* th_off;    // per instance: offset into theta
-  const int* status_h;  // per instance: structural check done on the host
-  double R_act, w_a, pen_frac;
-  InstDev* inst;
-  float4* obs;
-  float4* act;
-  int* status;
-};
-
 __device__ bool fin(float v) { return isfinite(v); }
 
+// Device-side validation and encoding, one warp per instance.  Batch layout
+// (slot == nullptr): instance i at index i, its actuators and obstacles at
+// their CSR positions.  Slot layout: instance i goes to slot[i], its
+// actuators to slot[i] * amax_s + k, obstacles to slot[i] * omax_s + k and
+// joint angles to slot[i] * nmax_s.
 __global__ void init_kernel(const InitArgs A) {
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (i >= A.n_inst) return;
   bool bad = A.status_h[i] != 0;
+  const int dst = A.slot ? A.slot[i] : i;
   const float ls = A.l_seg[i], R = A.radius[i], P = A.pressure[i];
   const float bx = A.base[3 * i], by = A.base[3 * i + 1], bpsi = A.base[3 * i + 2];
   bad = bad || !(fin(ls) && ls > 0.f && fin(R) && R > 0.f && fin(P) && P > 0.f && fin(bx) && fin(by) && fin(bpsi));
   const int a0 = A.act_ptr[i], a1 = A.act_ptr[i + 1], o0 = A.obs_ptr[i], o1 = A.obs_ptr[i + 1];
+  const int ad = A.slot ? dst * A.amax_s : a0, od = A.slot ? dst * A.omax_s : o0;
   bool badl = false;
   for (int a = a0 + lane; a < a1; a += 32) {
     const float b = A.act_begin[a], e = A.act_end[a], pa = A.act_pressure[a], l0 = A.act_l0[a];
@@ -84,7 +69,7 @@ __global__ void init_kernel(const InitArgs A) {
     badl = badl || !(fin(b) && fin(e) && b >= 0.f && e > b && (sd == 1 || sd == -1) && fin(pa) && pa >= 0.f &&
                      fin(l0) && l0 > 0.f);
     int bits = A.act_tab[a] | (sd < 0 ? (int)0x80000000 : 0);
-    A.act[a] = make_float4(b, e, pa, __int_as_float(bits));
+    A.act[ad + (a - a0)] = make_float4(b, e, pa, __int_as_float(bits));
   }
   for (int o = o0 + lane; o < o1; o += 32) {
     const int k = A.obs_kind[o];
@@ -93,10 +78,10 @@ __global__ void init_kernel(const InitArgs A) {
     if (k == 0) {
       badl = badl || !(fin(cx) && fin(cy) && fin(a) && a > 0.f);
       const double rr = (double)R + (double)a;
-      A.obs[o] = make_float4(rx, ry, (float)rr, -(float)(rr * rr));
+      A.obs[od + (o - o0)] = make_float4(rx, ry, (float)rr, -(float)(rr * rr));
     } else {
       badl = badl || !(k == 1 && fin(cx) && fin(cy) && fin(a) && a > 0.f && fin(b) && b > 0.f);
-      A.obs[o] = make_float4(rx, ry, a, b);
+      A.obs[od + (o - o0)] = make_float4(rx, ry, a, b);
     }
   }
   bad = __any_sync(0xffffffffu, badl) || bad;
@@ -115,15 +100,15 @@ __global__ void init_kernel(const InitArgs A) {
     d.by = by;
     d.pad0 = d.pad1 = 0.f;
     d.n_target = A.n_links[i];
-    d.act_off = a0;
+    d.act_off = ad;
     d.n_act = a1 - a0;
-    d.obs_off = o0;
+    d.obs_off = od;
     d.n_obs = o1 - o0;
-    d.th_off = A.th_off[i];
+    d.th_off = A.slot ? dst * A.nmax_s : A.th_off[i];
     d.n_circ = 0;
     d.pad2 = 0;
-    A.inst[i] = d;
-    A.status[i] = bad ? kBadInput : kOK;
+    A.inst[dst] = d;
+    A.status[dst] = bad ? kBadInput : kOK;
   }
 }
 
@@ -149,6 +134,12 @@ __global__ void actuator_update_kernel(const InstDev* inst, int n_inst, const fl
 }
 
 }  // namespace
+
+cudaError_t vine::launch_init(const InitArgs& a, cudaStream_t s) {
+  if (a.n_inst <= 0) return cudaSuccess;
+  init_kernel<<<(a.n_inst * 32 + 127) / 128, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
 
 void vine::set_last_error(const char* msg, const char* detail) {
   std::snprintf(g_err, sizeof(g_err), "%s%s", msg, detail ? detail : "");
@@ -418,8 +409,7 @@ vine_status vine_batch_create(const vine_batch_desc* D, const vine_params* P, vo
   // zero the per-instance state block (n .. resid) before validation writes status
   CKC(cudaMemsetAsync(P_(o_n), 0, (size_t)(o_ord - o_n), st));
   CKC(cudaMemsetAsync(P_(o_th), 0, sizeof(float) * std::max<int64_t>(tot, 1), st));
-  init_kernel<<<(n * 32 + 127) / 128, 128, 0, st>>>(ia);
-  CKC(cudaGetLastError());
+  CKC(launch_init(ia, st));
   CKC(cudaMemcpyAsync(P_(o_st0), P_(o_st), sizeof(int) * n, cudaMemcpyDeviceToDevice, st));
   // prologue tables
   GaussLegendre gl;

@@ -23,6 +23,8 @@
 // Lanes own contiguous blocks of links; obstacles and actuators of the robot
 // are staged in shared memory; the serial sweeps run warp-uniform.
 #include <cmath>
+#include <map>
+#include <mutex>
 
 #include "vine_internal.cuh"
 
@@ -899,8 +901,19 @@ size_t grow_smem_per_warp(int nmax, int omax, int amax) {
   return sizeof(float4) * (size_t)(omax + amax) + sizeof(float) * (16 * (size_t)nmax + 8);
 }
 
+// The attribute is per kernel and process-wide: batches and servers with
+// different slices share it, so it is only ever raised.
 cudaError_t grow_configure(int ks, size_t smem_per_cta) {
-  return cudaFuncSetAttribute(pick(ks), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_per_cta);
+  static std::mutex mu;
+  static std::map<std::pair<int, int>, size_t> set;  // (device, K_s) -> bytes
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& cur = set[{dev, ks}];
+  if (smem_per_cta <= cur) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(pick(ks), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_per_cta);
+  if (e == cudaSuccess) cur = smem_per_cta;
+  return e;
 }
 
 int grow_max_ctas_per_sm(int ks, size_t smem_per_cta) {
@@ -955,13 +968,19 @@ cudaError_t launch_probe(const GrowArgs& a, int ks, int inst, int N, const float
 // ---------------------------------------------------------------------------
 namespace {
 
-__global__ void pose_kernel(const InstDev* inst, int n_inst, const float* theta, const int* n_cur,
-                            const float* l_cur, float* out_theta, float* out_pose, float* out_tip) {
+// sel == nullptr: robot gw, outputs at its own joint-angle offset.  Else
+// robot sel[gw], outputs at out_off[gw] (a compact copy of selected robots);
+// the tip always goes to out_tip[2 gw].
+__global__ void pose_kernel(const InstDev* inst, int n_inst, const int* sel, const long long* out_off,
+                            const float* theta, const int* n_cur, const float* l_cur, float* out_theta,
+                            float* out_pose, float* out_tip) {
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (gw >= n_inst) return;
-  const InstDev I = inst[gw];
-  const int N = n_cur[gw];
-  const float l = l_cur[gw];
+  const int ri = sel ? sel[gw] : gw;
+  const InstDev I = inst[ri];
+  const int N = n_cur[ri];
+  const float l = l_cur[ri];
+  const size_t oo = sel ? (size_t)out_off[gw] : (size_t)I.th_off;
   const int B = (N + 31) >> 5;
   const int j0 = min(lane * B, N), j1 = min(j0 + B, N);
   const float* th = theta + I.th_off;
@@ -982,11 +1001,11 @@ __global__ void pose_kernel(const InstDev* inst, int n_inst, const float* theta,
   for (int j = j0; j < j1; ++j) {
     psi = ff_add(psi, th[j]);
     if (out_pose) {
-      out_pose[3 * ((size_t)I.th_off + j) + 0] = (px.hi + I.bx) + px.lo;
-      out_pose[3 * ((size_t)I.th_off + j) + 1] = (py.hi + I.by) + py.lo;
-      out_pose[3 * ((size_t)I.th_off + j) + 2] = psi.hi + psi.lo;
+      out_pose[3 * (oo + j) + 0] = (px.hi + I.bx) + px.lo;
+      out_pose[3 * (oo + j) + 1] = (py.hi + I.by) + py.lo;
+      out_pose[3 * (oo + j) + 2] = psi.hi + psi.lo;
     }
-    if (out_theta) out_theta[I.th_off + j] = th[j];
+    if (out_theta) out_theta[oo + j] = th[j];
     float sn, cs;
     sincosf(psi.hi, &sn, &cs);
     const float L = (j == N - 1) ? l : I.l_seg;
@@ -995,11 +1014,11 @@ __global__ void pose_kernel(const InstDev* inst, int n_inst, const float* theta,
   }
   for (int j = N + lane; j < I.n_target; j += 32) {
     if (out_pose) {
-      out_pose[3 * ((size_t)I.th_off + j) + 0] = 0.f;
-      out_pose[3 * ((size_t)I.th_off + j) + 1] = 0.f;
-      out_pose[3 * ((size_t)I.th_off + j) + 2] = 0.f;
+      out_pose[3 * (oo + j) + 0] = 0.f;
+      out_pose[3 * (oo + j) + 1] = 0.f;
+      out_pose[3 * (oo + j) + 2] = 0.f;
     }
-    if (out_theta) out_theta[I.th_off + j] = 0.f;
+    if (out_theta) out_theta[oo + j] = 0.f;
   }
   // the lane holding the last link has the tip in (px, py)
   if (out_tip && N > 0 && j1 == N && j0 < j1) {
@@ -1091,7 +1110,19 @@ cudaError_t launch_poses(const InstDev* inst, int n_inst, const float* theta, co
                          float* out_theta, float* out_pose, float* out_tip, cudaStream_t s) {
   const int threads = 128;
   const int blocks = (n_inst * 32 + threads - 1) / threads;
-  pose_kernel<<<blocks, threads, 0, s>>>(inst, n_inst, theta, n_cur, l_cur, out_theta, out_pose, out_tip);
+  pose_kernel<<<blocks, threads, 0, s>>>(inst, n_inst, nullptr, nullptr, theta, n_cur, l_cur, out_theta, out_pose,
+                                         out_tip);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_poses_sel(const InstDev* inst, const int* sel, const long long* out_off, int n_sel,
+                             const float* theta, const int* n_cur, const float* l_cur, float* out_theta,
+                             float* out_pose, float* out_tip, cudaStream_t s) {
+  if (n_sel <= 0) return cudaSuccess;
+  const int threads = 128;
+  const int blocks = (n_sel * 32 + threads - 1) / threads;
+  pose_kernel<<<blocks, threads, 0, s>>>(inst, n_sel, sel, out_off, theta, n_cur, l_cur, out_theta, out_pose,
+                                         out_tip);
   return cudaGetLastError();
 }
 

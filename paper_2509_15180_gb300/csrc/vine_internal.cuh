@@ -77,6 +77,32 @@ struct GrowArgs {
   int trace_inst, trace_cap;
 };
 
+// Descriptor validation and encoding (vine_api.cu): raw device copies of a
+// vine_batch_desc in, InstDev / obstacle / actuator records out.
+struct InitArgs {
+  int n_inst;
+  const int32_t* n_links;
+  const float *l_seg, *radius, *pressure, *base;
+  const int32_t* act_ptr;
+  const float *act_begin, *act_end;
+  const int8_t* act_side;
+  const float *act_pressure, *act_l0;
+  const int32_t* obs_ptr;
+  const uint8_t* obs_kind;
+  const float *obs_cx, *obs_cy, *obs_a, *obs_b;
+  const int* act_tab;   // per actuator: sPAM table index
+  const int* th_off;    // per instance: offset into theta (batch layout)
+  const int* status_h;  // per instance: structural check done on the host
+  const int* slot;      // null: batch layout; else per instance its slot (slot layout)
+  int nmax_s, omax_s, amax_s;  // slot capacities (slot layout)
+  double R_act, w_a, pen_frac;
+  InstDev* inst;
+  float4* obs;
+  float4* act;
+  int* status;
+};
+cudaError_t launch_init(const InitArgs& a, cudaStream_t s);
+
 // Adjoint outputs (vine_grad): device pointers.
 struct GradArgs {
   const float* goal;  // [2 n] goal points (absolute)
@@ -114,6 +140,9 @@ cudaError_t launch_probe(const GrowArgs& a, int ks, int inst, int N, const float
 cudaError_t launch_grad(const GrowArgs& a, const GradArgs& g, int ks, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_poses(const InstDev* inst, int n_inst, const float* theta, const int* n_cur, const float* l_cur,
                          float* out_theta, float* out_pose, float* out_tip, cudaStream_t s);
+cudaError_t launch_poses_sel(const InstDev* inst, const int* sel, const long long* out_off, int n_sel,
+                             const float* theta, const int* n_cur, const float* l_cur, float* out_theta,
+                             float* out_pose, float* out_tip, cudaStream_t s);
 cudaError_t launch_contacts(const InstDev* inst, int n_inst, const float4* obs, const float* theta, const int* n_cur,
                             const float* l_cur, int ks, int max_pairs, int* counts, int* pairs, cudaStream_t s);
 

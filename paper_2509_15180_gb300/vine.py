@@ -51,6 +51,24 @@ class vine_stats(C.Structure):
         (k, C.c_int32) for k in ("n_maxiter", "n_nonfinite", "n_badinput", "reserved")]
 
 
+class vine_server_config(C.Structure):
+    _fields_ = [("device_mem_budget", C.c_size_t)] + [
+        (k, C.c_int32) for k in ("max_slots", "max_links", "max_obs", "max_act", "max_request", "steps_per_tick",
+                                 "max_tables")]
+
+
+class vine_request_info(C.Structure):
+    _fields_ = [("n_inst", C.c_int32), ("reserved", C.c_int32), ("total_links", C.c_int64),
+                ("robot_link_steps", C.c_int64), ("t_submit", C.c_double), ("t_admit", C.c_double),
+                ("t_done", C.c_double)]
+
+
+class vine_server_stats(C.Structure):
+    _fields_ = [("ticks", C.c_int64), ("requests_done", C.c_int64), ("robot_link_steps", C.c_int64),
+                ("active_robots", C.c_int32), ("waiting_requests", C.c_int32), ("free_slots", C.c_int32),
+                ("max_slots", C.c_int32), ("busy_s", C.c_double)]
+
+
 _p, _i32, _i64 = C.c_void_p, C.c_int32, C.c_int64
 _SIG = {
     "vine_params_default": [_p],
@@ -72,6 +90,13 @@ _SIG = {
     "vine_set_actuators": [_p, _p, _p, _p, _i32, _p],
     "vine_grad": [_p, _p, _p, _p, _p, _p, _p, _i32, _p],
     "vine_batch_destroy": [_p],
+    "vine_server_config_default": [_p],
+    "vine_server_create": [_p, _p, _p],
+    "vine_serve_submit": [_p, _p, _p],
+    "vine_serve_poll": [_p, C.c_uint64, _i32, _p, _p, _p, _p, _p, _p, _p],
+    "vine_server_get_stats": [_p, _p],
+    "vine_serve_clock": [_p],
+    "vine_server_destroy": [_p],
 }
 for _name, _args in _SIG.items():
     _f = getattr(_lib, _name)
@@ -324,3 +349,83 @@ class Batch:
 
     def pose_of(self, st: dict, i: int):
         return st["pose"][self.offsets[i]: self.offsets[i] + st["N"][i]]
+
+
+# -------------------------------------------------------------------------
+# serving loop
+# -------------------------------------------------------------------------
+def serve_clock() -> float:
+    """The server clock (seconds, monotonic) of t_submit / t_admit / t_done."""
+    t = C.c_double()
+    _check(_lib.vine_serve_clock(C.byref(t)), "vine_serve_clock")
+    return t.value
+
+
+def _host_desc(scene: dict):
+    keep = {k: np.ascontiguousarray(np.asarray(scene[k]).reshape(-1), dtype=dt) for k, dt in _HOST_DTYPES.items()}
+    D = vine_batch_desc()
+    D.n_inst = int(len(keep["n_links"]))
+    D.mem_is_device = 0
+    for k in _HOST_DTYPES:
+        setattr(D, k, _ptr(keep[k]))
+    return D, keep
+
+
+class Server:
+    """A serving loop (vine_server_create); config keys as vine_server_config."""
+
+    def __init__(self, params: vine_params | None = None, **config):
+        cfg = vine_server_config()
+        _check(_lib.vine_server_config_default(C.byref(cfg)), "vine_server_config_default")
+        for k, v in config.items():
+            setattr(cfg, k, v)
+        self.params = params if params is not None else vine_params_default()
+        h = C.c_void_p()
+        _check(_lib.vine_server_create(C.byref(self.params), C.byref(cfg), C.byref(h)), "vine_server_create")
+        self.h = h
+        self._sizes = {}
+
+    def submit(self, scene: dict):
+        """Request id, or None when the server is full (VINE_EBUSY: retry later)."""
+        D, keep = _host_desc(scene)
+        rid = C.c_uint64()
+        st = _lib.vine_serve_submit(self.h, C.byref(D), C.byref(rid))
+        if st == VINE_EBUSY:
+            return None
+        _check(st, "vine_serve_submit")
+        self._sizes[rid.value] = (D.n_inst, int(keep["n_links"].sum()))
+        return rid.value
+
+    def poll(self, rid: int, timeout_us: int = 0):
+        """Result dict of a finished request (then released), or None if it is
+        not finished within timeout_us."""
+        n, T = self._sizes[rid]
+        out = dict(theta=np.zeros(max(T, 1), np.float32), l=np.zeros(n, np.float32), tip=np.zeros((n, 2), np.float32),
+                   N=np.zeros(n, np.int32), status=np.zeros(n, np.int32), iters=np.zeros(n, np.int32))
+        info = vine_request_info()
+        st = _lib.vine_serve_poll(self.h, C.c_uint64(rid), int(timeout_us), C.byref(info), _ptr(out["theta"]),
+                                  _ptr(out["l"]), _ptr(out["tip"]), _ptr(out["N"]), _ptr(out["status"]),
+                                  _ptr(out["iters"]))
+        if st == VINE_ETIMEOUT:
+            return None
+        self._sizes.pop(rid, None)
+        _check(st, "vine_serve_poll")
+        out["theta"] = out["theta"][:T]
+        out.update(rls=info.robot_link_steps, t_submit=info.t_submit, t_admit=info.t_admit, t_done=info.t_done)
+        return out
+
+    def stats(self) -> dict:
+        s = vine_server_stats()
+        _check(_lib.vine_server_get_stats(self.h, C.byref(s)), "vine_server_get_stats")
+        return {k: getattr(s, k) for k, _ in vine_server_stats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.vine_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

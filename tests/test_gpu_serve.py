@@ -1,0 +1,124 @@
+"""Serving loop (vine_server_*): each request's result is the same served
+alone, served in a mix with other requests, and computed by a batch of its
+own; admission by free slots; malformed requests are refused."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2509_15180_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2509_15180_gb300 import vine  # noqa: E402
+
+KEYS = ("theta", "l", "tip", "N", "status", "iters")
+
+
+def _requests(k, replicate=0):
+    rng = np.random.default_rng(100 + replicate)
+    out = []
+    for j in range(k):
+        n = int(rng.integers(1, 9))
+        out.append(scenes.config3(n, replicate=700 + 31 * replicate + j, n_range=(20, 60)))
+    return out
+
+
+def _batch_result(sc):
+    b = vine.Batch(sc)
+    b.simulate()
+    st = b.state()
+    b.close()
+    return dict(theta=st["theta"], l=st["l"], tip=st["tip"], N=st["N"], status=st["status"], iters=st["iters"])
+
+
+def _wait(srv, rid, limit_s=120.0):
+    t0 = time.time()
+    while time.time() - t0 < limit_s:
+        r = srv.poll(rid, timeout_us=200000)
+        if r is not None:
+            return r
+    raise AssertionError("request %d not finished within %.0f s" % (rid, limit_s))
+
+
+def _same(a, b, what):
+    for k in KEYS:
+        assert np.array_equal(np.asarray(a[k]).reshape(-1), np.asarray(b[k]).reshape(-1)), (what, k)
+
+
+def test_results_same_alone_in_mix_and_batched():
+    reqs = _requests(6)
+    ref = [_batch_result(sc) for sc in reqs]
+    srv = vine.Server(steps_per_tick=3, max_slots=512, max_links=64, max_obs=200, max_act=8, max_request=16)
+    alone = []
+    for sc in reqs:
+        rid = srv.submit(sc)
+        assert rid is not None
+        alone.append(_wait(srv, rid))
+    # the same requests submitted together, interleaved with other traffic
+    filler = _requests(6, replicate=1)
+    ids = []
+    for sc, f in zip(reqs, filler):
+        ids.append(srv.submit(sc))
+        srv.submit(f)
+        time.sleep(0.002)  # arrive while earlier ones are on the GPU
+    assert all(i is not None for i in ids)
+    mix = [_wait(srv, i) for i in ids]
+    st = srv.stats()
+    print("served: %d requests in %d ticks, %d robot-link-steps" % (st["requests_done"], st["ticks"],
+                                                                   st["robot_link_steps"]))
+    for j in range(len(reqs)):
+        _same(alone[j], ref[j], "alone vs batch, request %d" % j)
+        _same(mix[j], ref[j], "mix vs batch, request %d" % j)
+        assert mix[j]["rls"] == alone[j]["rls"]
+        assert mix[j]["t_submit"] <= mix[j]["t_admit"] <= mix[j]["t_done"]
+    srv.close()
+
+
+def test_admission_by_free_slots():
+    srv = vine.Server(max_slots=8, max_request=8, max_links=64, max_obs=200, max_act=8, steps_per_tick=2)
+    big = scenes.config3(6, replicate=900, n_range=(50, 60))
+    r1 = srv.submit(big)
+    assert r1 is not None
+    assert srv.submit(scenes.config3(6, replicate=901, n_range=(20, 30))) is None  # 6 + 6 > 8 slots: busy
+    r_small = srv.submit(scenes.config3(2, replicate=902, n_range=(20, 30)))
+    assert r_small is not None  # 6 + 2 fit
+    assert srv.stats()["free_slots"] == 0
+    _wait(srv, r1)
+    _wait(srv, r_small)
+    assert srv.stats()["free_slots"] == 8
+    assert srv.submit(scenes.config3(6, replicate=901, n_range=(20, 30))) is not None
+    srv.close()
+
+
+def test_refuses_malformed_requests():
+    srv = vine.Server(max_slots=64, max_request=4, max_links=40, max_obs=200, max_act=8)
+    with pytest.raises(vine.VineError) as e:
+        srv.submit(scenes.config3(5, replicate=903, n_range=(20, 30)))  # more robots than max_request
+    assert e.value.status == vine.VINE_EINVAL
+    with pytest.raises(vine.VineError) as e:
+        srv.submit(scenes.config3(2, replicate=904, n_range=(41, 50)))  # links beyond the slot capacity
+    assert e.value.status == vine.VINE_EINVAL
+    sc = scenes.config3(2, replicate=905, n_range=(20, 30))
+    sc["radius"] = sc["radius"].copy()
+    sc["radius"][1] = np.nan  # invalid value: that robot only is flagged
+    r = _wait(srv, srv.submit(sc))
+    assert r["status"][1] == vine.INST_BADINPUT and r["N"][1] == 0
+    assert r["N"][0] == sc["n_links"][0]
+    with pytest.raises(vine.VineError) as e:
+        srv.poll(123456789)
+    assert e.value.status == vine.VINE_EINVAL
+    srv.close()
+
+
+def test_poll_timeout_then_result():
+    srv = vine.Server(max_slots=256, max_request=64, max_links=320, steps_per_tick=4)
+    sc = scenes.config3(64, replicate=906, n_range=(200, 300))
+    rid = srv.submit(sc)
+    assert srv.poll(rid, timeout_us=0) is None  # 64 robots x 200-300 links are not done at once
+    r = _wait(srv, rid, limit_s=300.0)
+    assert np.all((r["N"] == sc["n_links"]) | (r["status"] == vine.INST_NONFINITE))
+    srv.close()
