@@ -399,7 +399,7 @@ class Server:
     def poll(self, rid: int, timeout_us: int = 0):
         """Result dict of a finished request (then released), or None if it is
         not finished within timeout_us."""
-        n, T = self._sizes[rid]
+        n, T = self._sizes.get(rid, (1, 1))  # unknown ids are reported by the library
         out = dict(theta=np.zeros(max(T, 1), np.float32), l=np.zeros(n, np.float32), tip=np.zeros((n, 2), np.float32),
                    N=np.zeros(n, np.int32), status=np.zeros(n, np.int32), iters=np.zeros(n, np.int32))
         info = vine_request_info()
