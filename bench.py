@@ -271,20 +271,23 @@ def serve_leg(args, vine, scenes):
     """Serving loop on request streams shaped like the serving workload
     (each request U{1..256} robots drawn as the uneven batch with U{20..300}
     links and 5-200 obstacles).  A pool of distinct requests is generated once
-    and cycled.  (1) capacity: closed loop, the client keeps the server full;
+    and cycled.  (1) capacity: closed loop, the client keeps the server's
+    slots full; robot-link-steps of the requests completed inside the window;
     (2) Poisson arrivals at 70 % of that capacity: p50/p99 latency from
     arrival to completion; (3) Poisson arrivals at 2000 requests/s (the
-    workload's rate, far beyond capacity): achieved vs offered."""
+    workload's rate, far beyond capacity): achieved vs offered.  Each phase
+    drains before the next."""
     import threading
 
     pool_t, pool = scenes.serve_requests(args.serve_pool, rate_hz=2000.0)
     sizes = [(int(len(r["n_links"])), scenes.robot_link_steps(r["n_links"])) for r in pool]
     srv = vine.Server(max_slots=args.serve_slots, max_links=320, max_obs=200, max_act=8, max_request=256,
-                      steps_per_tick=args.serve_tick)
+                      steps_per_tick=args.serve_tick, lanes=args.serve_lanes)
 
-    def run(rate, duration, warm):
-        """Open loop at `rate` req/s (None: closed loop).  Returns per-request
-        (arrival, done, rls) of the requests that arrived after `warm`."""
+    def run(rate, duration):
+        """Submissions for `duration` s: open loop at `rate` req/s (None:
+        closed loop).  Returns [(arrival, done, rls)] relative to the start,
+        the number submitted, and the drain end."""
         rng = np.random.default_rng(55)
         done, lock = [], threading.Lock()
         outstanding = {}
@@ -295,7 +298,7 @@ def serve_leg(args, vine, scenes):
             while not stop[0] or outstanding:
                 with lock:
                     items = list(outstanding.items())
-                for rid, (t_arr, k) in items:
+                for rid, t_arr in items:
                     r = srv.poll(rid, timeout_us=0)
                     if r is not None:
                         with lock:
@@ -306,10 +309,8 @@ def serve_leg(args, vine, scenes):
         th = threading.Thread(target=poller, daemon=True)
         th.start()
         k, t_next = 0, t0
-        while True:
+        while vine.serve_clock() - t0 < duration:
             now = vine.serve_clock()
-            if now - t0 >= duration:
-                break
             if rate is None:
                 t_arr = now
             else:
@@ -318,43 +319,45 @@ def serve_leg(args, vine, scenes):
                     continue
                 t_arr = t_next
                 t_next += rng.exponential(1.0 / rate)
-            j = k % len(pool)
-            while True:  # admission by free slots: retry while busy
-                rid = srv.submit(pool[j])
-                if rid is not None or vine.serve_clock() - t0 >= duration + 30.0:
-                    break
+            rid = srv.submit(pool[k % len(pool)])
+            while rid is None and vine.serve_clock() - t0 < duration:  # slots full: retry
                 time.sleep(0.0005)
+                rid = srv.submit(pool[k % len(pool)])
             if rid is None:
                 break
             with lock:
-                outstanding[rid] = (t_arr, j)
+                outstanding[rid] = t_arr
             k += 1
         stop[0] = True
-        th.join(timeout=120.0)
-        t_end = vine.serve_clock() - t0
-        kept = [d for d in done if d[0] >= warm]
-        return kept, k, t_end
+        th.join(timeout=300.0)
+        return done, k, vine.serve_clock() - t0
 
     out = {}
-    kept, k, t_end = run(None, args.serve_seconds, 1.0)
-    span = max(d[1] for d in kept) - min(d[0] for d in kept) if kept else 1.0
-    cap_rls = sum(d[2] for d in kept) / span if kept else 0.0
-    cap_req = len(kept) / span if kept else 0.0
-    out["capacity"] = {"requests_per_s": cap_req, "robot_link_steps_per_s": cap_rls, "requests": len(kept)}
-    rate = max(0.7 * cap_req, 0.5)
-    kept, k, t_end = run(rate, args.serve_seconds + 2.0, 2.0)
-    lat = np.array([d[1] - d[0] for d in kept]) if kept else np.zeros(1)
-    span = max(d[1] for d in kept) - min(d[0] for d in kept) if kept else 1.0
+    warm = 3.0
+    done, k, t_end = run(None, args.serve_seconds)
+    win = [d for d in done if warm <= d[1] <= args.serve_seconds]
+    span = args.serve_seconds - warm
+    cap_req = len(win) / span
+    out["capacity"] = {"requests_per_s": cap_req, "robot_link_steps_per_s": sum(d[2] for d in win) / span,
+                       "requests": len(win), "window_s": span}
+    rate = max(0.7 * cap_req, 0.2)
+    done, k, t_end = run(rate, args.serve_seconds + 2.0)
+    kept = [d for d in done if d[0] >= 2.0]
+    lat = np.array([d[1] - d[0] for d in kept]) if kept else np.full(1, np.nan)
+    win = [d for d in done if 2.0 <= d[1] <= args.serve_seconds + 2.0]
     out["poisson"] = {"offered_requests_per_s": rate, "requests": len(kept),
-                      "robot_link_steps_per_s": sum(d[2] for d in kept) / span if kept else 0.0,
+                      "robot_link_steps_per_s": sum(d[2] for d in win) / args.serve_seconds,
                       "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99))}
-    kept, k, t_end = run(2000.0, 3.0, 0.0)
-    out["offered_2000"] = {"offered_requests_per_s": 2000.0, "submitted": k, "completed": len(kept),
-                           "achieved_requests_per_s": len(kept) / max(t_end, 1e-9),
-                           "note": "submissions block while the slots are full, so arrivals fall behind"}
+    done, k, t_end = run(2000.0, 3.0)
+    win = [d for d in done if d[1] <= 3.0]
+    out["offered_2000"] = {"offered_requests_per_s": 2000.0, "submitted": k, "completed_in_3s": len(win),
+                           "achieved_requests_per_s": len(win) / 3.0,
+                           "note": "submission blocks while the slots are full, so arrivals fall behind"}
     st = srv.stats()
-    out.update({"slots": st["max_slots"], "steps_per_tick": args.serve_tick, "ticks": st["ticks"],
-                "pool": len(pool), "mean_robots_per_request": float(np.mean([s[0] for s in sizes])),
+    out.update({"slots": st["max_slots"], "steps_per_tick": args.serve_tick, "lanes": args.serve_lanes,
+                "launches": st["ticks"], "pool": len(pool),
+                "mean_robots_per_request": float(np.mean([s[0] for s in sizes])),
+                "mean_robot_link_steps_per_request": float(np.mean([s[1] for s in sizes])),
                 "what": "vine_server continuous batching; latency = completion - arrival (queueing included)"})
     srv.close()
     return out
@@ -418,10 +421,11 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--traffic", type=float, default=None)
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--serve-seconds", type=float, default=6.0)
+    ap.add_argument("--serve-seconds", type=float, default=12.0)
     ap.add_argument("--serve-pool", type=int, default=24)
-    ap.add_argument("--serve-slots", type=int, default=16384)
-    ap.add_argument("--serve-tick", type=int, default=8)
+    ap.add_argument("--serve-slots", type=int, default=8192)
+    ap.add_argument("--serve-lanes", type=int, default=4)
+    ap.add_argument("--serve-tick", type=int, default=32)
     args = ap.parse_args()
     res = run_reference(args) if args.impl == "reference" else run_gpu(args)
     if res is not None:

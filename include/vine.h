@@ -328,11 +328,14 @@ vine_status vine_spam_tables_noalloc(const double* l0, int32_t n_tab, const vine
  * A server owns a fixed arena of robot slots (design, obstacles, joint
  * angles and counters of one robot each, capacities below), the sPAM force
  * tables of every cell length seen so far and the wrinkling-energy table, and
- * one worker thread that owns its CUDA stream.  Each worker tick admits the
- * waiting requests into free slots (copy in, validate, encode, build missing
- * tables), grows every active robot by up to steps_per_tick links in one
- * persistent launch (largest remaining work first), reads back the links
- * present and status of the active robots, and retires the requests whose
+ * one worker thread that owns its CUDA streams.  The worker admits waiting
+ * requests into free slots (copy in, validate, encode, build missing tables)
+ * and assigns each to one of `lanes` launch lanes.  Each lane repeatedly
+ * launches the persistent growth kernel over up to `window` robots of its
+ * requests, oldest requests first, for up to steps_per_tick links each, on
+ * its own stream; lanes overlap on the GPU, so one lane's launch finishing
+ * its slowest robots leaves the SMs to the other.  After each launch the
+ * lane reads back links present and status, and retires the requests whose
  * robots are all done (reached n_links, or stopped non-finite / bad input).
  * A robot's result does not depend on the requests it shared launches with.
  * ------------------------------------------------------------------------- */
@@ -345,8 +348,10 @@ typedef struct {
   int32_t max_obs;          /* per slot: obstacles (0: 256) */
   int32_t max_act;          /* per slot: actuators (0: 16) */
   int32_t max_request;      /* robots per request (0: 256) */
-  int32_t steps_per_tick;   /* growth steps per robot per launch (0: 8) */
+  int32_t steps_per_tick;   /* growth steps per robot per launch (0: 32) */
   int32_t max_tables;       /* distinct sPAM cell lengths held (0: 256) */
+  int32_t lanes;            /* concurrent launch lanes, 1..8 (0: 4) */
+  int32_t window;           /* robots per launch and lane (0: half the resident warps) */
 } vine_server_config;
 
 typedef struct {

@@ -77,8 +77,10 @@ __global__ void init_kernel(const InitArgs A) {
     const float rx = (float)((double)cx - (double)bx), ry = (float)((double)cy - (double)by);
     if (k == 0) {
       badl = badl || !(fin(cx) && fin(cy) && fin(a) && a > 0.f);
+      // radius, and the squared contact distance (R + r)^2 with a 2e-6 margin
+      // for the FP32 pre-test (the penetration itself is evaluated exactly)
       const double rr = (double)R + (double)a;
-      A.obs[od + (o - o0)] = make_float4(rx, ry, (float)rr, -(float)(rr * rr));
+      A.obs[od + (o - o0)] = make_float4(rx, ry, a, -(float)(rr * rr * (1.0 + 2e-6)));
     } else {
       badl = badl || !(k == 1 && fin(cx) && fin(cy) && fin(a) && a > 0.f && fin(b) && b > 0.f);
       A.obs[od + (o - o0)] = make_float4(rx, ry, a, b);

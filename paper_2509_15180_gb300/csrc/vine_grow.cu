@@ -97,6 +97,7 @@ struct Smem {
   float4* act;
   float *TH, *TH0, *DTH, *LUX, *LUY, *G, *DD, *C0, *C1, *C2, *C3, *C4, *C5, *FX, *FY, *TL;
   float* LX;  // distal-link couplings: g_l contact part, h_ll, q0, q1, q2
+  int* Q;     // contact candidates of the link in progress, [kContactQueue][32 lanes]
 };
 
 __device__ __forceinline__ Smem carve(float* base, const GrowArgs& A) {
@@ -109,12 +110,50 @@ __device__ __forceinline__ Smem carve(float* base, const GrowArgs& A) {
   s.DD = p + 6 * n; s.C0 = p + 7 * n; s.C1 = p + 8 * n; s.C2 = p + 9 * n; s.C3 = p + 10 * n; s.C4 = p + 11 * n;
   s.C5 = p + 12 * n; s.FX = p + 13 * n; s.FY = p + 14 * n; s.TL = p + 15 * n;
   s.LX = p + 16 * n;
+  s.Q = reinterpret_cast<int*>(p + 16 * n + 8);
   return s;
+}
+
+// The wrinkling moment of Sec. 3.2 written in p = pi - gamma_0, the angle of
+// the unwrinkled arc's complement (sin^2(p/2) = eps_c / s, s = sin(|theta|/2)):
+//   m = Nn / Dn,  Nn = 2p - sin 2p,  Dn = 4 (sin p - p cos p),
+//   dm/dtheta = -4 eps_c cos(theta/2) F / (Dn^2 s^2),
+//   F = 4 sin^2 p - p sin 2p - 2p^2  (= sin p Dn - p Nn).
+// For a strongly bent joint p is small and all three are differences of
+// nearly equal terms (Nn, Dn ~ p^3, F ~ p^6): their Taylor series are used
+// below p = 1 (F: below 1.6), which keeps FP32 accuracy.
+__device__ __forceinline__ void wrinkle_terms(float p, float& Nn, float& Dn, float& F) {
+  const float p2 = p * p;
+  if (p < 1.f) {
+    const float x2 = 4.f * p2;
+    Nn = 8.f * p2 * p *
+         (1.6666666667e-1f + x2 * (-8.3333333333e-3f + x2 * (1.9841269841e-4f + x2 * (-2.7557319224e-6f +
+         x2 * (2.5052108385e-8f + x2 * (-1.6059043837e-10f + x2 * 7.6471637318e-13f))))));
+    Dn = 4.f * p2 * p *
+         (3.3333333333e-1f + p2 * (-3.3333333333e-2f + p2 * (1.1904761905e-3f + p2 * (-2.2045855379e-5f +
+         p2 * (2.5052108385e-7f + p2 * -1.9270852604e-9f)))));
+  } else {
+    float sp, cp;
+    sincosf(p, &sp, &cp);
+    Nn = 2.f * p - 2.f * sp * cp;
+    Dn = 4.f * (sp - p * cp);
+  }
+  if (p < 1.6f) {
+    const float x2 = 4.f * p2;
+    const float x6 = x2 * x2 * x2;
+    F = x6 * (-1.3888888889e-3f + x2 * (4.9603174603e-5f + x2 * (-8.2671957672e-7f + x2 * (8.3507027951e-9f +
+        x2 * (-5.7353727989e-11f + x2 * (2.8676863994e-13f + x2 * (-1.0933444878e-15f + x2 * (3.2882540986e-18f +
+        x2 * -8.0071122532e-21f))))))));
+  } else {
+    float sp, cp;
+    sincosf(p, &sp, &cp);
+    F = 4.f * sp * sp - 2.f * p * sp * cp - 2.f * p2;
+  }
 }
 
 // Wrinkling restoring moment per unit pi P R^3 (Sec. 3.2): value m, slope dm
 // and energy u = integral from 0.  At or below onset a linear ramp to 1/2;
-// above onset gamma_0 = 2 asin(sqrt(1 - eps_c / s)), s = sin(|theta| / 2).
+// above onset the form of wrinkle_terms.
 __device__ __forceinline__ void wrinkle(const GrowArgs& A, float th, float& m, float& dm, float& u) {
   const float a = fabsf(th);
   if (a <= A.theta_c) {
@@ -126,15 +165,11 @@ __device__ __forceinline__ void wrinkle(const GrowArgs& A, float th, float& m, f
   const float ac = fminf(a, kPi);
   float s, cs;
   sincosf(0.5f * ac, &s, &cs);
-  const float q = sqrtf(fmaxf(1.f - A.eps_c / s, 0.f));
-  const float g = 2.f * asinf(q);
-  float sg, cg;
-  sincosf(g, &sg, &cg);
-  const float pg = kPi - g;
-  const float Nn = 2.f * sg * cg + 2.f * pg;
-  const float Dn = 4.f * (sg + pg * cg);
+  const float p = 2.f * asinf(sqrtf(fminf(A.eps_c / s, 1.f)));
+  float Nn, Dn, F;
+  wrinkle_terms(p, Nn, Dn, F);
   m = copysignf(Nn / Dn, th);
-  dm = (a < kPi) ? 4.f * A.eps_c * cs * (Nn * pg - Dn * sg) / (Dn * Dn * s * s) : 0.f;
+  dm = (a < kPi) ? -4.f * A.eps_c * cs * F / (Dn * Dn * s * s) : 0.f;
   if (a >= kPi) {
     u = A.U_pi + A.m_pi * (a - kPi);
   } else {
@@ -207,16 +242,76 @@ __device__ __forceinline__ void add_contact(const Smem& S, int j, float pen, flo
   }
 }
 
-// Penetration of a disc (offset dx, dy from the obstacle centre, radius R).
-// Returns pen > 0, the outward normal and the curvature kinv of the signed
-// distance when the disc overlaps obstacle ob.
-__device__ __forceinline__ float disc_pen(const float4 ob, float dx, float dy, float R, float fbx, float fby,
-                                          float& nx, float& ny, float& kinv) {
-  if (ob.w < 0.f) {  // circle: ob.z = R + r, -ob.w = (R + r)^2
-    const float d2 = dx * dx + dy * dy;
-    if (!(d2 < -ob.w)) return 0.f;
-    const float d = sqrtf(d2);
-    const float pen = ob.z - d;
+// Float-float square and square root (error-free products by FMA; one Newton
+// correction of the FP32 root).
+__device__ __forceinline__ FF ff_sq(FF a) {
+  const float p = a.hi * a.hi;
+  float e = fmaf(a.hi, a.hi, -p);
+  e = fmaf(2.f * a.hi, a.lo, e);
+  return quick_two_sum(p, e);
+}
+__device__ __forceinline__ FF ff_sqrt(FF a) {
+  const float s = sqrtf(a.hi);
+  if (!(s > 0.f)) return {s, 0.f};
+  const float r = fmaf(-s, s, a.hi) + a.lo;
+  return quick_two_sum(s, r / (2.f * s));
+}
+__device__ __forceinline__ FF ff_neg(FF a) { return {-a.hi, -a.lo}; }
+
+// Penetration of a disc of radius R centred at (x, y) (float-float, relative
+// to the base) into obstacle ob, in float-float arithmetic, with the outward
+// normal and the curvature kinv of the signed distance.  The plain FP32
+// difference R + r - |x - c| loses ~5e-9 m to cancellation, a sizeable part
+// of a shallow penetration (the contact force is proportional to it), so
+// active contacts are resolved here.  May return pen <= 0 (not in contact).
+__device__ __forceinline__ float disc_pen_precise(const float4 ob, FF x, FF y, float R, float fbx, float fby, float& nx,
+                                  float& ny, float& kinv) {
+  const FF dx = ff_add(two_sum(x.hi, -ob.x), x.lo), dy = ff_add(two_sum(y.hi, -ob.y), y.lo);
+  if (ob.w < 0.f) {  // circle: ob.z = r
+    const FF d = ff_sqrt(ff_add(ff_sq(dx), ff_sq(dy)));
+    if (d.hi > 0.f) {
+      const float id = 1.f / d.hi;
+      nx = dx.hi * id;
+      ny = dy.hi * id;
+      kinv = id;
+    } else {
+      nx = fbx;
+      ny = fby;
+      kinv = 0.f;
+    }
+    return ff_add(two_sum(R, ob.z), ff_neg(d)).hi;
+  }
+  const float sx = dx.hi >= 0.f ? 1.f : -1.f, sy = dy.hi >= 0.f ? 1.f : -1.f;
+  const FF ax = ff_add(dx.hi >= 0.f ? dx : ff_neg(dx), -ob.z);
+  const FF ay = ff_add(dy.hi >= 0.f ? dy : ff_neg(dy), -ob.w);
+  FF sd;
+  kinv = 0.f;
+  if (ax.hi > 0.f && ay.hi > 0.f) {
+    sd = ff_sqrt(ff_add(ff_sq(ax), ff_sq(ay)));
+    const float id = 1.f / sd.hi;
+    nx = sx * ax.hi * id;
+    ny = sy * ay.hi * id;
+    kinv = id;
+  } else if (ax.hi > 0.f) {
+    sd = ax; nx = sx; ny = 0.f;
+  } else if (ay.hi > 0.f) {
+    sd = ay; nx = 0.f; ny = sy;
+  } else if (ax.hi >= ay.hi) {
+    sd = ax; nx = sx; ny = 0.f;
+  } else {
+    sd = ay; nx = 0.f; ny = sy;
+  }
+  return ff_add(FF{R, 0.f}, ff_neg(sd)).hi;
+}
+
+// Penetration in plain FP32 (error ~5e-9 m from rounding the offsets, the
+// squared distance and R + r), with the outward normal and the curvature
+// kinv of the signed distance.
+__device__ __forceinline__ float disc_pen_fast(const float4 ob, FF x, FF y, float R, float fbx, float fby, float& nx,
+                                               float& ny, float& kinv) {
+  const float dx = (x.hi - ob.x) + x.lo, dy = (y.hi - ob.y) + y.lo;
+  if (ob.w < 0.f) {  // circle: ob.z = r
+    const float d = sqrtf(dx * dx + dy * dy);
     if (d > 0.f) {
       const float id = 1.f / d;
       nx = dx * id;
@@ -227,10 +322,9 @@ __device__ __forceinline__ float disc_pen(const float4 ob, float dx, float dy, f
       ny = fby;
       kinv = 0.f;
     }
-    return pen;
+    return (R + ob.z) - d;
   }
   const float ax = fabsf(dx) - ob.z, ay = fabsf(dy) - ob.w;
-  if (!(fmaxf(ax, ay) < R)) return 0.f;
   const float sx = dx >= 0.f ? 1.f : -1.f, sy = dy >= 0.f ? 1.f : -1.f;
   float sd;
   kinv = 0.f;
@@ -250,6 +344,28 @@ __device__ __forceinline__ float disc_pen(const float4 ob, float dx, float dy, f
     sd = ay; nx = 0.f; ny = sy;
   }
   return R - sd;
+}
+
+// FP32 pre-test of a disc (centre x, y as float-float relative to the base)
+// against obstacle ob, with a small outward margin (circles: ob.w =
+// -(R + r)^2 inflated by 2e-6 at encoding; boxes: Rpre = R (1 + 1e-6)), so
+// that no pair with a positive penetration is missed.
+__device__ __forceinline__ bool contact_candidate(const float4 ob, FF x, FF y, float Rpre) {
+  const float dx = (x.hi - ob.x) + x.lo, dy = (y.hi - ob.y) + y.lo;
+  if (ob.w < 0.f) return dx * dx + dy * dy < -ob.w;
+  return fmaxf(fabsf(dx) - ob.z, fabsf(dy) - ob.w) < Rpre;
+}
+
+// Penetration of a disc (centre x, y as float-float relative to the base,
+// radius R) into obstacle ob: an FP32 test with a small outward margin
+// (circles: ob.w = -(R + r)^2 inflated by 2e-6 at encoding; boxes: Rpre =
+// R (1 + 1e-6)), then the float-float evaluation for the pairs that pass.
+// Returns pen > 0 with the outward normal and the curvature kinv of the
+// signed distance when the disc overlaps the obstacle, else pen <= 0.
+__device__ __forceinline__ float disc_pen(const float4 ob, FF x, FF y, float R, float Rpre, float fbx, float fby,
+                                          float& nx, float& ny, float& kinv) {
+  if (!contact_candidate(ob, x, y, Rpre)) return 0.f;
+  return disc_pen_precise(ob, x, y, R, fbx, fby, nx, ny, kinv);
 }
 
 struct EvalOut {
@@ -358,24 +474,45 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
 #pragma unroll
       for (int q = 0; q < 5; ++q) S.LX[q] = 0.f;
     }
+    // FP32 pre-test of every disc x obstacle pair; the candidates go to the
+    // lane's queue and are resolved after the sweep (or when the queue
+    // fills), so the warp runs the long contact code once per queue entry
+    // of its busiest lane instead of once per pair that any lane hits.
     float pen2 = 0.f, pen1 = 0.f;
-    for (int o = 0; o < I.n_obs; ++o) {
-      const float4 ob = S.obs[o];
-#pragma unroll
-      for (int k = 0; k < KS; ++k) {
-        const float dx = (xk[k].hi - ob.x) + xk[k].lo;
-        const float dy = (yk[k].hi - ob.y) + yk[k].lo;
+    const float Rpre = I.R * (1.f + 1e-6f);
+    int qn = 0;
+    auto resolve = [&]() {
+      for (int q = 0; q < qn; ++q) {
+        const int code = S.Q[q * 32 + lane];
+        const int o = code / KS, k = code - o * KS;
+        const float fr = (float)(k + 1) / (float)KS;
+        const FF x = ff_add(px, fr * lx), y = ff_add(py, fr * ly);
+        const float4 ob = S.obs[o];
         float nx, ny, kinv;
-        const float pen = disc_pen(ob, dx, dy, I.R, fbx, fby, nx, ny, kinv);
+        float pen = disc_pen_fast(ob, x, y, I.R, fbx, fby, nx, ny, kinv);
+        // shallow contacts: the FP32 rounding is a sizeable part of pen, and
+        // of the contact force that is proportional to it
+        if (pen < kRefinePen * I.R) pen = disc_pen_precise(ob, x, y, I.R, fbx, fby, nx, ny, kinv);
         if (pen > 0.f) {
-          const float fr = (float)(k + 1) / (float)KS;
           pen2 += pen * pen;
           pen1 += pen;
           if (exact) add_contact<true>(S, j, pen, nx, ny, kinv, fr, lx, ly, kap, last, ulx, uly);
           else add_contact<false>(S, j, pen, nx, ny, kinv, fr, lx, ly, kap, last, ulx, uly);
         }
       }
+      qn = 0;
+    };
+    for (int o = 0; o < I.n_obs; ++o) {
+      const float4 ob = S.obs[o];
+#pragma unroll
+      for (int k = 0; k < KS; ++k) {
+        if (contact_candidate(ob, xk[k], yk[k], Rpre)) {
+          S.Q[qn * 32 + lane] = o * KS + k;
+          if (++qn == kContactQueue) resolve();
+        }
+      }
     }
+    resolve();
     Jl += (double)(A.w_c * I.kc * pen2);
     Sl += (double)(A.w_c * I.kc) * ((double)pen2 + 2.0 * (double)I.R * (double)pen1);
     px = ff_add(px, lx);
@@ -898,7 +1035,8 @@ const void* pick(int ks) {
 }  // namespace
 
 size_t grow_smem_per_warp(int nmax, int omax, int amax) {
-  return sizeof(float4) * (size_t)(omax + amax) + sizeof(float) * (16 * (size_t)nmax + 8);
+  return sizeof(float4) * (size_t)(omax + amax) + sizeof(float) * (16 * (size_t)nmax + 8) +
+         sizeof(int) * 32 * (size_t)kContactQueue;
 }
 
 // The attribute is per kernel and process-wide: batches and servers with
@@ -1075,9 +1213,8 @@ __global__ void contacts_kernel(const InstDev* inst, int n_inst, const float4* o
         for (int k = 1; k <= ks && !hit; ++k) {
           const float fr = (float)k / (float)ks;
           const FF xk = ff_add(px, fr * lx), yk = ff_add(py, fr * ly);
-          const float dx = (xk.hi - b4.x) + xk.lo, dy = (yk.hi - b4.y) + yk.lo;
           float nx, ny, kinv;
-          hit = disc_pen(b4, dx, dy, I.R, -uy, ux, nx, ny, kinv) > 0.f;
+          hit = disc_pen(b4, xk, yk, I.R, I.R * (1.f + 1e-6f), -uy, ux, nx, ny, kinv) > 0.f;
         }
         if (hit) {
           if (pass == 1 && base + cnt < max_pairs && pairs) {

@@ -2,7 +2,7 @@
 //
 // HBM layout of a batch (one cudaMalloc, carved in this order):
 //   InstDev  inst[n]            80 B per instance: derived constants + CSR offsets
-//   float4   obs[n_obs_total]   (cx - bx, cy - by, p, q): circle p = R + r, q = -(R + r)^2;
+//   float4   obs[n_obs_total]   (cx - bx, cy - by, p, q): circle p = r, q = -(R + r)^2 (1 + 2e-6);
 //                               box p = half-width, q = half-height (> 0)
 //   float4   act[n_act_total]   (begin, end, P_act, table index as int bits, side in the sign bit)
 //   float4   tab_hdr[n_tab]     (eps_lo, h, 1/h, G(0)) per sPAM force table
@@ -21,6 +21,8 @@ namespace vine {
 constexpr int kKnots = 256;        // sPAM force table knots (uniform in strain)
 constexpr int kUCells = 1024;      // wrinkling energy table cells on [theta_c, pi]
 constexpr int kWarpsPerCta = 4;    // warps per CTA of the growth kernel
+constexpr int kContactQueue = 8;   // contact candidates a lane queues per link before resolving them
+constexpr float kRefinePen = 2e-3f;  // penetrations below this fraction of R are re-evaluated in float-float
 constexpr int kMaxLinks = 1024;
 constexpr int kMaxObs = 1024;
 constexpr int kMaxAct = 64;

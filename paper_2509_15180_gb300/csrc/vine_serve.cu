@@ -71,6 +71,7 @@ struct Request {
   int64_t out_base = 0;     // offset in the tick's result buffers
   double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
   int state = 0;            // 0 waiting, 1 active, 2 done, 3 failed
+  int lane = 0;             // launch lane its robots run in
   std::vector<float> theta, l_last, tip;
   std::vector<int32_t> n_present, status, iters;
   int64_t rls = 0;
@@ -112,6 +113,22 @@ __global__ void slot_reset_kernel(const int* slots, int n, int* n_cur, float* l_
 
 }  // namespace
 
+// A launch lane: its own stream, work queue and read-back buffers, so that
+// while one lane's launch waits on its slowest robot another lane's launch
+// fills the idle SMs.  Robots stay in the lane of their request.
+struct Lane {
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev = nullptr;
+  int* d_order = nullptr;   // [S]
+  int* d_counter = nullptr;
+  int* h_order = nullptr;   // pinned [S]
+  int* h_ncur = nullptr;    // pinned [S]
+  int* h_status = nullptr;  // pinned [S]
+  std::vector<int> robots;  // slots of the launch in flight
+  bool busy = false;
+  int load = 0;             // robots of its active requests
+};
+
 struct vine_server {
   vine_params prm{};
   vine_server_config cfg{};
@@ -134,13 +151,9 @@ struct vine_server {
   int* d_res_status = nullptr;
   int* d_res_iters = nullptr;
   long long* d_res_rls = nullptr;
-  // pinned host mirrors
-  int* h_order = nullptr;
-  int* h_ncur = nullptr;
-  int* h_status = nullptr;
+  // pinned host result staging
   char* h_res = nullptr;
   size_t h_res_bytes = 0;
-  cudaEvent_t ev = nullptr;
   // host state (mu)
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -155,7 +168,10 @@ struct vine_server {
   std::string error;
   vine_server_stats stats{};
   // worker-only per-slot host info
-  std::vector<int> slot_target, slot_nobs, slot_ncur;
+  std::vector<int> slot_target, slot_nobs, slot_ncur, slot_status;
+  std::vector<Lane> lanes;
+  int window = 0;             // robots per launch and lane
+  cudaEvent_t ev_admit = nullptr;
   std::thread worker;
 };
 
@@ -259,66 +275,76 @@ cudaError_t admit(vine_server* V, Request* R) {
     V->slot_target[s] = R->n_links[k];
     V->slot_nobs[s] = R->n_obs_r[k];
     V->slot_ncur[s] = 0;
+    V->slot_status[s] = kOK;
   }
+  // the lane with the fewest robots
+  int best = 0;
+  for (int q = 1; q < (int)V->lanes.size(); ++q)
+    if (V->lanes[q].load < V->lanes[best].load) best = q;
+  R->lane = best;
+  V->lanes[best].load += R->n;
   R->t_admit = clock_s();
   R->state = 1;
   V->active.push_back(R);
   return cudaSuccess;
 }
 
-// One growth launch over every active robot that still has links to grow.
-cudaError_t tick(vine_server* V, bool* grew) {
-  cudaStream_t st = V->stream;
+// Launches one growth step batch in lane q: the robots of its requests that
+// still grow, oldest requests first, at most `window` of them, ordered by
+// their contact work for the coming steps (largest first) for the atomic
+// queue.  Returns with *launched = false when the lane has nothing to grow.
+cudaError_t launch_lane(vine_server* V, int q, bool* launched) {
+  Lane& L = V->lanes[q];
   std::vector<std::pair<double, int>> work;
-  for (Request* R : V->active)
+  for (Request* R : V->active) {
+    if (R->lane != q) continue;
     for (int s : R->slots) {
       const int N = V->slot_ncur[s], T = V->slot_target[s];
-      if (N >= T) continue;
+      if (N >= T || V->slot_status[s] == kNonFinite || V->slot_status[s] == kBadInput) continue;
       const int M = std::min(T, N + V->cfg.steps_per_tick);
       // contact work of steps N+1..M: links x (discs x obstacles + joint terms)
       const double w = 0.5 * (double)(M - N) * (double)(N + 1 + M) * (V->ks * (double)V->slot_nobs[s] + 8.0);
       work.emplace_back(w, s);
     }
-  *grew = !work.empty();
+    if ((int)work.size() >= V->window) break;
+  }
+  *launched = !work.empty();
   if (work.empty()) return cudaSuccess;
   std::stable_sort(work.begin(), work.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
-  for (size_t k = 0; k < work.size(); ++k) V->h_order[k] = work[k].second;
-  cudaError_t e = cudaMemcpyAsync(const_cast<int*>(V->args.order), V->h_order, sizeof(int) * work.size(),
-                                  cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return e;
+  L.robots.resize(work.size());
+  for (size_t k = 0; k < work.size(); ++k) L.h_order[k] = L.robots[k] = work[k].second;
+  cudaError_t e = cudaStreamWaitEvent(L.st, V->ev_admit, 0);  // admitted robots and new tables
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(L.d_order, L.h_order, sizeof(int) * work.size(), cudaMemcpyHostToDevice, L.st);
   GrowArgs a = V->args;
+  a.order = L.d_order;
+  a.counter = L.d_counter;
   a.n_order = (int)work.size();
   a.n_steps = V->cfg.steps_per_tick;
   a.dynamic = 1;
-  e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
-  if (e != cudaSuccess) return e;
-  e = grow_configure(V->ks, V->smem_warp * kWarpsPerCta);
-  if (e != cudaSuccess) return e;
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.counter, 0, sizeof(int), L.st);
+  if (e == cudaSuccess) e = grow_configure(V->ks, V->smem_warp * kWarpsPerCta);
   const int grid = std::max(1, std::min(V->grid, (a.n_order + kWarpsPerCta - 1) / kWarpsPerCta));
-  e = launch_grow(a, V->ks, grid, 32 * kWarpsPerCta, V->smem_warp * kWarpsPerCta, st);
-  if (e != cudaSuccess) return e;
-  e = cudaMemcpyAsync(V->h_ncur, a.n_cur, sizeof(int) * V->S, cudaMemcpyDeviceToHost, st);
-  if (e != cudaSuccess) return e;
-  e = cudaMemcpyAsync(V->h_status, a.status, sizeof(int) * V->S, cudaMemcpyDeviceToHost, st);
-  if (e != cudaSuccess) return e;
-  e = cudaEventRecord(V->ev, st);
-  if (e != cudaSuccess) return e;
-  e = cudaEventSynchronize(V->ev);
-  if (e != cudaSuccess) return e;
-  for (size_t k = 0; k < work.size(); ++k) V->slot_ncur[work[k].second] = V->h_ncur[work[k].second];
-  return cudaSuccess;
+  if (e == cudaSuccess) e = launch_grow(a, V->ks, grid, 32 * kWarpsPerCta, V->smem_warp * kWarpsPerCta, L.st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(L.h_ncur, a.n_cur, sizeof(int) * V->S, cudaMemcpyDeviceToHost, L.st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(L.h_status, a.status, sizeof(int) * V->S, cudaMemcpyDeviceToHost, L.st);
+  if (e == cudaSuccess) e = cudaEventRecord(L.ev, L.st);
+  if (e == cudaSuccess) L.busy = true;
+  return e;
 }
 
-// Requests whose robots are all done: gather their results, free the slots.
-cudaError_t retire(vine_server* V) {
+// Requests of lane q whose robots are all done: gather their results on the
+// admission stream (the lane's launch has finished), free the slots.
+cudaError_t retire(vine_server* V, int q) {
   cudaStream_t st = V->stream;
   std::vector<Request*> done;
   int64_t nsel = 0, links = 0;
   for (Request* R : V->active) {
+    if (R->lane != q) continue;
     bool all = true;
     for (int k = 0; k < R->n && all; ++k) {
       const int s = R->slots[k];
-      all = robot_done(V->slot_ncur[s], V->slot_target[s], V->h_status[s]);
+      all = robot_done(V->slot_ncur[s], V->slot_target[s], V->slot_status[s]);
     }
     if (all) {
       done.push_back(R);
@@ -388,6 +414,7 @@ cudaError_t retire(vine_server* V) {
     for (int k = 0; k < R->n; ++k) R->rls += h_rls[b + k];
     R->t_done = t;
     R->state = 2;
+    V->lanes[R->lane].load -= R->n;
     for (int s : R->slots) V->free_slots.push_back(s);
     R->slots.clear();
     R->image.clear();
@@ -398,17 +425,19 @@ cudaError_t retire(vine_server* V) {
   V->active.erase(std::remove_if(V->active.begin(), V->active.end(), [](Request* R) { return R->state == 2; }),
                   V->active.end());
   V->cv_done.notify_all();
-  V->cv_work.notify_all();  // slots came free
   return cudaSuccess;
 }
 
 void worker_main(vine_server* V) {
   cudaSetDevice(V->device);
+  const int nl = (int)V->lanes.size();
   for (;;) {
     std::vector<Request*> adm;
+    bool any_busy = false;
+    for (const Lane& L : V->lanes) any_busy = any_busy || L.busy;
     {
       std::unique_lock<std::mutex> lk(V->mu);
-      if (V->active.empty())
+      if (V->active.empty() && !any_busy)
         V->cv_work.wait(lk, [&] { return V->stop || !V->waiting.empty(); });
       if (V->stop) break;
       while (!V->waiting.empty()) {
@@ -416,11 +445,11 @@ void worker_main(vine_server* V) {
         V->waiting.pop_front();
       }
     }
+    const double t0 = clock_s();
     cudaError_t e = cudaSuccess;
     for (Request* R : adm) {
       if (e == cudaSuccess) e = admit(V, R);
       if (e != cudaSuccess) {
-        // not admitted: return the promised slots and fail it below
         std::lock_guard<std::mutex> lk(V->mu);
         if (R->state == 0) {
           V->promised -= R->n;
@@ -428,10 +457,32 @@ void worker_main(vine_server* V) {
         }
       }
     }
-    bool grew = false;
-    const double t0 = clock_s();
-    if (e == cudaSuccess) e = tick(V, &grew);
-    if (e == cudaSuccess) e = retire(V);
+    if (e == cudaSuccess && !adm.empty()) e = cudaEventRecord(V->ev_admit, V->stream);
+    // idle lanes: retire what is done, launch what still grows
+    bool progressed = !adm.empty();
+    for (int q = 0; q < nl && e == cudaSuccess; ++q) {
+      Lane& L = V->lanes[q];
+      if (L.busy) {
+        const cudaError_t qe = cudaEventQuery(L.ev);
+        if (qe == cudaErrorNotReady) continue;
+        if (qe != cudaSuccess) {
+          e = qe;
+          break;
+        }
+        for (int s : L.robots) {
+          V->slot_ncur[s] = L.h_ncur[s];
+          V->slot_status[s] = L.h_status[s];
+        }
+        L.busy = false;
+        progressed = true;
+        std::lock_guard<std::mutex> lk(V->mu);
+        V->stats.ticks += 1;
+      }
+      e = retire(V, q);
+      bool launched = false;
+      if (e == cudaSuccess) e = launch_lane(V, q, &launched);
+      progressed = progressed || launched;
+    }
     if (e != cudaSuccess) {
       std::lock_guard<std::mutex> lk(V->mu);
       char b[384];
@@ -445,12 +496,17 @@ void worker_main(vine_server* V) {
       V->cv_done.notify_all();
       break;
     }
-    std::lock_guard<std::mutex> lk(V->mu);
-    if (grew) {
-      V->stats.ticks += 1;
+    any_busy = false;
+    for (const Lane& L : V->lanes) any_busy = any_busy || L.busy;
+    if (any_busy) {
+      std::unique_lock<std::mutex> lk(V->mu);
       V->stats.busy_s += clock_s() - t0;
+      // a launch is in flight: look again shortly, or as soon as a request arrives
+      if (!progressed) V->cv_work.wait_for(lk, std::chrono::microseconds(100));
     }
   }
+  for (Lane& L : V->lanes)
+    if (L.st) cudaStreamSynchronize(L.st);
 }
 
 }  // namespace
@@ -466,8 +522,10 @@ vine_status vine_server_config_default(vine_server_config* c) {
   c->max_obs = 256;
   c->max_act = 16;
   c->max_request = 256;
-  c->steps_per_tick = 8;
+  c->steps_per_tick = 32;
   c->max_tables = 256;
+  c->lanes = 4;
+  c->window = 0;
   return VINE_OK;
 }
 
@@ -502,9 +560,12 @@ vine_status vine_server_create(const vine_params* params, const vine_server_conf
     if (config->max_request) c.max_request = config->max_request;
     if (config->steps_per_tick) c.steps_per_tick = config->steps_per_tick;
     if (config->max_tables) c.max_tables = config->max_tables;
+    if (config->lanes) c.lanes = config->lanes;
+    if (config->window) c.window = config->window;
   }
   if (c.max_slots < 0 || c.max_links < 1 || c.max_links > kMaxLinks || c.max_obs < 1 || c.max_obs > kMaxObs ||
-      c.max_act < 1 || c.max_act > kMaxAct || c.max_request < 1 || c.steps_per_tick < 1 || c.max_tables < 1)
+      c.max_act < 1 || c.max_act > kMaxAct || c.max_request < 1 || c.steps_per_tick < 1 || c.max_tables < 1 ||
+      c.lanes < 1 || c.lanes > 8 || c.window < 0)
     return sfail(VINE_EINVAL, "vine_server_create: configuration out of range");
   auto V = new vine_server();
   V->prm = prm;
@@ -515,8 +576,8 @@ vine_status vine_server_create(const vine_params* params, const vine_server_conf
   V->amax = c.max_act;
   cudaGetDevice(&V->device);
   const int T = c.max_tables;
-  const size_t per_slot = sizeof(InstDev) + 16 * (size_t)(V->omax + V->amax) + 8 * (size_t)V->nmax + 72 + 4 + 12 +
-                          8 + 24 + 7 * 256 / 64;
+  const size_t per_slot = sizeof(InstDev) + 16 * (size_t)(V->omax + V->amax) + 8 * (size_t)V->nmax + 72 +
+                          4 * (size_t)c.lanes + 12 + 8 + 24 + 7 * 256 / 64;
   const size_t na_max = (size_t)c.max_request * c.max_act, no_max = (size_t)c.max_request * c.max_obs;
   const size_t n_req = (size_t)c.max_request;
   V->stage_bytes = up256(4 * n_req * 4 + 12 * n_req + 8 * (n_req + 1) + na_max * 21 + no_max * 17 + 4 * na_max +
@@ -556,7 +617,8 @@ vine_status vine_server_create(const vine_params* params, const vine_server_conf
                o_th = take(4 * Ss * V->nmax), o_n = take(4 * Ss), o_l = take(4 * Ss), o_st = take(4 * Ss),
                o_it = take(4 * Ss), o_cv = take(4 * Ss), o_sp = take(4 * Ss), o_rls = take(8 * Ss),
                o_ev = take(8 * Ss), o_le = take(8 * Ss), o_fb = take(8 * Ss), o_cy = take(8 * Ss),
-               o_rm = take(8 * Ss), o_ord = take(4 * Ss), o_cnt = take(16), o_hdr = take(16 * (size_t)T),
+               o_rm = take(8 * Ss), o_ord = take(4 * Ss * c.lanes), o_cnt = take(16 * (size_t)c.lanes),
+               o_hdr = take(16 * (size_t)T),
                o_tab = take(sizeof(float2) * (size_t)T * kKnots), o_ut = take(sizeof(float2) * (kUCells + 1)),
                o_l0 = take(8 * (size_t)T), o_scr = take(8 * (4 * (size_t)T + (size_t)T * kKnots + 2 * (kUCells + 1))),
                o_cst = take(32), o_stage = take(V->stage_bytes), o_sel = take(4 * Ss), o_oo = take(8 * Ss),
@@ -573,11 +635,15 @@ vine_status vine_server_create(const vine_params* params, const vine_server_conf
   }
   char* m = V->dmem;
   auto cleanup = [&]() {
-    if (V->h_order) cudaFreeHost(V->h_order);
-    if (V->h_ncur) cudaFreeHost(V->h_ncur);
-    if (V->h_status) cudaFreeHost(V->h_status);
+    for (Lane& L : V->lanes) {
+      if (L.h_order) cudaFreeHost(L.h_order);
+      if (L.h_ncur) cudaFreeHost(L.h_ncur);
+      if (L.h_status) cudaFreeHost(L.h_status);
+      if (L.ev) cudaEventDestroy(L.ev);
+      if (L.st) cudaStreamDestroy(L.st);
+    }
     if (V->h_res) cudaFreeHost(V->h_res);
-    if (V->ev) cudaEventDestroy(V->ev);
+    if (V->ev_admit) cudaEventDestroy(V->ev_admit);
     if (V->stream) cudaStreamDestroy(V->stream);
     cudaFree(V->dmem);
     delete V;
@@ -592,10 +658,18 @@ vine_status vine_server_create(const vine_params* params, const vine_server_conf
     }                                               \
   } while (0)
   CKS(cudaStreamCreateWithFlags(&V->stream, cudaStreamNonBlocking));
-  CKS(cudaEventCreateWithFlags(&V->ev, cudaEventBlockingSync | cudaEventDisableTiming));
-  CKS(cudaMallocHost(&V->h_order, 4 * Ss));
-  CKS(cudaMallocHost(&V->h_ncur, 4 * Ss));
-  CKS(cudaMallocHost(&V->h_status, 4 * Ss));
+  CKS(cudaEventCreateWithFlags(&V->ev_admit, cudaEventDisableTiming));
+  V->lanes.resize(c.lanes);
+  for (int q = 0; q < c.lanes; ++q) {
+    Lane& L = V->lanes[q];
+    CKS(cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking));
+    CKS(cudaEventCreateWithFlags(&L.ev, cudaEventDisableTiming));
+    CKS(cudaMallocHost(&L.h_order, 4 * Ss));
+    CKS(cudaMallocHost(&L.h_ncur, 4 * Ss));
+    CKS(cudaMallocHost(&L.h_status, 4 * Ss));
+    L.d_order = (int*)(m + o_ord) + (size_t)q * Ss;
+    L.d_counter = (int*)(m + o_cnt) + 4 * q;
+  }
   V->h_res_bytes = up16(4 * Ss * V->nmax) + up16(8 * Ss) + 4 * up16(4 * Ss) + up16(8 * Ss) + 256;
   CKS(cudaMallocHost(&V->h_res, V->h_res_bytes));
   CKS(cudaMemsetAsync(m, 0, off, V->stream));
@@ -607,6 +681,7 @@ vine_status vine_server_create(const vine_params* params, const vine_server_conf
                            (double*)(m + o_cst), V->stream));
   double cst[4];
   CKS(cudaMemcpyAsync(cst, m + o_cst, sizeof(cst), cudaMemcpyDeviceToHost, V->stream));
+  CKS(cudaEventRecord(V->ev_admit, V->stream));
   CKS(cudaStreamSynchronize(V->stream));
   if (!(std::isfinite(cst[0]) && std::isfinite(cst[1]))) {
     cleanup();
@@ -624,6 +699,10 @@ vine_status vine_server_create(const vine_params* params, const vine_server_conf
   }
   CKS(grow_configure(V->ks, smem_cta));
   V->grid = nsm * grow_max_ctas_per_sm(V->ks, smem_cta);
+  // half the resident warps per lane: two lanes fill the GPU, the others
+  // take over the SMs that a launch finishing its slowest robots leaves idle
+  V->window = c.window > 0 ? c.window : std::max(1, V->grid * kWarpsPerCta / 2);
+  V->cfg.window = V->window;
   GrowArgs& a = V->args;
   a.inst = (const InstDev*)(m + o_inst);
   a.obs = (const float4*)(m + o_obs);
@@ -692,6 +771,7 @@ vine_status vine_server_create(const vine_params* params, const vine_server_conf
   V->slot_target.assign(S, 0);
   V->slot_nobs.assign(S, 0);
   V->slot_ncur.assign(S, 0);
+  V->slot_status.assign(S, 0);
   V->stats.max_slots = S;
   V->worker = std::thread(worker_main, V);
   *out = V;
@@ -842,11 +922,16 @@ vine_status vine_server_destroy(vine_server* V) {
   if (V->worker.joinable()) V->worker.join();
   cudaStreamSynchronize(V->stream);
   for (auto& kv : V->reqs) delete kv.second;
-  cudaFreeHost(V->h_order);
-  cudaFreeHost(V->h_ncur);
-  cudaFreeHost(V->h_status);
+  for (Lane& L : V->lanes) {
+    cudaStreamSynchronize(L.st);
+    cudaFreeHost(L.h_order);
+    cudaFreeHost(L.h_ncur);
+    cudaFreeHost(L.h_status);
+    cudaEventDestroy(L.ev);
+    cudaStreamDestroy(L.st);
+  }
+  cudaEventDestroy(V->ev_admit);
   cudaFreeHost(V->h_res);
-  cudaEventDestroy(V->ev);
   cudaStreamDestroy(V->stream);
   cudaFree(V->dmem);
   delete V;

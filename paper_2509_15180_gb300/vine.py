@@ -54,7 +54,7 @@ class vine_stats(C.Structure):
 class vine_server_config(C.Structure):
     _fields_ = [("device_mem_budget", C.c_size_t)] + [
         (k, C.c_int32) for k in ("max_slots", "max_links", "max_obs", "max_act", "max_request", "steps_per_tick",
-                                 "max_tables")]
+                                 "max_tables", "lanes", "window")]
 
 
 class vine_request_info(C.Structure):
