@@ -205,8 +205,14 @@ def run_gpu(args):
         plain = _plain(scenes, vine, torch, sc, stream, n_plain)
 
     # --- roofline of the growth kernel: algorithmic FP32 flops per launch
-    flops = (40.0 * st_last["link_evaluations"] + 10.0 * st_last["circle_pair_tests"] +
-             14.0 * (st_last["pair_tests"] - st_last["circle_pair_tests"]))
+    # flops of the work the launch ran: 40 per link-evaluation, 10 per
+    # disc-circle and 14 per disc-box test actually executed (the broad phase
+    # skips obstacles out of reach; the circle share is the batch's)
+    fc = st_last["circle_pair_tests"] / max(st_last["pair_tests"], 1)
+    flops = (40.0 * st_last["link_evaluations"] +
+             st_last["pair_tests_executed"] * (10.0 * fc + 14.0 * (1.0 - fc)))
+    flops_all_pairs = (40.0 * st_last["link_evaluations"] + 10.0 * st_last["circle_pair_tests"] +
+                       14.0 * (st_last["pair_tests"] - st_last["circle_pair_tests"]))
     launch_s = float(np.mean(step_ms)) / 1e3
     achieved = flops / launch_s / 1e12
     traffic = args.traffic if args.traffic is not None else GROW_DRAM_BYTES_PER_ROBOT * n
@@ -215,7 +221,9 @@ def run_gpu(args):
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of a 1024-robot launch, "
                                   "scaled by robots",
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived; MEASURED_PEAKS has no FP32 figure)",
-                "flops_per_launch": flops}
+                "flops_per_launch": flops,
+                "all_pairs_flops_per_launch": flops_all_pairs,
+                "pair_tests_executed_fraction": st_last["pair_tests_executed"] / max(st_last["pair_tests"], 1)}
 
     result = None
     serve = None

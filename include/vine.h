@@ -84,7 +84,10 @@ typedef enum {
  *   Algorithm 1 (mode 0 = equilibrium; only mode 0 is implemented).
  * exact_hessian: 1 = Newton steps with the exact Hessian of the cost when it
  *   is positive definite, else with the Gauss-Newton matrix (contact second
- *   derivatives dropped); 0 = always Gauss-Newton (default 1). */
+ *   derivatives dropped); 0 = always Gauss-Newton (default 1).
+ * broad_phase: 1 = each link tests only the obstacles on a list built when
+ *   it last moved by more than 0.4 body radii (the result is the same as
+ *   with 0, which tests every obstacle at every evaluation; default 1). */
 typedef struct {
   double w_a, w_b, w_c;
   double eps_crit;
@@ -101,6 +104,7 @@ typedef struct {
   double gd_alpha;
   int32_t gd_steps;
   int32_t exact_hessian;
+  int32_t broad_phase;
 } vine_params;
 
 /* Batch of independent robot instances, structure-of-arrays with CSR
@@ -154,10 +158,12 @@ typedef struct {
   int64_t iterations;        /* Gauss-Newton iterations */
   int64_t evaluations;       /* cost/gradient evaluations (incl. line search) */
   int64_t link_evaluations;  /* sum over evaluations of the links present */
-  int64_t pair_tests;        /* disc-obstacle tests: sum over evaluations of N K_s n_obs */
+  int64_t pair_tests;        /* all-pairs disc-obstacle count: sum over evaluations of N K_s n_obs */
   int64_t circle_pair_tests; /* the part of pair_tests against circles */
   int64_t gn_fallbacks;      /* Newton steps that used the Gauss-Newton matrix */
   int32_t n_maxiter, n_nonfinite, n_badinput, reserved;
+  int64_t pair_tests_executed; /* disc-obstacle tests actually run (the broad phase skips the
+                                  obstacles that cannot reach a link) */
 } vine_stats;
 
 /* Defaults listed above. */

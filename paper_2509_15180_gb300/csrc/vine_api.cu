@@ -198,6 +198,7 @@ vine_status vine_params_default(vine_params* p) {
   p->gd_alpha = 0.0;
   p->gd_steps = 50;
   p->exact_hessian = 1;
+  p->broad_phase = 1;
   return VINE_OK;
 }
 
@@ -312,7 +313,8 @@ vine_status vine_batch_create(const vine_batch_desc* D, const vine_params* P, vo
                o_cv = take(sizeof(int) * n), o_sp = take(sizeof(int) * n), o_rls = take(sizeof(long long) * n),
                o_ev = take(sizeof(long long) * n), o_le = take(sizeof(long long) * n),
                o_fb = take(sizeof(long long) * n), o_cy = take(sizeof(long long) * n),
-               o_rm = take(sizeof(double) * n), o_ord = take(sizeof(int) * n), o_cnt = take(sizeof(int) * 4);
+               o_pt = take(sizeof(long long) * n), o_rm = take(sizeof(double) * n), o_ord = take(sizeof(int) * n),
+               o_cnt = take(sizeof(int) * 4);
   const size_t persistent = off;
   // setup scratch (freed at the end of create)
   const size_t o_acttab = take(sizeof(int) * n_act), o_thoff = take(sizeof(int) * n),
@@ -476,6 +478,7 @@ vine_status vine_batch_create(const vine_batch_desc* D, const vine_params* P, vo
   a.rls = (long long*)P_(o_rls);
   a.evals = (long long*)P_(o_ev);
   a.linkevals = (long long*)P_(o_le);
+  a.pairtests = (long long*)P_(o_pt);
   a.fallbacks = (long long*)P_(o_fb);
   a.cycles = (long long*)P_(o_cy);
   a.resid_max = (double*)P_(o_rm);
@@ -505,6 +508,7 @@ vine_status vine_batch_create(const vine_batch_desc* D, const vine_params* P, vo
   a.max_iter = prm.max_iter;
   a.max_halv = prm.max_halvings;
   a.exact = prm.exact_hessian;
+  a.broad = prm.broad_phase;
   B->status0 = (int*)P_(o_st0);
   (void)persistent;
   *out = B;
@@ -534,6 +538,7 @@ vine_status vine_batch_reset(vine_batch* B, void* stream_v) {
   CK(cudaMemsetAsync(a.rls, 0, sizeof(long long) * B->n_inst, st));
   CK(cudaMemsetAsync(a.evals, 0, sizeof(long long) * B->n_inst, st));
   CK(cudaMemsetAsync(a.linkevals, 0, sizeof(long long) * B->n_inst, st));
+  CK(cudaMemsetAsync(a.pairtests, 0, sizeof(long long) * B->n_inst, st));
   CK(cudaMemsetAsync(a.fallbacks, 0, sizeof(long long) * B->n_inst, st));
   CK(cudaMemsetAsync(a.cycles, 0, sizeof(long long) * B->n_inst, st));
   CK(cudaMemsetAsync(a.resid_max, 0, sizeof(double) * B->n_inst, st));
@@ -738,7 +743,7 @@ vine_status vine_get_stats(const vine_batch* B, vine_stats* out, void* stream_v)
   const GrowArgs& a = B->args;
   const int n = B->n_inst;
   std::vector<int> it(n), cv(n), sp(n), status(n);
-  std::vector<long long> rls(n), ev(n), le(n), fb(n);
+  std::vector<long long> rls(n), ev(n), le(n), fb(n), pt(n);
   CK(cudaMemcpyAsync(it.data(), a.iters, 4 * n, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(cv.data(), a.conv, 4 * n, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(sp.data(), a.steps, 4 * n, cudaMemcpyDeviceToHost, st));
@@ -747,6 +752,7 @@ vine_status vine_get_stats(const vine_batch* B, vine_stats* out, void* stream_v)
   CK(cudaMemcpyAsync(ev.data(), a.evals, 8 * n, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(le.data(), a.linkevals, 8 * n, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(fb.data(), a.fallbacks, 8 * n, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(pt.data(), a.pairtests, 8 * n, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   std::memset(out, 0, sizeof(*out));
   for (int i = 0; i < n; ++i) {
@@ -759,6 +765,7 @@ vine_status vine_get_stats(const vine_batch* B, vine_stats* out, void* stream_v)
     out->gn_fallbacks += fb[i];
     out->pair_tests += le[i] * B->ks * (int64_t)B->h_n_obs[i];
     out->circle_pair_tests += le[i] * B->ks * (int64_t)B->h_n_circ[i];
+    out->pair_tests_executed += pt[i];
     out->n_maxiter += status[i] == kMaxIter;
     out->n_nonfinite += status[i] == kNonFinite;
     out->n_badinput += status[i] == kBadInput;

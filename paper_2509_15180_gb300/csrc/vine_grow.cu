@@ -98,6 +98,8 @@ struct Smem {
   float *TH, *TH0, *DTH, *LUX, *LUY, *G, *DD, *C0, *C1, *C2, *C3, *C4, *C5, *FX, *FY, *TL;
   float* LX;  // distal-link couplings: g_l contact part, h_ll, q0, q1, q2
   int* Q;     // contact candidates of the link in progress, [kContactQueue][32 lanes]
+  unsigned short* CL;  // per link: obstacle list near it, [count, index...] x (kListCap + 1)
+  float* XB;           // per link: its end points when its list was built, [4]
 };
 
 __device__ __forceinline__ Smem carve(float* base, const GrowArgs& A) {
@@ -111,6 +113,8 @@ __device__ __forceinline__ Smem carve(float* base, const GrowArgs& A) {
   s.C5 = p + 12 * n; s.FX = p + 13 * n; s.FY = p + 14 * n; s.TL = p + 15 * n;
   s.LX = p + 16 * n;
   s.Q = reinterpret_cast<int*>(p + 16 * n + 8);
+  s.XB = p + 16 * n + 8 + 32 * kContactQueue;
+  s.CL = reinterpret_cast<unsigned short*>(s.XB + 4 * n);
   return s;
 }
 
@@ -372,7 +376,15 @@ struct EvalOut {
   double J, S;  // cost and the sum of the magnitudes of its terms
   float gl, hll, q0, q1, q2, ulx, uly;
   float kg_wb;  // growth stiffness w_b k_g (scale of the distal-length pivot)
+  int tests;    // disc-obstacle pre-tests the warp ran
 };
+
+// Every link's obstacle list is marked stale (robot start, or a state the
+// lists were not built for).
+__device__ __forceinline__ void reset_lists(const Smem& S, int n, int lane) {
+  for (int j = lane; j < n; j += 32) S.CL[j * (kListCap + 1)] = kListStale;
+  __syncwarp();
+}
 
 // Cost, gradient and the Newton data at the state (TH[0..N), l): the exact
 // Hessian when `exact`, else the Gauss-Newton matrix.
@@ -407,6 +419,7 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
   FF px = warp_excl_scan(sx, lane), py = warp_excl_scan(sy, lane);
   const float kap = 2.f * A.w_c * I.kc;
   const float floor_d = 1e-6f * A.w_a * I.PR3;
+  int ntest = 0;
   double Jl = 0.0, Sl = 0.0;
   for (int j = j0; j < j1; ++j) {
     // ---- bending and actuation at joint j (Eq. restoring_moment)
@@ -502,15 +515,74 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
       }
       qn = 0;
     };
-    for (int o = 0; o < I.n_obs; ++o) {
-      const float4 ob = S.obs[o];
+    // Broad phase: a link keeps the list of obstacles within kListMargin R
+    // of its discs, built at some earlier state; the discs lie on the segment
+    // between the link's end points, so while neither end point has moved
+    // by more than 0.8 of the margin no other obstacle can reach them and
+    // only the list is tested (in obstacle order, as a full scan would).
+    // The distal link (whose length changes within the step) and links with
+    // stale or overflowing lists scan every obstacle and rebuild the list.
+    const float pex = (px.hi + lx) + px.lo, pey = (py.hi + ly) + py.lo;  // link end, for the bound
+    const int lb = j * (kListCap + 1);
+    const float margin = kListMargin * I.R;
+    bool full = last || !A.broad || S.CL[lb] == kListStale;
+    if (!full) {
+      const float d0x = px.hi - S.XB[4 * j + 0], d0y = py.hi - S.XB[4 * j + 1], d1x = pex - S.XB[4 * j + 2], d1y = pey - S.XB[4 * j + 3];
+      const float mv = 0.64f * margin * margin;
+      full = !(d0x * d0x + d0y * d0y < mv && d1x * d1x + d1y * d1y < mv);
+    }
+    if (full) {
+      const float Rm = I.R + margin;
+      int cnt = 0;
+      for (int o = 0; o < I.n_obs; ++o) {
+        const float4 ob = S.obs[o];
+        bool near = false;
 #pragma unroll
-      for (int k = 0; k < KS; ++k) {
-        if (contact_candidate(ob, xk[k], yk[k], Rpre)) {
-          S.Q[qn * 32 + lane] = o * KS + k;
-          if (++qn == kContactQueue) resolve();
+        for (int k = 0; k < KS; ++k) {
+          const float dx = (xk[k].hi - ob.x) + xk[k].lo, dy = (yk[k].hi - ob.y) + yk[k].lo;
+          bool cand, nk;
+          if (ob.w < 0.f) {
+            const float d2 = dx * dx + dy * dy, rr = ob.z + Rm;
+            cand = d2 < -ob.w;
+            nk = d2 < rr * rr;
+          } else {
+            const float g = fmaxf(fabsf(dx) - ob.z, fabsf(dy) - ob.w);
+            cand = g < Rpre;
+            nk = g < Rm;
+          }
+          near = near || nk;
+          if (cand) {
+            S.Q[qn * 32 + lane] = o * KS + k;
+            if (++qn == kContactQueue) resolve();
+          }
+        }
+        if (near && cnt < kListCap) S.CL[lb + 1 + cnt] = (unsigned short)o;
+        cnt += near ? 1 : 0;
+      }
+      ntest += I.n_obs;
+      if (last || cnt > kListCap) {
+        S.CL[lb] = kListStale;
+      } else {
+        S.CL[lb] = (unsigned short)cnt;
+        S.XB[4 * j + 0] = px.hi;
+        S.XB[4 * j + 1] = py.hi;
+        S.XB[4 * j + 2] = pex;
+        S.XB[4 * j + 3] = pey;
+      }
+    } else {
+      const int cnt = S.CL[lb];
+      for (int q = 0; q < cnt; ++q) {
+        const int o = S.CL[lb + 1 + q];
+        const float4 ob = S.obs[o];
+#pragma unroll
+        for (int k = 0; k < KS; ++k) {
+          if (contact_candidate(ob, xk[k], yk[k], Rpre)) {
+            S.Q[qn * 32 + lane] = o * KS + k;
+            if (++qn == kContactQueue) resolve();
+          }
         }
       }
+      ntest += cnt;
     }
     resolve();
     Jl += (double)(A.w_c * I.kc * pen2);
@@ -557,6 +629,12 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
   E.uly = __shfl_sync(kFull, uly, owner);
   E.gl = -2.f * A.w_b * I.kg * (I.l_seg - l) - glc;
   E.kg_wb = A.w_b * I.kg;
+  {
+    int t = ntest;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) t += __shfl_xor_sync(kFull, t, d);
+    E.tests = t * KS;
+  }
   __syncwarp();
   return E;
 }
@@ -657,7 +735,7 @@ __device__ double gn_solve(const InstDev& I, const Smem& S, int N, bool lfix, co
 struct StepStats {
   int iters;
   double r;
-  long long evals, linkevals;
+  long long evals, linkevals, tests;
   int fallbacks;
 };
 
@@ -683,6 +761,7 @@ __device__ int solve_step(const GrowArgs& A, const InstDev& I, const Smem& S, in
   EvalOut E = eval<KS>(A, I, S, N, l, lane, exact);
   st.evals += 1;
   st.linkevals += N;
+  st.tests += E.tests;
   int status = kMaxIter, it;
   double r = 0.0;
   for (it = 1; it <= A.max_iter; ++it) {
@@ -700,6 +779,7 @@ __device__ int solve_step(const GrowArgs& A, const InstDev& I, const Smem& S, in
       E = eval<KS>(A, I, S, N, l, lane, false);
       st.evals += 1;
       st.linkevals += N;
+      st.tests += E.tests;
       st.fallbacks += 1;
       r = gn_solve(I, S, N, lfix, E, dl, lane, false, mdth);
     }
@@ -755,6 +835,7 @@ __device__ int solve_step(const GrowArgs& A, const InstDev& I, const Smem& S, in
       E = eval<KS>(A, I, S, N, lt, lane, exact);
       st.evals += 1;
       st.linkevals += N;
+      st.tests += E.tests;
       const double dec = (double)alpha * gd + (double)gl0 * ((double)lt - (double)l0);
       double sl = 0.0;
       const bool rounding = fabs(E.J - J0) <= (double)A.fval_eps * fmax(S0, E.S);
@@ -801,20 +882,21 @@ __device__ void process_instance(const GrowArgs& A, int inst, const Smem& S, int
   for (int k = lane; k < I.n_act; k += 32) S.act[k] = A.act[I.act_off + k];
   for (int k = lane; k < N; k += 32) S.TH[k] = A.theta[I.th_off + k];
   float l = A.l_cur[inst];
-  __syncwarp();
+  reset_lists(S, I.n_target, lane);
   int iters = 0, conv = 0, steps = 0;
-  long long rls = 0, evals = 0, linkevals = 0, fallbacks = 0;
+  long long rls = 0, evals = 0, linkevals = 0, fallbacks = 0, tests = 0;
   double rmax = 0.0;
   for (int s = 0; s < A.n_steps && N < I.n_target; ++s) {
     if (lane == 0) S.TH[N] = 0.f;  // new link at the tip
     N += 1;
     l = 0.f;
     __syncwarp();
-    StepStats st{0, 0.0, 0, 0, 0};
+    StepStats st{0, 0.0, 0, 0, 0, 0};
     const int res = solve_step<KS>(A, I, S, N, l, lane, st, inst);
     iters += st.iters;
     evals += st.evals;
     linkevals += st.linkevals;
+    tests += st.tests;
     fallbacks += st.fallbacks;
     steps += 1;
     if (!(st.r <= rmax)) rmax = st.r;
@@ -838,6 +920,7 @@ __device__ void process_instance(const GrowArgs& A, int inst, const Smem& S, int
     A.rls[inst] += rls;
     A.evals[inst] += evals;
     A.linkevals[inst] += linkevals;
+    A.pairtests[inst] += tests;
     A.fallbacks[inst] += fallbacks;
     A.cycles[inst] += clock64() - t_start;
     if (!(rmax <= A.resid_max[inst])) A.resid_max[inst] = rmax;
@@ -846,7 +929,7 @@ __device__ void process_instance(const GrowArgs& A, int inst, const Smem& S, int
 }
 
 template <int KS>
-__global__ void __launch_bounds__(32 * kWarpsPerCta, 4) grow_kernel(const GrowArgs A) {
+__global__ void __launch_bounds__(32 * kWarpsPerCta, 3) grow_kernel(const GrowArgs A) {
   extern __shared__ float4 smem4[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const Smem S = carve(reinterpret_cast<float*>(smem4) + (size_t)warp * A.warp_floats, A);
@@ -879,7 +962,7 @@ __global__ void __launch_bounds__(32) probe_kernel(const GrowArgs A, int inst, i
   for (int k = lane; k < I.n_obs; k += 32) S.obs[k] = A.obs[I.obs_off + k];
   for (int k = lane; k < I.n_act; k += 32) S.act[k] = A.act[I.act_off + k];
   for (int k = lane; k < N; k += 32) S.TH[k] = theta[k];
-  __syncwarp();
+  reset_lists(S, N, lane);
   EvalOut E = eval<KS>(A, I, S, N, l, lane, A.exact != 0);
   for (int k = lane; k < N; k += 32) out_g[k] = S.G[k];
   __syncwarp();
@@ -949,7 +1032,7 @@ __device__ void grad_instance(const GrowArgs& A, const GradArgs& G, int inst, co
   for (int k = lane; k < I.n_act; k += 32) S.act[k] = A.act[I.act_off + k];
   for (int k = lane; k < N; k += 32) S.TH[k] = A.theta[I.th_off + k];
   const float l = A.l_cur[inst];
-  __syncwarp();
+  reset_lists(S, N, lane);
   EvalOut E = eval<KS>(A, I, S, N, l, lane, true);
   const bool lfix = (l <= 0.f && E.gl > 0.f) || (l >= I.l_seg && E.gl < 0.f);
   // tip relative to the base, and dc/dtheta_j = s . (z x (p_N - p_j))
@@ -1036,7 +1119,8 @@ const void* pick(int ks) {
 
 size_t grow_smem_per_warp(int nmax, int omax, int amax) {
   return sizeof(float4) * (size_t)(omax + amax) + sizeof(float) * (16 * (size_t)nmax + 8) +
-         sizeof(int) * 32 * (size_t)kContactQueue;
+         sizeof(int) * 32 * (size_t)kContactQueue + sizeof(float) * 4 * (size_t)nmax +
+         ((sizeof(unsigned short) * (kListCap + 1) * (size_t)nmax + 15) & ~size_t(15));
 }
 
 // The attribute is per kernel and process-wide: batches and servers with

@@ -23,6 +23,9 @@ constexpr int kUCells = 1024;      // wrinkling energy table cells on [theta_c, 
 constexpr int kWarpsPerCta = 4;    // warps per CTA of the growth kernel
 constexpr int kContactQueue = 8;   // contact candidates a lane queues per link before resolving them
 constexpr float kRefinePen = 2e-3f;  // penetrations below this fraction of R are re-evaluated in float-float
+constexpr int kListCap = 7;            // obstacles a link's broad-phase list holds
+constexpr float kListMargin = 0.5f;    // broad-phase margin, in body radii
+constexpr unsigned short kListStale = 0xffff;
 constexpr int kMaxLinks = 1024;
 constexpr int kMaxObs = 1024;
 constexpr int kMaxAct = 64;
@@ -56,6 +59,7 @@ struct GrowArgs {
   long long* rls;
   long long* evals;
   long long* linkevals;
+  long long* pairtests;  // disc-obstacle pre-tests run (broad phase included)
   long long* fallbacks;  // Newton steps that fell back to the Gauss-Newton matrix
   long long* cycles;     // SM clock cycles the owning warp spent on the robot
   double* resid_max;
@@ -73,6 +77,7 @@ struct GrowArgs {
   double tol;
   int max_iter, max_halv;
   int exact;  // exact Hessian when positive definite (else Gauss-Newton)
+  int broad;  // per-link obstacle lists (else every obstacle at every evaluation)
   // diagnostics: per line-search trial records of one robot (off when null)
   double* trace;
   int* trace_count;

@@ -94,7 +94,8 @@ __global__ void gather_meta_kernel(const int* sel, int n, const int* n_cur, cons
 // Fresh state for newly admitted slots.
 __global__ void slot_reset_kernel(const int* slots, int n, int* n_cur, float* l_cur, int* iters, int* conv,
                                   int* steps, long long* rls, long long* evals, long long* linkevals,
-                                  long long* fallbacks, long long* cycles, double* resid_max) {
+                                  long long* fallbacks, long long* cycles, long long* pairtests,
+                                  double* resid_max) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   const int s = slots[k];
@@ -108,6 +109,7 @@ __global__ void slot_reset_kernel(const int* slots, int n, int* n_cur, float* l_
   linkevals[s] = 0;
   fallbacks[s] = 0;
   cycles[s] = 0;
+  pairtests[s] = 0;
   resid_max[s] = 0.0;
 }
 
@@ -267,7 +269,7 @@ cudaError_t admit(vine_server* V, Request* R) {
   const GrowArgs& a = V->args;
   slot_reset_kernel<<<(R->n + 127) / 128, 128, 0, st>>>(ia.slot, R->n, a.n_cur, a.l_cur, a.iters, a.conv, a.steps,
                                                         a.rls, a.evals, a.linkevals, a.fallbacks, a.cycles,
-                                                        a.resid_max);
+                                                        a.pairtests, a.resid_max);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   for (int k = 0; k < R->n; ++k) {
@@ -617,7 +619,7 @@ vine_status vine_server_create(const vine_params* params, const vine_server_conf
                o_th = take(4 * Ss * V->nmax), o_n = take(4 * Ss), o_l = take(4 * Ss), o_st = take(4 * Ss),
                o_it = take(4 * Ss), o_cv = take(4 * Ss), o_sp = take(4 * Ss), o_rls = take(8 * Ss),
                o_ev = take(8 * Ss), o_le = take(8 * Ss), o_fb = take(8 * Ss), o_cy = take(8 * Ss),
-               o_rm = take(8 * Ss), o_ord = take(4 * Ss * c.lanes), o_cnt = take(16 * (size_t)c.lanes),
+               o_pt = take(8 * Ss), o_rm = take(8 * Ss), o_ord = take(4 * Ss * c.lanes), o_cnt = take(16 * (size_t)c.lanes),
                o_hdr = take(16 * (size_t)T),
                o_tab = take(sizeof(float2) * (size_t)T * kKnots), o_ut = take(sizeof(float2) * (kUCells + 1)),
                o_l0 = take(8 * (size_t)T), o_scr = take(8 * (4 * (size_t)T + (size_t)T * kKnots + 2 * (kUCells + 1))),
@@ -720,6 +722,7 @@ vine_status vine_server_create(const vine_params* params, const vine_server_conf
   a.rls = (long long*)(m + o_rls);
   a.evals = (long long*)(m + o_ev);
   a.linkevals = (long long*)(m + o_le);
+  a.pairtests = (long long*)(m + o_pt);
   a.fallbacks = (long long*)(m + o_fb);
   a.cycles = (long long*)(m + o_cy);
   a.resid_max = (double*)(m + o_rm);
@@ -749,6 +752,7 @@ vine_status vine_server_create(const vine_params* params, const vine_server_conf
   a.max_iter = prm.max_iter;
   a.max_halv = prm.max_halvings;
   a.exact = prm.exact_hessian;
+  a.broad = prm.broad_phase;
   a.trace = nullptr;
   a.trace_count = nullptr;
   a.trace_inst = -1;

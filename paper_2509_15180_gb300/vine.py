@@ -34,7 +34,7 @@ class vine_params(C.Structure):
                 ("pen_frac", C.c_double), ("tol", C.c_double), ("fval_eps", C.c_double),
                 ("armijo_c1", C.c_double), ("max_iter", C.c_int32), ("discs_per_link", C.c_int32),
                 ("max_halvings", C.c_int32), ("mode", C.c_int32), ("gd_alpha", C.c_double),
-                ("gd_steps", C.c_int32), ("exact_hessian", C.c_int32)]
+                ("gd_steps", C.c_int32), ("exact_hessian", C.c_int32), ("broad_phase", C.c_int32)]
 
 
 class vine_batch_desc(C.Structure):
@@ -48,7 +48,8 @@ class vine_stats(C.Structure):
     _fields_ = [(k, C.c_int64) for k in ("robot_link_steps", "steps_converged", "steps_total", "iterations",
                                          "evaluations", "link_evaluations", "pair_tests", "circle_pair_tests",
                                          "gn_fallbacks")] + [
-        (k, C.c_int32) for k in ("n_maxiter", "n_nonfinite", "n_badinput", "reserved")]
+        (k, C.c_int32) for k in ("n_maxiter", "n_nonfinite", "n_badinput", "reserved")] + [
+        ("pair_tests_executed", C.c_int64)]
 
 
 class vine_server_config(C.Structure):

@@ -302,3 +302,24 @@ def test_device_inputs_match_host_inputs():
     for k in ("theta", "pose", "tip", "l", "iters"):
         assert np.array_equal(s1[k], s2[k]), k
     b1.close(); b2.close()
+
+
+def test_broad_phase_is_exact():
+    """The per-link obstacle lists skip only obstacles that cannot reach a
+    link, so the growth is bitwise the same as testing every obstacle."""
+    for sc in (scenes.config2(64), scenes.config3(48, n_range=(30, 120))):
+        out = []
+        for bp in (1, 0):
+            prm = vine.vine_params_default()
+            prm.broad_phase = bp
+            b = vine.Batch(sc, prm)
+            b.simulate()
+            out.append((b.state(), b.stats()))
+            b.close()
+        (s1, t1), (s0, t0) = out
+        for k in ("theta", "l", "N", "status", "iters", "resid"):
+            assert np.array_equal(s1[k], s0[k]), k
+        assert t1["evaluations"] == t0["evaluations"]
+        assert t0["pair_tests_executed"] == t0["pair_tests"]
+        print("broad phase: %.1f%% of the all-pairs tests run" % (100.0 * t1["pair_tests_executed"] / t1["pair_tests"]))
+        assert t1["pair_tests_executed"] < t0["pair_tests_executed"]
