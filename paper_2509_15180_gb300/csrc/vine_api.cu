@@ -155,6 +155,7 @@ struct vine_batch {
   int n_tab = 0;
   vine_params params{};
   int ks = 2;
+  int wpc = kWarpsPerCta;  // warps per CTA of the growth launch
   int nmax = 32, omax = 1, amax = 1;
   size_t smem_warp = 0;
   int grid = 1;
@@ -443,23 +444,16 @@ vine_status vine_batch_create(const vine_batch_desc* D, const vine_params* P, vo
   B->omax = omax;
   B->amax = amax;
   B->smem_warp = grow_smem_per_warp(B->nmax, B->omax, B->amax);
-  const size_t smem_cta = B->smem_warp * kWarpsPerCta;
   int dev_id = 0, nsm = 1;
-  size_t smem_optin = 0;
   cudaGetDevice(&dev_id);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev_id);
-  {
-    int v = 0;
-    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev_id);
-    smem_optin = (size_t)v;
-  }
-  if (smem_cta > smem_optin) {
+  int per_sm = 0;
+  B->wpc = grow_pick_block(B->ks, B->smem_warp, &per_sm);
+  if (B->wpc == 0 || per_sm == 0) {
     cleanup();
     return fail(VINE_EINVAL, "vine_batch_create: robot or obstacle set too large for shared memory");
   }
-  CKC(grow_configure(B->ks, smem_cta));
-  const int per_sm = grow_max_ctas_per_sm(B->ks, smem_cta);
-  B->grid = std::max(1, std::min((n + kWarpsPerCta - 1) / kWarpsPerCta, nsm * per_sm));
+  B->grid = std::max(1, std::min((n + B->wpc - 1) / B->wpc, nsm * per_sm));
 
   GrowArgs& a = B->args;
   a.inst = (const InstDev*)P_(o_inst);
@@ -521,7 +515,8 @@ static vine_status grow_launch(vine_batch* B, int n_steps, cudaStream_t st) {
   a.n_steps = n_steps;
   a.dynamic = 1;
   CK(cudaMemsetAsync(a.counter, 0, sizeof(int), st));
-  CK(launch_grow(a, B->ks, B->grid, 32 * kWarpsPerCta, B->smem_warp * kWarpsPerCta, st));
+  CK(grow_configure(B->ks, B->smem_warp * B->wpc));
+  CK(launch_grow(a, B->ks, B->grid, 32 * B->wpc, B->smem_warp * B->wpc, st));
   return VINE_OK;
 }
 
@@ -700,7 +695,7 @@ vine_status vine_grad(const vine_batch* B, const float* goal_xy, double* cost, d
   const int n = B->n_inst;
   const size_t na = (size_t)B->n_act;
   // one warp per CTA, several CTAs per SM; the robots come longest first
-  const int grid = std::max(1, std::min(n, B->grid * kWarpsPerCta));
+  const int grid = std::max(1, std::min(n, B->grid * B->wpc));
   GradArgs g{};
   if (ptrs_are_device) {
     g.goal = goal_xy;

@@ -100,6 +100,8 @@ struct Smem {
   int* Q;     // contact candidates of the link in progress, [kContactQueue][32 lanes]
   unsigned short* CL;  // per link: obstacle list near it, [count, index...] x (kListCap + 1)
   float* XB;           // per link: its end points when its list was built, [4]
+  float* PB;           // per link: its start point at the current evaluation, [2]
+  int* RQ;             // links whose lists are rebuilt in this evaluation
 };
 
 __device__ __forceinline__ Smem carve(float* base, const GrowArgs& A) {
@@ -114,7 +116,9 @@ __device__ __forceinline__ Smem carve(float* base, const GrowArgs& A) {
   s.LX = p + 16 * n;
   s.Q = reinterpret_cast<int*>(p + 16 * n + 8);
   s.XB = p + 16 * n + 8 + 32 * kContactQueue;
-  s.CL = reinterpret_cast<unsigned short*>(s.XB + 4 * n);
+  s.PB = s.XB + 4 * n;
+  s.RQ = reinterpret_cast<int*>(s.PB + 2 * n);
+  s.CL = reinterpret_cast<unsigned short*>(s.RQ + n);
   return s;
 }
 
@@ -386,6 +390,94 @@ __device__ __forceinline__ void reset_lists(const Smem& S, int n, int lane) {
   __syncwarp();
 }
 
+// Broad phase.  Every link keeps the list of obstacles within kListMargin R
+// of its discs and its two end points at the time the list was built.  The
+// discs lie on the segment between the end points, so while neither end
+// point has moved by 0.8 of the margin no other obstacle can reach them.
+// Each lane checks its links; the links that moved, have a stale list or are
+// the distal link (whose length changes within the step) are queued, and the
+// warp rebuilds their lists together, the lanes splitting the obstacles and
+// a ballot keeping obstacle order.  More than kListCap near obstacles mark
+// the link kListFull (it then tests every obstacle).  ntest counts the
+// pre-tests run (in obstacles).
+template <int KS>
+__device__ void rebuild_lists(const InstDev& I, const Smem& S, int N, int j0, int j1, FF px, FF py, int lane,
+                              int& ntest) {
+  const float margin = kListMargin * I.R, mv = 0.64f * margin * margin;
+  int nre = 0;
+  for (int j = j0; j < j1; ++j) {
+    const float x0 = px.hi, y0 = py.hi;
+    px = ff_add(px, S.LUX[j]);
+    py = ff_add(py, S.LUY[j]);
+    S.PB[2 * j] = x0;
+    S.PB[2 * j + 1] = y0;
+    const int lb = j * (kListCap + 1);
+    const unsigned short c = S.CL[lb];
+    bool stale = (j == N - 1) || c == kListStale || c == kListFull;
+    if (!stale) {
+      const float* xb = S.XB + 4 * j;
+      const float d0x = x0 - xb[0], d0y = y0 - xb[1], d1x = px.hi - xb[2], d1y = py.hi - xb[3];
+      stale = !(d0x * d0x + d0y * d0y < mv && d1x * d1x + d1y * d1y < mv);
+    }
+    if (stale) {
+      S.CL[lb] = kListStale;
+      nre += 1;
+    }
+  }
+  // queue the stale links in link order: exclusive prefix of the lanes' counts
+  int off = nre;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int v = __shfl_up_sync(kFull, off, d);
+    if (lane >= d) off += v;
+  }
+  const int total = __shfl_sync(kFull, off, 31);
+  off -= nre;
+  for (int j = j0; j < j1 && nre > 0; ++j)
+    if (S.CL[j * (kListCap + 1)] == kListStale) S.RQ[off++] = j;
+  __syncwarp();
+  const float Rm = I.R + margin;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int q = 0; q < total; ++q) {
+    const int j = S.RQ[q];
+    const float x0 = S.PB[2 * j], y0 = S.PB[2 * j + 1], lx = S.LUX[j], ly = S.LUY[j];
+    const int lb = j * (kListCap + 1);
+    int cnt = 0;
+    for (int o0 = 0; o0 < I.n_obs; o0 += 32) {
+      const int o = o0 + lane;
+      bool near = false;
+      if (o < I.n_obs) {
+        const float4 ob = S.obs[o];
+#pragma unroll
+        for (int k = 0; k < KS; ++k) {
+          const float fr = (float)(k + 1) / (float)KS;
+          const float dx = (x0 + fr * lx) - ob.x, dy = (y0 + fr * ly) - ob.y;
+          if (ob.w < 0.f) {
+            const float rr = ob.z + Rm;
+            near = near || (dx * dx + dy * dy < rr * rr);
+          } else {
+            near = near || (fmaxf(fabsf(dx) - ob.z, fabsf(dy) - ob.w) < Rm);
+          }
+        }
+      }
+      const unsigned bal = __ballot_sync(kFull, near);
+      const int pos = cnt + __popc(bal & lt);
+      if (near && pos < kListCap) S.CL[lb + 1 + pos] = (unsigned short)o;
+      cnt += __popc(bal);
+    }
+    if (lane == 0) {
+      S.CL[lb] = cnt > kListCap ? kListFull : (unsigned short)cnt;
+      float* xb = S.XB + 4 * j;
+      xb[0] = x0;
+      xb[1] = y0;
+      xb[2] = x0 + lx;
+      xb[3] = y0 + ly;
+    }
+  }
+  if (lane == 0) ntest += total * I.n_obs;
+  __syncwarp();
+}
+
 // Cost, gradient and the Newton data at the state (TH[0..N), l): the exact
 // Hessian when `exact`, else the Gauss-Newton matrix.
 template <int KS>
@@ -420,6 +512,7 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
   const float kap = 2.f * A.w_c * I.kc;
   const float floor_d = 1e-6f * A.w_a * I.PR3;
   int ntest = 0;
+  if (A.broad) rebuild_lists<KS>(I, S, N, j0, j1, px, py, lane, ntest);
   double Jl = 0.0, Sl = 0.0;
   for (int j = j0; j < j1; ++j) {
     // ---- bending and actuation at joint j (Eq. restoring_moment)
@@ -515,60 +608,21 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
       }
       qn = 0;
     };
-    // Broad phase: a link keeps the list of obstacles within kListMargin R
-    // of its discs, built at some earlier state; the discs lie on the segment
-    // between the link's end points, so while neither end point has moved
-    // by more than 0.8 of the margin no other obstacle can reach them and
-    // only the list is tested (in obstacle order, as a full scan would).
-    // The distal link (whose length changes within the step) and links with
-    // stale or overflowing lists scan every obstacle and rebuild the list.
-    const float pex = (px.hi + lx) + px.lo, pey = (py.hi + ly) + py.lo;  // link end, for the bound
+    // every obstacle (no broad phase, or too many near this link), else the
+    // link's list; both in obstacle order, so the result is the same
     const int lb = j * (kListCap + 1);
-    const float margin = kListMargin * I.R;
-    bool full = last || !A.broad || S.CL[lb] == kListStale;
-    if (!full) {
-      const float d0x = px.hi - S.XB[4 * j + 0], d0y = py.hi - S.XB[4 * j + 1], d1x = pex - S.XB[4 * j + 2], d1y = pey - S.XB[4 * j + 3];
-      const float mv = 0.64f * margin * margin;
-      full = !(d0x * d0x + d0y * d0y < mv && d1x * d1x + d1y * d1y < mv);
-    }
-    if (full) {
-      const float Rm = I.R + margin;
-      int cnt = 0;
+    if (!A.broad || S.CL[lb] == kListFull) {
       for (int o = 0; o < I.n_obs; ++o) {
         const float4 ob = S.obs[o];
-        bool near = false;
 #pragma unroll
         for (int k = 0; k < KS; ++k) {
-          const float dx = (xk[k].hi - ob.x) + xk[k].lo, dy = (yk[k].hi - ob.y) + yk[k].lo;
-          bool cand, nk;
-          if (ob.w < 0.f) {
-            const float d2 = dx * dx + dy * dy, rr = ob.z + Rm;
-            cand = d2 < -ob.w;
-            nk = d2 < rr * rr;
-          } else {
-            const float g = fmaxf(fabsf(dx) - ob.z, fabsf(dy) - ob.w);
-            cand = g < Rpre;
-            nk = g < Rm;
-          }
-          near = near || nk;
-          if (cand) {
+          if (contact_candidate(ob, xk[k], yk[k], Rpre)) {
             S.Q[qn * 32 + lane] = o * KS + k;
             if (++qn == kContactQueue) resolve();
           }
         }
-        if (near && cnt < kListCap) S.CL[lb + 1 + cnt] = (unsigned short)o;
-        cnt += near ? 1 : 0;
       }
       ntest += I.n_obs;
-      if (last || cnt > kListCap) {
-        S.CL[lb] = kListStale;
-      } else {
-        S.CL[lb] = (unsigned short)cnt;
-        S.XB[4 * j + 0] = px.hi;
-        S.XB[4 * j + 1] = py.hi;
-        S.XB[4 * j + 2] = pex;
-        S.XB[4 * j + 3] = pey;
-      }
     } else {
       const int cnt = S.CL[lb];
       for (int q = 0; q < cnt; ++q) {
@@ -1119,7 +1173,7 @@ const void* pick(int ks) {
 
 size_t grow_smem_per_warp(int nmax, int omax, int amax) {
   return sizeof(float4) * (size_t)(omax + amax) + sizeof(float) * (16 * (size_t)nmax + 8) +
-         sizeof(int) * 32 * (size_t)kContactQueue + sizeof(float) * 4 * (size_t)nmax +
+         sizeof(int) * 32 * (size_t)kContactQueue + sizeof(float) * 7 * (size_t)nmax +
          ((sizeof(unsigned short) * (kListCap + 1) * (size_t)nmax + 15) & ~size_t(15));
 }
 
@@ -1138,11 +1192,33 @@ cudaError_t grow_configure(int ks, size_t smem_per_cta) {
   return e;
 }
 
-int grow_max_ctas_per_sm(int ks, size_t smem_per_cta) {
+int grow_max_ctas_per_sm(int ks, size_t smem_per_cta, int threads) {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick(ks), 32 * kWarpsPerCta, smem_per_cta) != cudaSuccess)
-    return 1;
-  return n > 0 ? n : 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick(ks), threads, smem_per_cta) != cudaSuccess) return 0;
+  return n;
+}
+
+// Warps per CTA (4, 2 or 1) that keep the most warps resident per SM for a
+// warp slice of smem_warp bytes (a robot's obstacles and link arrays are
+// per warp, so smaller CTAs pack large slices more tightly); ties go to the
+// larger CTA.  Sets the kernel's shared-memory limit for the choice.
+int grow_pick_block(int ks, size_t smem_warp, int* ctas_per_sm) {
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  int best_w = 0, best_c = 0;
+  for (int w = kWarpsPerCta; w >= 1; w >>= 1) {
+    const size_t smem = smem_warp * w;
+    if (smem > (size_t)optin) continue;
+    if (grow_configure(ks, smem) != cudaSuccess) continue;
+    const int c = grow_max_ctas_per_sm(ks, smem, 32 * w);
+    if (c * w > best_c * best_w) {
+      best_w = w;
+      best_c = c;
+    }
+  }
+  if (ctas_per_sm) *ctas_per_sm = best_c;
+  return best_w;
 }
 
 cudaError_t launch_grow(const GrowArgs& a, int ks, int grid, int block, size_t smem, cudaStream_t s) {

@@ -25,7 +25,8 @@ constexpr int kContactQueue = 8;   // contact candidates a lane queues per link 
 constexpr float kRefinePen = 2e-3f;  // penetrations below this fraction of R are re-evaluated in float-float
 constexpr int kListCap = 7;            // obstacles a link's broad-phase list holds
 constexpr float kListMargin = 0.5f;    // broad-phase margin, in body radii
-constexpr unsigned short kListStale = 0xffff;
+constexpr unsigned short kListStale = 0xffff;  // list not built for the current link geometry
+constexpr unsigned short kListFull = 0xfffe;   // more than kListCap obstacles near the link
 constexpr int kMaxLinks = 1024;
 constexpr int kMaxObs = 1024;
 constexpr int kMaxAct = 64;
@@ -141,7 +142,8 @@ void set_last_error(const char* msg, const char* detail = nullptr);
 cudaError_t launch_grow(const GrowArgs& a, int ks, int grid, int block, size_t smem, cudaStream_t s);
 size_t grow_smem_per_warp(int nmax, int omax, int amax);
 cudaError_t grow_configure(int ks, size_t smem_per_cta);
-int grow_max_ctas_per_sm(int ks, size_t smem_per_cta);
+int grow_max_ctas_per_sm(int ks, size_t smem_per_cta, int threads);
+int grow_pick_block(int ks, size_t smem_warp, int* ctas_per_sm);  // warps per CTA, 0 if none fits
 cudaError_t launch_probe(const GrowArgs& a, int ks, int inst, int N, const float* theta, float l, double* J,
                          float* g, float* dx, double* r, int* lfix, size_t smem, cudaStream_t s);
 cudaError_t launch_grad(const GrowArgs& a, const GradArgs& g, int ks, int grid, size_t smem, cudaStream_t s);

@@ -136,7 +136,7 @@ struct vine_server {
   vine_server_config cfg{};
   int device = 0;
   cudaStream_t stream = nullptr;
-  int S = 0, nmax = 0, omax = 0, amax = 0, ks = 2, grid = 1;
+  int S = 0, nmax = 0, omax = 0, amax = 0, ks = 2, grid = 1, wpc = kWarpsPerCta;
   size_t smem_warp = 0, stage_bytes = 0;
   char* dmem = nullptr;
   GrowArgs args{};
@@ -325,9 +325,9 @@ cudaError_t launch_lane(vine_server* V, int q, bool* launched) {
   a.n_steps = V->cfg.steps_per_tick;
   a.dynamic = 1;
   if (e == cudaSuccess) e = cudaMemsetAsync(a.counter, 0, sizeof(int), L.st);
-  if (e == cudaSuccess) e = grow_configure(V->ks, V->smem_warp * kWarpsPerCta);
-  const int grid = std::max(1, std::min(V->grid, (a.n_order + kWarpsPerCta - 1) / kWarpsPerCta));
-  if (e == cudaSuccess) e = launch_grow(a, V->ks, grid, 32 * kWarpsPerCta, V->smem_warp * kWarpsPerCta, L.st);
+  if (e == cudaSuccess) e = grow_configure(V->ks, V->smem_warp * V->wpc);
+  const int grid = std::max(1, std::min(V->grid, (a.n_order + V->wpc - 1) / V->wpc));
+  if (e == cudaSuccess) e = launch_grow(a, V->ks, grid, 32 * V->wpc, V->smem_warp * V->wpc, L.st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(L.h_ncur, a.n_cur, sizeof(int) * V->S, cudaMemcpyDeviceToHost, L.st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(L.h_status, a.status, sizeof(int) * V->S, cudaMemcpyDeviceToHost, L.st);
   if (e == cudaSuccess) e = cudaEventRecord(L.ev, L.st);
@@ -691,19 +691,17 @@ vine_status vine_server_create(const vine_params* params, const vine_server_conf
   }
   // launch configuration
   V->smem_warp = grow_smem_per_warp(V->nmax, V->omax, V->amax);
-  const size_t smem_cta = V->smem_warp * kWarpsPerCta;
-  int nsm = 1, optin = 0;
+  int nsm = 1, per_sm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, V->device);
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, V->device);
-  if (smem_cta > (size_t)optin) {
+  V->wpc = grow_pick_block(V->ks, V->smem_warp, &per_sm);
+  if (V->wpc == 0 || per_sm == 0) {
     cleanup();
     return sfail(VINE_EINVAL, "vine_server_create: slot capacities too large for shared memory");
   }
-  CKS(grow_configure(V->ks, smem_cta));
-  V->grid = nsm * grow_max_ctas_per_sm(V->ks, smem_cta);
+  V->grid = nsm * per_sm;
   // half the resident warps per lane: two lanes fill the GPU, the others
   // take over the SMs that a launch finishing its slowest robots leaves idle
-  V->window = c.window > 0 ? c.window : std::max(1, V->grid * kWarpsPerCta / 2);
+  V->window = c.window > 0 ? c.window : std::max(1, V->grid * V->wpc / 2);
   V->cfg.window = V->window;
   GrowArgs& a = V->args;
   a.inst = (const InstDev*)(m + o_inst);

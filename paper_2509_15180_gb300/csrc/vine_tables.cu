@@ -7,7 +7,8 @@
 //    Gauss-Legendre quadrature of their integrands (smooth for m <= 1/2);
 //    the unsaturated root of Eq. (sPAM_2) by a coarse scan for the first sign
 //    change followed by safeguarded Newton; m at each knot by the Illinois
-//    variant of regula falsi.  Branch rule: the smallest root in
+//    variant of regula falsi.  One warp per knot: the scan points and the
+//    quadrature nodes are spread over the lanes.  Branch rule: the smallest root in
 //    (0, phi_sat], else the saturated branch phi = acos(R_c / R_act).
 //  * the wrinkling energy table, Sec. 3.2 Eq. (wrinkling_model): the integral
 //    of the restoring moment from onset to pi on 1024 cells, with the moment
@@ -68,35 +69,58 @@ __device__ double ellip_F(const GaussLegendre& gl, double phi, double m) {
   return F;
 }
 
-// Residual of Eq. (sPAM_2) on the unsaturated branch (l_a = l_0), lam = l_0 / R_c.
+// Residual of Eq. (sPAM_2) on the unsaturated branch (l_a = l_0), lam = l_0 / R_c,
+// with the quadrature run by the calling thread alone.
 __device__ double resid2(const GaussLegendre& gl, const SpamConst& c, double phi, double m, double lam) {
   if (phi <= 0.0) return -lam * (1.0 + c.a / (2.0 * m));
   double cp = cos(phi);
   return ellip_F(gl, phi, m) / (sqrt(m) * cp) - lam * (1.0 + c.a / (2.0 * m * cp * cp));
 }
 
-// Model at contraction parameter m: strain eps and force per pressure f.
-__device__ void spam_model(const GaussLegendre& gl, const SpamConst& c, double m, double l0, double* eps,
-                           double* f) {
+// The same quadrature of F(phi|m) and E(phi|m) spread over a warp: lane i
+// takes node i, a butterfly sum, and lane 0's total broadcast so that every
+// lane holds bit-identical values (the callers branch on them warp-uniformly).
+__device__ void ellip_FE_warp(const GaussLegendre& gl, double phi, double m, int lane, double* F, double* E) {
+  const double hh = 0.5 * phi;
+  double sf = 0.0, se = 0.0;
+  for (int i = lane; i < gl.n; i += 32) {
+    const double t = hh * (1.0 + gl.x[i]);
+    const double s = sin(t);
+    const double q = sqrt(1.0 - m * s * s);
+    sf += gl.w[i] / q;
+    se += gl.w[i] * q;
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    sf += __shfl_xor_sync(0xffffffffu, sf, d);
+    se += __shfl_xor_sync(0xffffffffu, se, d);
+  }
+  *F = hh * __shfl_sync(0xffffffffu, sf, 0);
+  *E = hh * __shfl_sync(0xffffffffu, se, 0);
+}
+
+// Model at contraction parameter m: strain eps and force per pressure f, by
+// one warp (all lanes return the same values).  The first sign change of the
+// residual on the 32-point scan of (0, phi_sat] is found with one scan point
+// per lane.
+__device__ void spam_model_warp(const GaussLegendre& gl, const SpamConst& c, double m, double l0, int lane,
+                                double* eps, double* f) {
   const double lam = l0 / c.Rc;
   const int nscan = 32;
-  double lo = 0.0, hi = -1.0;
-  for (int k = 1; k <= nscan; ++k) {
-    double ph = c.phi_sat * (double)k / nscan;
-    if (resid2(gl, c, ph, m, lam) >= 0.0) {
-      hi = ph;
-      break;
-    }
-    lo = ph;
-  }
+  const double ph_l = c.phi_sat * (double)(lane + 1) / nscan;
+  const unsigned pos = __ballot_sync(0xffffffffu, resid2(gl, c, ph_l, m, lam) >= 0.0);
   double phi, la;
   const double sm = sqrt(m);
-  if (hi > 0.0) {
+  if (pos != 0u) {
+    const int kk = __ffs(pos) - 1;  // first scan point with a non-negative residual
+    double hi = c.phi_sat * (double)(kk + 1) / nscan;
+    double lo = kk == 0 ? 0.0 : c.phi_sat * (double)kk / nscan;
     // safeguarded Newton inside [lo, hi] (residual < 0 at lo, >= 0 at hi)
     double x = 0.5 * (lo + hi);
     for (int it = 0; it < 100; ++it) {
       double cp = cos(x), sp = sin(x);
-      double F = ellip_F(gl, x, m);
+      double F, E;
+      ellip_FE_warp(gl, x, m, lane, &F, &E);
       double r = F / (sm * cp) - lam * (1.0 + c.a / (2.0 * m * cp * cp));
       if (r >= 0.0) hi = x; else lo = x;
       double dF = 1.0 / sqrt(1.0 - m * sp * sp);
@@ -114,23 +138,26 @@ __device__ void spam_model(const GaussLegendre& gl, const SpamConst& c, double m
   } else {
     phi = c.phi_sat;
     double cp = cos(phi);
-    la = c.Rc * ellip_F(gl, phi, m) / (sm * cp) / (1.0 + c.a / (2.0 * m * cp * cp));
+    double F, E;
+    ellip_FE_warp(gl, phi, m, lane, &F, &E);
+    la = c.Rc * F / (sm * cp) / (1.0 + c.a / (2.0 * m * cp * cp));
   }
   double cp = cos(phi);
   double F, E;
-  ellip_FE(gl, phi, m, &F, &E);
+  ellip_FE_warp(gl, phi, m, lane, &F, &E);
   // Eq. (sPAM_1) solved for the strain
   *eps = (la - 2.0 * c.Rc * (E - 0.5 * F) / (sm * cp)) / l0;
   // Eq. (sPAM_force) per unit actuation pressure
   *f = kPiD * c.Rc * c.Rc * (1.0 - 2.0 * m) / (2.0 * m * cp * cp);
 }
 
-// One thread per (table, knot): knots 1..254 by Illinois on eps(m) - target.
+// One warp per (table, knot): knots 1..254 by Illinois on eps(m) - target.
 __global__ void spam_knots_kernel(const double* l0s, SpamConst c, GaussLegendre gl, const double* bounds,
                                   double* fknots) {
   const int t = blockIdx.y;
-  const int k = 1 + blockIdx.x * blockDim.x + threadIdx.x;
-  if (k > kKnots - 2) return;
+  const int lane = threadIdx.x & 31;
+  const int k = 1 + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (k > kKnots - 2) return;  // whole warps leave together
   const double l0 = l0s[t];
   const double elo = bounds[4 * t + 0], ehi = bounds[4 * t + 1];
   const double target = elo + (ehi - elo) * (double)k / (kKnots - 1);
@@ -140,7 +167,7 @@ __global__ void spam_knots_kernel(const double* l0s, SpamConst c, GaussLegendre 
   for (int it = 0; it < 200; ++it) {
     m = (a * fb - b * fa) / (fb - fa);
     if (!(m > a && m < b)) m = 0.5 * (a + b);
-    spam_model(gl, c, m, l0, &e, &f);
+    spam_model_warp(gl, c, m, l0, lane, &e, &f);
     double fm = e - target;
     if (fm == 0.0 || b - a <= 1e-15 * b) break;
     if ((fm < 0.0) == (fa < 0.0)) {
@@ -156,21 +183,24 @@ __global__ void spam_knots_kernel(const double* l0s, SpamConst c, GaussLegendre 
     }
     if (fabs(fm) <= 1e-15 * (fabs(target) + 1e-3)) break;
   }
-  fknots[t * kKnots + k] = f;
+  if (lane == 0) fknots[t * kKnots + k] = f;
 }
 
-// One thread per table: eps at m_lo and m = 1/2 (the table's strain range).
+// One warp per table: eps at m_lo and m = 1/2 (the table's strain range).
 __global__ void spam_bounds_kernel(const double* l0s, int n_tab, SpamConst c, GaussLegendre gl, double* bounds,
                                    double* fknots) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
   if (t >= n_tab) return;
   double elo, flo, ehi, fhi;
-  spam_model(gl, c, c.m_lo, l0s[t], &elo, &flo);
-  spam_model(gl, c, 0.5, l0s[t], &ehi, &fhi);
-  bounds[4 * t + 0] = elo;
-  bounds[4 * t + 1] = ehi;
-  fknots[t * kKnots + 0] = flo;
-  fknots[t * kKnots + kKnots - 1] = 0.0;
+  spam_model_warp(gl, c, c.m_lo, l0s[t], lane, &elo, &flo);
+  spam_model_warp(gl, c, 0.5, l0s[t], lane, &ehi, &fhi);
+  if (lane == 0) {
+    bounds[4 * t + 0] = elo;
+    bounds[4 * t + 1] = ehi;
+    fknots[t * kKnots + 0] = flo;
+    fknots[t * kKnots + kKnots - 1] = 0.0;
+  }
 }
 
 // One thread per table: cumulative trapezoid integral from eps_lo (exact for
@@ -264,9 +294,9 @@ cudaError_t launch_spam_tables(const double* l0, int n_tab, double R_c, double R
   SpamConst c{R_c, R_act, a_spam, m_lo, std::acos(R_c / R_act)};
   double* bounds = scratch;              // [4 n_tab]
   double* fk = scratch + 4 * n_tab;      // [n_tab * 256]
-  spam_bounds_kernel<<<(n_tab + 31) / 32, 32, 0, s>>>(l0, n_tab, c, gl, bounds, fk);
-  dim3 grid((kKnots - 2 + 31) / 32, n_tab);
-  spam_knots_kernel<<<grid, 32, 0, s>>>(l0, c, gl, bounds, fk);
+  spam_bounds_kernel<<<(n_tab + 3) / 4, 128, 0, s>>>(l0, n_tab, c, gl, bounds, fk);
+  dim3 grid((kKnots - 2 + 3) / 4, n_tab);  // 4 warps per block, one knot each
+  spam_knots_kernel<<<grid, 128, 0, s>>>(l0, c, gl, bounds, fk);
   spam_finish_kernel<<<(n_tab + 31) / 32, 32, 0, s>>>(n_tab, bounds, fk, hdr, tab);
   return cudaGetLastError();
 }
