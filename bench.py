@@ -229,6 +229,9 @@ def run_gpu(args):
     serve = None
     if rank == 0 and not args.no_serve:
         serve = serve_leg(args, vine, scenes)
+    uneven = None
+    if rank == 0 and args.uneven_robots > 0:
+        uneven = uneven_leg(args, vine, scenes, torch, stream, flush)
     if rank == 0:
         cpu = cpu_baseline(args, sc) if ws == 1 and not args.no_cpu else None
         lat = {"p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
@@ -242,7 +245,7 @@ def run_gpu(args):
                        "robot_link_steps_per_step": rls_per_step, "l2": "flushed between timed steps (512 MiB write)",
                        "tol": 1e-6},
             "e2e": e2e, "plain": plain, "latency": lat, "roofline": roofline, "cpu_baseline": cpu,
-            "adjoint": adjoint, "serving": serve,
+            "adjoint": adjoint, "serving": serve, "uneven": uneven,
             "clocks": ck, "gpu_launches": args.steps, "robots": robots,
             "solver": {"iters_per_step": st_last["iterations"] / max(st_last["steps_total"], 1),
                        "evals_per_step": st_last["evaluations"] / max(st_last["steps_total"], 1),
@@ -371,6 +374,44 @@ def serve_leg(args, vine, scenes):
     return out
 
 
+def uneven_leg(args, vine, scenes, torch, stream, flush):
+    """Uneven persistent batch (links U{30..300}, 0-8 actuators, 5-200
+    obstacles): robot-link-steps/s of vine_simulate with the launch
+    configuration picked at creation, then after vine_autotune on a sample."""
+    sc = scenes.config3(args.uneven_robots)
+    b = vine.Batch(sc, stream=stream)
+
+    def timed(k):
+        b.reset(stream)
+        b.simulate(stream)  # warm (records the graph)
+        torch.cuda.synchronize()
+        ms, rls = [], 0
+        for _ in range(k):
+            flush.zero_()
+            b.reset(stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.simulate(stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            rls += b.stats(stream)["robot_link_steps"]
+        return rls / (sum(ms) / 1e3), float(np.mean(ms))
+
+    v0, ms0 = timed(2)
+    tune = b.autotune(args.uneven_sample, stream)
+    v1, ms1 = timed(2)
+    b.close()
+    return {"workload": "uneven batch: %d robots, links U{30..300} of U[1,3] cm, 5-200 obstacles, 0-8 actuators"
+                        % args.uneven_robots,
+            "robot_link_steps_per_step": scenes.robot_link_steps(sc["n_links"]),
+            "default": {"value": v0, "ms_per_step": ms0},
+            "autotuned": {"value": v1, "ms_per_step": ms1, "warps_per_cta": tune["warps_per_cta"],
+                          "list_margin_R": tune["list_margin"], "candidates": tune["candidates"],
+                          "sample": tune["sample"]},
+            "unit": UNIT}
+
+
 def cpu_baseline(args, sc, robots=None):
     """The FP64 oracle as it stands, OpenMP over robots on all host cores, on a
     bounded sample of the workload (the first `robots` robots)."""
@@ -429,6 +470,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--traffic", type=float, default=None)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--uneven-robots", type=int, default=4096)
+    ap.add_argument("--uneven-sample", type=int, default=2048)
     ap.add_argument("--serve-seconds", type=float, default=12.0)
     ap.add_argument("--serve-pool", type=int, default=24)
     ap.add_argument("--serve-slots", type=int, default=8192)

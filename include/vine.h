@@ -187,6 +187,25 @@ vine_status vine_grow_step(vine_batch* b, int32_t n_steps, void* cuda_stream);
  * longest-first work queue, replayed from a CUDA graph.  Async. */
 vine_status vine_simulate(vine_batch* b, void* cuda_stream);
 
+/* Launch autotuner for uneven batches.  Grows a sample of `sample`
+ * instances (0: 4096; spread evenly over the longest-first order) from
+ * reset to full length once per candidate configuration -- warps per CTA
+ * (4, 2, 1: one robot per warp; fewer warps per CTA pack large per-robot
+ * shared-memory slices more tightly) x broad-phase margin (0.25, 0.5, 1 body
+ * radii: list length against rebuild frequency) -- times each launch with
+ * CUDA events, and adopts the fastest for later vine_grow_step /
+ * vine_simulate calls.  Neither knob changes any result.  Leaves the batch
+ * reset.  Synchronises the stream. */
+typedef struct {
+  int32_t warps_per_cta;   /* chosen */
+  float list_margin;       /* chosen, body radii */
+  double best_ms;          /* sample growth time with the chosen configuration */
+  double default_ms;       /* with the configuration chosen at creation (-1 if not tried) */
+  int32_t candidates;      /* configurations timed */
+  int32_t sample;          /* instances grown per candidate */
+} vine_tune_result;
+vine_status vine_autotune(vine_batch* b, int32_t sample, void* cuda_stream, vine_tune_result* out);
+
 /* Same result as vine_simulate, computed with one launch per instance in
  * sequence (the comparison form).  Async. */
 vine_status vine_simulate_plain(vine_batch* b, void* cuda_stream);

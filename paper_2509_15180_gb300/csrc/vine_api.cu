@@ -503,6 +503,7 @@ vine_status vine_batch_create(const vine_batch_desc* D, const vine_params* P, vo
   a.max_halv = prm.max_halvings;
   a.exact = prm.exact_hessian;
   a.broad = prm.broad_phase;
+  a.list_margin = kListMargin;
   B->status0 = (int*)P_(o_st0);
   (void)persistent;
   *out = B;
@@ -568,6 +569,86 @@ vine_status vine_simulate(vine_batch* B, void* stream_v) {
   }
   CK(cudaGraphLaunch(B->graph_exec, st));
   return VINE_OK;
+}
+
+static vine_status ensure_stage(const vine_batch* Bc, size_t bytes);
+
+vine_status vine_autotune(vine_batch* B, int32_t sample, void* stream_v, vine_tune_result* out) {
+  if (!B || !out) return fail(VINE_EINVAL, "vine_autotune: null argument");
+  if (sample < 0) return fail(VINE_EINVAL, "vine_autotune: negative sample size");
+  cudaStream_t st = (cudaStream_t)stream_v;
+  const int n = B->n_inst;
+  const int ns = std::min(n, sample > 0 ? sample : 4096);
+  // sample spread evenly over the longest-first order (keeps its cost mix),
+  // itself longest first
+  std::vector<int> idx(ns);
+  for (int k = 0; k < ns; ++k) idx[k] = B->h_order[(int64_t)k * n / ns];
+  vine_status s = ensure_stage(B, 4 * (size_t)ns);
+  if (s != VINE_OK) return s;
+  int* d_idx = (int*)B->stage;
+  CK(cudaMemcpyAsync(d_idx, idx.data(), 4 * (size_t)ns, cudaMemcpyHostToDevice, st));
+  int dev_id = 0, nsm = 1;
+  cudaGetDevice(&dev_id);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev_id);
+  const float margins[3] = {0.25f, kListMargin, 1.0f};
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  std::memset(out, 0, sizeof(*out));
+  out->best_ms = 1e30;
+  out->default_ms = -1.0;
+  out->sample = ns;
+  vine_status rs = VINE_OK;
+  for (int w = kWarpsPerCta; w >= 1 && rs == VINE_OK; w >>= 1) {
+    const size_t smem = B->smem_warp * w;
+    if (grow_configure(B->ks, smem) != cudaSuccess) continue;
+    const int ctas = grow_max_ctas_per_sm(B->ks, smem, 32 * w);
+    if (ctas <= 0) continue;
+    for (float m : margins) {
+      GrowArgs a = B->args;
+      a.order = d_idx;
+      a.n_order = ns;
+      a.n_steps = B->max_target;
+      a.dynamic = 1;
+      a.list_margin = m;
+      const int grid = std::max(1, std::min((ns + w - 1) / w, nsm * ctas));
+      if ((rs = vine_batch_reset(B, st)) != VINE_OK) break;
+      cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+      if (e == cudaSuccess) e = launch_grow(a, B->ks, grid, 32 * w, smem, st);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) {
+        rs = cuda_fail(e, "vine_autotune");
+        break;
+      }
+      out->candidates += 1;
+      if (w == B->wpc && m == kListMargin) out->default_ms = ms;
+      if (ms < out->best_ms) {
+        out->best_ms = ms;
+        out->warps_per_cta = w;
+        out->list_margin = m;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rs != VINE_OK) return rs;
+  if (out->candidates == 0) return fail(VINE_EINVAL, "vine_autotune: no launch configuration fits");
+  // adopt the fastest (results do not depend on either knob)
+  B->wpc = out->warps_per_cta;
+  const int ctas = grow_max_ctas_per_sm(B->ks, B->smem_warp * B->wpc, 32 * B->wpc);
+  B->grid = std::max(1, std::min((n + B->wpc - 1) / B->wpc, nsm * std::max(ctas, 1)));
+  B->args.list_margin = out->list_margin;
+  if (B->graph_exec) {  // the recorded launch carries the old configuration
+    cudaGraphExecDestroy(B->graph_exec);
+    cudaGraphDestroy(B->graph);
+    B->graph_exec = nullptr;
+    B->graph = nullptr;
+  }
+  return vine_batch_reset(B, st);
 }
 
 vine_status vine_simulate_plain(vine_batch* B, void* stream_v) {

@@ -390,7 +390,7 @@ __device__ __forceinline__ void reset_lists(const Smem& S, int n, int lane) {
   __syncwarp();
 }
 
-// Broad phase.  Every link keeps the list of obstacles within kListMargin R
+// Broad phase.  Every link keeps the list of obstacles within margin R
 // of its discs and its two end points at the time the list was built.  The
 // discs lie on the segment between the end points, so while neither end
 // point has moved by 0.8 of the margin no other obstacle can reach them.
@@ -402,8 +402,8 @@ __device__ __forceinline__ void reset_lists(const Smem& S, int n, int lane) {
 // pre-tests run (in obstacles).
 template <int KS>
 __device__ void rebuild_lists(const InstDev& I, const Smem& S, int N, int j0, int j1, FF px, FF py, int lane,
-                              int& ntest) {
-  const float margin = kListMargin * I.R, mv = 0.64f * margin * margin;
+                              float margin_r, int& ntest) {
+  const float margin = margin_r * I.R, mv = 0.64f * margin * margin;
   int nre = 0;
   for (int j = j0; j < j1; ++j) {
     const float x0 = px.hi, y0 = py.hi;
@@ -512,7 +512,7 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
   const float kap = 2.f * A.w_c * I.kc;
   const float floor_d = 1e-6f * A.w_a * I.PR3;
   int ntest = 0;
-  if (A.broad) rebuild_lists<KS>(I, S, N, j0, j1, px, py, lane, ntest);
+  if (A.broad) rebuild_lists<KS>(I, S, N, j0, j1, px, py, lane, A.list_margin, ntest);
   double Jl = 0.0, Sl = 0.0;
   for (int j = j0; j < j1; ++j) {
     // ---- bending and actuation at joint j (Eq. restoring_moment)

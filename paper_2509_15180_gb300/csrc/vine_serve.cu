@@ -751,6 +751,7 @@ vine_status vine_server_create(const vine_params* params, const vine_server_conf
   a.max_halv = prm.max_halvings;
   a.exact = prm.exact_hessian;
   a.broad = prm.broad_phase;
+  a.list_margin = kListMargin;
   a.trace = nullptr;
   a.trace_count = nullptr;
   a.trace_inst = -1;

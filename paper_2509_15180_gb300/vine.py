@@ -70,6 +70,11 @@ class vine_server_stats(C.Structure):
                 ("max_slots", C.c_int32), ("busy_s", C.c_double)]
 
 
+class vine_tune_result(C.Structure):
+    _fields_ = [("warps_per_cta", C.c_int32), ("list_margin", C.c_float), ("best_ms", C.c_double),
+                ("default_ms", C.c_double), ("candidates", C.c_int32), ("sample", C.c_int32)]
+
+
 _p, _i32, _i64 = C.c_void_p, C.c_int32, C.c_int64
 _SIG = {
     "vine_params_default": [_p],
@@ -89,6 +94,7 @@ _SIG = {
     "vine_spam_tables_noalloc": [_p, _i32, _p, _p, _p, _p],
     "vine_debug_trace_read": [_p, _p, _i32, _p],
     "vine_set_actuators": [_p, _p, _p, _p, _i32, _p],
+    "vine_autotune": [_p, _i32, _p, _p],
     "vine_grad": [_p, _p, _p, _p, _p, _p, _p, _i32, _p],
     "vine_batch_destroy": [_p],
     "vine_server_config_default": [_p],
@@ -226,6 +232,13 @@ class Batch:
 
     def simulate(self, stream=None):
         _check(_lib.vine_simulate(self.h, _stream(stream)), "vine_simulate")
+
+    def autotune(self, sample: int = 4096, stream=None) -> dict:
+        """Time launch configurations on a sample and adopt the fastest
+        (vine_autotune); leaves the batch reset."""
+        r = vine_tune_result()
+        _check(_lib.vine_autotune(self.h, int(sample), _stream(stream), C.byref(r)), "vine_autotune")
+        return {k: getattr(r, k) for k, _ in vine_tune_result._fields_}
 
     def simulate_plain(self, stream=None):
         _check(_lib.vine_simulate_plain(self.h, _stream(stream)), "vine_simulate_plain")
