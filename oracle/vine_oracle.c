@@ -61,6 +61,9 @@ typedef struct {
   int32_t discs_per_link; /* contact discs per link (K_s) */
   int32_t max_halvings;   /* line-search halvings */
   int32_t exact_hessian;  /* 1: exact Hessian of J when positive definite, else Gauss-Newton; 0: Gauss-Newton */
+  int32_t mode;           /* 0: equilibrium; 1: Algorithm 1 read literally (frozen actuator force, descent) */
+  int32_t gd_steps;       /* mode 1: descent steps per growth step (Algorithm 1: 50) */
+  double gd_alpha;        /* mode 1: step as a fraction of the free-space Newton step (see gd_solve) */
 } orc_params;
 
 void orc_params_default(orc_params* p) {
@@ -76,6 +79,9 @@ void orc_params_default(orc_params* p) {
   p->discs_per_link = 2;
   p->max_halvings = 30;
   p->exact_hessian = 1;
+  p->mode = 0;
+  p->gd_steps = 50;
+  p->gd_alpha = 0.05;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -454,6 +460,7 @@ typedef struct {
   double l_seg, R, P, d; /* d = 2 R + R_act: moment arm of Eq. (restoring_moment) */
   double kc, kg;         /* contact and growth stiffness */
   int a0, a1, o0, o1;
+  const double* th_frozen; /* mode 1: joint angles at which the actuator strains are frozen (else NULL) */
 } inst_t;
 
 static void inst_init(inst_t* I, const orc_params* p, const orc_batch* b, const orc_tables* T, int i) {
@@ -467,6 +474,7 @@ static void inst_init(inst_t* I, const orc_params* p, const orc_batch* b, const 
   I->kg = ORC_PI * I->P * I->R * I->R / (2.0 * I->l_seg);
   I->a0 = b->act_ptr[i]; I->a1 = b->act_ptr[i + 1];
   I->o0 = b->obs_ptr[i]; I->o1 = b->obs_ptr[i + 1];
+  I->th_frozen = NULL;
 }
 
 /* Link start points p[0..N], unit directions u[0..N-1], lengths L[0..N-1]:
@@ -575,8 +583,19 @@ static double energy_h(const inst_t* I, int N, const double* th, double l, doubl
       double s = (double)b->act_side[a];
       double Pa = b->act_pressure[a];
       const orc_table* t = &I->T->tab[I->T->act_tab[a]];
-      double e = s * I->d * th[j] / I->l_seg; /* Eq. (restoring_moment), strain */
       double f, fp;
+      if (I->th_frozen) {
+        /* Algorithm 1: the force is computed once, at the step's initial
+         * strain, and held while the joint angle moves (linear potential) */
+        const double e0 = s * I->d * I->th_frozen[j] / I->l_seg;
+        table_f(t, e0, &f, &fp);
+        M -= c * s * Pa * f * I->d;
+        const double Ua = c * s * Pa * f * I->d * th[j];
+        U -= Ua;
+        Um += fabs(Ua);
+        continue;
+      }
+      double e = s * I->d * th[j] / I->l_seg; /* Eq. (restoring_moment), strain */
       table_f(t, e, &f, &fp);
       M -= c * s * Pa * f * I->d;
       dM -= c * Pa * fp * I->d * I->d / I->l_seg;
@@ -998,6 +1017,45 @@ double orc_sdf(const orc_batch* b, int o, double x, double y, double* nx, double
   return obs_sdf(b, o, x, y, 1.0, 0.0, nx, ny);
 }
 
+/* Algorithm 1 of Sec. 4.1 read literally (mode 1): the actuator forces are
+ * evaluated once from the strains at the step's initial state and held; then
+ * gd_steps steps of gradient descent on J.  The paper's single learning rate
+ * alpha is not printed and would mix units (rad per N m for the joint
+ * angles, m per N for the distal length), so each unknown gets the step
+ * gd_alpha / (its free-space stiffness): w_a pi P R^3 / (2 theta_c), the
+ * slope of the moment ramp below wrinkling onset, for the joint angles and
+ * 2 w_b k_g for the distal length, which is kept in [0, l_seg].  With
+ * gd_alpha = 1 a lone unactuated joint below onset would reach its
+ * equilibrium in one step.  No convergence test: the step ends after
+ * gd_steps updates (status OK unless the state becomes non-finite). */
+static int gd_solve(const inst_t* I0, int N, double* th, double* l) {
+  const orc_params* p = I0->p;
+  inst_t I = *I0;
+  const int n = N + 1;
+  double* th0 = (double*)malloc(sizeof(double) * n);
+  double* g = (double*)malloc(sizeof(double) * n);
+  geo_t G;
+  geo_alloc(&G, N);
+  memcpy(th0, th, sizeof(double) * N);
+  I.th_frozen = th0;
+  const double thc = 2.0 * asin(p->eps_crit);
+  const double PR3 = ORC_PI * I.P * I.R * I.R * I.R;
+  const double a_th = p->gd_alpha * 2.0 * thc / (p->w_a * PR3);
+  const double a_l = p->gd_alpha / (2.0 * p->w_b * I.kg);
+  int status = ORC_OK;
+  for (int k = 0; k < p->gd_steps; ++k) {
+    const double J = energy_h(&I, N, th, *l, g, NULL, &G, NULL, 0);
+    if (!isfinite(J)) { status = ORC_NONFINITE; break; }
+    for (int j = 0; j < N; ++j) th[j] -= a_th * g[j];
+    *l = fmin(fmax(*l - a_l * g[N], 0.0), I.l_seg);
+  }
+  for (int j = 0; j < N && status == ORC_OK; ++j)
+    if (!isfinite(th[j])) status = ORC_NONFINITE;
+  free(th0); free(g);
+  geo_free(&G);
+  return status;
+}
+
 /* Grow every instance by up to n_steps links (one link per step, capped at
  * n_links) and solve each step to equilibrium.  State is in/out:
  * N_state[i] links present, theta_state (CSR by n_links), l_state.
@@ -1029,7 +1087,14 @@ int orc_run(const orc_params* p, const orc_batch* b, const orc_tables* T, int n_
       int it = 0;
       double r = 0.0;
       long long ev = 0;
-      int st = solve_step(&I, N, th, &l_state[i], &it, &r, &ev);
+      int st;
+      if (p->mode == 1) {
+        st = gd_solve(&I, N, th, &l_state[i]);
+        it = p->gd_steps;
+        ev = p->gd_steps;
+      } else {
+        st = solve_step(&I, N, th, &l_state[i], &it, &r, &ev);
+      }
       iters_total[i] += it;
       evals[i] += ev;
       if (st == ORC_OK) {
