@@ -91,6 +91,34 @@ class ClockSampler:
         return out
 
 
+def _hbm_fraction(traffic_bytes, launch_s):
+    """DRAM bytes per launch over the launch time, against the measured copy
+    bandwidth (MEASURED_PEAKS.json; the fallback 6.8 TB/s if it is absent)."""
+    peak, src = 6800.0, "fallback"
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak, src = float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        pass
+    if traffic_bytes is None:
+        return None
+    gbs = traffic_bytes / launch_s / 1e9
+    return {"achieved_gbs": gbs, "peak_gbs": peak, "frac": gbs / peak, "peak_source": src}
+
+
+def reduce_over_ranks(seconds: float, units: float, device: str):
+    """Whole-job figures under torchrun: the slowest rank's time and the sum
+    of the units all ranks processed (weak scaling, one replica per rank)."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(u[0])
+
+
 def run_gpu(args):
     import torch
 
@@ -141,11 +169,7 @@ def run_gpu(args):
     step_ms = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
     total_s = float(step_ms.sum()) / 1e3
     if ws > 1:
-        t = torch.tensor([total_s, conv_rls], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        total_s, conv_all = float(tmax[0]), float(t[1])
+        total_s, conv_all = reduce_over_ranks(total_s, conv_rls, "cuda")
     else:
         conv_all = float(conv_rls)
     value = conv_all / total_s
@@ -222,6 +246,7 @@ def run_gpu(args):
                                   "scaled by robots",
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived; MEASURED_PEAKS has no FP32 figure)",
                 "flops_per_launch": flops,
+                "hbm": _hbm_fraction(traffic, launch_s),
                 "all_pairs_flops_per_launch": flops_all_pairs,
                 "pair_tests_executed_fraction": st_last["pair_tests_executed"] / max(st_last["pair_tests"], 1)}
 

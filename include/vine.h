@@ -80,8 +80,16 @@ typedef enum {
  * max_iter: Gauss-Newton iterations per growth step (100).
  * discs_per_link: contact discs K_s of radius R at fractions k/K_s of each
  *   link (2; 1..4 supported).
- * mode, gd_alpha, gd_steps: reserved for the fixed-step gradient descent of
- *   Algorithm 1 (mode 0 = equilibrium; only mode 0 is implemented).
+ * mode: 0 = each step solved to equilibrium (default); 1 = Algorithm 1 of
+ *   Sec. 4.1 read literally: the actuator forces are evaluated once per step
+ *   at the step's initial joint strains and held, then gd_steps steps of
+ *   gradient descent on the cost (no convergence test; every completed step
+ *   counts in robot_link_steps).  The printed learning rate is not given and
+ *   would mix units, so the joint angles step by gd_alpha 2 theta_c /
+ *   (w_a pi P R^3) times their gradient (gd_alpha times the inverse slope of
+ *   the moment ramp below wrinkling onset) and the distal length by
+ *   gd_alpha / (2 w_b k_g) times its gradient, kept in [0, l_seg].
+ * gd_alpha, gd_steps: mode 1 step fraction (0.005) and steps (50).
  * exact_hessian: 1 = Newton steps with the exact Hessian of the cost when it
  *   is positive definite, else with the Gauss-Newton matrix (contact second
  *   derivatives dropped); 0 = always Gauss-Newton (default 1).

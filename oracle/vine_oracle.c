@@ -81,7 +81,7 @@ void orc_params_default(orc_params* p) {
   p->exact_hessian = 1;
   p->mode = 0;
   p->gd_steps = 50;
-  p->gd_alpha = 0.05;
+  p->gd_alpha = 0.005;
 }
 
 /* ------------------------------------------------------------------------ */

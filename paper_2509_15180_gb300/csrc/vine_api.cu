@@ -196,7 +196,7 @@ vine_status vine_params_default(vine_params* p) {
   p->discs_per_link = 2;
   p->max_halvings = 30;
   p->mode = 0;
-  p->gd_alpha = 0.0;
+  p->gd_alpha = 0.005;
   p->gd_steps = 50;
   p->exact_hessian = 1;
   p->broad_phase = 1;
@@ -219,11 +219,11 @@ vine_status vine_batch_create(const vine_batch_desc* D, const vine_params* P, vo
   *out = nullptr;
   vine_params prm;
   if (P) prm = *P; else vine_params_default(&prm);
-  if (prm.mode != 0) return fail(VINE_EINVAL, "vine_batch_create: only mode 0 (equilibrium) is implemented");
   if (prm.discs_per_link < 1 || prm.discs_per_link > 4)
     return fail(VINE_EINVAL, "vine_batch_create: discs_per_link must be 1..4");
   if (!(prm.tol > 0.0) || prm.max_iter < 1 || prm.max_halvings < 0 || !(prm.eps_crit > 0.0 && prm.eps_crit < 1.0) ||
-      !(prm.R_c > 0.0 && prm.R_act > prm.R_c) || !(prm.m_lo > 0.0 && prm.m_lo < 0.5) || !(prm.pen_frac > 0.0) || !(prm.fval_eps >= 0.0) || !(prm.armijo_c1 > 0.0 && prm.armijo_c1 < 0.5))
+      !(prm.R_c > 0.0 && prm.R_act > prm.R_c) || !(prm.m_lo > 0.0 && prm.m_lo < 0.5) || !(prm.pen_frac > 0.0) || !(prm.fval_eps >= 0.0) || !(prm.armijo_c1 > 0.0 && prm.armijo_c1 < 0.5) ||
+      (prm.mode != 0 && prm.mode != 1) || (prm.mode == 1 && (prm.gd_steps < 1 || !(prm.gd_alpha > 0.0))))
     return fail(VINE_EINVAL, "vine_batch_create: parameter out of range");
   const int n = D->n_inst;
   if (n <= 0) return fail(VINE_EINVAL, "vine_batch_create: n_inst must be positive");
@@ -503,6 +503,9 @@ vine_status vine_batch_create(const vine_batch_desc* D, const vine_params* P, vo
   a.max_halv = prm.max_halvings;
   a.exact = prm.exact_hessian;
   a.broad = prm.broad_phase;
+  a.mode = prm.mode;
+  a.gd_steps = prm.gd_steps;
+  a.gd_alpha = (float)prm.gd_alpha;
   a.list_margin = kListMargin;
   B->status0 = (int*)P_(o_st0);
   (void)persistent;

@@ -528,7 +528,9 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
       const int bits = __float_as_int(ac.w);
       const float side = bits < 0 ? -1.f : 1.f;
       const int tid = bits & 0x7fffffff;
-      const float e = side * I.d * th / I.l_seg;
+      // Algorithm 1 (mode 1): the force is taken at the step's initial strain
+      const bool frozen = A.mode == 1;
+      const float e = side * I.d * (frozen ? S.TH0[j] : th) / I.l_seg;
       const float4 hd = A.tab_hdr[tid];
       const float2* tb = A.tab + (size_t)tid * kKnots;
       const float uu = (e - hd.x) * hd.z;
@@ -547,6 +549,12 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
         Gi = k0.y + 0.5f * tau * hd.y * (k0.x + f);
       }
       M -= cov * side * ac.z * f * I.d;
+      if (frozen) {  // held force: linear potential, no stiffness
+        const float Ua = cov * side * ac.z * f * I.d * th;
+        U -= Ua;
+        Um += fabsf(Ua);
+        continue;
+      }
       dM -= cov * ac.z * fp * I.d * I.d / I.l_seg;
       const float Ua = cov * ac.z * I.l_seg * (Gi - hd.w);
       U -= Ua;
@@ -924,6 +932,36 @@ __device__ int solve_step(const GrowArgs& A, const InstDev& I, const Smem& S, in
   return status;
 }
 
+// Algorithm 1 of Sec. 4.1 read literally (mode 1): the actuator forces are
+// held at the step's initial strains (eval reads them from TH0), then
+// gd_steps steps of gradient descent, each unknown scaled by its free-space
+// stiffness: joint angles by gd_alpha 2 theta_c / (w_a pi P R^3), the distal
+// length by gd_alpha / (2 w_b k_g), kept in [0, l_seg].  No convergence test.
+template <int KS>
+__device__ int descend_step(const GrowArgs& A, const InstDev& I, const Smem& S, int N, float& l, int lane,
+                            StepStats& st) {
+  for (int k = lane; k < N; k += 32) S.TH0[k] = S.TH[k];
+  __syncwarp();
+  const float a_th = A.gd_alpha * 2.f * A.theta_c / (A.w_a * I.PR3);
+  const float a_l = A.gd_alpha / (2.f * A.w_b * I.kg);
+  for (int it = 0; it < A.gd_steps; ++it) {
+    const EvalOut E = eval<KS>(A, I, S, N, l, lane, false);
+    st.evals += 1;
+    st.linkevals += N;
+    st.tests += E.tests;
+    st.iters += 1;
+    if (!isfinite(E.J)) return kNonFinite;
+    for (int k = lane; k < N; k += 32) S.TH[k] -= a_th * S.G[k];
+    l = fminf(fmaxf(l - a_l * E.gl, 0.f), I.l_seg);
+    __syncwarp();
+  }
+  for (int k = lane; k < N; k += 32)
+    if (!isfinite(S.TH[k])) st.r = 1.0;  // marks a non-finite angle
+  const bool bad = __any_sync(kFull, st.r != 0.0);
+  st.r = 0.0;
+  return bad ? kNonFinite : kOK;
+}
+
 template <int KS>
 __device__ void process_instance(const GrowArgs& A, int inst, const Smem& S, int lane) {
   const long long t_start = clock64();
@@ -946,7 +984,8 @@ __device__ void process_instance(const GrowArgs& A, int inst, const Smem& S, int
     l = 0.f;
     __syncwarp();
     StepStats st{0, 0.0, 0, 0, 0, 0};
-    const int res = solve_step<KS>(A, I, S, N, l, lane, st, inst);
+    const int res = A.mode == 1 ? descend_step<KS>(A, I, S, N, l, lane, st)
+                                : solve_step<KS>(A, I, S, N, l, lane, st, inst);
     iters += st.iters;
     evals += st.evals;
     linkevals += st.linkevals;

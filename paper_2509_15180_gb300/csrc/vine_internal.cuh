@@ -80,6 +80,9 @@ struct GrowArgs {
   int exact;  // exact Hessian when positive definite (else Gauss-Newton)
   int broad;  // per-link obstacle lists (else every obstacle at every evaluation)
   float list_margin;  // broad-phase margin in body radii
+  int mode;           // 0 equilibrium; 1 Algorithm 1 read literally (frozen actuator force, descent)
+  int gd_steps;       // mode 1: descent steps per growth step
+  float gd_alpha;     // mode 1: step as a fraction of the free-space Newton step
   // diagnostics: per line-search trial records of one robot (off when null)
   double* trace;
   int* trace_count;

@@ -549,7 +549,8 @@ vine_status vine_server_create(const vine_params* params, const vine_server_conf
   if (!(prm.tol > 0.0) || prm.max_iter < 1 || prm.max_halvings < 0 || !(prm.eps_crit > 0.0 && prm.eps_crit < 1.0) ||
       !(prm.R_c > 0.0 && prm.R_act > prm.R_c) || !(prm.m_lo > 0.0 && prm.m_lo < 0.5) || !(prm.pen_frac > 0.0) ||
       !(prm.fval_eps >= 0.0) || !(prm.armijo_c1 > 0.0 && prm.armijo_c1 < 0.5) || prm.discs_per_link < 1 ||
-      prm.discs_per_link > 4)
+      prm.discs_per_link > 4 || (prm.mode != 0 && prm.mode != 1) ||
+      (prm.mode == 1 && (prm.gd_steps < 1 || !(prm.gd_alpha > 0.0))))
     return sfail(VINE_EINVAL, "vine_server_create: parameter out of range");
   vine_server_config c;
   vine_server_config_default(&c);
@@ -751,6 +752,9 @@ vine_status vine_server_create(const vine_params* params, const vine_server_conf
   a.max_halv = prm.max_halvings;
   a.exact = prm.exact_hessian;
   a.broad = prm.broad_phase;
+  a.mode = prm.mode;
+  a.gd_steps = prm.gd_steps;
+  a.gd_alpha = (float)prm.gd_alpha;
   a.list_margin = kListMargin;
   a.trace = nullptr;
   a.trace_count = nullptr;

@@ -1,0 +1,42 @@
+"""The multi-rank path of the benchmark on CPU (gloo, world size 2): every
+rank grows its own replica of the workload (distinct seeds, no data
+exchange), and the reported figures are the slowest rank's time and the sum
+of all ranks' robot-link-steps."""
+import os
+import sys
+
+import numpy as np
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _worker(rank, world, port, out):
+    sys.path.insert(0, ROOT)
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    from paper_2509_15180_gb300 import scenes
+    sc = scenes.config2(8, replicate=rank)
+    units = scenes.robot_link_steps(sc["n_links"]) * (rank + 1)
+    t, u = bench.reduce_over_ranks(1.5 + rank, units, "cpu")
+    out[rank] = (t, u, float(sc["pressure"][0]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_ranks_report_max_time_and_summed_units():
+    ctx = mp.get_context("spawn")
+    manager = ctx.Manager()
+    out = manager.dict()
+    port = 29000 + (os.getpid() % 1000)
+    mp.start_processes(_worker, args=(2, port, out), nprocs=2, start_method="spawn", join=True)
+    (t0, u0, p0), (t1, u1, p1) = out[0], out[1]
+    rls = 8 * 100 * 101 // 2
+    assert t0 == t1 == 2.5
+    assert u0 == u1 == rls * 3
+    assert p0 != p1  # each rank grows a different replica
