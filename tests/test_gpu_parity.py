@@ -323,3 +323,52 @@ def test_broad_phase_is_exact():
         assert t0["pair_tests_executed"] == t0["pair_tests"]
         print("broad phase: %.1f%% of the all-pairs tests run" % (100.0 * t1["pair_tests_executed"] / t1["pair_tests"]))
         assert t1["pair_tests_executed"] < t0["pair_tests_executed"]
+
+
+def test_maximum_sizes_and_empty_batch():
+    """A robot at every per-robot maximum (1024 links, 1024 obstacles, 64
+    actuators) grown 24 steps against the oracle; one link more is a bad
+    input; an empty batch is refused."""
+    rng = np.random.default_rng(17)
+    base = scenes.config1(1)
+    n_obs, n_act = 1024, 64
+    cx = rng.uniform(0.08, 0.6, n_obs)
+    cy = rng.uniform(-0.3, 0.3, n_obs)
+    keep = np.hypot(cx, cy) > 0.05 + 0.006  # clear of the base
+    cx, cy = np.where(keep, cx, cx + 0.1), cy
+    sc = dict(base)
+    sc["n_links"] = np.array([1024], np.int32)
+    sc["obs_ptr"] = np.array([0, n_obs], np.int32)
+    sc["obs_kind"] = np.zeros(n_obs, np.uint8)
+    sc["obs_cx"] = cx.astype(np.float32)
+    sc["obs_cy"] = cy.astype(np.float32)
+    sc["obs_a"] = rng.uniform(0.002, 0.006, n_obs).astype(np.float32)
+    sc["obs_b"] = np.zeros(n_obs, np.float32)
+    sc["act_ptr"] = np.array([0, n_act], np.int32)
+    b0 = rng.integers(0, 20, n_act).astype(np.float32)
+    sc["act_begin"] = b0
+    sc["act_end"] = (b0 + rng.uniform(0.5, 3.0, n_act)).astype(np.float32)
+    sc["act_side"] = np.where(rng.random(n_act) < 0.5, 1, -1).astype(np.int8)
+    sc["act_pressure"] = rng.uniform(0.0, 300.0, n_act).astype(np.float32)
+    sc["act_l0"] = np.full(n_act, 0.02, np.float32)
+    b = vine.Batch(sc)
+    b.grow_step(24)
+    st = b.state()
+    counts, pairs = b.contacts(256)
+    orc = _oracle(sc)
+    ost = orc.new_state()
+    orc.run(ost, 24, threads=1)
+    assert st["N"][0] == 24 and st["status"][0] == 0 and ost["status"][0] == 0
+    cls = _classify(b, st, orc, ost, sc, counts, pairs)
+    assert cls[0] in ("match", "tol"), cls
+    b.close()
+    # one link beyond the maximum: that robot is flagged, the batch runs
+    big = scenes.concat([scenes.config1(1), dict(sc, n_links=np.array([1025], np.int32))])
+    b = vine.Batch(big)
+    b.grow_step(3)
+    st = b.state()
+    assert st["status"][1] == vine.INST_BADINPUT and st["N"][1] == 0 and st["N"][0] == 3
+    b.close()
+    with pytest.raises(vine.VineError) as e:
+        vine.Batch(scenes.subset(scenes.config1(2), []))
+    assert e.value.status == vine.VINE_EINVAL
