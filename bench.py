@@ -251,11 +251,12 @@ def run_gpu(args):
                 "pair_tests_executed_fraction": st_last["pair_tests_executed"] / max(st_last["pair_tests"], 1)}
 
     result = None
+    # the serving and uneven-batch legs describe one GPU: they run at N = 1
     serve = None
-    if rank == 0 and not args.no_serve:
+    if ws == 1 and not args.no_serve:
         serve = serve_leg(args, vine, scenes)
     uneven = None
-    if rank == 0 and args.uneven_robots > 0:
+    if ws == 1 and args.uneven_robots > 0:
         uneven = uneven_leg(args, vine, scenes, torch, stream, flush)
     if rank == 0:
         cpu = cpu_baseline(args, sc) if ws == 1 and not args.no_cpu else None
