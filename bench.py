@@ -258,6 +258,9 @@ def run_gpu(args):
     uneven = None
     if ws == 1 and args.uneven_robots > 0:
         uneven = uneven_leg(args, vine, scenes, torch, stream, flush)
+    robust = None
+    if ws == 1 and args.robust_perturb > 0:
+        robust = robust_leg(args, vine, scenes, torch, stream, flush)
     if rank == 0:
         cpu = cpu_baseline(args, sc) if ws == 1 and not args.no_cpu else None
         lat = {"p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
@@ -271,7 +274,7 @@ def run_gpu(args):
                        "robot_link_steps_per_step": rls_per_step, "l2": "flushed between timed steps (512 MiB write)",
                        "tol": 1e-6},
             "e2e": e2e, "plain": plain, "latency": lat, "roofline": roofline, "cpu_baseline": cpu,
-            "adjoint": adjoint, "serving": serve, "uneven": uneven,
+            "adjoint": adjoint, "serving": serve, "uneven": uneven, "robustness": robust,
             "clocks": ck, "gpu_launches": args.steps, "robots": robots,
             "solver": {"iters_per_step": st_last["iterations"] / max(st_last["steps_total"], 1),
                        "evals_per_step": st_last["evaluations"] / max(st_last["steps_total"], 1),
@@ -438,6 +441,39 @@ def uneven_leg(args, vine, scenes, torch, stream, flush):
             "unit": UNIT}
 
 
+def robust_leg(args, vine, scenes, torch, stream, flush):
+    """Robustness batch with gradients: designs of 150 links and 60 obstacles,
+    each perturbed (obstacle centres, actuator ends, pressures); one
+    vine_simulate plus one vine_grad (tip-to-goal distance and its
+    derivatives w.r.t. every actuator's pressure and span) per step."""
+    sc, goals = scenes.config4(n_designs=args.robust_designs, n_perturb=args.robust_perturb)
+    b = vine.Batch(sc, stream=stream)
+    g = torch.from_numpy(goals).cuda()
+    b.simulate(stream)
+    b.grad(g, stream)
+    torch.cuda.synchronize()
+    ms_f, ms_g, rls = [], [], 0
+    for _ in range(2):
+        flush.zero_()
+        b.reset(stream)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        b.simulate(stream)
+        e1.record(stream)
+        out = b.grad(g, stream)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        ms_f.append(e0.elapsed_time(e1))
+        ms_g.append(e1.elapsed_time(e2))
+        rls += b.stats(stream)["robot_link_steps"]
+    st = out["status"].cpu().numpy()
+    b.close()
+    return {"workload": "robustness batch: %d designs x %d perturbations, 150 links, 60 obstacles, 2.25 m box"
+                        % (args.robust_designs, args.robust_perturb),
+            "value": rls / (sum(ms_f) / 1e3), "unit": UNIT, "simulate_ms": float(np.mean(ms_f)),
+            "grad_ms": float(np.mean(ms_g)), "grad_ok": int((st == 0).sum()), "robots": int(st.size)}
+
+
 def cpu_baseline(args, sc, robots=None):
     """The FP64 oracle as it stands, OpenMP over robots on all host cores, on a
     bounded sample of the workload (the first `robots` robots)."""
@@ -498,6 +534,8 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--uneven-robots", type=int, default=4096)
     ap.add_argument("--uneven-sample", type=int, default=2048)
+    ap.add_argument("--robust-designs", type=int, default=64)
+    ap.add_argument("--robust-perturb", type=int, default=32)
     ap.add_argument("--serve-seconds", type=float, default=12.0)
     ap.add_argument("--serve-pool", type=int, default=24)
     ap.add_argument("--serve-slots", type=int, default=8192)
