@@ -130,7 +130,7 @@ def run_gpu(args):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    sc = scenes.config2(args.robots, replicate=rank)
+    sc = scenes.design_batch(args.robots, replicate=rank)
     rls_per_step = scenes.robot_link_steps(sc["n_links"])
     stream = torch.cuda.current_stream()
     dsc = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in sc.items()}
@@ -407,7 +407,7 @@ def uneven_leg(args, vine, scenes, torch, stream, flush):
     """Uneven persistent batch (links U{30..300}, 0-8 actuators, 5-200
     obstacles): robot-link-steps/s of vine_simulate with the launch
     configuration picked at creation, then after vine_autotune on a sample."""
-    sc = scenes.config3(args.uneven_robots)
+    sc = scenes.uneven_batch(args.uneven_robots)
     b = vine.Batch(sc, stream=stream)
 
     def timed(k):
@@ -446,7 +446,7 @@ def robust_leg(args, vine, scenes, torch, stream, flush):
     each perturbed (obstacle centres, actuator ends, pressures); one
     vine_simulate plus one vine_grad (tip-to-goal distance and its
     derivatives w.r.t. every actuator's pressure and span) per step."""
-    sc, goals = scenes.config4(n_designs=args.robust_designs, n_perturb=args.robust_perturb)
+    sc, goals = scenes.robustness_batch(n_designs=args.robust_designs, n_perturb=args.robust_perturb)
     b = vine.Batch(sc, stream=stream)
     g = torch.from_numpy(goals).cuda()
     b.simulate(stream)
@@ -499,7 +499,7 @@ def run_reference(args):
     ws, rank = _dist()
     if rank != 0:
         return None
-    sc = scenes.config2(4096)
+    sc = scenes.design_batch(4096)
     vals, times = [], []
     for _ in range(args.warmup):
         cpu_baseline(args, sc, robots=8)

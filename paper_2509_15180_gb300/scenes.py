@@ -23,7 +23,7 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["config1", "config2", "config3", "config4", "goal_points", "make", "serve_requests", "robot_link_steps",
+__all__ = ["parity_batch", "design_batch", "uneven_batch", "robustness_batch", "goal_points", "serve_requests", "robot_link_steps",
            "concat", "subset"]
 
 
@@ -98,7 +98,7 @@ def _pack(rows):
     return sc
 
 
-def config1(n_inst: int = 64, replicate: int = 0) -> dict:
+def parity_batch(n_inst: int = 64, replicate: int = 0) -> dict:
     """64 robots x 20 links of 2 cm, R 2.5 cm, P 5 kPa; with probability 1/2 one
     actuator over 5 consecutive links at U[0, 10] kPa; 10 circles of radius
     U[1, 3] cm in a 0.5 m box ahead of the base."""
@@ -112,7 +112,7 @@ def config1(n_inst: int = 64, replicate: int = 0) -> dict:
     return _pack(rows)
 
 
-def config2(n_inst: int = 4096, replicate: int = 0) -> dict:
+def design_batch(n_inst: int = 4096, replicate: int = 0) -> dict:
     """4096 robots x 100 links of 1.5 cm, R U[2, 4] cm, P U[2, 10] kPa; 0-6
     actuators over 3-15 links at U[0, 15] kPa; 20 circles (r U[1, 5] cm) and
     20 boxes (sides U[2, 10] cm) in a 1.5 m box."""
@@ -128,8 +128,8 @@ def config2(n_inst: int = 4096, replicate: int = 0) -> dict:
     return _pack(rows)
 
 
-def config3(n_inst: int = 16384, replicate: int = 0, n_range=(30, 300)) -> dict:
-    """Uneven batch: links U{30..300} of U[1, 3] cm, R and P as config 2, 0-8
+def uneven_batch(n_inst: int = 16384, replicate: int = 0, n_range=(30, 300)) -> dict:
+    """Uneven batch: links U{30..300} of U[1, 3] cm, R and P as the design batch, 0-8
     actuators, 5-200 obstacles (half circles, half boxes) in a box whose side
     is the robot's length."""
     rng = _rng(3, replicate)
@@ -147,9 +147,9 @@ def config3(n_inst: int = 16384, replicate: int = 0, n_range=(30, 300)) -> dict:
     return _pack(rows)
 
 
-def config4(n_designs: int = 64, n_perturb: int = 1024, replicate: int = 0, n_links: int = 150,
+def robustness_batch(n_designs: int = 64, n_perturb: int = 1024, replicate: int = 0, n_links: int = 150,
             box: float = 2.25, n_circ: int = 30, n_box: int = 30) -> tuple[dict, np.ndarray]:
-    """Robustness batch: designs as config 2 with 150 links and 60 obstacles in
+    """Robustness batch: designs as the design batch with 150 links and 60 obstacles in
     a 2.25 m box, each perturbed n_perturb times (obstacle centres + N(0, 1 cm),
     actuator endpoints + N(0, 0.5 link), pressures x U[0.95, 1.05]).  Returns
     the scene and one goal point per instance (uniform in the far half of the
@@ -188,26 +188,16 @@ def goal_points(n_inst: int, box: float, replicate: int = 0) -> np.ndarray:
     return np.stack([gx, gy], axis=1).astype(np.float32)
 
 
-def make(config: int, n_inst: int | None = None, replicate: int = 0) -> dict:
-    if config == 1:
-        return config1(64 if n_inst is None else n_inst, replicate)
-    if config == 2:
-        return config2(4096 if n_inst is None else n_inst, replicate)
-    if config == 3:
-        return config3(16384 if n_inst is None else n_inst, replicate)
-    raise ValueError("unknown configuration %r" % config)
-
-
 def serve_requests(n_req: int, rate_hz: float = 2000.0, replicate: int = 0, max_inst: int = 256):
     """Poisson request stream for the serving loop: arrival times (s) and, per
-    request, a scene of U{1..max_inst} instances drawn as config 3 but with
+    request, a scene of U{1..max_inst} instances drawn as the uneven batch but with
     links U{20..300}."""
     rng = _rng(5, replicate)
     t = np.cumsum(rng.exponential(1.0 / rate_hz, n_req))
     sizes = rng.integers(1, max_inst + 1, n_req)
     reqs = []
     for k in range(n_req):
-        sub = config3(int(sizes[k]), replicate=5000 + 7919 * replicate + k, n_range=(20, 300))
+        sub = uneven_batch(int(sizes[k]), replicate=5000 + 7919 * replicate + k, n_range=(20, 300))
         reqs.append(sub)
     return t, reqs
 

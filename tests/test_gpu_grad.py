@@ -16,7 +16,7 @@ from paper_2509_15180_gb300.autograd import VineSim  # noqa: E402
 
 
 def _scene(n_designs=6, n_perturb=2, n_links=30):
-    return scenes.config4(n_designs=n_designs, n_perturb=n_perturb, n_links=n_links, box=0.015 * n_links,
+    return scenes.robustness_batch(n_designs=n_designs, n_perturb=n_perturb, n_links=n_links, box=0.015 * n_links,
                           n_circ=8, n_box=8)
 
 
@@ -100,7 +100,7 @@ def test_grad_device_path_equals_host_path():
 def test_grad_full_length_robustness_designs_sampled():
     """Config-4 shaped designs (150 links, 60 obstacles, 2.25 m box), 8 designs
     x 16 perturbations, one launch; 24 robots checked against the oracle."""
-    sc, goals = scenes.config4(n_designs=8, n_perturb=16)
+    sc, goals = scenes.robustness_batch(n_designs=8, n_perturb=16)
     b = vine.Batch(sc)
     b.simulate()
     st = b.state()

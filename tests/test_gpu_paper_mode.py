@@ -36,7 +36,7 @@ def _pose_error(orc, ost, io, b, st, ig, ls):
 
 
 def test_paper_mode_step_matches_oracle():
-    sc = scenes.config1()
+    sc = scenes.parity_batch()
     n = 64
     prm = vine.vine_params_default()
     prm.mode = 1

@@ -36,7 +36,7 @@ def _oracle(sc, tol=1e-10):
 
 
 def test_prologue_tables_match_oracle():
-    sc = scenes.config2(16)
+    sc = scenes.design_batch(16)
     b = vine.Batch(sc)
     T = b.tables()
     orc = _oracle(sc)
@@ -116,9 +116,9 @@ def _classify(b, st, orc, ost, sc, counts, pairs, idx_gpu=None):
     return out
 
 
-def test_config1_full_parity():
+def test_parity_batch_full():
     """64 robots x 20 steps, independent trajectories."""
-    sc = scenes.config1()
+    sc = scenes.parity_batch()
     b = vine.Batch(sc)
     b.simulate()
     st = b.state()
@@ -131,7 +131,7 @@ def test_config1_full_parity():
     assert stats["steps_converged"] == 64 * 20
     assert stats["robot_link_steps"] == scenes.robot_link_steps(sc["n_links"])
     cls = _classify(b, st, orc, ost, sc, counts, pairs)
-    print("config 1: %d match, %d tol, %d basin switches" % (cls.count("match"), cls.count("tol"),
+    print("parity batch: %d match, %d tol, %d basin switches" % (cls.count("match"), cls.count("tol"),
                                                             cls.count("switch")))
     assert cls.count("switch") <= 6
     b.close()
@@ -170,11 +170,11 @@ def _stepwise(sc, steps):
     return tally
 
 
-def test_config1_stepwise_resynced_parity():
+def test_parity_batch_stepwise_resynced():
     """Each step, the oracle starts from the GPU's previous state; the step's
     result must match unless that step is a snap-through to another valid
     equilibrium."""
-    sc = scenes.config1()
+    sc = scenes.parity_batch()
     tally = _stepwise(sc, 20)
     print("stepwise: %s in %d robot-steps" % (tally, 20 * 64))
     assert tally["flagged"] == 0
@@ -185,7 +185,7 @@ def test_uneven_stepwise_resynced_parity():
     """Uneven robots (40-90 links, 5-200 obstacles, 0-8 actuators), resynced
     every step: over a whole growth the trajectories of two solvers can part
     at a snap-through, but single steps from the same state agree."""
-    sc = scenes.config3(12, n_range=(40, 90))
+    sc = scenes.uneven_batch(12, n_range=(40, 90))
     steps = int(sc["n_links"].max())
     tally = _stepwise(sc, steps)
     total = int(sc["n_links"].sum())
@@ -198,7 +198,7 @@ def test_uneven_stepwise_resynced_parity():
 
 
 def test_plain_form_is_bitwise_identical():
-    sc = scenes.config1(16)
+    sc = scenes.parity_batch(16)
     b1, b2 = vine.Batch(sc), vine.Batch(sc)
     b1.simulate()
     b2.simulate_plain()
@@ -208,10 +208,10 @@ def test_plain_form_is_bitwise_identical():
     b1.close(); b2.close()
 
 
-def test_config2_full_size_sampled():
+def test_design_batch_full_size_sampled():
     """4096 robots x 100 links in the launch the benchmark times; 12 sampled
     robots recomputed by the oracle."""
-    sc = scenes.config2()
+    sc = scenes.design_batch()
     b = vine.Batch(sc)
     b.simulate()
     torch.cuda.synchronize()
@@ -230,7 +230,7 @@ def test_config2_full_size_sampled():
     ost = orc.new_state()
     orc.run(ost, 100, threads=THREADS)
     cls = _classify(b, st, orc, ost, sub, counts, pairs, idx_gpu=idx)
-    print("config 2 sample: %d match, %d tol, %d basin switches, %d flagged" % (
+    print("design batch sample: %d match, %d tol, %d basin switches, %d flagged" % (
         cls.count("match"), cls.count("tol"), cls.count("switch"), cls.count("flagged")))
     assert cls.count("match") + cls.count("tol") >= 9
     assert stats["robot_link_steps"] >= 0.99 * scenes.robot_link_steps(sc["n_links"])
@@ -239,7 +239,7 @@ def test_config2_full_size_sampled():
 
 def test_uneven_batch_sampled():
     """Uneven robots (30-120 links, 5-200 obstacles, 0-8 actuators) in one launch."""
-    sc = scenes.config3(96, n_range=(30, 120))
+    sc = scenes.uneven_batch(96, n_range=(30, 120))
     b = vine.Batch(sc)
     b.simulate()
     st = b.state()
@@ -262,7 +262,7 @@ def test_uneven_batch_sampled():
 
 def test_edge_cases():
     # straight tube, no obstacles/actuators; one-link robot; bad input next to good ones
-    sc = scenes.config1(4)
+    sc = scenes.parity_batch(4)
     sc["act_ptr"] = np.zeros(5, np.int32)
     for k in ("act_begin", "act_end", "act_pressure", "act_l0"):
         sc[k] = np.zeros(0, np.float32)
@@ -294,7 +294,7 @@ def test_edge_cases():
 
 
 def test_device_inputs_match_host_inputs():
-    sc = scenes.config1(8)
+    sc = scenes.parity_batch(8)
     dsc = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in sc.items()}
     b1, b2 = vine.Batch(sc), vine.Batch(dsc)
     b1.simulate(); b2.simulate()
@@ -307,7 +307,7 @@ def test_device_inputs_match_host_inputs():
 def test_broad_phase_is_exact():
     """The per-link obstacle lists skip only obstacles that cannot reach a
     link, so the growth is bitwise the same as testing every obstacle."""
-    for sc in (scenes.config2(64), scenes.config3(48, n_range=(30, 120))):
+    for sc in (scenes.design_batch(64), scenes.uneven_batch(48, n_range=(30, 120))):
         out = []
         for bp in (1, 0):
             prm = vine.vine_params_default()
@@ -330,7 +330,7 @@ def test_maximum_sizes_and_empty_batch():
     actuators) grown 24 steps against the oracle; one link more is a bad
     input; an empty batch is refused."""
     rng = np.random.default_rng(17)
-    base = scenes.config1(1)
+    base = scenes.parity_batch(1)
     n_obs, n_act = 1024, 64
     cx = rng.uniform(0.08, 0.6, n_obs)
     cy = rng.uniform(-0.3, 0.3, n_obs)
@@ -363,12 +363,12 @@ def test_maximum_sizes_and_empty_batch():
     assert cls[0] in ("match", "tol"), cls
     b.close()
     # one link beyond the maximum: that robot is flagged, the batch runs
-    big = scenes.concat([scenes.config1(1), dict(sc, n_links=np.array([1025], np.int32))])
+    big = scenes.concat([scenes.parity_batch(1), dict(sc, n_links=np.array([1025], np.int32))])
     b = vine.Batch(big)
     b.grow_step(3)
     st = b.state()
     assert st["status"][1] == vine.INST_BADINPUT and st["N"][1] == 0 and st["N"][0] == 3
     b.close()
     with pytest.raises(vine.VineError) as e:
-        vine.Batch(scenes.subset(scenes.config1(2), []))
+        vine.Batch(scenes.subset(scenes.parity_batch(2), []))
     assert e.value.status == vine.VINE_EINVAL

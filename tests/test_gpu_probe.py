@@ -40,15 +40,15 @@ def _states(sc, steps, every):
     return orc, out
 
 
-@pytest.mark.parametrize("cfg", [1, 2])
+@pytest.mark.parametrize("batch", ["parity", "design"])
 @pytest.mark.parametrize("exact", [0, 1])
-def test_probe_matches_oracle(cfg, exact):
+def test_probe_matches_oracle(batch, exact):
     """Gauss-Newton mode checks the O(N) sweep at every state, including
     states pushed off equilibrium; exact-Hessian mode at the equilibrium
     states only (off equilibrium the exact Hessian can be near singular,
     where FP32 and FP64 steps legitimately part)."""
-    sc = scenes.config1(16) if cfg == 1 else scenes.config2(8)
-    steps, every = (20, 5) if cfg == 1 else (60, 15)
+    sc = scenes.parity_batch(16) if batch == "parity" else scenes.design_batch(8)
+    steps, every = (20, 5) if batch == "parity" else (60, 15)
     orc, states = _states(sc, steps, every)
     orc = oracle.Oracle(sc, oracle.default_params(exact_hessian=exact))
     prm = vine.vine_params_default()
@@ -90,7 +90,7 @@ def test_probe_matches_oracle(cfg, exact):
             # tol = 1e-6: at equilibrium both sides read FP32/FP64 noise of
             # about that size, so the bar is tol plus 2% of the residual
             worst["r"] = max(worst["r"], abs(rg - ro) / (1e-6 + 2e-2 * ro))
-    print("probe cfg %d exact %d worst relative errors: %s" % (cfg, exact, worst))
+    print("probe %s batch, exact %d, worst relative errors: %s" % (batch, exact, worst))
     # FP32 terms and the Hermite-tabulated wrinkling energy near onset
     assert worst["J"] < 1e-4
     assert worst["g"] < 5e-3  # FP32 contact forces: ~1e-8 m penetration error x stiffness x lever

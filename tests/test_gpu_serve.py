@@ -23,7 +23,7 @@ def _requests(k, replicate=0):
     out = []
     for j in range(k):
         n = int(rng.integers(1, 9))
-        out.append(scenes.config3(n, replicate=700 + 31 * replicate + j, n_range=(20, 60)))
+        out.append(scenes.uneven_batch(n, replicate=700 + 31 * replicate + j, n_range=(20, 60)))
     return out
 
 
@@ -80,29 +80,29 @@ def test_results_same_alone_in_mix_and_batched():
 
 def test_admission_by_free_slots():
     srv = vine.Server(max_slots=8, max_request=8, max_links=64, max_obs=200, max_act=8, steps_per_tick=2)
-    big = scenes.config3(6, replicate=900, n_range=(50, 60))
+    big = scenes.uneven_batch(6, replicate=900, n_range=(50, 60))
     r1 = srv.submit(big)
     assert r1 is not None
-    assert srv.submit(scenes.config3(6, replicate=901, n_range=(20, 30))) is None  # 6 + 6 > 8 slots: busy
-    r_small = srv.submit(scenes.config3(2, replicate=902, n_range=(20, 30)))
+    assert srv.submit(scenes.uneven_batch(6, replicate=901, n_range=(20, 30))) is None  # 6 + 6 > 8 slots: busy
+    r_small = srv.submit(scenes.uneven_batch(2, replicate=902, n_range=(20, 30)))
     assert r_small is not None  # 6 + 2 fit
     assert srv.stats()["free_slots"] == 0
     _wait(srv, r1)
     _wait(srv, r_small)
     assert srv.stats()["free_slots"] == 8
-    assert srv.submit(scenes.config3(6, replicate=901, n_range=(20, 30))) is not None
+    assert srv.submit(scenes.uneven_batch(6, replicate=901, n_range=(20, 30))) is not None
     srv.close()
 
 
 def test_refuses_malformed_requests():
     srv = vine.Server(max_slots=64, max_request=4, max_links=40, max_obs=200, max_act=8)
     with pytest.raises(vine.VineError) as e:
-        srv.submit(scenes.config3(5, replicate=903, n_range=(20, 30)))  # more robots than max_request
+        srv.submit(scenes.uneven_batch(5, replicate=903, n_range=(20, 30)))  # more robots than max_request
     assert e.value.status == vine.VINE_EINVAL
     with pytest.raises(vine.VineError) as e:
-        srv.submit(scenes.config3(2, replicate=904, n_range=(41, 50)))  # links beyond the slot capacity
+        srv.submit(scenes.uneven_batch(2, replicate=904, n_range=(41, 50)))  # links beyond the slot capacity
     assert e.value.status == vine.VINE_EINVAL
-    sc = scenes.config3(2, replicate=905, n_range=(20, 30))
+    sc = scenes.uneven_batch(2, replicate=905, n_range=(20, 30))
     sc["radius"] = sc["radius"].copy()
     sc["radius"][1] = np.nan  # invalid value: that robot only is flagged
     r = _wait(srv, srv.submit(sc))
@@ -116,7 +116,7 @@ def test_refuses_malformed_requests():
 
 def test_poll_timeout_then_result():
     srv = vine.Server(max_slots=256, max_request=64, max_links=320, steps_per_tick=4)
-    sc = scenes.config3(64, replicate=906, n_range=(200, 300))
+    sc = scenes.uneven_batch(64, replicate=906, n_range=(200, 300))
     rid = srv.submit(sc)
     assert srv.poll(rid, timeout_us=0) is None  # 64 robots x 200-300 links are not done at once
     r = _wait(srv, rid, limit_s=300.0)

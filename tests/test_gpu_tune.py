@@ -14,7 +14,7 @@ from paper_2509_15180_gb300 import vine  # noqa: E402
 
 
 def test_autotune_picks_a_candidate_and_keeps_results():
-    sc = scenes.config3(192, n_range=(30, 120))
+    sc = scenes.uneven_batch(192, n_range=(30, 120))
     b = vine.Batch(sc)
     b.simulate()
     ref = b.state()

@@ -21,7 +21,7 @@ def _worker(rank, world, port, out):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     import bench
     from paper_2509_15180_gb300 import scenes
-    sc = scenes.config2(8, replicate=rank)
+    sc = scenes.design_batch(8, replicate=rank)
     units = scenes.robot_link_steps(sc["n_links"]) * (rank + 1)
     t, u = bench.reduce_over_ranks(1.5 + rank, units, "cpu")
     out[rank] = (t, u, float(sc["pressure"][0]))

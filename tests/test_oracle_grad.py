@@ -19,7 +19,7 @@ H_S = 1e-4   # link units
 
 
 def _scene():
-    sc, goals = scenes.config4(n_designs=6, n_perturb=2, n_links=30, box=0.45, n_circ=8, n_box=8)
+    sc, goals = scenes.robustness_batch(n_designs=6, n_perturb=2, n_links=30, box=0.45, n_circ=8, n_box=8)
     # FD steps of 1e-3 Pa and 1e-6 link are below float32 resolution: widen
     sc = {k: (v.astype(np.float64) if v.dtype == np.float32 else v) for k, v in sc.items()}
     return sc, goals.astype(np.float64)

@@ -7,7 +7,7 @@ from paper_2509_15180_gb300 import scenes
 
 
 def _bare(n_inst, n_links):
-    sc = scenes.config1(n_inst)
+    sc = scenes.parity_batch(n_inst)
     sc["n_links"] = np.full(n_inst, n_links, np.int32)
     sc["act_ptr"] = np.zeros(n_inst + 1, np.int32)
     for k in ("act_begin", "act_end", "act_pressure", "act_l0"):
@@ -71,7 +71,7 @@ def test_one_descent_step_is_the_preconditioned_gradient_step():
     step sizes gd_alpha 2 theta_c / (w_a pi P R^3) (joint angles) and
     gd_alpha / (2 w_b k_g) (distal length), using the gradient of the
     separately pinned cost (the new link starts at theta = 0, l = 0)."""
-    sc = scenes.config1(6)
+    sc = scenes.parity_batch(6)
     sc["act_ptr"] = np.zeros(7, np.int32)
     for k in ("act_begin", "act_end", "act_pressure", "act_l0"):
         sc[k] = np.zeros(0, np.float32)

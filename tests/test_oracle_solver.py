@@ -318,7 +318,7 @@ def test_static_balance_at_equilibrium():
     """At the returned state every joint balances: w_a M_tot,j equals the moment
     about p_j of the contact forces 2 w_c k_c pen n on all distal discs, and the
     tip force balances growth (forces recomputed here from poses alone)."""
-    sc = scenes.config1(24)
+    sc = scenes.parity_batch(24)
     o = oracle.Oracle(sc, oracle.default_params(tol=1e-11))
     st = grow(o, 20)
     checked = 0
@@ -396,7 +396,7 @@ def test_tiny_scene_local_minimum():
 
 # ------------------------------------------------------------------ P8 symmetry
 def test_mirror_symmetry():
-    sc = scenes.config1(12)
+    sc = scenes.parity_batch(12)
     mir = {k: v.copy() for k, v in sc.items()}
     mir["obs_cy"] = -sc["obs_cy"]
     mir["act_side"] = -sc["act_side"]
@@ -410,7 +410,7 @@ def test_mirror_symmetry():
 def test_rigid_motion_equivariance():
     """Translating base and obstacles, or rotating both by 90 degrees (boxes swap
     half-sizes), leaves the joint angles unchanged."""
-    sc = scenes.config2(6)
+    sc = scenes.design_batch(6)
     sh = {k: v.copy() for k, v in sc.items()}
     for k, dv in (("obs_cx", 0.25), ("obs_cy", -0.5)):
         sh[k] = (sc[k].astype(np.float64) + dv).astype(np.float32)
@@ -434,7 +434,7 @@ def test_rigid_motion_equivariance():
 def test_converged_state_close_to_tight_solve():
     """The state at tol 1e-6 (with its final step applied) is within 1e-4 link
     lengths of the state solved to 1e-12 from the same warm start."""
-    sc = scenes.config1(16)
+    sc = scenes.parity_batch(16)
     o6 = oracle.Oracle(sc)
     o12 = oracle.Oracle(sc, oracle.default_params(tol=1e-12))
     s = grow(o6, 19)

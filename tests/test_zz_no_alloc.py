@@ -49,8 +49,8 @@ def _noalloc(l0):
 
 def test_noalloc_tables_match_batch_tables_on_two_calls():
     # robots with different segment lengths give several distinct cell lengths
-    sc1 = scenes.config3(24, n_range=(30, 40))
-    sc2 = scenes.config3(24, replicate=3, n_range=(30, 40))
+    sc1 = scenes.uneven_batch(24, n_range=(30, 40))
+    sc2 = scenes.uneven_batch(24, replicate=3, n_range=(30, 40))
     for sc in (sc1, sc2):  # two calls in a row, different inputs
         l0 = _first_appearance(sc["act_l0"])
         assert 2 <= len(l0) <= vine.NOALLOC_MAX_TABLES
