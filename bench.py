@@ -540,7 +540,7 @@ def main():
     ap.add_argument("--serve-pool", type=int, default=24)
     ap.add_argument("--serve-slots", type=int, default=8192)
     ap.add_argument("--serve-lanes", type=int, default=4)
-    ap.add_argument("--serve-tick", type=int, default=32)
+    ap.add_argument("--serve-tick", type=int, default=64)
     args = ap.parse_args()
     res = run_reference(args) if args.impl == "reference" else run_gpu(args)
     if res is not None:

@@ -381,7 +381,7 @@ typedef struct {
   int32_t max_obs;          /* per slot: obstacles (0: 256) */
   int32_t max_act;          /* per slot: actuators (0: 16) */
   int32_t max_request;      /* robots per request (0: 256) */
-  int32_t steps_per_tick;   /* growth steps per robot per launch (0: 32) */
+  int32_t steps_per_tick;   /* growth steps per robot per launch (0: 64) */
   int32_t max_tables;       /* distinct sPAM cell lengths held (0: 256) */
   int32_t lanes;            /* concurrent launch lanes, 1..8 (0: 4) */
   int32_t window;           /* robots per launch and lane (0: half the resident warps) */

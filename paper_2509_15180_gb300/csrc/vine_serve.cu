@@ -524,7 +524,7 @@ vine_status vine_server_config_default(vine_server_config* c) {
   c->max_obs = 256;
   c->max_act = 16;
   c->max_request = 256;
-  c->steps_per_tick = 32;
+  c->steps_per_tick = 64;
   c->max_tables = 256;
   c->lanes = 4;
   c->window = 0;
