@@ -322,7 +322,7 @@ def serve_leg(args, vine, scenes):
     pool_t, pool = scenes.serve_requests(args.serve_pool, rate_hz=2000.0)
     sizes = [(int(len(r["n_links"])), scenes.robot_link_steps(r["n_links"])) for r in pool]
     srv = vine.Server(max_slots=args.serve_slots, max_links=320, max_obs=200, max_act=8, max_request=256,
-                      steps_per_tick=args.serve_tick, lanes=args.serve_lanes)
+                      steps_per_tick=args.serve_tick, lanes=args.serve_lanes, window=args.serve_window)
 
     def run(rate, duration):
         """Submissions for `duration` s: open loop at `rate` req/s (None:
@@ -540,6 +540,7 @@ def main():
     ap.add_argument("--serve-pool", type=int, default=24)
     ap.add_argument("--serve-slots", type=int, default=8192)
     ap.add_argument("--serve-lanes", type=int, default=4)
+    ap.add_argument("--serve-window", type=int, default=0, help="robots per launch and lane (0: the library's default)")
     ap.add_argument("--serve-tick", type=int, default=64)
     args = ap.parse_args()
     res = run_reference(args) if args.impl == "reference" else run_gpu(args)
