@@ -258,6 +258,9 @@ def run_gpu(args):
     uneven = None
     if ws == 1 and args.uneven_robots > 0:
         uneven = uneven_leg(args, vine, scenes, torch, stream, flush)
+    overlapped = None
+    if ws == 1 and not args.no_overlap:
+        overlapped = overlapped_leg(args, vine, scenes, torch, sc)
     robust = None
     if ws == 1 and args.robust_perturb > 0:
         robust = robust_leg(args, vine, scenes, torch, stream, flush)
@@ -275,6 +278,7 @@ def run_gpu(args):
                        "tol": 1e-6},
             "e2e": e2e, "plain": plain, "latency": lat, "roofline": roofline, "cpu_baseline": cpu,
             "adjoint": adjoint, "serving": serve, "uneven": uneven, "robustness": robust,
+            "overlapped": overlapped,
             "clocks": ck, "gpu_launches": args.steps, "robots": robots,
             "solver": {"iters_per_step": st_last["iterations"] / max(st_last["steps_total"], 1),
                        "evals_per_step": st_last["evaluations"] / max(st_last["steps_total"], 1),
@@ -474,6 +478,44 @@ def robust_leg(args, vine, scenes, torch, stream, flush):
             "grad_ms": float(np.mean(ms_g)), "grad_ok": int((st == 0).sum()), "robots": int(st.size)}
 
 
+def overlapped_leg(args, vine, scenes, torch, sc):
+    """The design batch as a stream of independent batches: two batch
+    instances alternate on two CUDA streams, so that one batch's last robots
+    finish while the next batch fills the freed SMs (as a robustness study
+    or a sweep over independent design sets would run).  No L2 flush between
+    steps (the working set of a batch is a few MB and the kernel does not
+    depend on it)."""
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    bs = [vine.Batch(sc, stream=streams[q]) for q in range(2)]
+    for q in range(2):
+        bs[q].simulate(streams[q])
+    torch.cuda.synchronize()
+    k = max(4, 2 * args.steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ends = [torch.cuda.Event() for _ in range(2)]
+    cur = torch.cuda.current_stream()
+    e0.record(cur)
+    for q in range(2):
+        streams[q].wait_event(e0)
+    for i in range(k):
+        q = i % 2
+        bs[q].reset(streams[q])
+        bs[q].simulate(streams[q])
+    for q in range(2):
+        ends[q].record(streams[q])
+        cur.wait_event(ends[q])
+    e1.record(cur)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    rls = sum(b.stats(streams[q])["robot_link_steps"] for q, b in enumerate(bs))  # last step of each
+    for b in bs:
+        b.close()
+    per = scenes.robot_link_steps(sc["n_links"])
+    return {"value": k * (rls / 2.0) / (ms / 1e3), "unit": UNIT, "batches": k, "ms_per_batch": ms / k,
+            "robot_link_steps_per_batch": per,
+            "what": "two instances of the design batch alternating on two streams; converged robot-link-steps"}
+
+
 def cpu_baseline(args, sc, robots=None):
     """The FP64 oracle as it stands, OpenMP over robots on all host cores, on a
     bounded sample of the workload (the first `robots` robots)."""
@@ -532,16 +574,17 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--traffic", type=float, default=None)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-overlap", action="store_true")
     ap.add_argument("--uneven-robots", type=int, default=4096)
     ap.add_argument("--uneven-sample", type=int, default=2048)
     ap.add_argument("--robust-designs", type=int, default=64)
     ap.add_argument("--robust-perturb", type=int, default=32)
     ap.add_argument("--serve-seconds", type=float, default=12.0)
     ap.add_argument("--serve-pool", type=int, default=24)
-    ap.add_argument("--serve-slots", type=int, default=8192)
+    ap.add_argument("--serve-slots", type=int, default=32768)
     ap.add_argument("--serve-lanes", type=int, default=4)
     ap.add_argument("--serve-window", type=int, default=0, help="robots per launch and lane (0: the library's default)")
-    ap.add_argument("--serve-tick", type=int, default=64)
+    ap.add_argument("--serve-tick", type=int, default=0, help="growth steps per launch (0: to completion)")
     args = ap.parse_args()
     res = run_reference(args) if args.impl == "reference" else run_gpu(args)
     if res is not None:

@@ -381,10 +381,10 @@ typedef struct {
   int32_t max_obs;          /* per slot: obstacles (0: 256) */
   int32_t max_act;          /* per slot: actuators (0: 16) */
   int32_t max_request;      /* robots per request (0: 256) */
-  int32_t steps_per_tick;   /* growth steps per robot per launch (0: 64) */
+  int32_t steps_per_tick;   /* growth steps per robot per launch (0: max_links, i.e. to completion) */
   int32_t max_tables;       /* distinct sPAM cell lengths held (0: 256) */
   int32_t lanes;            /* concurrent launch lanes, 1..8 (0: 4) */
-  int32_t window;           /* robots per launch and lane (0: half the resident warps) */
+  int32_t window;           /* robots per launch and lane (0: twice the resident warps) */
 } vine_server_config;
 
 typedef struct {
@@ -404,7 +404,8 @@ typedef struct {
   double busy_s;              /* wall time of ticks with active robots */
 } vine_server_stats;
 
-/* Zeroes in every field: the defaults listed above. */
+/* The defaults listed above (a zero field in a config passed to
+ * vine_server_create also selects its default). */
 vine_status vine_server_config_default(vine_server_config* out);
 
 /* Allocates the slot arena and tables (one cudaMalloc within the budget),

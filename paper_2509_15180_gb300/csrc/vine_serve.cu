@@ -524,7 +524,7 @@ vine_status vine_server_config_default(vine_server_config* c) {
   c->max_obs = 256;
   c->max_act = 16;
   c->max_request = 256;
-  c->steps_per_tick = 64;
+  c->steps_per_tick = 0;  // to completion: a robot grows to its full length within one launch
   c->max_tables = 256;
   c->lanes = 4;
   c->window = 0;
@@ -561,15 +561,16 @@ vine_status vine_server_create(const vine_params* params, const vine_server_conf
     if (config->max_obs) c.max_obs = config->max_obs;
     if (config->max_act) c.max_act = config->max_act;
     if (config->max_request) c.max_request = config->max_request;
-    if (config->steps_per_tick) c.steps_per_tick = config->steps_per_tick;
+    c.steps_per_tick = config->steps_per_tick;
     if (config->max_tables) c.max_tables = config->max_tables;
     if (config->lanes) c.lanes = config->lanes;
     if (config->window) c.window = config->window;
   }
   if (c.max_slots < 0 || c.max_links < 1 || c.max_links > kMaxLinks || c.max_obs < 1 || c.max_obs > kMaxObs ||
-      c.max_act < 1 || c.max_act > kMaxAct || c.max_request < 1 || c.steps_per_tick < 1 || c.max_tables < 1 ||
+      c.max_act < 1 || c.max_act > kMaxAct || c.max_request < 1 || c.steps_per_tick < 0 || c.max_tables < 1 ||
       c.lanes < 1 || c.lanes > 8 || c.window < 0)
     return sfail(VINE_EINVAL, "vine_server_create: configuration out of range");
+  if (c.steps_per_tick == 0 || c.steps_per_tick > c.max_links) c.steps_per_tick = c.max_links;
   auto V = new vine_server();
   V->prm = prm;
   V->cfg = c;
@@ -700,9 +701,10 @@ vine_status vine_server_create(const vine_params* params, const vine_server_conf
     return sfail(VINE_EINVAL, "vine_server_create: slot capacities too large for shared memory");
   }
   V->grid = nsm * per_sm;
-  // half the resident warps per lane: two lanes fill the GPU, the others
-  // take over the SMs that a launch finishing its slowest robots leaves idle
-  V->window = c.window > 0 ? c.window : std::max(1, V->grid * V->wpc / 2);
+  // twice the resident warps per lane: the lanes' launches queue their CTAs
+  // behind each other, so the SMs a launch leaves idle while its slowest
+  // robots finish are taken at once by the next launch
+  V->window = c.window > 0 ? c.window : std::max(1, 2 * V->grid * V->wpc);
   V->cfg.window = V->window;
   GrowArgs& a = V->args;
   a.inst = (const InstDev*)(m + o_inst);
