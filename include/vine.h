@@ -251,6 +251,25 @@ vine_status vine_get_contacts(const vine_batch* b, int32_t* counts, int32_t* pai
 vine_status vine_set_actuators(vine_batch* b, const float* pressure, const float* begin, const float* end,
                                int32_t ptrs_are_device, void* cuda_stream);
 
+/* Sets every instance's present state, so that the next vine_grow_step or
+ * vine_simulate continues growth from it (Sec. 4.1: a growth step starts
+ * from the previous step's joint angles; Algorithm 2 propagates tree nodes
+ * from their stored states).  Arrays in the layouts vine_get_state returns:
+ *   n_present[n]     links present, 0 <= n_present[i] <= n_links[i]
+ *   theta[sum n_links] joint angles (rad), CSR by n_links; entries at or
+ *                    past n_present are ignored (NULL allowed when every
+ *                    instance has zero target links)
+ *   l_last[n]        distal link length (m), 0 <= l_last <= l_seg (ignored
+ *                    when n_present = 0)
+ * Counters and statistics are cleared as by vine_batch_reset.  A state
+ * outside these ranges (or non-finite) marks the instance
+ * VINE_INST_BADINPUT with zero links until the next reset or
+ * vine_set_state.  Continuing from a state read by vine_get_state gives
+ * bitwise the same result as continuing in place.  ptrs_are_device as for
+ * vine_grad (host pointers: the stream is synchronised). */
+vine_status vine_set_state(vine_batch* b, const int32_t* n_present, const float* theta, const float* l_last,
+                           int32_t ptrs_are_device, void* cuda_stream);
+
 /* Adjoint of the equilibrium (implicit differentiation; the gradient a
  * design optimisation over the models of Sec. 3 needs).  For every instance,
  * at its current state taken as the equilibrium of its last growth step:

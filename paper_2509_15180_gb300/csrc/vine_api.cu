@@ -135,6 +135,35 @@ __global__ void actuator_update_kernel(const InstDev* inst, int n_inst, const fl
   }
 }
 
+// Loads caller states (vine_set_state), one warp per instance: the present
+// link count, the joint angles in the batch's CSR layout and the distal
+// length.  Entries past the present links are zeroed, as growth leaves them.
+// A state outside its ranges marks the instance BADINPUT and leaves it empty.
+__global__ void state_load_kernel(const InstDev* inst, int n_inst, const int* n_present, const float* theta,
+                                  const float* l_last, float* th, int* n_cur, float* l_cur, const int* status0,
+                                  int* status) {
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (i >= n_inst) return;
+  const InstDev I = inst[i];
+  const int N = n_present[i];
+  bool bad = !(N >= 0 && N <= I.n_target);
+  const int n_ok = bad ? 0 : N;
+  bool badl = false;
+  for (int k = lane; k < I.n_target; k += 32) {
+    const float t = k < n_ok ? theta[I.th_off + k] : 0.f;
+    badl = badl || !fin(t);
+    th[I.th_off + k] = t;
+  }
+  bad = __any_sync(0xffffffffu, badl) || bad;
+  const float l = n_ok > 0 ? l_last[i] : 0.f;
+  bad = bad || !(fin(l) && l >= 0.f && l <= I.l_seg);
+  if (lane == 0) {
+    n_cur[i] = bad ? 0 : N;
+    l_cur[i] = bad ? 0.f : l;
+    status[i] = (bad || status0[i] == kBadInput) ? kBadInput : status0[i];
+  }
+}
+
 }  // namespace
 
 cudaError_t vine::launch_init(const InitArgs& a, cudaStream_t s) {
@@ -766,6 +795,38 @@ vine_status vine_set_actuators(vine_batch* B, const float* pressure, const float
   const int threads = 128, blocks = (B->n_inst * 32 + threads - 1) / threads;
   actuator_update_kernel<<<blocks, threads, 0, st>>>(a.inst, B->n_inst, dp, db, de, const_cast<float4*>(a.act),
                                                      B->status0, a.status);
+  CK(cudaGetLastError());
+  if (!ptrs_are_device) CK(cudaStreamSynchronize(st));
+  return VINE_OK;
+}
+
+vine_status vine_set_state(vine_batch* B, const int32_t* n_present, const float* theta, const float* l_last,
+                           int32_t ptrs_are_device, void* stream_v) {
+  if (!B) return fail(VINE_EINVAL, "vine_set_state: null batch");
+  if (!n_present || !l_last || (B->total_links > 0 && !theta))
+    return fail(VINE_EINVAL, "vine_set_state: null argument");
+  cudaStream_t st = (cudaStream_t)stream_v;
+  vine_status s = vine_batch_reset(B, stream_v);  // counters cleared, validation status restored
+  if (s != VINE_OK) return s;
+  const size_t n = (size_t)B->n_inst, nl = (size_t)B->total_links;
+  if (n == 0) return VINE_OK;
+  const int32_t* dn = n_present;
+  const float *dt = theta, *dl = l_last;
+  if (!ptrs_are_device) {
+    s = ensure_stage(B, align256(4 * n) + align256(4 * n) + align256(4 * std::max<size_t>(nl, 1)));
+    if (s != VINE_OK) return s;
+    char* sg = (char*)B->stage;
+    CK(cudaMemcpyAsync(sg, n_present, 4 * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(sg + align256(4 * n), l_last, 4 * n, cudaMemcpyHostToDevice, st));
+    if (nl) CK(cudaMemcpyAsync(sg + 2 * align256(4 * n), theta, 4 * nl, cudaMemcpyHostToDevice, st));
+    dn = (const int32_t*)sg;
+    dl = (const float*)(sg + align256(4 * n));
+    dt = (const float*)(sg + 2 * align256(4 * n));
+  }
+  const GrowArgs& a = B->args;
+  const int threads = 128, blocks = (int)((n * 32 + threads - 1) / threads);
+  state_load_kernel<<<blocks, threads, 0, st>>>(a.inst, B->n_inst, dn, dt, dl, a.theta, a.n_cur, a.l_cur,
+                                                B->status0, a.status);
   CK(cudaGetLastError());
   if (!ptrs_are_device) CK(cudaStreamSynchronize(st));
   return VINE_OK;

@@ -94,6 +94,7 @@ _SIG = {
     "vine_spam_tables_noalloc": [_p, _i32, _p, _p, _p, _p],
     "vine_debug_trace_read": [_p, _p, _i32, _p],
     "vine_set_actuators": [_p, _p, _p, _p, _i32, _p],
+    "vine_set_state": [_p, _p, _p, _p, _i32, _p],
     "vine_autotune": [_p, _i32, _p, _p],
     "vine_grad": [_p, _p, _p, _p, _p, _p, _p, _i32, _p],
     "vine_batch_destroy": [_p],
@@ -257,6 +258,27 @@ class Batch:
         _check(_lib.vine_set_actuators(self.h, _ptr(args[0]), _ptr(args[1]), _ptr(args[2]), dev, _stream(stream)),
                "vine_set_actuators")
         self._act_keep = args  # alive until the async copy has run
+
+    def set_state(self, n_present, theta, l_last, stream=None):
+        """Present state to continue growth from (vine_set_state): links
+        present [n], joint angles [sum n_links] in the CSR layout of state(),
+        distal lengths [n].  numpy arrays (synchronous) or CUDA tensors
+        (int32 / float32, async).  Counters are cleared."""
+        n, T = self.n_inst, self.total_links
+        dev = int(hasattr(theta, "is_cuda") and theta.is_cuda)
+        if dev:
+            args = [n_present.contiguous(), theta.contiguous(), l_last.contiguous()]
+            sizes = [x.numel() for x in args]
+        else:
+            args = [np.ascontiguousarray(np.asarray(n_present).reshape(-1), np.int32),
+                    np.ascontiguousarray(np.asarray(theta).reshape(-1), np.float32),
+                    np.ascontiguousarray(np.asarray(l_last).reshape(-1), np.float32)]
+            sizes = [x.size for x in args]
+        if sizes[0] != n or sizes[2] != n or sizes[1] < T:
+            raise ValueError("set_state: expected [%d], [%d] and [%d] values" % (n, T, n))
+        _check(_lib.vine_set_state(self.h, _ptr(args[0]), _ptr(args[1]), _ptr(args[2]), dev, _stream(stream)),
+               "vine_set_state")
+        self._state_keep = args  # alive until the async copy has run
 
     def grad(self, goal, stream=None) -> dict:
         """Tip-distance cost |p_tip - goal| and its adjoint derivatives at the

@@ -1,5 +1,6 @@
 """GPU adjoint (vine_grad) against the FP64 oracle's adjoint at the same
-state, the actuator update path, and the torch.autograd.Function."""
+state (the oracle's equilibria, loaded into the GPU batch), the actuator
+update path, and the torch.autograd.Function."""
 import numpy as np
 import pytest
 
@@ -33,28 +34,60 @@ def _cond(orc, i, th, l):
     return float(w.max() / max(w.min(), 1e-300))
 
 
-def _compare(sc, goals, b, st, g, min_checked):
-    """Oracle adjoint at the GPU's own final state (float32 angles widened).
-    Bar per derivative: 2e-2 of the largest derivative of its kind in the
-    sample, or, for a robot whose Hessian is ill-conditioned, 2e-6 x its
-    condition number of the derivative itself (an FP32 solve of H lambda = c
-    carries a relative error of order cond x 6e-8)."""
+def _oracle_equilibria(sc):
+    """The oracle's growth of every robot to full length, rounded to FP32 (the
+    GPU's storage precision): the states at which both adjoints are taken."""
     orc = oracle.Oracle(sc)
+    ost = orc.new_state()
+    orc.run(ost, int(sc["n_links"].max()), threads=16)
+    ost["theta"][:] = ost["theta"].astype(np.float32)
+    ost["l"][:] = ost["l"].astype(np.float32)
+    return orc, ost
+
+
+def _load(b, sc, orc, ost, idx=None, base=None):
+    """vine_set_state with the oracle's states: robot idx[j] of the GPU batch
+    gets the oracle's robot j; the others keep the state `base` (a state()
+    of the batch itself)."""
+    n = sc["n_links"].size
+    idx = np.arange(n) if idx is None else np.asarray(idx)
+    if base is None:
+        N = np.zeros(n, np.int32)
+        th = np.zeros(max(b.total_links, 1), np.float32)
+        l = np.zeros(n, np.float32)
+    else:
+        N, th, l = base["N"].copy(), base["theta"].copy(), base["l"].copy()
+    for j, i in enumerate(idx):
+        N[i] = ost["N"][j]
+        th[b.offsets[i]: b.offsets[i] + N[i]] = orc.theta_of(ost, j)
+        l[i] = ost["l"][j]
+    b.set_state(N, th, l)
+
+
+def _compare(sc, orc, ost, goals, g, min_checked, idx=None):
+    """GPU adjoint against the FP64 oracle's at the same state (the oracle's
+    own equilibrium rounded to FP32, loaded with vine_set_state).  Oracle
+    robot j is GPU robot idx[j].  Bar per derivative: 2e-2 of the largest
+    derivative of its kind in the sample, or, for a robot whose Hessian is
+    ill-conditioned, 2e-6 x its condition number of the derivative itself
+    (an FP32 solve of H lambda = c carries a relative error of order
+    cond x 6e-8)."""
+    idx = np.arange(orc.n) if idx is None else np.asarray(idx)
     rows = []
     skipped = 0
     conds = {}
-    for i in range(sc["n_links"].size):
+    for j, i in enumerate(idx):
         a0, a1 = int(sc["act_ptr"][i]), int(sc["act_ptr"][i + 1])
-        if st["status"][i] != 0 or g["status"][i] != 0:
+        if ost["status"][j] != 0 or g["status"][i] != 0:
             skipped += 1
             continue
-        th = b.theta_of(st, i).astype(np.float64)
-        c, dP, dB, dE, rc = orc.grad(i, th, float(st["l"][i]), goals[i].astype(np.float64))
+        th, l = orc.theta_of(ost, j), float(ost["l"][j])
+        c, dP, dB, dE, rc = orc.grad(j, th, l, goals[i].astype(np.float64))
         if rc != 0:
             skipped += 1
             continue
         assert abs(g["cost"][i] - c) <= 1e-6 * max(c, 1e-3), (i, g["cost"][i], c)
-        conds[i] = _cond(orc, i, th, float(st["l"][i]))
+        conds[i] = _cond(orc, j, th, l)
         for k, v in (("dP", dP), ("dB", dB), ("dE", dE)):
             for a in range(a1 - a0):
                 rows.append((k, i, a, g[k][a0 + a], v[a]))
@@ -67,8 +100,8 @@ def _compare(sc, goals, b, st, g, min_checked):
         errs = [abs(r[3] - r[4]) / max(2e-2 * scale, 2e-6 * conds[r[1]] * max(abs(r[4]), abs(r[3])))
                 for r in sel]
         worst[k] = max(errs)
-        j = int(np.argmax(errs))
-        assert worst[k] < 1.0, (k, worst[k], sel[j], "cond %.3g" % conds[sel[j][1]])
+        q = int(np.argmax(errs))
+        assert worst[k] < 1.0, (k, worst[k], sel[q], "cond %.3g" % conds[sel[q][1]])
     print("adjoint parity: %d derivatives, %d robots skipped, worst (fraction of the bar) per kind %s, "
           "largest condition number %.3g" % (len(rows), skipped, worst, max(conds.values()) if conds else 0.0))
     assert len(rows) >= min_checked
@@ -77,11 +110,11 @@ def _compare(sc, goals, b, st, g, min_checked):
 
 def test_grad_matches_oracle_adjoint_small():
     sc, goals = _scene()
+    orc, ost = _oracle_equilibria(sc)
     b = vine.Batch(sc)
-    b.simulate()
-    st = b.state()
+    _load(b, sc, orc, ost)
     g = b.grad(goals)
-    _compare(sc, goals, b, st, g, 40)
+    _compare(sc, orc, ost, goals, g, 40)
     b.close()
 
 
@@ -98,8 +131,11 @@ def test_grad_device_path_equals_host_path():
 
 
 def test_grad_full_length_robustness_designs_sampled():
-    """Config-4 shaped designs (150 links, 60 obstacles, 2.25 m box), 8 designs
-    x 16 perturbations, one launch; 24 robots checked against the oracle."""
+    """Robustness-batch designs at full size (150 links, 60 obstacles, 2.25 m
+    box), 8 designs x 16 perturbations grown in one launch; then 24 sampled
+    robots are set to the oracle's equilibria and the adjoint of the whole
+    batch is taken in one launch, the sampled robots checked against the
+    oracle's adjoint."""
     sc, goals = scenes.robustness_batch(n_designs=8, n_perturb=16)
     b = vine.Batch(sc)
     b.simulate()
@@ -109,17 +145,10 @@ def test_grad_full_length_robustness_designs_sampled():
     print("robots with a gradient: %d of %d (status %s)" % (ok.sum(), ok.size, np.bincount(g["status"])))
     assert ok.mean() >= 0.8
     idx = np.sort(np.random.default_rng(3).choice(len(goals), 24, replace=False))
-    sub = scenes.subset(sc, idx)
-    stsub = {k: v[idx] for k, v in st.items() if k in ("status", "l", "N")}
-    thetas = [b.theta_of(st, i) for i in idx]
-
-    class _View:
-        def theta_of(self, s, j):
-            return thetas[j]
-
-    asub = np.concatenate([np.arange(sc["act_ptr"][i], sc["act_ptr"][i + 1]) for i in idx]).astype(np.int64)
-    gsub = dict(cost=g["cost"][idx], status=g["status"][idx], dP=g["dP"][asub], dB=g["dB"][asub], dE=g["dE"][asub])
-    _compare(sub, goals[idx], _View(), stsub, gsub, 30)
+    orc, ost = _oracle_equilibria(scenes.subset(sc, idx))
+    _load(b, sc, orc, ost, idx=idx, base=st)
+    g = b.grad(goals)
+    _compare(sc, orc, ost, goals, g, 30, idx=idx)
     b.close()
 
 

@@ -6,8 +6,9 @@ Undamped descent in contact oscillates and can be chaotic: in the FP64
 oracle itself, a relative perturbation of 6e-8 (FP32 rounding) of the state
 that starts a growth step moves the step's result by more than 1e-4 link
 lengths for ~6 % of the robot-steps of this scene, by up to several link
-lengths.  So every step the oracle starts from the GPU's previous state and
-takes the same step, as is and from three copies of the state perturbed by
+lengths.  So every step the GPU starts from the oracle's previous state
+(rounded to FP32 and loaded with vine_set_state), and the oracle takes the
+same step, as is and from three copies of the state perturbed by
 seeded relative noise of 5e-7 (FP32 rounding accumulated over the 50
 updates, ~sqrt(50) x 6e-8; with a small absolute floor, since the first
 step starts from zeros); the GPU's result must match within 1e-4 link
@@ -45,14 +46,11 @@ def test_paper_mode_step_matches_oracle():
     orc = oracle.Oracle(sc, oracle.default_params(mode=1, gd_alpha=0.005, gd_steps=50))
     rng = np.random.default_rng(5)
     errs, sens = [], []
-    prev = None
+    ost = orc.new_state()
     for step in range(20):
-        ost = orc.new_state()
-        if prev is not None:
-            ost["N"][:] = prev["N"]
-            for i in range(n):
-                ost["theta"][orc.off[i]: orc.off[i] + prev["N"][i]] = b.theta_of(prev, i).astype(np.float64)
-            ost["l"][:] = prev["l"].astype(np.float64)
+        ost["theta"][:] = ost["theta"].astype(np.float32)
+        ost["l"][:] = ost["l"].astype(np.float32)
+        b.set_state(ost["N"], ost["theta"].astype(np.float32), ost["l"].astype(np.float32))
         psts = []
         for _ in range(3):
             pst = {k: v.copy() for k, v in ost.items()}
@@ -69,6 +67,7 @@ def test_paper_mode_step_matches_oracle():
             orc.run(pst, 1, threads=16)
         st = b.state()
         assert np.all(st["status"] == 0) and np.all(st["N"] == step + 1)
+        assert b.stats()["iterations"] == n * 50
         for i in range(n):
             ls = float(sc["l_seg"][i])
             errs.append(_pose_error(orc, ost, i, b, st, i, ls))
@@ -78,7 +77,6 @@ def test_paper_mode_step_matches_oracle():
                 p1 = np.array(orc.poses(i, orc.theta_of(pst, i), pst["l"][i])[:2])
                 sv = max(sv, np.max(np.abs(p0 - p1)) / ls)
             sens.append(sv)
-        prev = st
     errs, sens = np.array(errs), np.array(sens)
     calm = sens <= 1e-6
     miss = int((errs[calm] > 1e-4).sum())
@@ -94,6 +92,4 @@ def test_paper_mode_step_matches_oracle():
     assert miss <= 0.01 * calm.sum()
     assert np.median(errs[calm]) <= 1e-6
     assert np.mean(~calm) <= 0.35
-    stats = b.stats()
-    assert stats["iterations"] == n * 20 * 50
     b.close()
