@@ -264,6 +264,9 @@ def run_gpu(args):
     robust = None
     if ws == 1 and args.robust_perturb > 0:
         robust = robust_leg(args, vine, scenes, torch, stream, flush)
+    plan = None
+    if ws == 1 and args.plan_seconds > 0:
+        plan = planner_leg(args, scenes)
     if rank == 0:
         cpu = cpu_baseline(args, sc) if ws == 1 and not args.no_cpu else None
         lat = {"p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
@@ -278,7 +281,7 @@ def run_gpu(args):
                        "tol": 1e-6},
             "e2e": e2e, "plain": plain, "latency": lat, "roofline": roofline, "cpu_baseline": cpu,
             "adjoint": adjoint, "serving": serve, "uneven": uneven, "robustness": robust,
-            "overlapped": overlapped,
+            "overlapped": overlapped, "planner": plan,
             "clocks": ck, "gpu_launches": args.steps, "robots": robots,
             "solver": {"iters_per_step": st_last["iterations"] / max(st_last["steps_total"], 1),
                        "evals_per_step": st_last["evaluations"] / max(st_last["steps_total"], 1),
@@ -516,6 +519,41 @@ def overlapped_leg(args, vine, scenes, torch, sc):
             "what": "two instances of the design batch alternating on two streams; converged robot-link-steps"}
 
 
+def planner_leg(args, scenes):
+    """Batched SST* (Algorithm 2) on the channel planning environment: B
+    expansions per iteration, each grown 5-20 links from its parent's stored
+    state, pruned against the tree.  Reports the wall time per iteration (the
+    paper's "iter time", Sec. 6.2 table: 5-7 s on its machine) split into its
+    parts, and the first iteration that reached the goal."""
+    from paper_2509_15180_gb300 import planner
+    env = scenes.planning_env("channel")
+    p = planner.Planner(env, planner.PlanConfig(batch=args.plan_batch, seed=0))
+    p.run(2, stop_at_goal=False)  # warm-up: library state, tables, allocator
+    p = planner.Planner(env, planner.PlanConfig(batch=args.plan_batch, seed=0))
+    t0 = time.perf_counter()
+    first_goal = None
+    while time.perf_counter() - t0 < args.plan_seconds and p.i <= args.plan_iters:
+        h = p.step()
+        if h["goal"] and first_goal is None:
+            first_goal = (h["iteration"], time.perf_counter() - t0)
+    wall = time.perf_counter() - t0
+    hist = p.history
+    it_s = [h["t_select"] + h.get("t_build", 0.0) + h["t_sim"] + h["t_prune"] + h["t_host"] for h in hist]
+    best = p.best_goal()
+    rls = sum(h.get("robot_link_steps", 0) for h in hist)
+    return {"iterations": len(hist), "batch": args.plan_batch, "wall_s": wall,
+            "ms_per_iteration_median": 1e3 * float(np.median(it_s)),
+            "ms_parts_median": {k: 1e3 * float(np.median([h.get(k, 0.0) for h in hist]))
+                                for k in ("t_select", "t_build", "t_sim", "t_prune", "t_host")},
+            "expansions_per_s": sum(h["expanded"] for h in hist) / wall,
+            "robot_link_steps_per_s": rls / wall, "tree_nodes": p.size,
+            "active_nodes": int(p.active[: p.size].sum()), "radius": p.radius,
+            "first_goal": None if first_goal is None else {"iteration": first_goal[0], "seconds": first_goal[1]},
+            "best_cost": None if best is None else float(p.cost[best]),
+            "what": "channel environment (88 circles, 90-degree bend, goal 1.9 m of corridor away); wall clock "
+                    "per iteration including the host tree"}
+
+
 def cpu_baseline(args, sc, robots=None):
     """The FP64 oracle as it stands, OpenMP over robots on all host cores, on a
     bounded sample of the workload (the first `robots` robots)."""
@@ -579,6 +617,9 @@ def main():
     ap.add_argument("--uneven-sample", type=int, default=2048)
     ap.add_argument("--robust-designs", type=int, default=64)
     ap.add_argument("--robust-perturb", type=int, default=32)
+    ap.add_argument("--plan-seconds", type=float, default=20.0, help="planner leg budget (0: skip)")
+    ap.add_argument("--plan-iters", type=int, default=60)
+    ap.add_argument("--plan-batch", type=int, default=1024)
     ap.add_argument("--serve-seconds", type=float, default=12.0)
     ap.add_argument("--serve-pool", type=int, default=24)
     ap.add_argument("--serve-slots", type=int, default=32768)

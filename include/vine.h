@@ -371,6 +371,38 @@ vine_status vine_batch_destroy(vine_batch* b);
 vine_status vine_spam_tables_noalloc(const double* l0, int32_t n_tab, const vine_params* params, float* hdr,
                                      float* knots, void* cuda_stream);
 
+/* Tree operations of the batched SST* planner (Sec. 5.2, Algorithm 2).
+ * Tip poses are (x, y, phi) triples, float32 [3 n], headings in [-pi, pi],
+ * positions in any length unit; rho converts radians to that unit, so that
+ *   d^2 = dx^2 + dy^2 + (rho * dphi)^2,  dphi wrapped to [-pi, pi],
+ * evaluated in float32 with every product and sum rounded on its own (no
+ * fused multiply-add).  Two states overlap when d < r (strictly).  Costs
+ * are float64 and should be finite.  States are ordered by the key
+ * (cost, id): ties go to the lower id, tree nodes (ids 0 .. n_old-1)
+ * before new states (ids n_old ..).
+ * ptrs_are_device = 1: every array is a device pointer (async on the
+ * stream); 0: host pointers (the stream is synchronised).  Device scratch
+ * is taken from the stream-ordered allocator for the call.  Counts up to
+ * 2^31 - 1 in total. */
+
+/* Pruning of overlapping states (Algorithm 2, prune).  new_keep[j] = 1
+ * exactly when no overlapping state -- an active tree node or another new
+ * state of finite cost -- has a smaller key (a new state of non-finite cost
+ * is never kept); old_deactivate[i] = 1 exactly when tree node i is active
+ * and a kept new state of smaller key overlaps it.  radius, rho >= 0. */
+vine_status vine_sst_prune(int32_t n_old, const float* old_pose, const double* old_cost, const uint8_t* old_active,
+                           int32_t n_new, const float* new_pose, const double* new_cost, float radius, float rho,
+                           uint8_t* new_keep, uint8_t* old_deactivate, int32_t ptrs_are_device, void* cuda_stream);
+
+/* Best-near selection of the nodes to expand (Algorithm 2, sample: lowest
+ * cost first).  For every sample pose: among the active nodes within delta
+ * of it, the one of smallest key; if none is within delta, the nearest
+ * active node (ties to the lower index); -1 when no node is active.
+ * delta, rho >= 0. */
+vine_status vine_sst_select(int32_t n_nodes, const float* pose, const double* cost, const uint8_t* active,
+                            int32_t n_samples, const float* sample_pose, float delta, float rho, int32_t* chosen,
+                            int32_t ptrs_are_device, void* cuda_stream);
+
 /* ---------------------------------------------------------------------------
  * Serving loop: continuous batching of growth requests on one GPU.  The
  * paper's planners (Sec. 5) issue many small simulation requests; a server

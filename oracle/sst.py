@@ -138,6 +138,34 @@ def prune_one(j, old_pose, old_cost, old_active, new_pose, new_cost, radius, rho
     return int(not np.any(fin & lowern & (k != j) & (d2n < r2)))
 
 
+def deactivate_one(i, old_pose, old_cost, old_active, new_pose, new_cost, keep, radius, rho):
+    """deactivate[i] of ``prune`` for one tree node, given the keep flags of
+    the new states, vectorised over them with the same float32 rounding."""
+    if not old_active[i]:
+        return 0
+    ci = float(old_cost[i])
+    r2 = F32(F32(radius) * F32(radius))
+    d2 = _dist2_rows(old_pose[i], new_pose, rho)
+    lower = new_cost < ci   # a new state's id is above every tree node's
+    return int(np.any((np.asarray(keep) != 0) & lower & (d2 < r2)))
+
+
+def select_one(q, pose, cost, active, delta, rho):
+    """``select`` for one sample pose, vectorised over the nodes."""
+    act = np.nonzero(np.asarray(active) != 0)[0]
+    if act.size == 0:
+        return -1
+    d2 = _dist2_rows(q, np.asarray(pose)[act], rho)
+    d2lim = F32(F32(delta) * F32(delta))
+    inside = act[d2 < d2lim]
+    if inside.size:
+        c = np.asarray(cost)[inside]
+        # smallest cost, then lowest index (inside is increasing)
+        return int(inside[np.lexsort((inside, c))[0]])
+    m = d2.min()
+    return int(act[np.nonzero(d2 == m)[0][0]])
+
+
 def _dist2_rows(a, P, rho):
     """se2_dist2(a, P[i]) for every row of P, the same float32 operations."""
     P = np.asarray(P, F32)

@@ -23,8 +23,8 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["parity_batch", "design_batch", "uneven_batch", "robustness_batch", "goal_points", "serve_requests", "robot_link_steps",
-           "concat", "subset"]
+__all__ = ["parity_batch", "design_batch", "uneven_batch", "robustness_batch", "goal_points", "serve_requests",
+           "planning_env", "robot_link_steps", "concat", "subset"]
 
 
 def _rng(config: int, replicate: int = 0) -> np.random.Generator:
@@ -200,6 +200,68 @@ def serve_requests(n_req: int, rate_hz: float = 2000.0, replicate: int = 0, max_
         sub = uneven_batch(int(sizes[k]), replicate=5000 + 7919 * replicate + k, n_range=(20, 300))
         reqs.append(sub)
     return t, reqs
+
+
+def planning_env(kind: str = "channel", replicate: int = 0) -> dict:
+    """A planning environment for the batched SST* planner (Sec. 5.2), with
+    the paper's robot: R_vine 33.35 mm, P_vine 1.5 psi, 25 mm segments, sPAM
+    cells on the 1 mm grid (Sec. 4.2).  The paper's environments exist only
+    as figures, so two seeded stand-ins:
+
+    * "channel": a corridor of 2 cm circles (walls 5 cm from the body on
+      either side, centres jittered by U[-3, 3] mm) that runs 0.6 m straight
+      ahead, bends 90 degrees to the left on a 0.6 m centreline radius and
+      runs 0.4 m up; the goal (50 mm radius) is at the corridor's end.
+    * "clutter": 40 circles of radius U[2, 6] cm uniform in a 1.4 m box
+      ahead of the base (keeping 0.15 m clear around the base); the goal
+      (60 mm radius) is at x = 1.4 m, y = U[-0.4, 0.4] m.
+
+    Returns dict(l_seg, radius, pressure, base[3], obs_kind, obs_cx, obs_cy,
+    obs_a, obs_b (arrays), goal[2] (m), goal_radius (m), box[4] = x0, x1, y0,
+    y1 (m, the sampling region), max_links)."""
+    rng = _rng(7, 100 * replicate + (0 if kind == "channel" else 1))
+    ls, R, P = 0.025, 0.03335, 1.5 * 6894.757293168
+    cx, cy, ca = [], [], []
+    if kind == "channel":
+        L1, Rc, L2 = 0.6, 0.6, 0.4
+        off = R + 0.05 + 0.02
+        arc = 0.5 * np.pi * Rc
+        total = L1 + arc + L2
+        s = 0.0
+        while s <= total + 1e-9:
+            if s <= L1:
+                px, py, tx, ty = s, 0.0, 1.0, 0.0
+            elif s <= L1 + arc:
+                a = (s - L1) / Rc
+                px, py = L1 + Rc * np.sin(a), Rc * (1.0 - np.cos(a))
+                tx, ty = np.cos(a), np.sin(a)
+            else:
+                px, py, tx, ty = L1 + Rc, Rc + (s - L1 - arc), 0.0, 1.0
+            nx, ny = -ty, tx
+            for side in (1.0, -1.0):
+                cx.append(px + side * off * nx + rng.uniform(-0.003, 0.003))
+                cy.append(py + side * off * ny + rng.uniform(-0.003, 0.003))
+                ca.append(0.02)
+            s += 0.045
+        goal, goal_r = (L1 + Rc, Rc + L2), 0.05
+        box = (-0.1, 1.4, -0.3, 1.2)
+        max_links = int(np.ceil(total / ls)) + 12
+    elif kind == "clutter":
+        while len(cx) < 40:
+            x, y, r = rng.uniform(0.1, 1.5), rng.uniform(-0.7, 0.7), rng.uniform(0.02, 0.06)
+            if np.hypot(x, y) > r + 0.15:
+                cx.append(x); cy.append(y); ca.append(r)
+        goal, goal_r = (1.4, rng.uniform(-0.4, 0.4)), 0.06
+        box = (-0.1, 1.6, -0.8, 0.8)
+        max_links = 80
+    else:
+        raise ValueError("planning_env: kind must be 'channel' or 'clutter'")
+    n = len(cx)
+    return dict(l_seg=ls, radius=R, pressure=P, base=np.zeros(3, np.float32),
+                obs_kind=np.zeros(n, np.uint8), obs_cx=np.array(cx, np.float32), obs_cy=np.array(cy, np.float32),
+                obs_a=np.array(ca, np.float32), obs_b=np.zeros(n, np.float32),
+                goal=np.array(goal, np.float64), goal_radius=goal_r, box=np.array(box, np.float64),
+                max_links=max_links)
 
 
 def robot_link_steps(n_links) -> int:

@@ -95,6 +95,8 @@ _SIG = {
     "vine_debug_trace_read": [_p, _p, _i32, _p],
     "vine_set_actuators": [_p, _p, _p, _p, _i32, _p],
     "vine_set_state": [_p, _p, _p, _p, _i32, _p],
+    "vine_sst_prune": [_i32, _p, _p, _p, _i32, _p, _p, C.c_float, C.c_float, _p, _p, _i32, _p],
+    "vine_sst_select": [_i32, _p, _p, _p, _i32, _p, C.c_float, C.c_float, _p, _i32, _p],
     "vine_autotune": [_p, _i32, _p, _p],
     "vine_grad": [_p, _p, _p, _p, _p, _p, _p, _i32, _p],
     "vine_batch_destroy": [_p],
@@ -385,6 +387,65 @@ class Batch:
 
     def pose_of(self, st: dict, i: int):
         return st["pose"][self.offsets[i]: self.offsets[i] + st["N"][i]]
+
+
+# -------------------------------------------------------------------------
+# planner tree operations (Sec. 5.2, Algorithm 2)
+# -------------------------------------------------------------------------
+def _is_cuda(x) -> bool:
+    return hasattr(x, "is_cuda") and x.is_cuda
+
+
+def sst_prune(old_pose, old_cost, old_active, new_pose, new_cost, radius: float, rho: float, stream=None):
+    """vine_sst_prune.  Poses [n, 3] float32, costs [n] float64, active [n]
+    uint8: numpy arrays (returns numpy, synchronous) or CUDA tensors
+    (returns CUDA uint8 tensors, async).  Returns (keep[n_new],
+    deactivate[n_old])."""
+    if _is_cuda(new_pose) or _is_cuda(old_pose):
+        import torch
+        dev = new_pose.device if _is_cuda(new_pose) else old_pose.device
+        a = [old_pose.contiguous(), old_cost.contiguous(), old_active.contiguous(), new_pose.contiguous(),
+             new_cost.contiguous()]
+        n_old, n_new = a[1].numel(), a[4].numel()
+        keep = torch.empty(n_new, dtype=torch.uint8, device=dev)
+        deact = torch.empty(n_old, dtype=torch.uint8, device=dev)
+        flag = 1
+    else:
+        a = [np.ascontiguousarray(np.asarray(old_pose, np.float32).reshape(-1, 3)),
+             np.ascontiguousarray(np.asarray(old_cost, np.float64).reshape(-1)),
+             np.ascontiguousarray(np.asarray(old_active, np.uint8).reshape(-1)),
+             np.ascontiguousarray(np.asarray(new_pose, np.float32).reshape(-1, 3)),
+             np.ascontiguousarray(np.asarray(new_cost, np.float64).reshape(-1))]
+        n_old, n_new = a[1].size, a[4].size
+        keep = np.zeros(n_new, np.uint8)
+        deact = np.zeros(n_old, np.uint8)
+        flag = 0
+    _check(_lib.vine_sst_prune(n_old, _ptr(a[0]), _ptr(a[1]), _ptr(a[2]), n_new, _ptr(a[3]), _ptr(a[4]),
+                               float(radius), float(rho), _ptr(keep), _ptr(deact), flag, _stream(stream)),
+           "vine_sst_prune")
+    return keep, deact
+
+
+def sst_select(pose, cost, active, samples, delta: float, rho: float, stream=None):
+    """vine_sst_select.  Returns the chosen node per sample (int32; -1 when no
+    node is active): numpy for numpy inputs, a CUDA tensor for CUDA inputs."""
+    if _is_cuda(samples):
+        import torch
+        a = [pose.contiguous(), cost.contiguous(), active.contiguous(), samples.contiguous()]
+        n_nodes, n_s = a[1].numel(), a[3].numel() // 3
+        out = torch.empty(n_s, dtype=torch.int32, device=samples.device)
+        flag = 1
+    else:
+        a = [np.ascontiguousarray(np.asarray(pose, np.float32).reshape(-1, 3)),
+             np.ascontiguousarray(np.asarray(cost, np.float64).reshape(-1)),
+             np.ascontiguousarray(np.asarray(active, np.uint8).reshape(-1)),
+             np.ascontiguousarray(np.asarray(samples, np.float32).reshape(-1, 3))]
+        n_nodes, n_s = a[1].size, a[3].shape[0]
+        out = np.zeros(n_s, np.int32)
+        flag = 0
+    _check(_lib.vine_sst_select(n_nodes, _ptr(a[0]), _ptr(a[1]), _ptr(a[2]), n_s, _ptr(a[3]), float(delta),
+                                float(rho), _ptr(out), flag, _stream(stream)), "vine_sst_select")
+    return out
 
 
 # -------------------------------------------------------------------------

@@ -155,3 +155,24 @@ def test_select_best_near_and_nearest():
     out = sst.select(pose, np.array([1.0, 1.0, 1.0, 1.0]), np.ones(4, np.uint8), _poses((2, 0), (27, 0)), 5.0, 1.0)
     assert out.tolist() == [0, 1]
     assert sst.select(pose, cost, np.zeros(4, np.uint8), samples, 5.0, 1.0).tolist() == [-1] * 4
+
+
+def test_vectorised_forms_equal_the_plain_rules():
+    rng = np.random.default_rng(4)
+    for trial in range(3):
+        n_old, n_new = 60, 40
+        old = np.stack([rng.integers(0, 15, n_old), rng.integers(0, 15, n_old),
+                        rng.choice([-3.0, -1.0, 0.0, 1.0, 3.0], n_old)], 1).astype(np.float32)
+        new = np.stack([rng.integers(0, 15, n_new), rng.integers(0, 15, n_new),
+                        rng.choice([-3.0, -1.0, 0.0, 1.0, 3.0], n_new)], 1).astype(np.float32)
+        oc = rng.integers(0, 5, n_old).astype(np.float64)
+        nc = rng.integers(0, 5, n_new).astype(np.float64)
+        nc[rng.integers(0, n_new)] = np.nan
+        act = (rng.random(n_old) < 0.6).astype(np.uint8)
+        r = [2.0, 3.0, 5.0][trial]
+        keep, deact = sst.prune(old, oc, act, new, nc, r, 1.5)
+        assert [sst.deactivate_one(i, old, oc, act, new, nc, keep, r, 1.5) for i in range(n_old)] == deact.tolist()
+        samples = np.stack([rng.integers(0, 15, 50), rng.integers(0, 15, 50), rng.uniform(-3, 3, 50)],
+                           1).astype(np.float32)
+        sel = sst.select(old, oc, act, samples, r, 1.5)
+        assert [sst.select_one(q, old, oc, act, r, 1.5) for q in samples] == sel.tolist()
