@@ -814,36 +814,119 @@ __device__ __forceinline__ void trace_rec(const GrowArgs& A, int inst, int lane,
   o[10] = lt; o[11] = lfix; o[12] = 0.0;
 }
 
+// One growth step, solved by one of two methods:
+//  * mode 0: to equilibrium from the warm start.  Newton iterations with the
+//    exact Hessian when it is positive definite (else the Gauss-Newton
+//    matrix, re-evaluated), then a line search on the projected path
+//    P(x + a dx): Armijo on J, or, when the cost change is at the rounding
+//    level of J, the approximate Wolfe condition of Hager and Zhang (2005)
+//    on the directional slope;
+//  * mode 1: Algorithm 1 of Sec. 4.1 read literally: the actuator forces
+//    are held at the step's initial strains (eval reads them from TH0), then
+//    gd_steps steps of gradient descent, each unknown scaled by its
+//    free-space stiffness (joint angles by gd_alpha 2 theta_c / (w_a pi P
+//    R^3), the distal length by gd_alpha / (2 w_b k_g), kept in [0, l_seg]);
+//    no convergence test.
+// Written as one loop around a single evaluation: the first evaluation, the
+// Gauss-Newton re-evaluation, every line-search trial and every descent step
+// pass through the same call, so the evaluation's code is inlined once (the
+// kernel's first stall is instruction fetch).
 template <int KS>
-__device__ int solve_step(const GrowArgs& A, const InstDev& I, const Smem& S, int N, float& l, int lane,
+__device__ int step_solve(const GrowArgs& A, const InstDev& I, const Smem& S, int N, float& l, int lane,
                           StepStats& st, int inst) {
   const int B = (N + 31) >> 5;
   const int j0 = min(lane * B, N), j1 = min(j0 + B, N);
   const bool exact = A.exact != 0;
-  EvalOut E = eval<KS>(A, I, S, N, l, lane, exact);
-  st.evals += 1;
-  st.linkevals += N;
-  st.tests += E.tests;
-  int status = kMaxIter, it;
+  const bool descend = A.mode == 1;
+  float a_th = 0.f, a_l = 0.f;
+  if (descend) {
+    for (int k = lane; k < N; k += 32) S.TH0[k] = S.TH[k];
+    __syncwarp();
+    a_th = A.gd_alpha * 2.f * A.theta_c / (A.w_a * I.PR3);
+    a_l = A.gd_alpha / (2.f * A.w_b * I.kg);
+  }
+  enum : int { kNewton, kFallback, kTrial };
+  int phase = kNewton;
+  bool ev_exact = exact && !descend;
+  float l_ev = l;
+  int status = kMaxIter, it = 0, h = 0, k_desc = 0;
   double r = 0.0;
-  for (it = 1; it <= A.max_iter; ++it) {
-    if (!isfinite(E.J)) {
-      status = kNonFinite;
-      break;
+  double gd = 0.0, J0 = 0.0, S0 = 0.0, slope0 = 0.0;
+  float alpha = 1.f, lt = l, l0 = l, gl0 = 0.f, dl = 0.f, mdth = 0.f;
+  bool lfix = false;
+  // every path below advances it, h or k_desc, all bounded; the cap is a
+  // second guarantee that the loop ends
+  const long long cap = (long long)(max(A.max_iter, 0) + 1) * (max(A.max_halv, 0) + 3) + max(A.gd_steps, 0) + 4;
+  for (long long guard = 0; guard < cap; ++guard) {
+    const EvalOut E = eval<KS>(A, I, S, N, l_ev, lane, ev_exact);
+    st.evals += 1;
+    st.linkevals += N;
+    st.tests += E.tests;
+    if (descend) {
+      st.iters += 1;
+      if (!isfinite(E.J)) {
+        status = kNonFinite;
+        break;
+      }
+      for (int k = lane; k < N; k += 32) S.TH[k] -= a_th * S.G[k];
+      l = fminf(fmaxf(l - a_l * E.gl, 0.f), I.l_seg);
+      l_ev = l;
+      __syncwarp();
+      if (++k_desc >= A.gd_steps) {
+        status = kOK;
+        break;
+      }
+      continue;
     }
-    const bool lfix = (l <= 0.f && E.gl > 0.f) || (l >= I.l_seg && E.gl < 0.f);
-    float dl;
-    float mdth;
-    r = gn_solve(I, S, N, lfix, E, dl, lane, exact, mdth);
-    if (exact && !(r >= 0.0 && isfinite(r))) {
+    if (phase == kTrial) {
+      const double dec = (double)alpha * gd + (double)gl0 * ((double)lt - (double)l0);
+      double sl = 0.0;
+      const bool rounding = fabs(E.J - J0) <= (double)A.fval_eps * fmax(S0, E.S);
+      if (A.trace != nullptr || rounding) {
+        for (int j = j0; j < j1; ++j) sl += (double)S.G[j] * (double)S.DTH[j];
+        sl = warp_sum(sl);
+        if (lt > 0.f && lt < I.l_seg) sl += (double)E.gl * (double)dl;
+      }
+      trace_rec(A, inst, lane, N, it, h, alpha, r, J0, E.J, dec, slope0, sl, lt, lfix ? 1.0 : 0.0);
+      const bool accepted =
+          E.J <= J0 + (double)A.c1 * dec || (rounding && sl <= (2.0 * (double)A.c1 - 1.0) * slope0);
+      if (!accepted) {
+        if (h < A.max_halv) {
+          alpha *= 0.5f;
+          ++h;
+          for (int j = j0; j < j1; ++j) S.TH[j] = S.TH0[j] + alpha * S.DTH[j];
+          lt = fminf(fmaxf(l0 + alpha * dl, 0.f), I.l_seg);
+          l_ev = lt;
+          __syncwarp();
+          continue;
+        }
+        // no acceptable trial: the step ends at the last accepted iterate
+        for (int j = j0; j < j1; ++j) S.TH[j] = S.TH0[j];
+        l = l0;
+        __syncwarp();
+        break;
+      }
+      l = lt;
+      phase = kNewton;
+    }
+    if (phase == kNewton) {
+      if (++it > A.max_iter) break;
+      if (!isfinite(E.J)) {
+        status = kNonFinite;
+        break;
+      }
+      lfix = (l <= 0.f && E.gl > 0.f) || (l >= I.l_seg && E.gl < 0.f);
+    }
+    const bool use_exact = exact && phase == kNewton;
+    r = gn_solve(I, S, N, lfix, E, dl, lane, use_exact, mdth);
+    if (use_exact && !(r >= 0.0 && isfinite(r))) {
       // exact Hessian not positive definite here: Gauss-Newton matrix instead
       trace_rec(A, inst, lane, N, it, -2, 0.0, r, E.J, E.J, 0.0, 0.0, (double)E.hll, l, lfix ? 1.0 : 0.0);
-      E = eval<KS>(A, I, S, N, l, lane, false);
-      st.evals += 1;
-      st.linkevals += N;
-      st.tests += E.tests;
       st.fallbacks += 1;
-      r = gn_solve(I, S, N, lfix, E, dl, lane, false, mdth);
+      phase = kFallback;
+      ev_exact = false;
+      l_ev = l;
+      continue;
     }
     if (!isfinite(E.J)) {
       status = kNonFinite;
@@ -875,91 +958,42 @@ __device__ int solve_step(const GrowArgs& A, const InstDev& I, const Smem& S, in
       status = kOK;
       break;
     }
-    // Line search on the projected path P(x + a dx): Armijo on J, or, when the
-    // cost change is at the rounding level of J, the approximate Wolfe
-    // condition (Hager and Zhang 2005) on the directional slope.
-    double gd = 0.0;
+    // line search: first trial at the full step
+    gd = 0.0;
     for (int j = j0; j < j1; ++j) {
       gd += (double)S.G[j] * (double)S.DTH[j];
       S.TH0[j] = S.TH[j];
     }
     gd = warp_sum(gd);
-    const float l0 = l, gl0 = E.gl;
-    const double J0 = E.J, S0 = E.S;
+    l0 = l;
+    gl0 = E.gl;
+    J0 = E.J;
+    S0 = E.S;
     const bool l_moves = !((l0 <= 0.f && dl < 0.f) || (l0 >= I.l_seg && dl > 0.f));
-    const double slope0 = gd + (l_moves ? (double)gl0 * (double)dl : 0.0);
-    float alpha = 1.f, lt = l0;
-    bool accepted = false;
-    for (int h = 0; h <= A.max_halv; ++h) {
-      for (int j = j0; j < j1; ++j) S.TH[j] = S.TH0[j] + alpha * S.DTH[j];
-      lt = fminf(fmaxf(l0 + alpha * dl, 0.f), I.l_seg);
-      __syncwarp();
-      E = eval<KS>(A, I, S, N, lt, lane, exact);
-      st.evals += 1;
-      st.linkevals += N;
-      st.tests += E.tests;
-      const double dec = (double)alpha * gd + (double)gl0 * ((double)lt - (double)l0);
-      double sl = 0.0;
-      const bool rounding = fabs(E.J - J0) <= (double)A.fval_eps * fmax(S0, E.S);
-      if (A.trace != nullptr || rounding) {
-        for (int j = j0; j < j1; ++j) sl += (double)S.G[j] * (double)S.DTH[j];
-        sl = warp_sum(sl);
-        if (lt > 0.f && lt < I.l_seg) sl += (double)E.gl * (double)dl;
-      }
-      trace_rec(A, inst, lane, N, it, h, alpha, r, J0, E.J, dec, slope0, sl, lt, lfix ? 1.0 : 0.0);
-      if (E.J <= J0 + (double)A.c1 * dec) {
-        accepted = true;
-        break;
-      }
-      if (rounding && sl <= (2.0 * (double)A.c1 - 1.0) * slope0) {
-        accepted = true;
-        break;
-      }
-      alpha *= 0.5f;
+    slope0 = gd + (l_moves ? (double)gl0 * (double)dl : 0.0);
+    alpha = 1.f;
+    h = 0;
+    for (int j = j0; j < j1; ++j) S.TH[j] = S.TH0[j] + alpha * S.DTH[j];
+    lt = fminf(fmaxf(l0 + alpha * dl, 0.f), I.l_seg);
+    l_ev = lt;
+    phase = kTrial;
+    ev_exact = exact;
+    __syncwarp();
+  }
+  if (descend) {
+    if (status == kOK) {
+      bool badl = false;
+      for (int k = lane; k < N; k += 32) badl = badl || !isfinite(S.TH[k]);
+      if (__any_sync(kFull, badl)) status = kNonFinite;
     }
-    if (!accepted) {  // no acceptable trial: the step ends at the last accepted iterate
-      for (int j = j0; j < j1; ++j) S.TH[j] = S.TH0[j];
-      l = l0;
-      __syncwarp();
-      break;
-    }
-    l = lt;
+    st.r = 0.0;
+    return status;
   }
   if (it > A.max_iter) it = A.max_iter;
   __syncwarp();
   st.iters = it;
   st.r = r;
   return status;
-}
-
-// Algorithm 1 of Sec. 4.1 read literally (mode 1): the actuator forces are
-// held at the step's initial strains (eval reads them from TH0), then
-// gd_steps steps of gradient descent, each unknown scaled by its free-space
-// stiffness: joint angles by gd_alpha 2 theta_c / (w_a pi P R^3), the distal
-// length by gd_alpha / (2 w_b k_g), kept in [0, l_seg].  No convergence test.
-template <int KS>
-__device__ int descend_step(const GrowArgs& A, const InstDev& I, const Smem& S, int N, float& l, int lane,
-                            StepStats& st) {
-  for (int k = lane; k < N; k += 32) S.TH0[k] = S.TH[k];
-  __syncwarp();
-  const float a_th = A.gd_alpha * 2.f * A.theta_c / (A.w_a * I.PR3);
-  const float a_l = A.gd_alpha / (2.f * A.w_b * I.kg);
-  for (int it = 0; it < A.gd_steps; ++it) {
-    const EvalOut E = eval<KS>(A, I, S, N, l, lane, false);
-    st.evals += 1;
-    st.linkevals += N;
-    st.tests += E.tests;
-    st.iters += 1;
-    if (!isfinite(E.J)) return kNonFinite;
-    for (int k = lane; k < N; k += 32) S.TH[k] -= a_th * S.G[k];
-    l = fminf(fmaxf(l - a_l * E.gl, 0.f), I.l_seg);
-    __syncwarp();
-  }
-  for (int k = lane; k < N; k += 32)
-    if (!isfinite(S.TH[k])) st.r = 1.0;  // marks a non-finite angle
-  const bool bad = __any_sync(kFull, st.r != 0.0);
-  st.r = 0.0;
-  return bad ? kNonFinite : kOK;
 }
 
 template <int KS>
@@ -984,8 +1018,7 @@ __device__ void process_instance(const GrowArgs& A, int inst, const Smem& S, int
     l = 0.f;
     __syncwarp();
     StepStats st{0, 0.0, 0, 0, 0, 0};
-    const int res = A.mode == 1 ? descend_step<KS>(A, I, S, N, l, lane, st)
-                                : solve_step<KS>(A, I, S, N, l, lane, st, inst);
+    const int res = step_solve<KS>(A, I, S, N, l, lane, st, inst);
     iters += st.iters;
     evals += st.evals;
     linkevals += st.linkevals;
