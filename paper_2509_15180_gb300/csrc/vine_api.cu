@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -162,6 +163,47 @@ __global__ void state_load_kernel(const InstDev* inst, int n_inst, const int* n_
     l_cur[i] = bad ? 0.f : l;
     status[i] = (bad || status0[i] == kBadInput) ? kBadInput : status0[i];
   }
+}
+
+// Prologue tables already built in this process, per device: the
+// wrinkling-energy table depends only on eps_crit, an sPAM force table only
+// on its cell length and the sPAM constants.  Batch creation copies a cached
+// table (device to device) instead of rebuilding it; the kernels that build
+// them are deterministic, so the copy is bitwise the table a rebuild gives.
+// Entries live until the process exits (2 KB per sPAM table, 8 KB per
+// wrinkling table, at most kCacheSpam + kCacheWrinkle entries).
+constexpr size_t kCacheSpam = 4096, kCacheWrinkle = 16;
+struct SpamEntry {
+  int dev;
+  double l0, R_c, R_act, a, m_lo;
+  float4* hdr;   // [1]
+  float2* tab;   // [kKnots]
+};
+struct WrinkleEntry {
+  int dev;
+  double eps;
+  float2* utab;  // [kUCells + 1]
+  double cst[4];
+};
+struct TableCache {
+  std::mutex mu;
+  std::vector<SpamEntry> spam;
+  std::vector<WrinkleEntry> wrinkle;
+};
+TableCache& table_cache() {
+  static TableCache* c = new TableCache();  // never destroyed: outlives CUDA teardown at exit
+  return *c;
+}
+const SpamEntry* find_spam(const TableCache& c, int dev, double l0, const vine_params& p) {
+  for (const SpamEntry& e : c.spam)
+    if (e.dev == dev && e.l0 == l0 && e.R_c == p.R_c && e.R_act == p.R_act && e.a == p.a_spam && e.m_lo == p.m_lo)
+      return &e;
+  return nullptr;
+}
+const WrinkleEntry* find_wrinkle(const TableCache& c, int dev, double eps) {
+  for (const WrinkleEntry& e : c.wrinkle)
+    if (e.dev == dev && e.eps == eps) return &e;
+  return nullptr;
 }
 
 }  // namespace
@@ -445,16 +487,41 @@ vine_status vine_batch_create(const vine_batch_desc* D, const vine_params* P, vo
   CKC(cudaMemsetAsync(P_(o_th), 0, sizeof(float) * std::max<int64_t>(tot, 1), st));
   CKC(launch_init(ia, st));
   CKC(cudaMemcpyAsync(P_(o_st0), P_(o_st), sizeof(int) * n, cudaMemcpyDeviceToDevice, st));
-  // prologue tables
+  // prologue tables: copied from the process's table cache where present,
+  // else built (FP64) and added to it after the synchronisation below
   GaussLegendre gl;
   gauss_legendre(24, &gl);
   double* scr = (double*)P_(o_scr);
-  CKC(launch_spam_tables((const double*)P_(o_l0), B->n_tab, prm.R_c, prm.R_act, prm.a_spam, prm.m_lo, gl,
-                         (float4*)P_(o_hdr), (float2*)P_(o_tab), scr, st));
-  CKC(launch_wrinkle_table(prm.eps_crit, gl, (float2*)P_(o_ut), scr + 4 * nt + nt * kKnots, (double*)P_(o_cst),
-                           st));
+  int cur_dev = 0;
+  cudaGetDevice(&cur_dev);
+  bool spam_cached = true, wrinkle_cached = false;
   double cst[4];
-  CKC(cudaMemcpyAsync(cst, P_(o_cst), sizeof(cst), cudaMemcpyDeviceToHost, st));
+  {
+    TableCache& tc = table_cache();
+    std::lock_guard<std::mutex> lk(tc.mu);
+    for (int t = 0; t < B->n_tab && spam_cached; ++t) spam_cached = find_spam(tc, cur_dev, tabs[t], prm) != nullptr;
+    if (spam_cached) {
+      for (int t = 0; t < B->n_tab; ++t) {
+        const SpamEntry* e = find_spam(tc, cur_dev, tabs[t], prm);
+        CKC(cudaMemcpyAsync((float4*)P_(o_hdr) + t, e->hdr, sizeof(float4), cudaMemcpyDeviceToDevice, st));
+        CKC(cudaMemcpyAsync((float2*)P_(o_tab) + (size_t)t * kKnots, e->tab, sizeof(float2) * kKnots,
+                            cudaMemcpyDeviceToDevice, st));
+      }
+    }
+    if (const WrinkleEntry* e = find_wrinkle(tc, cur_dev, prm.eps_crit)) {
+      wrinkle_cached = true;
+      CKC(cudaMemcpyAsync(P_(o_ut), e->utab, sizeof(float2) * (kUCells + 1), cudaMemcpyDeviceToDevice, st));
+      std::memcpy(cst, e->cst, sizeof(cst));
+    }
+  }
+  if (!spam_cached)
+    CKC(launch_spam_tables((const double*)P_(o_l0), B->n_tab, prm.R_c, prm.R_act, prm.a_spam, prm.m_lo, gl,
+                           (float4*)P_(o_hdr), (float2*)P_(o_tab), scr, st));
+  if (!wrinkle_cached) {
+    CKC(launch_wrinkle_table(prm.eps_crit, gl, (float2*)P_(o_ut), scr + 4 * nt + nt * kKnots, (double*)P_(o_cst),
+                             st));
+    CKC(cudaMemcpyAsync(cst, P_(o_cst), sizeof(cst), cudaMemcpyDeviceToHost, st));
+  }
   // longest-first order
   B->h_order.resize(n);
   std::iota(B->h_order.begin(), B->h_order.end(), 0);
@@ -467,6 +534,38 @@ vine_status vine_batch_create(const vine_batch_desc* D, const vine_params* P, vo
   if (!(std::isfinite(cst[0]) && std::isfinite(cst[1]))) {
     cleanup();
     return fail(VINE_ECUDA, "vine_batch_create: wrinkling table build failed");
+  }
+  if (!spam_cached || !wrinkle_cached) {  // keep the tables just built (best effort: a failed copy is not cached)
+    TableCache& tc = table_cache();
+    std::lock_guard<std::mutex> lk(tc.mu);
+    if (!wrinkle_cached && tc.wrinkle.size() < kCacheWrinkle && !find_wrinkle(tc, cur_dev, prm.eps_crit)) {
+      WrinkleEntry e{cur_dev, prm.eps_crit, nullptr, {cst[0], cst[1], cst[2], cst[3]}};
+      if (cudaMalloc(&e.utab, sizeof(float2) * (kUCells + 1)) == cudaSuccess) {
+        if (cudaMemcpyAsync(e.utab, P_(o_ut), sizeof(float2) * (kUCells + 1), cudaMemcpyDeviceToDevice, st) ==
+                cudaSuccess &&
+            cudaStreamSynchronize(st) == cudaSuccess)
+          tc.wrinkle.push_back(e);
+        else
+          cudaFree(e.utab);
+      }
+    }
+    for (int t = 0; !spam_cached && t < B->n_tab && tc.spam.size() < kCacheSpam; ++t) {
+      if (find_spam(tc, cur_dev, tabs[t], prm)) continue;
+      SpamEntry e{cur_dev, tabs[t], prm.R_c, prm.R_act, prm.a_spam, prm.m_lo, nullptr, nullptr};
+      char* m = nullptr;
+      if (cudaMalloc(&m, sizeof(float4) + sizeof(float2) * kKnots) != cudaSuccess) break;
+      e.hdr = (float4*)m;
+      e.tab = (float2*)(m + sizeof(float4));
+      if (cudaMemcpyAsync(e.hdr, (float4*)P_(o_hdr) + t, sizeof(float4), cudaMemcpyDeviceToDevice, st) ==
+              cudaSuccess &&
+          cudaMemcpyAsync(e.tab, (float2*)P_(o_tab) + (size_t)t * kKnots, sizeof(float2) * kKnots,
+                          cudaMemcpyDeviceToDevice, st) == cudaSuccess &&
+          cudaStreamSynchronize(st) == cudaSuccess)
+        tc.spam.push_back(e);
+      else
+        cudaFree(m);
+    }
+    cudaGetLastError();  // a failed cache copy leaves no sticky error for the caller
   }
   // ---- launch configuration
   B->nmax = (nmax + 31) & ~31;
