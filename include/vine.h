@@ -191,6 +191,18 @@ vine_status vine_batch_reset(vine_batch* b, void* cuda_stream);
  * step solved to equilibrium, in one persistent launch.  Async. */
 vine_status vine_grow_step(vine_batch* b, int32_t n_steps, void* cuda_stream);
 
+/* Re-solves every instance's equilibrium at its present links without
+ * adding one: the same solver as a growth step (or, in mode 1, the same
+ * descent), from the present state and with the present actuators.  With
+ * fix_length = 1 the distal length is held fixed, so the robot does not
+ * grow while its actuation changes: the tip-steering of the paper's
+ * supplement, where growth is stunted by penalising changes in length and
+ * an actuator at the tip is pressurised.  fix_length = 0 leaves it free in
+ * [0, l_seg].  Instances with no links, non-finite or bad input are
+ * skipped.  Counted in the statistics like a growth step.  (vine_grad
+ * treats the distal length as free unless it sits at a bound.)  Async. */
+vine_status vine_relax(vine_batch* b, int32_t fix_length, void* cuda_stream);
+
 /* Grows every instance to its n_links: one persistent launch over a
  * longest-first work queue, replayed from a CUDA graph.  Async. */
 vine_status vine_simulate(vine_batch* b, void* cuda_stream);
@@ -242,8 +254,10 @@ vine_status vine_get_contacts(const vine_batch* b, int32_t* counts, int32_t* pai
 
 /* Replaces every actuator's pressure and span (arrays [sum n_act] in the
  * descriptor's actuator order; Pa and link units), keeping its side and cell
- * length, for the next growth from reset: the design update of an
- * optimisation loop without rebuilding the batch or its tables.  Values that
+ * length.  Takes effect at the next launch that reads the design
+ * (vine_grow_step, vine_simulate, vine_relax, vine_grad): the design update
+ * of an optimisation loop without rebuilding the batch or its tables, or a
+ * change of actuation in the middle of a growth (tip-steering).  Values that
  * fail the create-time checks (finite, 0 <= begin < end, pressure >= 0) mark
  * the instance VINE_INST_BADINPUT until the batch is recreated.
  * ptrs_are_device as for vine_grad (host pointers: the stream is

@@ -85,18 +85,20 @@ def lib():
         L.orc_energy_exact.restype = d
         L.orc_energy_exact.argtypes = [p, p, p, i, i, p, d, p, p]
         L.orc_solve.restype = i
-        L.orc_solve.argtypes = [p, p, p, i, i, p, p, p, p]
+        L.orc_solve.argtypes = [p, p, p, i, i, p, p, p, p, i]
         L.orc_poses.argtypes = [p, p, p, i, i, p, d, p, p, p]
         L.orc_gaps.argtypes = [p, p, p, i, i, p, d, p]
         L.orc_sdf.restype = d
         L.orc_sdf.argtypes = [p, i, d, d, p, p]
         L.orc_gn_step.restype = i
-        L.orc_gn_step.argtypes = [p, p, p, i, i, p, d, p, p, p, p]
+        L.orc_gn_step.argtypes = [p, p, p, i, i, p, d, p, p, p, p, i]
         L.orc_grad.restype = i
         L.orc_grad.argtypes = [p, p, p, i, i, p, d, d, d, p, p, p, p]
         L.orc_set_trace.argtypes = [i]
         L.orc_run.restype = i
         L.orc_run.argtypes = [p, p, p, i, p, p, p, p, p, p, p, p, p, i]
+        L.orc_relax.restype = i
+        L.orc_relax.argtypes = [p, p, p, i, p, p, p, p, p, p, p, p, p, i]
         _lib = L
     return _lib
 
@@ -169,6 +171,7 @@ class Oracle:
 
     def __init__(self, scene: dict, params: Params | None = None):
         self.P = params or default_params()
+        self.fix_length = False  # solve / gn_step: hold the distal length fixed (relaxation)
         self.n = int(len(scene["n_links"]))
         f64 = lambda k: np.ascontiguousarray(scene[k], dtype=np.float64)
         i32 = lambda k: np.ascontiguousarray(scene[k], dtype=np.int32)
@@ -234,7 +237,7 @@ class Oracle:
         lv = C.c_double(float(l))
         it, r = C.c_int(), C.c_double()
         st = lib().orc_solve(C.byref(self.P), C.byref(self.B), self.T, int(i), th.size, _ptr(th), C.byref(lv),
-                             C.byref(it), C.byref(r))
+                             C.byref(it), C.byref(r), int(self.fix_length))
         return th, lv.value, it.value, r.value, st
 
     def gn_step(self, i: int, theta, l: float):
@@ -245,7 +248,7 @@ class Oracle:
         dx = np.zeros(N + 1)
         r, J, lf = C.c_double(), C.c_double(), C.c_int()
         rc = lib().orc_gn_step(C.byref(self.P), C.byref(self.B), self.T, int(i), N, _ptr(th), float(l), _ptr(dx),
-                               C.byref(r), C.byref(J), C.byref(lf))
+                               C.byref(r), C.byref(J), C.byref(lf), int(self.fix_length))
         if rc != 0:
             raise ValueError("Gauss-Newton matrix not positive definite")
         return dx, r.value, J.value, bool(lf.value)
@@ -296,6 +299,15 @@ class Oracle:
         lib().orc_run(C.byref(self.P), C.byref(self.B), self.T, int(n_steps), _ptr(s["N"]), _ptr(s["theta"]),
                       _ptr(s["l"]), _ptr(s["iters"]), _ptr(s["resid"]), _ptr(s["status"]), _ptr(s["rls"]),
                       _ptr(s["conv"]), _ptr(s["evals"]), int(threads))
+        return s
+
+    def relax(self, state: dict, fix_length: bool = True, threads: int = 1) -> dict:
+        """Re-solve every instance at its present links (no link added); the
+        distal length held fixed with fix_length.  state is updated in place."""
+        s = state
+        lib().orc_relax(C.byref(self.P), C.byref(self.B), self.T, int(bool(fix_length)), _ptr(s["N"]),
+                        _ptr(s["theta"]), _ptr(s["l"]), _ptr(s["iters"]), _ptr(s["resid"]), _ptr(s["status"]),
+                        _ptr(s["rls"]), _ptr(s["conv"]), _ptr(s["evals"]), int(threads))
         return s
 
     def theta_of(self, state: dict, i: int):

@@ -461,6 +461,7 @@ typedef struct {
   double kc, kg;         /* contact and growth stiffness */
   int a0, a1, o0, o1;
   const double* th_frozen; /* mode 1: joint angles at which the actuator strains are frozen (else NULL) */
+  int fix_l;             /* 1: the distal length is held fixed (relaxation for tip-steering) */
 } inst_t;
 
 static void inst_init(inst_t* I, const orc_params* p, const orc_batch* b, const orc_tables* T, int i) {
@@ -475,6 +476,7 @@ static void inst_init(inst_t* I, const orc_params* p, const orc_batch* b, const 
   I->a0 = b->act_ptr[i]; I->a1 = b->act_ptr[i + 1];
   I->o0 = b->obs_ptr[i]; I->o1 = b->obs_ptr[i + 1];
   I->th_frozen = NULL;
+  I->fix_l = 0;
 }
 
 /* Link start points p[0..N], unit directions u[0..N-1], lengths L[0..N-1]:
@@ -777,7 +779,7 @@ static int solve_step(const inst_t* I, int N, double* th, double* l, int* iters_
   ++evals;
   for (it = 1; it <= p->max_iter; ++it) {
     if (!isfinite(J)) { status = ORC_NONFINITE; break; }
-    int lfix = (*l <= 0.0 && g[N] > 0.0) || (*l >= I->l_seg && g[N] < 0.0);
+    int lfix = I->fix_l || (*l <= 0.0 && g[N] > 0.0) || (*l >= I->l_seg && g[N] < 0.0);
     int m = lfix ? N : n;
     for (int k = 0; k < m; ++k) rhs[k] = -g[k];
     /* Newton step with the exact Hessian of J when it is positive definite,
@@ -870,9 +872,10 @@ double orc_energy_exact(const orc_params* p, const orc_batch* b, const orc_table
 }
 
 int orc_solve(const orc_params* p, const orc_batch* b, const orc_tables* T, int i, int N, double* th, double* l,
-              int* iters, double* resid) {
+              int* iters, double* resid, int fix_l) {
   inst_t I;
   inst_init(&I, p, b, T, i);
+  I.fix_l = fix_l ? 1 : 0;
   return solve_step(&I, N, th, l, iters, resid, NULL);
 }
 
@@ -880,7 +883,7 @@ int orc_solve(const orc_params* p, const orc_batch* b, const orc_tables* T, int 
  * dx[0..N] (dx[N] for l; 0 when the bound on l is active), its predicted
  * displacement residual, and the cost.  Returns 0 on success. */
 int orc_gn_step(const orc_params* p, const orc_batch* b, const orc_tables* T, int i, int N, const double* th,
-                double l, double* dx, double* resid, double* J, int* lfix_out) {
+                double l, double* dx, double* resid, double* J, int* lfix_out, int fix_l) {
   inst_t I;
   inst_init(&I, p, b, T, i);
   const int n = N + 1;
@@ -890,7 +893,7 @@ int orc_gn_step(const orc_params* p, const orc_batch* b, const orc_tables* T, in
   double* H = (double*)malloc(sizeof(double) * n * n);
   double* rhs = (double*)malloc(sizeof(double) * n);
   *J = energy(&I, N, th, l, g, H, &G, NULL);
-  int lfix = (l <= 0.0 && g[N] > 0.0) || (l >= I.l_seg && g[N] < 0.0);
+  int lfix = fix_l || (l <= 0.0 && g[N] > 0.0) || (l >= I.l_seg && g[N] < 0.0);
   int m = lfix ? N : n;
   for (int k = 0; k < m; ++k) rhs[k] = -g[k];
   int rc = 1;
@@ -1047,7 +1050,7 @@ static int gd_solve(const inst_t* I0, int N, double* th, double* l) {
     const double J = energy_h(&I, N, th, *l, g, NULL, &G, NULL, 0);
     if (!isfinite(J)) { status = ORC_NONFINITE; break; }
     for (int j = 0; j < N; ++j) th[j] -= a_th * g[j];
-    *l = fmin(fmax(*l - a_l * g[N], 0.0), I.l_seg);
+    if (!I.fix_l) *l = fmin(fmax(*l - a_l * g[N], 0.0), I.l_seg);
   }
   for (int j = 0; j < N && status == ORC_OK; ++j)
     if (!isfinite(th[j])) status = ORC_NONFINITE;
@@ -1062,6 +1065,53 @@ static int gd_solve(const inst_t* I0, int N, double* th, double* l) {
  * Per instance: iterations summed, largest final residual, status (sticky
  * worst), robot-link-steps of converged steps, converged steps, energy
  * evaluations.  OpenMP over instances when n_threads > 1. */
+/* Relaxation at the present links (supplement, tip-steering): every
+ * instance with at least one link is solved again from its state with the
+ * present actuators, no link added; with fix_l the distal length is held
+ * fixed (growth stunted), else it stays free in [0, l_seg].  Counters and
+ * status are updated as by a growth step. */
+int orc_relax(const orc_params* p, const orc_batch* b, const orc_tables* T, int fix_l, int32_t* N_state,
+              double* theta_state, double* l_state, int32_t* iters_total, double* resid_max, int32_t* status,
+              int64_t* rls, int32_t* conv_steps, int64_t* evals, int n_threads) {
+  int64_t* off = (int64_t*)malloc(sizeof(int64_t) * (b->n_inst + 1));
+  off[0] = 0;
+  for (int i = 0; i < b->n_inst; ++i) off[i + 1] = off[i] + b->n_links[i];
+#ifdef _OPENMP
+  if (n_threads < 1) n_threads = 1;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads)
+#endif
+  for (int i = 0; i < b->n_inst; ++i) {
+    if (status[i] == ORC_NONFINITE || status[i] == ORC_BADINPUT || N_state[i] < 1) continue;
+    inst_t I;
+    inst_init(&I, p, b, T, i);
+    I.fix_l = fix_l ? 1 : 0;
+    const int N = N_state[i];
+    double* th = theta_state + off[i];
+    int it = 0;
+    double r = 0.0;
+    long long ev = 0;
+    int st;
+    if (p->mode == 1) {
+      st = gd_solve(&I, N, th, &l_state[i]);
+      it = p->gd_steps;
+      ev = p->gd_steps;
+    } else {
+      st = solve_step(&I, N, th, &l_state[i], &it, &r, &ev);
+    }
+    iters_total[i] += it;
+    evals[i] += ev;
+    if (st == ORC_OK) {
+      rls[i] += N;
+      conv_steps[i] += 1;
+    } else if (st > status[i]) {
+      status[i] = st;
+    }
+    if (r > resid_max[i] || !isfinite(r)) resid_max[i] = r;
+  }
+  free(off);
+  return 0;
+}
+
 int orc_run(const orc_params* p, const orc_batch* b, const orc_tables* T, int n_steps, int32_t* N_state,
             double* theta_state, double* l_state, int32_t* iters_total, double* resid_max, int32_t* status,
             int64_t* rls, int32_t* conv_steps, int64_t* evals, int n_threads) {

@@ -680,6 +680,21 @@ vine_status vine_grow_step(vine_batch* B, int32_t n_steps, void* stream_v) {
   return grow_launch(B, n_steps, (cudaStream_t)stream_v);
 }
 
+vine_status vine_relax(vine_batch* B, int32_t fix_length, void* stream_v) {
+  if (!B) return fail(VINE_EINVAL, "vine_relax: null batch");
+  if (fix_length != 0 && fix_length != 1) return fail(VINE_EINVAL, "vine_relax: fix_length must be 0 or 1");
+  cudaStream_t st = (cudaStream_t)stream_v;
+  GrowArgs a = B->args;
+  a.n_steps = 1;
+  a.dynamic = 1;
+  a.relax = 1;
+  a.fix_l = fix_length;
+  CK(cudaMemsetAsync(a.counter, 0, sizeof(int), st));
+  CK(grow_configure(B->ks, B->smem_warp * B->wpc));
+  CK(launch_grow(a, B->ks, B->grid, 32 * B->wpc, B->smem_warp * B->wpc, st));
+  return VINE_OK;
+}
+
 vine_status vine_simulate(vine_batch* B, void* stream_v) {
   if (!B) return fail(VINE_EINVAL, "vine_simulate: null batch");
   cudaStream_t st = (cudaStream_t)stream_v;

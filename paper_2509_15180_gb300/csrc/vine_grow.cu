@@ -869,7 +869,7 @@ __device__ int step_solve(const GrowArgs& A, const InstDev& I, const Smem& S, in
         break;
       }
       for (int k = lane; k < N; k += 32) S.TH[k] -= a_th * S.G[k];
-      l = fminf(fmaxf(l - a_l * E.gl, 0.f), I.l_seg);
+      if (!A.fix_l) l = fminf(fmaxf(l - a_l * E.gl, 0.f), I.l_seg);
       l_ev = l;
       __syncwarp();
       if (++k_desc >= A.gd_steps) {
@@ -915,7 +915,7 @@ __device__ int step_solve(const GrowArgs& A, const InstDev& I, const Smem& S, in
         status = kNonFinite;
         break;
       }
-      lfix = (l <= 0.f && E.gl > 0.f) || (l >= I.l_seg && E.gl < 0.f);
+      lfix = A.fix_l || (l <= 0.f && E.gl > 0.f) || (l >= I.l_seg && E.gl < 0.f);
     }
     const bool use_exact = exact && phase == kNewton;
     r = gn_solve(I, S, N, lfix, E, dl, lane, use_exact, mdth);
@@ -1003,7 +1003,7 @@ __device__ void process_instance(const GrowArgs& A, int inst, const Smem& S, int
   int status = A.status[inst];
   if (status == kBadInput || status == kNonFinite) return;
   int N = A.n_cur[inst];
-  if (N >= I.n_target || A.n_steps <= 0) return;
+  if (A.n_steps <= 0 || (A.relax ? N == 0 : N >= I.n_target)) return;
   for (int k = lane; k < I.n_obs; k += 32) S.obs[k] = A.obs[I.obs_off + k];
   for (int k = lane; k < I.n_act; k += 32) S.act[k] = A.act[I.act_off + k];
   for (int k = lane; k < N; k += 32) S.TH[k] = A.theta[I.th_off + k];
@@ -1012,10 +1012,12 @@ __device__ void process_instance(const GrowArgs& A, int inst, const Smem& S, int
   int iters = 0, conv = 0, steps = 0;
   long long rls = 0, evals = 0, linkevals = 0, fallbacks = 0, tests = 0;
   double rmax = 0.0;
-  for (int s = 0; s < A.n_steps && N < I.n_target; ++s) {
-    if (lane == 0) S.TH[N] = 0.f;  // new link at the tip
-    N += 1;
-    l = 0.f;
+  for (int s = 0; s < A.n_steps && (A.relax || N < I.n_target); ++s) {
+    if (!A.relax) {
+      if (lane == 0) S.TH[N] = 0.f;  // new link at the tip
+      N += 1;
+      l = 0.f;
+    }
     __syncwarp();
     StepStats st{0, 0.0, 0, 0, 0, 0};
     const int res = step_solve<KS>(A, I, S, N, l, lane, st, inst);

@@ -83,6 +83,8 @@ struct GrowArgs {
   int mode;           // 0 equilibrium; 1 Algorithm 1 read literally (frozen actuator force, descent)
   int gd_steps;       // mode 1: descent steps per growth step
   float gd_alpha;     // mode 1: step as a fraction of the free-space Newton step
+  int relax;          // 1: re-solve the present links without adding one (vine_relax)
+  int fix_l;          // 1: hold the distal length fixed while solving
   // diagnostics: per line-search trial records of one robot (off when null)
   double* trace;
   int* trace_count;

@@ -95,6 +95,7 @@ _SIG = {
     "vine_debug_trace_read": [_p, _p, _i32, _p],
     "vine_set_actuators": [_p, _p, _p, _p, _i32, _p],
     "vine_set_state": [_p, _p, _p, _p, _i32, _p],
+    "vine_relax": [_p, _i32, _p],
     "vine_sst_prune": [_i32, _p, _p, _p, _i32, _p, _p, C.c_float, C.c_float, _p, _p, _i32, _p],
     "vine_sst_select": [_i32, _p, _p, _p, _i32, _p, C.c_float, C.c_float, _p, _i32, _p],
     "vine_autotune": [_p, _i32, _p, _p],
@@ -232,6 +233,10 @@ class Batch:
 
     def grow_step(self, n_steps: int = 1, stream=None):
         _check(_lib.vine_grow_step(self.h, int(n_steps), _stream(stream)), "vine_grow_step")
+
+    def relax(self, fix_length: bool = True, stream=None):
+        """vine_relax: re-solve at the present links, no link added."""
+        _check(_lib.vine_relax(self.h, int(bool(fix_length)), _stream(stream)), "vine_relax")
 
     def simulate(self, stream=None):
         _check(_lib.vine_simulate(self.h, _stream(stream)), "vine_simulate")
