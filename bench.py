@@ -267,6 +267,7 @@ def run_gpu(args):
     plan = None
     if ws == 1 and args.plan_seconds > 0:
         plan = planner_leg(args, scenes)
+    synth_r = synthesis_leg(args) if ws == 1 and args.synth_targets > 0 else None
     if rank == 0:
         cpu = cpu_baseline(args, sc) if ws == 1 and not args.no_cpu else None
         lat = {"p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
@@ -281,7 +282,7 @@ def run_gpu(args):
                        "tol": 1e-6},
             "e2e": e2e, "plain": plain, "latency": lat, "roofline": roofline, "cpu_baseline": cpu,
             "adjoint": adjoint, "serving": serve, "uneven": uneven, "robustness": robust,
-            "overlapped": overlapped, "planner": plan,
+            "overlapped": overlapped, "planner": plan, "synthesis": synth_r,
             "clocks": ck, "gpu_launches": args.steps, "robots": robots,
             "solver": {"iters_per_step": st_last["iterations"] / max(st_last["steps_total"], 1),
                        "evals_per_step": st_last["evaluations"] / max(st_last["steps_total"], 1),
@@ -554,6 +555,26 @@ def planner_leg(args, scenes):
                     "per iteration including the host tree"}
 
 
+def synthesis_leg(args):
+    """Actuator design synthesis (Sec. 4.2) for a batch of target angles per
+    joint: 10 pressures x 61 cell lengths (1 mm grid), the paper's body.
+    Wall time of one vine_synthesize call (tables, pair equilibria, choices,
+    host copies), after one warm-up call."""
+    from paper_2509_15180_gb300 import vine
+    rng = np.random.default_rng(0)
+    targets = rng.uniform(0.005, 0.11, args.synth_targets)
+    kw = dict(R=0.03335, P_vine=10342.0, l_seg=0.025, pressures=np.arange(10e3, 100e3 + 1, 10e3), l0_min=0.020,
+              l0_step=0.001, n_l0=61, tol=0.004)
+    vine.synthesize(targets[:16], **kw)
+    t0 = time.perf_counter()
+    out = vine.synthesize(targets, **kw)
+    wall = time.perf_counter() - t0
+    return {"targets": int(targets.size), "pairs": 610, "ms": 1e3 * wall, "us_per_design": 1e6 * wall / targets.size,
+            "feasible": float(np.mean(out["p_index"] >= 0)),
+            "what": "one vine_synthesize call: sPAM tables for 61 cell lengths, 610 pair equilibria, one choice "
+                    "per target (paper: milliseconds per numerical solve)"}
+
+
 def cpu_baseline(args, sc, robots=None):
     """The FP64 oracle as it stands, OpenMP over robots on all host cores, on a
     bounded sample of the workload (the first `robots` robots)."""
@@ -618,6 +639,7 @@ def main():
     ap.add_argument("--robust-designs", type=int, default=64)
     ap.add_argument("--robust-perturb", type=int, default=32)
     ap.add_argument("--plan-seconds", type=float, default=20.0, help="planner leg budget (0: skip)")
+    ap.add_argument("--synth-targets", type=int, default=100000, help="design-synthesis leg targets (0: skip)")
     ap.add_argument("--plan-iters", type=int, default=60)
     ap.add_argument("--plan-batch", type=int, default=1024)
     ap.add_argument("--serve-seconds", type=float, default=12.0)

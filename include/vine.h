@@ -385,6 +385,39 @@ vine_status vine_batch_destroy(vine_batch* b);
 vine_status vine_spam_tables_noalloc(const double* l0, int32_t n_tab, const vine_params* params, float* hdr,
                                      float* knots, void* cuda_stream);
 
+/* Actuator design synthesis (Sec. 4.2): for every target angle per joint
+ * theta_target[q] (rad), the sPAM design -- a pressure from the caller's
+ * discrete set and a cell length on the caller's grid -- whose actuator holds
+ * a free joint of the body (no contact) at theta_target within tol.
+ *   A design (P, l0) holds the joint at theta_eq(P, l0) in (0, pi], where the
+ *   wrinkling moment (Eq. wrinkling_model) equals the actuator moment
+ *   (Eq. sPAM_force per pressure times P times the arm 2 R + R_act of
+ *   Sec. 3.3) at the actuator strain (2 R + R_act) theta / l_seg, the force
+ *   per pressure from the cell length's sPAM table (the growth step's table,
+ *   built here in FP64); pi when the actuator still wins at pi.
+ *   Among the designs with |theta_eq - theta_target| <= tol: the highest
+ *   pressure (the paper's rule), then the closest angle, then the shorter
+ *   cell, then the lower pressure index.  None: indices -1, theta_eq NaN.
+ * A per-joint target times the number of covered joints is the segment's
+ * turning angle.  spec: body radius R (m), body pressure P_vine (Pa),
+ * segment length l_seg (m), pressures[n_p] (Pa, > 0), cell lengths
+ * l0_min + k l0_step (m), k < n_l0, tol (rad, >= 0); n_p, n_l0 in [1, 4096],
+ * n_p n_l0 <= 2^20.  params: sPAM constants and eps_crit (NULL: defaults).
+ * Outputs (host): p_index[n_targets], l0_index[n_targets],
+ * theta_eq[n_targets], and theta_pairs[n_p][n_l0] (may be NULL).  Host
+ * pointers; the stream is synchronised. */
+typedef struct {
+  double R, P_vine, l_seg;
+  const double* pressures;
+  int32_t n_p;
+  double l0_min, l0_step;
+  int32_t n_l0;
+  double tol;
+} vine_synth_spec;
+vine_status vine_synthesize(const vine_synth_spec* spec, const vine_params* params, const double* theta_target,
+                            int32_t n_targets, int32_t* p_index, int32_t* l0_index, double* theta_eq,
+                            double* theta_pairs, void* cuda_stream);
+
 /* Tree operations of the batched SST* planner (Sec. 5.2, Algorithm 2).
  * Tip poses are (x, y, phi) triples, float32 [3 n], headings in [-pi, pi],
  * positions in any length unit; rho converts radians to that unit, so that

@@ -31,11 +31,12 @@ from scipy import optimize
 import oracle
 
 
-def joint_equilibrium(P: float, l0: float, R: float, Pv: float, ls: float, params=None) -> float:
-    """theta_eq(P, l0): the root in (0, pi] of the free-joint balance."""
+def joint_equilibrium(P: float, l0: float, R: float, Pv: float, ls: float, params=None, table=None) -> float:
+    """theta_eq(P, l0): the root in (0, pi] of the free-joint balance.
+    table: (eps_lo, eps_hi, f) of the cell length, if already built."""
     prm = params or oracle.default_params()
     d = 2.0 * R + prm.R_act
-    lo, hi, fk = oracle.spam_table(l0, prm)
+    lo, hi, fk = table if table is not None else oracle.spam_table(l0, prm)
     M0 = math.pi * Pv * R ** 3
 
     def h(th):
@@ -52,8 +53,9 @@ def joint_equilibrium(P: float, l0: float, R: float, Pv: float, ls: float, param
 
 def pair_table(pressures, l0_grid, R, Pv, ls, params=None) -> np.ndarray:
     """theta_eq for every (pressure, cell length): [n_p, n_l0]."""
-    return np.array([[joint_equilibrium(float(P), float(l0), R, Pv, ls, params) for l0 in l0_grid]
-                     for P in pressures])
+    tabs = [oracle.spam_table(float(l0), params or oracle.default_params()) for l0 in l0_grid]
+    return np.array([[joint_equilibrium(float(P), float(l0), R, Pv, ls, params, tabs[k])
+                      for k, l0 in enumerate(l0_grid)] for P in pressures])
 
 
 def choose(theta_t: float, pairs: np.ndarray, pressures, tol: float):

@@ -946,6 +946,60 @@ vine_status vine_set_state(vine_batch* B, const int32_t* n_present, const float*
   return VINE_OK;
 }
 
+vine_status vine_synthesize(const vine_synth_spec* spec, const vine_params* params, const double* theta_target,
+                            int32_t n_targets, int32_t* p_index, int32_t* l0_index, double* theta_eq,
+                            double* theta_pairs, void* stream_v) {
+  if (!spec || n_targets < 0 || (n_targets > 0 && (!theta_target || !p_index || !l0_index || !theta_eq)))
+    return fail(VINE_EINVAL, "vine_synthesize: null argument or negative count");
+  const vine_synth_spec& c = *spec;
+  auto pos = [](double v) { return std::isfinite(v) && v > 0.0; };
+  if (!pos(c.R) || !pos(c.P_vine) || !pos(c.l_seg) || !pos(c.l0_min) || !(std::isfinite(c.l0_step) && c.l0_step >= 0.0) ||
+      !(std::isfinite(c.tol) && c.tol >= 0.0) || c.n_p < 1 || c.n_l0 < 1 || c.n_p > 4096 || c.n_l0 > 4096 ||
+      (int64_t)c.n_p * c.n_l0 > (1 << 20) || !c.pressures)
+    return fail(VINE_EINVAL, "vine_synthesize: specification out of range");
+  for (int i = 0; i < c.n_p; ++i)
+    if (!pos(c.pressures[i])) return fail(VINE_EINVAL, "vine_synthesize: pressures must be finite and positive");
+  vine_params prm;
+  if (params) prm = *params; else vine_params_default(&prm);
+  cudaStream_t st = (cudaStream_t)stream_v;
+  const size_t nt = (size_t)n_targets, np = (size_t)c.n_p, nl = (size_t)c.n_l0, npl = np * nl;
+  std::vector<double> l0s(nl);
+  for (size_t k = 0; k < nl; ++k) l0s[k] = c.l0_min + (double)k * c.l0_step;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += align256(std::max<size_t>(bytes, 16));
+    return o;
+  };
+  const size_t o_tg = take(8 * nt), o_pr = take(8 * np), o_l0 = take(8 * nl), o_scr = take(8 * (4 + kKnots) * nl),
+               o_hdr = take(sizeof(float4) * nl), o_tab = take(sizeof(float2) * kKnots * nl), o_pair = take(8 * npl),
+               o_pi = take(4 * nt), o_li = take(4 * nt), o_eq = take(8 * nt);
+  char* mem = nullptr;
+  CK(cudaMallocAsync((void**)&mem, off, st));
+  struct Free {
+    char* m;
+    cudaStream_t s;
+    ~Free() { cudaFreeAsync(m, s); }
+  } fr{mem, st};
+  if (nt) CK(cudaMemcpyAsync(mem + o_tg, theta_target, 8 * nt, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(mem + o_pr, c.pressures, 8 * np, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(mem + o_l0, l0s.data(), 8 * nl, cudaMemcpyHostToDevice, st));
+  GaussLegendre gl;
+  gauss_legendre(24, &gl);
+  CK(launch_synth(n_targets, (const double*)(mem + o_tg), c.n_p, c.n_l0, (const double*)(mem + o_pr),
+                  (const double*)(mem + o_l0), c.R, c.P_vine, c.l_seg, c.tol, prm.R_c, prm.R_act, prm.a_spam, prm.m_lo,
+                  prm.eps_crit, gl, (double*)(mem + o_scr), (float4*)(mem + o_hdr), (float2*)(mem + o_tab),
+                  (double*)(mem + o_pair), (int*)(mem + o_pi), (int*)(mem + o_li), (double*)(mem + o_eq), st));
+  if (nt) {
+    CK(cudaMemcpyAsync(p_index, mem + o_pi, 4 * nt, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(l0_index, mem + o_li, 4 * nt, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(theta_eq, mem + o_eq, 8 * nt, cudaMemcpyDeviceToHost, st));
+  }
+  if (theta_pairs) CK(cudaMemcpyAsync(theta_pairs, mem + o_pair, 8 * npl, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return VINE_OK;
+}
+
 vine_status vine_grad(const vine_batch* B, const float* goal_xy, double* cost, double* d_pressure, double* d_begin,
                       double* d_end, int32_t* grad_status, int32_t ptrs_are_device, void* stream_v) {
   if (!B || !goal_xy || !cost || !grad_status || (B->n_act > 0 && (!d_pressure || !d_begin || !d_end)))

@@ -285,6 +285,116 @@ __global__ void wrinkle_finish_kernel(double ec, const double* cells, const doub
   consts[3] = (kPiD - thc) / kUCells;
 }
 
+// ---- actuator design synthesis (Sec. 4.2) ----------------------------------
+// Free-joint balance of a design (P, l0): h(theta) = pi P_v R^3 mhat(theta)
+// - P f_l0(d theta / l_seg) d, with f_l0 the piecewise-linear force per
+// pressure on the table's FP64 knots (its first knot below the strain range,
+// zero beyond it).  h is increasing on (0, pi]: the equilibrium by bisection.
+__device__ double synth_f(const double* bounds, const double* fk, int t, double eps) {
+  const double elo = bounds[4 * t + 0], ehi = bounds[4 * t + 1];
+  const double h = (ehi - elo) / (kKnots - 1);
+  const double u = (eps - elo) / h;
+  const double* f = fk + (size_t)t * kKnots;
+  if (u <= 0.0) return f[0];
+  if (u >= (double)(kKnots - 1)) return 0.0;
+  const int k = (int)u;
+  return f[k] + (u - k) * (f[k + 1] - f[k]);
+}
+
+__device__ double synth_mhat(double th, double ec) {
+  const double thc = 2.0 * asin(ec);
+  return th <= thc ? th / (2.0 * thc) : mhat_above(th, ec);
+}
+
+// One thread per (pressure, cell length): theta_eq, or pi when the actuator
+// still wins at pi, or 0 when it cannot bend the joint at all.
+__global__ void synth_pairs_kernel(int n_p, int n_l0, const double* pressures, const double* bounds,
+                                   const double* fk, double R, double Pv, double ls, double R_act, double ec,
+                                   double* theta_pair) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n_p * n_l0) return;
+  const int ip = q / n_l0, il = q - ip * n_l0;
+  const double P = pressures[ip], d = 2.0 * R + R_act, M0 = kPiD * Pv * R * R * R;
+  auto h = [&](double th) { return M0 * synth_mhat(th, ec) - P * synth_f(bounds, fk, il, d * th / ls) * d; };
+  double th;
+  if (h(kPiD) <= 0.0) {
+    th = kPiD;
+  } else if (h(0.0) >= 0.0) {
+    th = 0.0;
+  } else {
+    double lo = 0.0, hi = kPiD;
+    for (int it = 0; it < 200 && hi - lo > 1e-15; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (h(mid) < 0.0) lo = mid; else hi = mid;
+    }
+    th = 0.5 * (lo + hi);
+  }
+  theta_pair[q] = th;
+}
+
+// One CTA per target: the feasible pair (|theta_eq - target| <= tol) of
+// highest pressure, then closest angle, then shorter cell; a block-wide
+// reduction over the pairs.
+__global__ void synth_choose_kernel(int n_targets, const double* target, int n_p, int n_l0, const double* pressures,
+                                    const double* theta_pair, double tol, int* p_index, int* l0_index,
+                                    double* theta_eq) {
+  __shared__ double kp[256], kd[256];
+  __shared__ int kl[256], ki[256];
+  const int t = blockIdx.x;
+  if (t >= n_targets) return;
+  const double tg = target[t];
+  double bp = 0.0, bd = 0.0;
+  int bl = 0, bi = -1;  // bi: pair index, -1 none
+  for (int q = threadIdx.x; q < n_p * n_l0; q += blockDim.x) {
+    const double dev = fabs(theta_pair[q] - tg);
+    if (!(dev <= tol)) continue;
+    const int ip = q / n_l0, il = q - ip * n_l0;
+    const double P = pressures[ip];
+    // key (-P, dev, il, ip), smaller is better
+    const bool better = bi < 0 || P > bp || (P == bp && (dev < bd || (dev == bd && (il < bl ||
+                        (il == bl && ip < bi / n_l0)))));
+    if (better) {
+      bp = P;
+      bd = dev;
+      bl = il;
+      bi = q;
+    }
+  }
+  kp[threadIdx.x] = bp;
+  kd[threadIdx.x] = bd;
+  kl[threadIdx.x] = bl;
+  ki[threadIdx.x] = bi;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      const int o = threadIdx.x + w;
+      const int ai = ki[threadIdx.x], oi = ki[o];
+      bool take = false;
+      if (oi >= 0) {
+        if (ai < 0) take = true;
+        else {
+          const double ap = kp[threadIdx.x], op = kp[o], ad = kd[threadIdx.x], od = kd[o];
+          const int al = kl[threadIdx.x], ol = kl[o];
+          take = op > ap || (op == ap && (od < ad || (od == ad && (ol < al || (ol == al && oi / n_l0 < ai / n_l0)))));
+        }
+      }
+      if (take) {
+        kp[threadIdx.x] = kp[o];
+        kd[threadIdx.x] = kd[o];
+        kl[threadIdx.x] = kl[o];
+        ki[threadIdx.x] = oi;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const int q = ki[0];
+    p_index[t] = q < 0 ? -1 : q / n_l0;
+    l0_index[t] = q < 0 ? -1 : q % n_l0;
+    theta_eq[t] = q < 0 ? __longlong_as_double(0x7ff8000000000000ll) : theta_pair[q];
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_spam_tables(const double* l0, int n_tab, double R_c, double R_act, double a_spam, double m_lo,
@@ -298,6 +408,25 @@ cudaError_t launch_spam_tables(const double* l0, int n_tab, double R_c, double R
   dim3 grid((kKnots - 2 + 3) / 4, n_tab);  // 4 warps per block, one knot each
   spam_knots_kernel<<<grid, 128, 0, s>>>(l0, c, gl, bounds, fk);
   spam_finish_kernel<<<(n_tab + 31) / 32, 32, 0, s>>>(n_tab, bounds, fk, hdr, tab);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_synth(int n_targets, const double* target, int n_p, int n_l0, const double* pressures,
+                         const double* l0s, double R, double Pv, double ls, double tol, double R_c, double R_act,
+                         double a_spam, double m_lo, double eps_c, const GaussLegendre& gl, double* scratch,
+                         float4* hdr, float2* tab, double* theta_pair, int* p_index, int* l0_index,
+                         double* theta_eq, cudaStream_t s) {
+  cudaError_t e = launch_spam_tables(l0s, n_l0, R_c, R_act, a_spam, m_lo, gl, hdr, tab, scratch, s);
+  if (e != cudaSuccess) return e;
+  const double* bounds = scratch;
+  const double* fk = scratch + 4 * n_l0;
+  const int np = n_p * n_l0;
+  synth_pairs_kernel<<<(np + 127) / 128, 128, 0, s>>>(n_p, n_l0, pressures, bounds, fk, R, Pv, ls, R_act, eps_c,
+                                                      theta_pair);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || n_targets == 0) return e;
+  synth_choose_kernel<<<n_targets, 256, 0, s>>>(n_targets, target, n_p, n_l0, pressures, theta_pair, tol, p_index,
+                                                l0_index, theta_eq);
   return cudaGetLastError();
 }
 

@@ -96,6 +96,7 @@ _SIG = {
     "vine_set_actuators": [_p, _p, _p, _p, _i32, _p],
     "vine_set_state": [_p, _p, _p, _p, _i32, _p],
     "vine_relax": [_p, _i32, _p],
+    "vine_synthesize": [_p, _p, _p, _i32, _p, _p, _p, _p, _p],
     "vine_sst_prune": [_i32, _p, _p, _p, _i32, _p, _p, C.c_float, C.c_float, _p, _p, _i32, _p],
     "vine_sst_select": [_i32, _p, _p, _p, _i32, _p, C.c_float, C.c_float, _p, _i32, _p],
     "vine_autotune": [_p, _i32, _p, _p],
@@ -392,6 +393,33 @@ class Batch:
 
     def pose_of(self, st: dict, i: int):
         return st["pose"][self.offsets[i]: self.offsets[i] + st["N"][i]]
+
+
+# -------------------------------------------------------------------------
+# actuator design synthesis (Sec. 4.2)
+# -------------------------------------------------------------------------
+class vine_synth_spec(C.Structure):
+    _fields_ = [("R", C.c_double), ("P_vine", C.c_double), ("l_seg", C.c_double), ("pressures", C.c_void_p),
+                ("n_p", C.c_int32), ("l0_min", C.c_double), ("l0_step", C.c_double), ("n_l0", C.c_int32),
+                ("tol", C.c_double)]
+
+
+def synthesize(theta_targets, R: float, P_vine: float, l_seg: float, pressures, l0_min: float, l0_step: float,
+               n_l0: int, tol: float, params: vine_params | None = None, stream=None) -> dict:
+    """vine_synthesize: per target angle per joint, the chosen pressure index,
+    cell-length index (-1: none feasible) and the angle the design holds;
+    and the angle of every (pressure, cell length) pair."""
+    tg = np.ascontiguousarray(np.asarray(theta_targets, np.float64).reshape(-1))
+    pr = np.ascontiguousarray(np.asarray(pressures, np.float64).reshape(-1))
+    spec = vine_synth_spec(float(R), float(P_vine), float(l_seg), pr.ctypes.data, pr.size, float(l0_min),
+                           float(l0_step), int(n_l0), float(tol))
+    n = tg.size
+    out = dict(p_index=np.zeros(n, np.int32), l0_index=np.zeros(n, np.int32), theta_eq=np.zeros(n),
+               pairs=np.zeros((pr.size, int(n_l0))))
+    _check(_lib.vine_synthesize(C.byref(spec), C.byref(params) if params is not None else None, _ptr(tg), n,
+                                _ptr(out["p_index"]), _ptr(out["l0_index"]), _ptr(out["theta_eq"]),
+                                _ptr(out["pairs"]), _stream(stream)), "vine_synthesize")
+    return out
 
 
 # -------------------------------------------------------------------------
