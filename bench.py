@@ -268,6 +268,7 @@ def run_gpu(args):
     if ws == 1 and args.plan_seconds > 0:
         plan = planner_leg(args, scenes)
     synth_r = synthesis_leg(args) if ws == 1 and args.synth_targets > 0 else None
+    surr = surrogate_leg(args) if ws == 1 and args.surrogate_steps > 0 else None
     if rank == 0:
         cpu = cpu_baseline(args, sc) if ws == 1 and not args.no_cpu else None
         lat = {"p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
@@ -282,7 +283,7 @@ def run_gpu(args):
                        "tol": 1e-6},
             "e2e": e2e, "plain": plain, "latency": lat, "roofline": roofline, "cpu_baseline": cpu,
             "adjoint": adjoint, "serving": serve, "uneven": uneven, "robustness": robust,
-            "overlapped": overlapped, "planner": plan, "synthesis": synth_r,
+            "overlapped": overlapped, "planner": plan, "synthesis": synth_r, "surrogate": surr,
             "clocks": ck, "gpu_launches": args.steps, "robots": robots,
             "solver": {"iters_per_step": st_last["iterations"] / max(st_last["steps_total"], 1),
                        "evals_per_step": st_last["evaluations"] / max(st_last["steps_total"], 1),
@@ -575,6 +576,38 @@ def synthesis_leg(args):
                     "per target (paper: milliseconds per numerical solve)"}
 
 
+def surrogate_leg(args):
+    """The sPAM surrogate of Sec. 4.3: exact-model samples, training (40 000
+    samples split 80/10/10, full-batch Adam), held-out normalised MSE
+    (paper: 0.003), and throughput of the network against the exact model
+    (paper: four orders of magnitude)."""
+    import torch
+    from paper_2509_15180_gb300 import surrogate, vine
+    t0 = time.perf_counter()
+    x, y, _ = surrogate.make_dataset(40000, 0)
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    r = surrogate.train(40000, steps=args.surrogate_steps, lr=0.01)
+    t_train = time.perf_counter() - t0 - t_data  # train() regenerates the same samples
+    n = 1 << 22
+    xi = torch.from_numpy(np.tile(x, (n // x.shape[0] + 1, 1))[:n].copy()).cuda()
+    vine.surrogate_eval(r["net"], xi)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    vine.surrogate_eval(r["net"], xi)
+    e1.record()
+    torch.cuda.synchronize()
+    net_per_s = n / (e0.elapsed_time(e1) / 1e3)
+    exact_per_s = 40000 / t_data
+    return {"samples": 40000, "steps": args.surrogate_steps, "train_s": t_train, "test_mse": r["test_mse"],
+            "val_mse": r["val_mse"], "paper_mse": 0.003, "eval_per_s": net_per_s, "exact_model_per_s": exact_per_s,
+            "speedup": net_per_s / exact_per_s,
+            "what": "2-32-2 ReLU network (strain, cell length) -> (m, phi_Rc); exact model: vine_spam_samples "
+                    "(FP64, one warp per sample, host round trip included); network: vine_surrogate_eval on "
+                    "4M device-resident inputs, CUDA events"}
+
+
 def cpu_baseline(args, sc, robots=None):
     """The FP64 oracle as it stands, OpenMP over robots on all host cores, on a
     bounded sample of the workload (the first `robots` robots)."""
@@ -640,6 +673,7 @@ def main():
     ap.add_argument("--robust-perturb", type=int, default=32)
     ap.add_argument("--plan-seconds", type=float, default=20.0, help="planner leg budget (0: skip)")
     ap.add_argument("--synth-targets", type=int, default=100000, help="design-synthesis leg targets (0: skip)")
+    ap.add_argument("--surrogate-steps", type=int, default=3000, help="surrogate leg Adam steps (0: skip)")
     ap.add_argument("--plan-iters", type=int, default=60)
     ap.add_argument("--plan-batch", type=int, default=1024)
     ap.add_argument("--serve-seconds", type=float, default=12.0)

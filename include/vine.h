@@ -418,6 +418,46 @@ vine_status vine_synthesize(const vine_synth_spec* spec, const vine_params* para
                             int32_t n_targets, int32_t* p_index, int32_t* l0_index, double* theta_eq,
                             double* theta_pairs, void* cuda_stream);
 
+/* sPAM neural surrogate (Sec. 4.3).  The paper replaces the numerical
+ * solution of Eq. sPAM_1/sPAM_2 inside its simulator by a 2-32-2 network
+ * (ReLU hidden units, He initialisation) from (strain, cell length) to
+ * (m, phi_Rc), trained on 40k samples of the exact model by mean squared
+ * error on normalised outputs.
+ *
+ * vine_spam_samples: the exact model at given (m[i] in (0, 0.5], l0[i] > 0)
+ * -- strain eps (Eq. sPAM_1), phi_Rc (the smallest root of Eq. sPAM_2 in
+ * (0, acos(R_c / R_act)], else that bound: the saturated branch), force per
+ * pressure f (Eq. sPAM_force), saturated flag -- in FP64, one warp per
+ * sample.  params: sPAM constants (NULL: defaults).  Host pointers; the
+ * stream is synchronised.
+ *
+ * vine_surrogate: the network's 162 parameters, W1[32][2] (hidden, input),
+ * b1[32], W2[2][32] (output, hidden), b2[2], and its normalisation:
+ * x_i = (input_i - in_lo_i) in_scale_i, output_k = y_k / out_scale_k.
+ *
+ * vine_surrogate_train: full-batch Adam (beta 0.9 / 0.999, eps 1e-8) for
+ * `steps` steps of learning rate lr on the loss (1 / 2n) sum |y - t|^2,
+ * t the normalised targets (m, phi) times out_scale; inputs[n][2] =
+ * (strain, cell length), targets[n][2] = (m, phi).  net holds the initial
+ * parameters on entry and the trained ones on return; loss_history[steps]
+ * (may be NULL) the loss before each step.  The gradient sums run in a
+ * fixed order: the result does not depend on scheduling.  Host pointers;
+ * the stream is synchronised.
+ *
+ * vine_surrogate_eval: outputs[n][2] = (m, phi) of the network at
+ * inputs[n][2]; ptrs_are_device as for vine_grad (net itself is a host
+ * struct). */
+typedef struct {
+  float theta[162];
+  float in_lo[2], in_scale[2], out_scale[2];
+} vine_surrogate;
+vine_status vine_spam_samples(const double* m, const double* l0, int32_t n, const vine_params* params, double* eps,
+                              double* phi, double* f, int32_t* saturated, void* cuda_stream);
+vine_status vine_surrogate_train(vine_surrogate* net, const double* inputs, const double* targets, int32_t n,
+                                 int32_t steps, float lr, float* loss_history, void* cuda_stream);
+vine_status vine_surrogate_eval(const vine_surrogate* net, const double* inputs, int32_t n, double* outputs,
+                                int32_t ptrs_are_device, void* cuda_stream);
+
 /* Tree operations of the batched SST* planner (Sec. 5.2, Algorithm 2).
  * Tip poses are (x, y, phi) triples, float32 [3 n], headings in [-pi, pi],
  * positions in any length unit; rho converts radians to that unit, so that

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libvine.so")
-SOURCES = ["vine_tables.cu", "vine_grow.cu", "vine_api.cu", "vine_serve.cu", "vine_plan.cu"]
+SOURCES = ["vine_tables.cu", "vine_grow.cu", "vine_api.cu", "vine_serve.cu", "vine_plan.cu", "vine_surrogate.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]

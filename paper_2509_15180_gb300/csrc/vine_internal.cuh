@@ -140,6 +140,12 @@ cudaError_t launch_spam_tables(const double* l0, int n_tab, double R_c, double R
                                cudaStream_t s);
 cudaError_t launch_wrinkle_table(double eps_c, const GaussLegendre& gl, float2* utab, double* scratch,
                                  double* consts /*device [4]: U(pi), m(pi), theta_c, h*/, cudaStream_t s);
+// Exact sPAM model at (m[i], l0[i]): strain, phi_Rc, force per pressure,
+// saturated flag (the surrogate's training data).
+cudaError_t launch_spam_samples(int n, const double* m, const double* l0, double R_c, double R_act, double a_spam,
+                                const GaussLegendre& gl, double* eps, double* phi, double* f, int* sat,
+                                cudaStream_t s);
+
 // Actuator design synthesis (vine_synthesize): sPAM tables for the cell
 // lengths l0s[n_l0] (scratch >= (4 + kKnots) n_l0 doubles; hdr / tab as for
 // launch_spam_tables), the free-joint equilibrium of every (pressure, cell

@@ -104,7 +104,7 @@ __device__ void ellip_FE_warp(const GaussLegendre& gl, double phi, double m, int
 // residual on the 32-point scan of (0, phi_sat] is found with one scan point
 // per lane.
 __device__ void spam_model_warp(const GaussLegendre& gl, const SpamConst& c, double m, double l0, int lane,
-                                double* eps, double* f) {
+                                double* eps, double* f, double* phi_out = nullptr, int* sat_out = nullptr) {
   const double lam = l0 / c.Rc;
   const int nscan = 32;
   const double ph_l = c.phi_sat * (double)(lane + 1) / nscan;
@@ -149,6 +149,26 @@ __device__ void spam_model_warp(const GaussLegendre& gl, const SpamConst& c, dou
   *eps = (la - 2.0 * c.Rc * (E - 0.5 * F) / (sm * cp)) / l0;
   // Eq. (sPAM_force) per unit actuation pressure
   *f = kPiD * c.Rc * c.Rc * (1.0 - 2.0 * m) / (2.0 * m * cp * cp);
+  if (phi_out) *phi_out = phi;
+  if (sat_out) *sat_out = pos != 0u ? 0 : 1;
+}
+
+// Samples of the exact model (training data of the surrogate): one warp per
+// (m, l0): strain, phi_Rc, force per pressure and the branch.
+__global__ void spam_samples_kernel(int n, const double* m, const double* l0, SpamConst c, GaussLegendre gl,
+                                    double* eps, double* phi, double* f, int* sat) {
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= n) return;  // whole warps leave together
+  double e, ff, ph;
+  int st;
+  spam_model_warp(gl, c, m[i], l0[i], lane, &e, &ff, &ph, &st);
+  if (lane == 0) {
+    eps[i] = e;
+    phi[i] = ph;
+    f[i] = ff;
+    sat[i] = st;
+  }
 }
 
 // One warp per (table, knot): knots 1..254 by Illinois on eps(m) - target.
@@ -427,6 +447,15 @@ cudaError_t launch_synth(int n_targets, const double* target, int n_p, int n_l0,
   if (e != cudaSuccess || n_targets == 0) return e;
   synth_choose_kernel<<<n_targets, 256, 0, s>>>(n_targets, target, n_p, n_l0, pressures, theta_pair, tol, p_index,
                                                 l0_index, theta_eq);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spam_samples(int n, const double* m, const double* l0, double R_c, double R_act, double a_spam,
+                                const GaussLegendre& gl, double* eps, double* phi, double* f, int* sat,
+                                cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  SpamConst c{R_c, R_act, a_spam, 0.0, std::acos(R_c / R_act)};
+  spam_samples_kernel<<<(n + 3) / 4, 128, 0, s>>>(n, m, l0, c, gl, eps, phi, f, sat);
   return cudaGetLastError();
 }
 

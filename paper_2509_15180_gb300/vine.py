@@ -97,6 +97,9 @@ _SIG = {
     "vine_set_state": [_p, _p, _p, _p, _i32, _p],
     "vine_relax": [_p, _i32, _p],
     "vine_synthesize": [_p, _p, _p, _i32, _p, _p, _p, _p, _p],
+    "vine_spam_samples": [_p, _p, _i32, _p, _p, _p, _p, _p, _p],
+    "vine_surrogate_train": [_p, _p, _p, _i32, _i32, C.c_float, _p, _p],
+    "vine_surrogate_eval": [_p, _p, _i32, _p, _i32, _p],
     "vine_sst_prune": [_i32, _p, _p, _p, _i32, _p, _p, C.c_float, C.c_float, _p, _p, _i32, _p],
     "vine_sst_select": [_i32, _p, _p, _p, _i32, _p, C.c_float, C.c_float, _p, _i32, _p],
     "vine_autotune": [_p, _i32, _p, _p],
@@ -419,6 +422,64 @@ def synthesize(theta_targets, R: float, P_vine: float, l_seg: float, pressures, 
     _check(_lib.vine_synthesize(C.byref(spec), C.byref(params) if params is not None else None, _ptr(tg), n,
                                 _ptr(out["p_index"]), _ptr(out["l0_index"]), _ptr(out["theta_eq"]),
                                 _ptr(out["pairs"]), _stream(stream)), "vine_synthesize")
+    return out
+
+
+# -------------------------------------------------------------------------
+# sPAM surrogate (Sec. 4.3)
+# -------------------------------------------------------------------------
+class vine_surrogate(C.Structure):
+    _fields_ = [("theta", C.c_float * 162), ("in_lo", C.c_float * 2), ("in_scale", C.c_float * 2),
+                ("out_scale", C.c_float * 2)]
+
+
+def _net_struct(net: dict) -> vine_surrogate:
+    s = vine_surrogate()
+    s.theta[:] = [float(v) for v in np.asarray(net["theta"], np.float32)]
+    for k in ("in_lo", "in_scale", "out_scale"):
+        getattr(s, k)[:] = [float(v) for v in np.asarray(net[k], np.float32)]
+    return s
+
+
+def spam_samples(m, l0, params: vine_params | None = None, stream=None) -> dict:
+    """vine_spam_samples: the exact sPAM model at (m, l0) pairs."""
+    m = np.ascontiguousarray(np.asarray(m, np.float64).reshape(-1))
+    l0 = np.ascontiguousarray(np.asarray(l0, np.float64).reshape(-1))
+    n = m.size
+    out = dict(eps=np.zeros(n), phi=np.zeros(n), f=np.zeros(n), saturated=np.zeros(n, np.int32))
+    _check(_lib.vine_spam_samples(_ptr(m), _ptr(l0), n, C.byref(params) if params is not None else None,
+                                  _ptr(out["eps"]), _ptr(out["phi"]), _ptr(out["f"]), _ptr(out["saturated"]),
+                                  _stream(stream)), "vine_spam_samples")
+    return out
+
+
+def surrogate_train(net: dict, inputs, targets, steps: int, lr: float, history: bool = True, stream=None):
+    """vine_surrogate_train: returns (trained net dict, loss history or None)."""
+    s = _net_struct(net)
+    x = np.ascontiguousarray(np.asarray(inputs, np.float64).reshape(-1, 2))
+    t = np.ascontiguousarray(np.asarray(targets, np.float64).reshape(-1, 2))
+    hist = np.zeros(max(int(steps), 1), np.float32) if history else None
+    _check(_lib.vine_surrogate_train(C.byref(s), _ptr(x), _ptr(t), x.shape[0], int(steps), float(lr),
+                                     _ptr(hist) if history else None, _stream(stream)), "vine_surrogate_train")
+    out = dict(net, theta=np.array(s.theta[:], np.float32))
+    return out, (hist[: int(steps)] if history else None)
+
+
+def surrogate_eval(net: dict, inputs, stream=None):
+    """vine_surrogate_eval: (m, phi) per input row; numpy in/out, or CUDA
+    float64 tensors [n, 2] (async)."""
+    s = _net_struct(net)
+    if hasattr(inputs, "is_cuda") and inputs.is_cuda:
+        import torch
+        x = inputs.contiguous()
+        out = torch.empty_like(x)
+        _check(_lib.vine_surrogate_eval(C.byref(s), _ptr(x), x.shape[0], _ptr(out), 1, _stream(stream)),
+               "vine_surrogate_eval")
+        return out
+    x = np.ascontiguousarray(np.asarray(inputs, np.float64).reshape(-1, 2))
+    out = np.zeros_like(x)
+    _check(_lib.vine_surrogate_eval(C.byref(s), _ptr(x), x.shape[0], _ptr(out), 0, _stream(stream)),
+           "vine_surrogate_eval")
     return out
 
 
