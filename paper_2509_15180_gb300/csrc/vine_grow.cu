@@ -513,7 +513,11 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
   const float floor_d = 1e-6f * A.w_a * I.PR3;
   int ntest = 0;
   if (A.broad) rebuild_lists<KS>(I, S, N, j0, j1, px, py, lane, A.list_margin, ntest);
-  double Jl = 0.0, Sl = 0.0;
+  // cost terms summed per lane in float-float (each term is an FP32 value;
+  // the sum keeps ~48 bits, far below the rounding-level test on J), their
+  // magnitudes in FP32 (only a scale for that test): GB300's FP64 rate is low
+  FF Jl{0.f, 0.f};
+  float Sl = 0.f;
   for (int j = j0; j < j1; ++j) {
     // ---- bending and actuation at joint j (Eq. restoring_moment)
     const float th = S.TH[j];
@@ -560,8 +564,8 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
       U -= Ua;
       Um += fabsf(Ua);
     }
-    Jl += (double)(A.w_a * U);
-    Sl += (double)(A.w_a * Um);
+    Jl = ff_add(Jl, A.w_a * U);
+    Sl += A.w_a * Um;
     S.G[j] = A.w_a * M;
     S.DD[j] = fmaxf(A.w_a * dM, floor_d);
     // ---- contacts of link j: KS discs x every obstacle
@@ -647,8 +651,8 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
       ntest += cnt;
     }
     resolve();
-    Jl += (double)(A.w_c * I.kc * pen2);
-    Sl += (double)(A.w_c * I.kc) * ((double)pen2 + 2.0 * (double)I.R * (double)pen1);
+    Jl = ff_add(Jl, A.w_c * I.kc * pen2);
+    Sl += (A.w_c * I.kc) * (pen2 + 2.f * I.R * pen1);
     px = ff_add(px, lx);
     py = ff_add(py, ly);
   }
@@ -679,8 +683,11 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
   // ---- reductions
   EvalOut E;
   const double dlr = (double)I.l_seg - (double)l;
-  E.J = warp_sum(Jl) + (double)A.w_b * (double)I.kg * dlr * dlr;
-  E.S = warp_sum(Sl) + (double)A.w_b * (double)I.kg * dlr * dlr;
+  float Ss = Sl;
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) Ss += __shfl_xor_sync(kFull, Ss, d);
+  E.J = warp_sum((double)Jl.hi + (double)Jl.lo) + (double)A.w_b * (double)I.kg * dlr * dlr;
+  E.S = (double)Ss + (double)A.w_b * (double)I.kg * dlr * dlr;
   const int owner = (N - 1) / B;
   const float glc = S.LX[0];  // written by the owner lane before the __syncwarp above
   E.hll = 2.f * A.w_b * I.kg + S.LX[1];
