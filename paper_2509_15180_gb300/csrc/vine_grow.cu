@@ -808,7 +808,6 @@ struct StepStats {
   int fallbacks;
 };
 
-// Solves the current growth step to equilibrium from the warm start.
 // Diagnostic record of one line-search trial (only for A.trace_inst).
 __device__ __forceinline__ void trace_rec(const GrowArgs& A, int inst, int lane, int N, int it, int h, double a,
                                           double r, double J0, double Jt, double dec, double s0, double st, double lt,
@@ -834,6 +833,9 @@ __device__ __forceinline__ void trace_rec(const GrowArgs& A, int inst, int lane,
 //    free-space stiffness (joint angles by gd_alpha 2 theta_c / (w_a pi P
 //    R^3), the distal length by gd_alpha / (2 w_b k_g), kept in [0, l_seg]);
 //    no convergence test.
+// With A.relax the step re-solves the present links (no link added), and
+// with A.fix_l the distal length is held (the length unknown is dropped
+// from the Newton system; the descent leaves it).
 // Written as one loop around a single evaluation: the first evaluation, the
 // Gauss-Newton re-evaluation, every line-search trial and every descent step
 // pass through the same call, so the evaluation's code is inlined once (the
