@@ -599,9 +599,24 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
     float pen2 = 0.f, pen1 = 0.f;
     const float Rpre = I.R * (1.f + 1e-6f);
     int qn = 0;
-    auto resolve = [&]() {
-      for (int q = 0; q < qn; ++q) {
-        const int code = S.Q[q * 32 + lane];
+    // every obstacle (no broad phase, or too many near this link), else the
+    // link's list; both in obstacle order, so the result is the same.  The
+    // pre-tests fill the queue up to the last obstacle that cannot overflow
+    // it, then the queue is resolved in order: one call site for the long
+    // contact code, and the candidates meet add_contact in scan order.
+    const int lb = j * (kListCap + 1);
+    const bool every = !A.broad || S.CL[lb] == kListFull;
+    const int cnt = every ? I.n_obs : (int)S.CL[lb];
+    for (int q = 0;;) {
+      for (; q < cnt && qn <= kContactQueue - KS; ++q) {
+        const int o = every ? q : (int)S.CL[lb + 1 + q];
+        const float4 ob = S.obs[o];
+#pragma unroll
+        for (int k = 0; k < KS; ++k)
+          if (contact_candidate(ob, xk[k], yk[k], Rpre)) S.Q[(qn++) * 32 + lane] = o * KS + k;
+      }
+      for (int e = 0; e < qn; ++e) {
+        const int code = S.Q[e * 32 + lane];
         const int o = code / KS, k = code - o * KS;
         const float fr = (float)(k + 1) / (float)KS;
         const FF x = ff_add(px, fr * lx), y = ff_add(py, fr * ly);
@@ -619,38 +634,9 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
         }
       }
       qn = 0;
-    };
-    // every obstacle (no broad phase, or too many near this link), else the
-    // link's list; both in obstacle order, so the result is the same
-    const int lb = j * (kListCap + 1);
-    if (!A.broad || S.CL[lb] == kListFull) {
-      for (int o = 0; o < I.n_obs; ++o) {
-        const float4 ob = S.obs[o];
-#pragma unroll
-        for (int k = 0; k < KS; ++k) {
-          if (contact_candidate(ob, xk[k], yk[k], Rpre)) {
-            S.Q[qn * 32 + lane] = o * KS + k;
-            if (++qn == kContactQueue) resolve();
-          }
-        }
-      }
-      ntest += I.n_obs;
-    } else {
-      const int cnt = S.CL[lb];
-      for (int q = 0; q < cnt; ++q) {
-        const int o = S.CL[lb + 1 + q];
-        const float4 ob = S.obs[o];
-#pragma unroll
-        for (int k = 0; k < KS; ++k) {
-          if (contact_candidate(ob, xk[k], yk[k], Rpre)) {
-            S.Q[qn * 32 + lane] = o * KS + k;
-            if (++qn == kContactQueue) resolve();
-          }
-        }
-      }
-      ntest += cnt;
+      if (q >= cnt) break;
     }
-    resolve();
+    ntest += cnt;
     Jl = ff_add(Jl, A.w_c * I.kc * pen2);
     Sl += (A.w_c * I.kc) * (pen2 + 2.f * I.R * pen1);
     px = ff_add(px, lx);
