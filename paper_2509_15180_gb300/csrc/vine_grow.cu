@@ -132,6 +132,8 @@ __device__ __forceinline__ Smem carve(float* base, const GrowArgs& A) {
 // below p = 1 (F: below 1.6), which keeps FP32 accuracy.
 __device__ __forceinline__ void wrinkle_terms(float p, float& Nn, float& Dn, float& F) {
   const float p2 = p * p;
+  float sp = 0.f, cp = 1.f;
+  if (p >= 1.f) sincosf(p, &sp, &cp);  // one evaluation serves both closed forms
   if (p < 1.f) {
     const float x2 = 4.f * p2;
     Nn = 8.f * p2 * p *
@@ -141,8 +143,6 @@ __device__ __forceinline__ void wrinkle_terms(float p, float& Nn, float& Dn, flo
          (3.3333333333e-1f + p2 * (-3.3333333333e-2f + p2 * (1.1904761905e-3f + p2 * (-2.2045855379e-5f +
          p2 * (2.5052108385e-7f + p2 * -1.9270852604e-9f)))));
   } else {
-    float sp, cp;
-    sincosf(p, &sp, &cp);
     Nn = 2.f * p - 2.f * sp * cp;
     Dn = 4.f * (sp - p * cp);
   }
@@ -153,8 +153,6 @@ __device__ __forceinline__ void wrinkle_terms(float p, float& Nn, float& Dn, flo
         x2 * (-5.7353727989e-11f + x2 * (2.8676863994e-13f + x2 * (-1.0933444878e-15f + x2 * (3.2882540986e-18f +
         x2 * -8.0071122532e-21f))))))));
   } else {
-    float sp, cp;
-    sincosf(p, &sp, &cp);
     F = 4.f * sp * sp - 2.f * p * sp * cp - 2.f * p2;
   }
 }
