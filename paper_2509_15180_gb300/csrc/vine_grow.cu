@@ -396,8 +396,8 @@ __device__ __forceinline__ void reset_lists(const Smem& S, int n, int lane) {
 // the distal link (whose length changes within the step) are queued, and the
 // warp rebuilds their lists together, the lanes splitting the obstacles and
 // a ballot keeping obstacle order.  More than kListCap near obstacles mark
-// the link kListFull (it then tests every obstacle).  ntest counts the
-// pre-tests run (in obstacles).
+// the link kListFull (it then tests every obstacle until it has moved like
+// any other list).  ntest counts the pre-tests run (in obstacles).
 template <int KS>
 __device__ void rebuild_lists(const InstDev& I, const Smem& S, int N, int j0, int j1, FF px, FF py, int lane,
                               float margin_r, int& ntest) {
@@ -411,7 +411,10 @@ __device__ void rebuild_lists(const InstDev& I, const Smem& S, int N, int j0, in
     S.PB[2 * j + 1] = y0;
     const int lb = j * (kListCap + 1);
     const unsigned short c = S.CL[lb];
-    bool stale = (j == N - 1) || c == kListStale || c == kListFull;
+    // a full list (more than kListCap near obstacles) makes the link test
+    // every obstacle, which is right wherever it has moved to within the
+    // margin; it is rebuilt, like any list, once the link has moved further
+    bool stale = (j == N - 1) || c == kListStale;
     if (!stale) {
       const float* xb = S.XB + 4 * j;
       const float d0x = x0 - xb[0], d0y = y0 - xb[1], d1x = px.hi - xb[2], d1y = py.hi - xb[3];
