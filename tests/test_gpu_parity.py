@@ -156,7 +156,7 @@ def _stepwise(sc, steps):
     flagged_robots = set()
     for step in range(steps):
         _to_fp32(ost)
-        # an unconverged earlier step is judged on its own step: both sides
+        # an unconverged earlier step is assessed on its own step: both sides
         # start this one with a clean status
         ost["status"][ost["status"] == 1] = 0
         b.set_state(ost["N"], ost["theta"][: max(b.total_links, 1)].astype(np.float32),
