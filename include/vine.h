@@ -211,7 +211,7 @@ vine_status vine_simulate(vine_batch* b, void* cuda_stream);
  * instances (0: 4096; spread evenly over the longest-first order) from
  * reset to full length once per candidate configuration -- warps per CTA
  * (4, 2, 1: one robot per warp; fewer warps per CTA pack large per-robot
- * shared-memory slices more tightly) x broad-phase margin (0.25, 0.5, 1 body
+ * shared-memory slices more tightly) x broad-phase margin (0.5, 1, 2 body
  * radii: list length against rebuild frequency) -- times each launch with
  * CUDA events, and adopts the fastest for later vine_grow_step /
  * vine_simulate calls.  Neither knob changes any result.  Leaves the batch

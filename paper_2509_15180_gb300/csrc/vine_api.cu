@@ -736,7 +736,7 @@ vine_status vine_autotune(vine_batch* B, int32_t sample, void* stream_v, vine_tu
   int dev_id = 0, nsm = 1;
   cudaGetDevice(&dev_id);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev_id);
-  const float margins[3] = {0.25f, kListMargin, 1.0f};
+  const float margins[3] = {0.5f, kListMargin, 2.0f};
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));

@@ -24,7 +24,7 @@ constexpr int kWarpsPerCta = 4;    // warps per CTA of the growth kernel
 constexpr int kContactQueue = 8;   // contact candidates a lane queues per link before resolving them
 constexpr float kRefinePen = 2e-3f;  // penetrations below this fraction of R are re-evaluated in float-float
 constexpr int kListCap = 7;            // obstacles a link's broad-phase list holds
-constexpr float kListMargin = 0.5f;    // default broad-phase margin, in body radii
+constexpr float kListMargin = 1.0f;    // default broad-phase margin, in body radii
 constexpr unsigned short kListStale = 0xffff;  // list not built for the current link geometry
 constexpr unsigned short kListFull = 0xfffe;   // more than kListCap obstacles near the link
 constexpr int kMaxLinks = 1024;
