@@ -134,7 +134,9 @@ def run_gpu(args):
     rls_per_step = scenes.robot_link_steps(sc["n_links"])
     stream = torch.cuda.current_stream()
     dsc = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in sc.items()}
-    b = vine.Batch(dsc, stream=stream)
+    prm = vine.vine_params_default()
+    prm.threads_per_robot = args.threads_per_robot
+    b = vine.Batch(dsc, prm, stream=stream)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def one_step():
@@ -204,7 +206,7 @@ def run_gpu(args):
     n = len(sc["n_links"])
     d2h = T * 4 + T * 12 + n * (8 + 4 + 4 + 4 + 8 + 4)
     if e2e_steps:
-        bw = vine.Batch(host, stream=stream)  # warm (tables, graph) once
+        bw = vine.Batch(host, prm, stream=stream)  # warm (tables, graph) once
         bw.simulate(stream)
         bw.state(stream)
         bw.close()
@@ -212,7 +214,7 @@ def run_gpu(args):
     t0 = time.perf_counter()
     e2e_rls = 0
     for _ in range(e2e_steps):
-        be = vine.Batch(host, stream=stream)
+        be = vine.Batch(host, prm, stream=stream)
         be.simulate(stream)
         out = be.state(stream)
         e2e_rls += int(be.stats(stream)["robot_link_steps"])
@@ -226,7 +228,7 @@ def run_gpu(args):
     n_plain = args.plain_robots
     plain = None
     if n_plain > 0:
-        plain = _plain(scenes, vine, torch, sc, stream, n_plain)
+        plain = _plain(scenes, vine, torch, sc, stream, n_plain, prm)
 
     # --- roofline of the growth kernel: algorithmic FP32 flops per launch
     # flops of the work the launch ran: 40 per link-evaluation, 10 per
@@ -278,7 +280,7 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 residual test)", "data": "synthetic",
             "config": {"workload": WORKLOAD if n == 4096 else WORKLOAD.replace("4096", str(n)),
-                       "robots_per_gpu": n, "links": 100,
+                       "robots_per_gpu": n, "links": 100, "threads_per_robot": args.threads_per_robot,
                        "robot_link_steps_per_step": rls_per_step, "l2": "flushed between timed steps (512 MiB write)",
                        "tol": 1e-6},
             "e2e": e2e, "plain": plain, "latency": lat, "roofline": roofline, "cpu_baseline": cpu,
@@ -297,10 +299,10 @@ def run_gpu(args):
     return result
 
 
-def _plain(scenes, vine, torch, sc, stream, n_plain):
+def _plain(scenes, vine, torch, sc, stream, n_plain, prm=None):
     """Plain form: one launch per robot, same kernel, on the first robots."""
     sub = scenes.subset(sc, np.arange(n_plain))
-    bp = vine.Batch(sub, stream=stream)
+    bp = vine.Batch(sub, prm, stream=stream)
     bp.simulate_plain(stream)
     torch.cuda.synchronize()
     bp.reset(stream)
@@ -491,7 +493,9 @@ def overlapped_leg(args, vine, scenes, torch, sc):
     steps (the working set of a batch is a few MB and the kernel does not
     depend on it)."""
     streams = [torch.cuda.Stream(), torch.cuda.Stream()]
-    bs = [vine.Batch(sc, stream=streams[q]) for q in range(2)]
+    prm = vine.vine_params_default()
+    prm.threads_per_robot = args.threads_per_robot
+    bs = [vine.Batch(sc, prm, stream=streams[q]) for q in range(2)]
     for q in range(2):
         bs[q].simulate(streams[q])
     torch.cuda.synchronize()
@@ -659,6 +663,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--robots", type=int, default=4096, help="robots per GPU (the workload has 4096)")
+    ap.add_argument("--threads-per-robot", type=int, default=64, choices=[32, 64],
+                    help="design-batch legs: one warp (32) or a two-warp team (64) per robot")
     ap.add_argument("--plain-robots", type=int, default=64)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-robots", type=int, default=96)

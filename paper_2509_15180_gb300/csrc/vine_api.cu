@@ -226,7 +226,8 @@ struct vine_batch {
   int n_tab = 0;
   vine_params params{};
   int ks = 2;
-  int wpc = kWarpsPerCta;  // warps per CTA of the growth launch
+  int wpc = kWarpsPerCta;  // robots (teams) per CTA of the growth launch
+  int team = 32;           // threads per robot
   int nmax = 32, omax = 1, amax = 1;
   size_t smem_warp = 0;
   int grid = 1;
@@ -271,6 +272,7 @@ vine_status vine_params_default(vine_params* p) {
   p->gd_steps = 50;
   p->exact_hessian = 1;
   p->broad_phase = 1;
+  p->threads_per_robot = 32;
   return VINE_OK;
 }
 
@@ -294,7 +296,8 @@ vine_status vine_batch_create(const vine_batch_desc* D, const vine_params* P, vo
     return fail(VINE_EINVAL, "vine_batch_create: discs_per_link must be 1..4");
   if (!(prm.tol > 0.0) || prm.max_iter < 1 || prm.max_halvings < 0 || !(prm.eps_crit > 0.0 && prm.eps_crit < 1.0) ||
       !(prm.R_c > 0.0 && prm.R_act > prm.R_c) || !(prm.m_lo > 0.0 && prm.m_lo < 0.5) || !(prm.pen_frac > 0.0) || !(prm.fval_eps >= 0.0) || !(prm.armijo_c1 > 0.0 && prm.armijo_c1 < 0.5) ||
-      (prm.mode != 0 && prm.mode != 1) || (prm.mode == 1 && (prm.gd_steps < 1 || !(prm.gd_alpha > 0.0))))
+      (prm.mode != 0 && prm.mode != 1) || (prm.mode == 1 && (prm.gd_steps < 1 || !(prm.gd_alpha > 0.0))) ||
+      (prm.threads_per_robot != 0 && prm.threads_per_robot != 32 && prm.threads_per_robot != 64))
     return fail(VINE_EINVAL, "vine_batch_create: parameter out of range");
   const int n = D->n_inst;
   if (n <= 0) return fail(VINE_EINVAL, "vine_batch_create: n_inst must be positive");
@@ -571,12 +574,13 @@ vine_status vine_batch_create(const vine_batch_desc* D, const vine_params* P, vo
   B->nmax = (nmax + 31) & ~31;
   B->omax = omax;
   B->amax = amax;
-  B->smem_warp = grow_smem_per_warp(B->nmax, B->omax, B->amax);
+  B->team = prm.threads_per_robot == 64 ? 64 : 32;
+  B->smem_warp = grow_smem_per_warp(B->nmax, B->omax, B->amax, B->team);
   int dev_id = 0, nsm = 1;
   cudaGetDevice(&dev_id);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev_id);
   int per_sm = 0;
-  B->wpc = grow_pick_block(B->ks, B->smem_warp, &per_sm);
+  B->wpc = grow_pick_block(B->ks, B->smem_warp, &per_sm, B->team);
   if (B->wpc == 0 || per_sm == 0) {
     cleanup();
     return fail(VINE_EINVAL, "vine_batch_create: robot or obstacle set too large for shared memory");
@@ -631,6 +635,7 @@ vine_status vine_batch_create(const vine_batch_desc* D, const vine_params* P, vo
   a.max_halv = prm.max_halvings;
   a.exact = prm.exact_hessian;
   a.broad = prm.broad_phase;
+  a.team = B->team;
   a.mode = prm.mode;
   a.gd_steps = prm.gd_steps;
   a.gd_alpha = (float)prm.gd_alpha;
@@ -647,8 +652,8 @@ static vine_status grow_launch(vine_batch* B, int n_steps, cudaStream_t st) {
   a.n_steps = n_steps;
   a.dynamic = 1;
   CK(cudaMemsetAsync(a.counter, 0, sizeof(int), st));
-  CK(grow_configure(B->ks, B->smem_warp * B->wpc));
-  CK(launch_grow(a, B->ks, B->grid, 32 * B->wpc, B->smem_warp * B->wpc, st));
+  CK(grow_configure(B->ks, B->smem_warp * B->wpc, B->team));
+  CK(launch_grow(a, B->ks, B->grid, B->team * B->wpc, B->smem_warp * B->wpc, st));
   return VINE_OK;
 }
 
@@ -690,8 +695,8 @@ vine_status vine_relax(vine_batch* B, int32_t fix_length, void* stream_v) {
   a.relax = 1;
   a.fix_l = fix_length;
   CK(cudaMemsetAsync(a.counter, 0, sizeof(int), st));
-  CK(grow_configure(B->ks, B->smem_warp * B->wpc));
-  CK(launch_grow(a, B->ks, B->grid, 32 * B->wpc, B->smem_warp * B->wpc, st));
+  CK(grow_configure(B->ks, B->smem_warp * B->wpc, B->team));
+  CK(launch_grow(a, B->ks, B->grid, B->team * B->wpc, B->smem_warp * B->wpc, st));
   return VINE_OK;
 }
 
@@ -745,10 +750,10 @@ vine_status vine_autotune(vine_batch* B, int32_t sample, void* stream_v, vine_tu
   out->default_ms = -1.0;
   out->sample = ns;
   vine_status rs = VINE_OK;
-  for (int w = kWarpsPerCta; w >= 1 && rs == VINE_OK; w >>= 1) {
+  for (int w = B->team == 64 ? 1 : kWarpsPerCta; w >= 1 && rs == VINE_OK; w >>= 1) {
     const size_t smem = B->smem_warp * w;
-    if (grow_configure(B->ks, smem) != cudaSuccess) continue;
-    const int ctas = grow_max_ctas_per_sm(B->ks, smem, 32 * w);
+    if (grow_configure(B->ks, smem, B->team) != cudaSuccess) continue;
+    const int ctas = grow_max_ctas_per_sm(B->ks, smem, B->team * w, B->team);
     if (ctas <= 0) continue;
     for (float m : margins) {
       GrowArgs a = B->args;
@@ -761,7 +766,7 @@ vine_status vine_autotune(vine_batch* B, int32_t sample, void* stream_v, vine_tu
       if ((rs = vine_batch_reset(B, st)) != VINE_OK) break;
       cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
       if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-      if (e == cudaSuccess) e = launch_grow(a, B->ks, grid, 32 * w, smem, st);
+      if (e == cudaSuccess) e = launch_grow(a, B->ks, grid, B->team * w, smem, st);
       if (e == cudaSuccess) e = cudaEventRecord(e1, st);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
       float ms = 0.f;
@@ -785,7 +790,7 @@ vine_status vine_autotune(vine_batch* B, int32_t sample, void* stream_v, vine_tu
   if (out->candidates == 0) return fail(VINE_EINVAL, "vine_autotune: no launch configuration fits");
   // adopt the fastest (results do not depend on either knob)
   B->wpc = out->warps_per_cta;
-  const int ctas = grow_max_ctas_per_sm(B->ks, B->smem_warp * B->wpc, 32 * B->wpc);
+  const int ctas = grow_max_ctas_per_sm(B->ks, B->smem_warp * B->wpc, B->team * B->wpc, B->team);
   B->grid = std::max(1, std::min((n + B->wpc - 1) / B->wpc, nsm * std::max(ctas, 1)));
   B->args.list_margin = out->list_margin;
   if (B->graph_exec) {  // the recorded launch carries the old configuration
@@ -806,7 +811,8 @@ vine_status vine_simulate_plain(vine_batch* B, void* stream_v) {
   a.n_order = 1;
   for (int k = 0; k < B->n_inst; ++k) {
     a.order = B->args.order + k;
-    CK(launch_grow(a, B->ks, 1, 32, B->smem_warp, st));
+    CK(grow_configure(B->ks, B->smem_warp, B->team));
+    CK(launch_grow(a, B->ks, 1, B->team, B->smem_warp, st));
   }
   return VINE_OK;
 }

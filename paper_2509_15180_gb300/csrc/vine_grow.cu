@@ -91,19 +91,163 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// A team of TP threads owns one robot: one warp (TP = 32, the default), or
+// two warps of one CTA (TP = 64), which split the link loops in half.  The
+// team operations below are the warp's own for TP = 32; for TP = 64 the two
+// warps' partial results meet in shared-memory scratch between CTA barriers.
+// Every branch around them depends only on team-uniform values (reductions,
+// broadcasts, the robot's sizes), so both warps reach every barrier.
+template <int TP>
+struct Team {
+  int r;       // rank in the team
+  float* scr;  // S.TS
+  __device__ __forceinline__ int lane() const { return r & 31; }
+  __device__ __forceinline__ int warp() const { return r >> 5; }
+  __device__ __forceinline__ void sync() const {
+    if (TP == 32)
+      __syncwarp();
+    else
+      __syncthreads();
+  }
+};
+
+template <int TP>
+__device__ __forceinline__ FF team_excl_scan(FF v, const Team<TP>& t) {
+  FF x = warp_excl_scan(v, t.lane());
+  if (TP == 32) return x;
+  if (t.r == 31) {
+    const FF inc = ff_add(x, v);  // warp 0's total
+    t.scr[0] = inc.hi;
+    t.scr[1] = inc.lo;
+  }
+  t.sync();
+  if (t.warp() == 1) x = ff_add(FF{t.scr[0], t.scr[1]}, x);
+  t.sync();
+  return x;
+}
+
+template <int TP>
+__device__ __forceinline__ float team_excl_suffix(float v, const Team<TP>& t) {
+  float x = warp_excl_suffix(v, t.lane());
+  if (TP == 32) return x;
+  if (t.r == 32) t.scr[2] = x + v;  // warp 1's total
+  t.sync();
+  if (t.warp() == 0) x += t.scr[2];
+  t.sync();
+  return x;
+}
+
+template <int TP>
+__device__ __forceinline__ double team_sum(double v, const Team<TP>& t) {
+  v = warp_sum(v);
+  if (TP == 32) return v;
+  double* d = reinterpret_cast<double*>(t.scr + 4);
+  if (t.lane() == 0) d[t.warp()] = v;
+  t.sync();
+  const double s = d[0] + d[1];
+  t.sync();
+  return s;
+}
+
+template <int TP>
+__device__ __forceinline__ float team_sum_f(float v, const Team<TP>& t) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
+  if (TP == 32) return v;
+  if (t.lane() == 0) t.scr[8 + t.warp()] = v;
+  t.sync();
+  const float s = t.scr[8] + t.scr[9];
+  t.sync();
+  return s;
+}
+
+template <int TP>
+__device__ __forceinline__ int team_sum_i(int v, const Team<TP>& t) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
+  if (TP == 32) return v;
+  int* q = reinterpret_cast<int*>(t.scr + 10);
+  if (t.lane() == 0) q[t.warp()] = v;
+  t.sync();
+  const int s = q[0] + q[1];
+  t.sync();
+  return s;
+}
+
+template <int TP>
+__device__ __forceinline__ float team_max(float v, const Team<TP>& t) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, d));
+  if (TP == 32) return v;
+  if (t.lane() == 0) t.scr[12 + t.warp()] = v;
+  t.sync();
+  const float m = fmaxf(t.scr[12], t.scr[13]);
+  t.sync();
+  return m;
+}
+
+template <int TP>
+__device__ __forceinline__ bool team_any(bool b, const Team<TP>& t) {
+  const bool w = __any_sync(kFull, b);
+  if (TP == 32) return w;
+  int* q = reinterpret_cast<int*>(t.scr + 14);
+  if (t.lane() == 0) q[t.warp()] = w ? 1 : 0;
+  t.sync();
+  const bool a = (q[0] | q[1]) != 0;
+  t.sync();
+  return a;
+}
+
+// value of rank `owner`, for every rank
+template <int TP>
+__device__ __forceinline__ float team_bcast(float v, int owner, const Team<TP>& t) {
+  if (TP == 32) return __shfl_sync(kFull, v, owner);
+  if (t.r == owner) t.scr[3] = v;
+  t.sync();
+  const float b = t.scr[3];
+  t.sync();
+  return b;
+}
+
+// exclusive prefix of integer counts over the ranks, and their total
+template <int TP>
+__device__ __forceinline__ int team_excl_scan_i(int v, int& total, const Team<TP>& t) {
+  int off = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int o = __shfl_up_sync(kFull, off, d);
+    if (t.lane() >= d) off += o;
+  }
+  int wt = __shfl_sync(kFull, off, 31);  // the warp's total
+  off -= v;
+  if (TP == 32) {
+    total = wt;
+    return off;
+  }
+  int* q = reinterpret_cast<int*>(t.scr + 10);
+  if (t.lane() == 0) q[t.warp()] = wt;
+  t.sync();
+  total = q[0] + q[1];
+  if (t.warp() == 1) off += q[0];
+  t.sync();
+  return off;
+}
+
 // Per-warp shared-memory slice.
 struct Smem {
   float4* obs;
   float4* act;
   float *TH, *TH0, *DTH, *LUX, *LUY, *G, *DD, *C0, *C1, *C2, *C3, *C4, *C5, *FX, *FY, *TL;
   float* LX;  // distal-link couplings: g_l contact part, h_ll, q0, q1, q2
-  int* Q;     // contact candidates of the link in progress, [kContactQueue][32 lanes]
+  int* Q;     // contact candidates of the link in progress, [kContactQueue][team threads]
+  float* TS;  // team scratch (two-warp teams): 16 floats
   unsigned short* CL;  // per link: obstacle list near it, [count, index...] x (kListCap + 1)
   float* XB;           // per link: its end points when its list was built, [4]
   float* PB;           // per link: its start point at the current evaluation, [2]
   int* RQ;             // links whose lists are rebuilt in this evaluation
 };
 
+template <int TP>
 __device__ __forceinline__ Smem carve(float* base, const GrowArgs& A) {
   Smem s;
   s.obs = reinterpret_cast<float4*>(base);
@@ -115,7 +259,8 @@ __device__ __forceinline__ Smem carve(float* base, const GrowArgs& A) {
   s.C5 = p + 12 * n; s.FX = p + 13 * n; s.FY = p + 14 * n; s.TL = p + 15 * n;
   s.LX = p + 16 * n;
   s.Q = reinterpret_cast<int*>(p + 16 * n + 8);
-  s.XB = p + 16 * n + 8 + 32 * kContactQueue;
+  s.TS = p + 16 * n + 8 + TP * kContactQueue;
+  s.XB = s.TS + 16;
   s.PB = s.XB + 4 * n;
   s.RQ = reinterpret_cast<int*>(s.PB + 2 * n);
   s.CL = reinterpret_cast<unsigned short*>(s.RQ + n);
@@ -383,9 +528,10 @@ struct EvalOut {
 
 // Every link's obstacle list is marked stale (robot start, or a state the
 // lists were not built for).
-__device__ __forceinline__ void reset_lists(const Smem& S, int n, int lane) {
-  for (int j = lane; j < n; j += 32) S.CL[j * (kListCap + 1)] = kListStale;
-  __syncwarp();
+template <int TP>
+__device__ __forceinline__ void reset_lists(const Smem& S, int n, const Team<TP>& tm) {
+  for (int j = tm.r; j < n; j += TP) S.CL[j * (kListCap + 1)] = kListStale;
+  tm.sync();
 }
 
 // Broad phase.  Every link keeps the list of obstacles within margin R
@@ -398,9 +544,10 @@ __device__ __forceinline__ void reset_lists(const Smem& S, int n, int lane) {
 // a ballot keeping obstacle order.  More than kListCap near obstacles mark
 // the link kListFull (it then tests every obstacle until it has moved like
 // any other list).  ntest counts the pre-tests run (in obstacles).
-template <int KS>
-__device__ void rebuild_lists(const InstDev& I, const Smem& S, int N, int j0, int j1, FF px, FF py, int lane,
-                              float margin_r, int& ntest) {
+template <int KS, int TP>
+__device__ void rebuild_lists(const InstDev& I, const Smem& S, int N, int j0, int j1, FF px, FF py,
+                              const Team<TP>& tm, float margin_r, int& ntest) {
+  const int lane = tm.lane();
   const float margin = margin_r * I.R, mv = 0.64f * margin * margin;
   int nre = 0;
   for (int j = j0; j < j1; ++j) {
@@ -426,17 +573,11 @@ __device__ void rebuild_lists(const InstDev& I, const Smem& S, int N, int j0, in
     }
   }
   // queue the stale links in link order: exclusive prefix of the lanes' counts
-  int off = nre;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const int v = __shfl_up_sync(kFull, off, d);
-    if (lane >= d) off += v;
-  }
-  const int total = __shfl_sync(kFull, off, 31);
-  off -= nre;
+  int total;
+  int off = team_excl_scan_i(nre, total, tm);
   for (int j = j0; j < j1 && nre > 0; ++j)
     if (S.CL[j * (kListCap + 1)] == kListStale) S.RQ[off++] = j;
-  __syncwarp();
+  tm.sync();
   const float Rm = I.R + margin;
   const unsigned lt = (1u << lane) - 1u;
   for (int q = 0; q < total; ++q) {
@@ -444,8 +585,8 @@ __device__ void rebuild_lists(const InstDev& I, const Smem& S, int N, int j0, in
     const float x0 = S.PB[2 * j], y0 = S.PB[2 * j + 1], lx = S.LUX[j], ly = S.LUY[j];
     const int lb = j * (kListCap + 1);
     int cnt = 0;
-    for (int o0 = 0; o0 < I.n_obs; o0 += 32) {
-      const int o = o0 + lane;
+    for (int o0 = 0; o0 < I.n_obs; o0 += TP) {
+      const int o = o0 + tm.r;
       bool near = false;
       if (o < I.n_obs) {
         const float4 ob = S.obs[o];
@@ -462,11 +603,20 @@ __device__ void rebuild_lists(const InstDev& I, const Smem& S, int N, int j0, in
         }
       }
       const unsigned bal = __ballot_sync(kFull, near);
-      const int pos = cnt + __popc(bal & lt);
+      int before = 0, here = __popc(bal);  // near obstacles of the lower warp, of this chunk
+      if (TP > 32) {
+        int* q = reinterpret_cast<int*>(tm.scr + 10);
+        if (lane == 0) q[tm.warp()] = here;
+        tm.sync();
+        before = tm.warp() == 1 ? q[0] : 0;
+        here = q[0] + q[1];
+        tm.sync();
+      }
+      const int pos = cnt + before + __popc(bal & lt);
       if (near && pos < kListCap) S.CL[lb + 1 + pos] = (unsigned short)o;
-      cnt += __popc(bal);
+      cnt += here;
     }
-    if (lane == 0) {
+    if (tm.r == 0) {
       S.CL[lb] = cnt > kListCap ? kListFull : (unsigned short)cnt;
       float* xb = S.XB + 4 * j;
       xb[0] = x0;
@@ -475,21 +625,21 @@ __device__ void rebuild_lists(const InstDev& I, const Smem& S, int N, int j0, in
       xb[3] = y0 + ly;
     }
   }
-  if (lane == 0) ntest += total * I.n_obs;
-  __syncwarp();
+  if (tm.r == 0) ntest += total * I.n_obs;
+  tm.sync();
 }
 
 // Cost, gradient and the Newton data at the state (TH[0..N), l): the exact
 // Hessian when `exact`, else the Gauss-Newton matrix.
-template <int KS>
-__device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int N, float l, int lane,
+template <int KS, int TP>
+__device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int N, float l, const Team<TP>& tm,
                         bool exact) {
-  const int B = (N + 31) >> 5;
-  const int j0 = min(lane * B, N), j1 = min(j0 + B, N);
+  const int B = (N + TP - 1) / TP;
+  const int j0 = min(tm.r * B, N), j1 = min(j0 + B, N);
   // headings psi_j = psi_b + sum_{i<=j} theta_i
   FF hs{0.f, 0.f};
   for (int j = j0; j < j1; ++j) hs = ff_add(hs, S.TH[j]);
-  FF psi = ff_add(warp_excl_scan(hs, lane), I.bpsi);
+  FF psi = ff_add(team_excl_scan(hs, tm), I.bpsi);
   FF sx{0.f, 0.f}, sy{0.f, 0.f};
   float ulx = 0.f, uly = 0.f;
   for (int j = j0; j < j1; ++j) {
@@ -509,11 +659,12 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
     sy = ff_add(sy, ly);
   }
   // link start points relative to the base
-  FF px = warp_excl_scan(sx, lane), py = warp_excl_scan(sy, lane);
+  FF px = team_excl_scan(sx, tm);
+  FF py = team_excl_scan(sy, tm);
   const float kap = 2.f * A.w_c * I.kc;
   const float floor_d = 1e-6f * A.w_a * I.PR3;
   int ntest = 0;
-  if (A.broad) rebuild_lists<KS>(I, S, N, j0, j1, px, py, lane, A.list_margin, ntest);
+  if (A.broad) rebuild_lists<KS, TP>(I, S, N, j0, j1, px, py, tm, A.list_margin, ntest);
   // cost terms summed per lane in float-float (each term is an FP32 value;
   // the sum keeps ~48 bits, far below the rounding-level test on J), their
   // magnitudes in FP32 (only a scale for that test): GB300's FP64 rate is low
@@ -614,10 +765,10 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
         const float4 ob = S.obs[o];
 #pragma unroll
         for (int k = 0; k < KS; ++k)
-          if (contact_candidate(ob, xk[k], yk[k], Rpre)) S.Q[(qn++) * 32 + lane] = o * KS + k;
+          if (contact_candidate(ob, xk[k], yk[k], Rpre)) S.Q[(qn++) * TP + tm.r] = o * KS + k;
       }
       for (int e = 0; e < qn; ++e) {
-        const int code = S.Q[e * 32 + lane];
+        const int code = S.Q[e * TP + tm.r];
         const int o = code / KS, k = code - o * KS;
         const float fr = (float)(k + 1) / (float)KS;
         const FF x = ff_add(px, fr * lx), y = ff_add(py, fr * ly);
@@ -643,7 +794,7 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
     px = ff_add(px, lx);
     py = ff_add(py, ly);
   }
-  __syncwarp();
+  tm.sync();
   // ---- gradient: g_j = w_a M_tot,j - T_j, T_j = moment about p_j of the
   // contact forces on links >= j = sum_{i>=j} (tl_i + Lu_i x F_{>i}).
   float tfx = 0.f, tfy = 0.f;
@@ -651,7 +802,8 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
     tfx += S.FX[j];
     tfy += S.FY[j];
   }
-  float fsx = warp_excl_suffix(tfx, lane), fsy = warp_excl_suffix(tfy, lane);
+  float fsx = team_excl_suffix(tfx, tm);
+  float fsy = team_excl_suffix(tfy, tm);
   float tt = 0.f;
   for (int j = j1 - 1; j >= j0; --j) {
     const float t = S.TL[j] + (S.LUX[j] * fsy - S.LUY[j] * fsx);
@@ -662,7 +814,7 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
     fsx += S.FX[j];
     fsy += S.FY[j];
   }
-  float run = warp_excl_suffix(tt, lane);
+  float run = team_excl_suffix(tt, tm);
   for (int j = j1 - 1; j >= j0; --j) {
     run += S.TL[j];
     S.G[j] -= run;
@@ -670,28 +822,21 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
   // ---- reductions
   EvalOut E;
   const double dlr = (double)I.l_seg - (double)l;
-  float Ss = Sl;
-#pragma unroll
-  for (int d = 16; d > 0; d >>= 1) Ss += __shfl_xor_sync(kFull, Ss, d);
-  E.J = warp_sum((double)Jl.hi + (double)Jl.lo) + (double)A.w_b * (double)I.kg * dlr * dlr;
+  const float Ss = team_sum_f(Sl, tm);
+  E.J = team_sum((double)Jl.hi + (double)Jl.lo, tm) + (double)A.w_b * (double)I.kg * dlr * dlr;
   E.S = (double)Ss + (double)A.w_b * (double)I.kg * dlr * dlr;
   const int owner = (N - 1) / B;
-  const float glc = S.LX[0];  // written by the owner lane before the __syncwarp above
+  const float glc = S.LX[0];  // written by the owner thread before the team barrier above
   E.hll = 2.f * A.w_b * I.kg + S.LX[1];
   E.q0 = S.LX[2];
   E.q1 = S.LX[3];
   E.q2 = S.LX[4];
-  E.ulx = __shfl_sync(kFull, ulx, owner);
-  E.uly = __shfl_sync(kFull, uly, owner);
+  E.ulx = team_bcast(ulx, owner, tm);
+  E.uly = team_bcast(uly, owner, tm);
   E.gl = -2.f * A.w_b * I.kg * (I.l_seg - l) - glc;
   E.kg_wb = A.w_b * I.kg;
-  {
-    int t = ntest;
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) t += __shfl_xor_sync(kFull, t, d);
-    E.tests = t * KS;
-  }
-  __syncwarp();
+  E.tests = team_sum_i(ntest, tm) * KS;
+  tm.sync();
   return E;
 }
 
@@ -703,14 +848,21 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
 // Gauss-Newton matrix is positive definite in exact arithmetic, so there a
 // pivot lost to FP32 rounding (distal-length Schur complement of a buckled
 // joint) is raised to a small positive floor instead.
+template <int TP>
 __device__ double gn_solve(const InstDev& I, const Smem& S, int N, bool lfix, const EvalOut& E, float& dl,
-                           int lane, bool strict, float& max_dth) {
+                           const Team<TP>& tm, bool strict, float& max_dth) {
   float A00 = 0.f, A01 = 0.f, A02 = 0.f, A11 = 0.f, A12 = 0.f, A22 = 0.f;
   float b0 = 0.f, b1 = 0.f, b2 = 0.f;
   if (strict && !lfix && !(E.hll > 1e-3f * 2.f * E.kg_wb)) return -1.0;
   const float iH = lfix ? 0.f : 1.f / E.hll;
   bool pd = true;
-  for (int j = N - 1; j >= 0; --j) {
+  float V0 = 0.f, V1 = 0.f, V2 = 0.f, rmax = 0.f, dmax = 0.f;
+  dl = 0.f;
+  // The sweeps overwrite the stiffness entries they read, so a two-warp
+  // team runs them on its first warp alone (the second would lag behind the
+  // writes) and takes the results from the scratch.
+  const bool sweeper = TP == 32 || tm.warp() == 0;
+  for (int j = sweeper ? N - 1 : -1; j >= 0; --j) {
     float c00 = S.C0[j], c01 = S.C1[j], c02 = S.C2[j], c11 = S.C3[j], c12 = S.C4[j], c22 = S.C5[j];
     const float dj = S.DD[j], gj = S.G[j], lx = S.LUX[j], ly = S.LUY[j];
     float e0 = 0.f, e1 = 0.f, e2 = 0.f;
@@ -752,7 +904,7 @@ __device__ double gn_solve(const InstDev& I, const Smem& S, int N, bool lfix, co
     b0 = h0 - C00 * cc * iD;
     b1 = h1 - C01 * cc * iD;
     b2 = h2 - C02 * cc * iD;
-    if (lane == 0) {
+    if (tm.r == 0) {
       S.C0[j] = C00;
       S.C1[j] = C01;
       S.C2[j] = C02;
@@ -760,11 +912,13 @@ __device__ double gn_solve(const InstDev& I, const Smem& S, int N, bool lfix, co
       S.C4[j] = cc;
     }
   }
-  __syncwarp();
-  if (!pd) return -1.0;
-  float V0 = 0.f, V1 = 0.f, V2 = 0.f, rmax = 0.f, dmax = 0.f;
-  dl = 0.f;
-  for (int j = 0; j < N; ++j) {
+  if (TP == 32) {
+    tm.sync();
+    if (!pd) return -1.0;
+  } else {
+    __syncwarp();
+  }
+  for (int j = 0; sweeper && pd && j < N; ++j) {
     const float h0 = S.C0[j], h1 = S.C1[j], h2 = S.C2[j], iD = S.C3[j], cc = S.C4[j];
     const float lx = S.LUX[j], ly = S.LUY[j];
     const float dth = -(cc + h0 * V0 + h1 * V1 + h2 * V2) * iD;
@@ -781,9 +935,25 @@ __device__ double gn_solve(const InstDev& I, const Smem& S, int N, bool lfix, co
     const float v = fmaxf(sqrtf(dx * dx + dy * dy), I.l_seg * fabsf(dth));
     if (!(v <= rmax)) rmax = v;  // keeps NaN
     if (!(fabsf(dth) <= dmax)) dmax = fabsf(dth);
-    if (lane == 0) S.DTH[j] = dth;
+    if (tm.r == 0) S.DTH[j] = dth;
   }
-  __syncwarp();
+  if (TP > 32) {
+    if (tm.r == 0) {
+      tm.scr[4] = pd ? 1.f : 0.f;
+      tm.scr[5] = rmax;
+      tm.scr[6] = dl;
+      tm.scr[7] = dmax;
+    }
+    tm.sync();
+    pd = tm.scr[4] != 0.f;
+    rmax = tm.scr[5];
+    dl = tm.scr[6];
+    dmax = tm.scr[7];
+    tm.sync();
+    if (!pd) return -1.0;
+  } else {
+    tm.sync();
+  }
   max_dth = dmax;
   return (double)rmax / ((double)N * (double)I.l_seg);
 }
@@ -796,10 +966,10 @@ struct StepStats {
 };
 
 // Diagnostic record of one line-search trial (only for A.trace_inst).
-__device__ __forceinline__ void trace_rec(const GrowArgs& A, int inst, int lane, int N, int it, int h, double a,
+__device__ __forceinline__ void trace_rec(const GrowArgs& A, int inst, int rank, int N, int it, int h, double a,
                                           double r, double J0, double Jt, double dec, double s0, double st, double lt,
                                           double lfix) {
-  if (A.trace == nullptr || inst != A.trace_inst || lane != 0) return;
+  if (A.trace == nullptr || inst != A.trace_inst || rank != 0) return;
   const int k = atomicAdd(A.trace_count, 1);
   if (k >= A.trace_cap) return;
   double* o = A.trace + 13 * (size_t)k;
@@ -827,17 +997,17 @@ __device__ __forceinline__ void trace_rec(const GrowArgs& A, int inst, int lane,
 // Gauss-Newton re-evaluation, every line-search trial and every descent step
 // pass through the same call, so the evaluation's code is inlined once (the
 // kernel's first stall is instruction fetch).
-template <int KS>
-__device__ int step_solve(const GrowArgs& A, const InstDev& I, const Smem& S, int N, float& l, int lane,
+template <int KS, int TP>
+__device__ int step_solve(const GrowArgs& A, const InstDev& I, const Smem& S, int N, float& l, const Team<TP>& tm,
                           StepStats& st, int inst) {
-  const int B = (N + 31) >> 5;
-  const int j0 = min(lane * B, N), j1 = min(j0 + B, N);
+  const int B = (N + TP - 1) / TP;
+  const int j0 = min(tm.r * B, N), j1 = min(j0 + B, N);
   const bool exact = A.exact != 0;
   const bool descend = A.mode == 1;
   float a_th = 0.f, a_l = 0.f;
   if (descend) {
-    for (int k = lane; k < N; k += 32) S.TH0[k] = S.TH[k];
-    __syncwarp();
+    for (int k = tm.r; k < N; k += TP) S.TH0[k] = S.TH[k];
+    tm.sync();
     a_th = A.gd_alpha * 2.f * A.theta_c / (A.w_a * I.PR3);
     a_l = A.gd_alpha / (2.f * A.w_b * I.kg);
   }
@@ -854,7 +1024,7 @@ __device__ int step_solve(const GrowArgs& A, const InstDev& I, const Smem& S, in
   // second guarantee that the loop ends
   const long long cap = (long long)(max(A.max_iter, 0) + 1) * (max(A.max_halv, 0) + 3) + max(A.gd_steps, 0) + 4;
   for (long long guard = 0; guard < cap; ++guard) {
-    const EvalOut E = eval<KS>(A, I, S, N, l_ev, lane, ev_exact);
+    const EvalOut E = eval<KS, TP>(A, I, S, N, l_ev, tm, ev_exact);
     st.evals += 1;
     st.linkevals += N;
     st.tests += E.tests;
@@ -864,10 +1034,10 @@ __device__ int step_solve(const GrowArgs& A, const InstDev& I, const Smem& S, in
         status = kNonFinite;
         break;
       }
-      for (int k = lane; k < N; k += 32) S.TH[k] -= a_th * S.G[k];
+      for (int k = tm.r; k < N; k += TP) S.TH[k] -= a_th * S.G[k];
       if (!A.fix_l) l = fminf(fmaxf(l - a_l * E.gl, 0.f), I.l_seg);
       l_ev = l;
-      __syncwarp();
+      tm.sync();
       if (++k_desc >= A.gd_steps) {
         status = kOK;
         break;
@@ -880,10 +1050,10 @@ __device__ int step_solve(const GrowArgs& A, const InstDev& I, const Smem& S, in
       const bool rounding = fabs(E.J - J0) <= (double)A.fval_eps * fmax(S0, E.S);
       if (A.trace != nullptr || rounding) {
         for (int j = j0; j < j1; ++j) sl += (double)S.G[j] * (double)S.DTH[j];
-        sl = warp_sum(sl);
+        sl = team_sum(sl, tm);
         if (lt > 0.f && lt < I.l_seg) sl += (double)E.gl * (double)dl;
       }
-      trace_rec(A, inst, lane, N, it, h, alpha, r, J0, E.J, dec, slope0, sl, lt, lfix ? 1.0 : 0.0);
+      trace_rec(A, inst, tm.r, N, it, h, alpha, r, J0, E.J, dec, slope0, sl, lt, lfix ? 1.0 : 0.0);
       const bool accepted =
           E.J <= J0 + (double)A.c1 * dec || (rounding && sl <= (2.0 * (double)A.c1 - 1.0) * slope0);
       if (!accepted) {
@@ -893,13 +1063,13 @@ __device__ int step_solve(const GrowArgs& A, const InstDev& I, const Smem& S, in
           for (int j = j0; j < j1; ++j) S.TH[j] = S.TH0[j] + alpha * S.DTH[j];
           lt = fminf(fmaxf(l0 + alpha * dl, 0.f), I.l_seg);
           l_ev = lt;
-          __syncwarp();
+          tm.sync();
           continue;
         }
         // no acceptable trial: the step ends at the last accepted iterate
         for (int j = j0; j < j1; ++j) S.TH[j] = S.TH0[j];
         l = l0;
-        __syncwarp();
+        tm.sync();
         break;
       }
       l = lt;
@@ -914,10 +1084,10 @@ __device__ int step_solve(const GrowArgs& A, const InstDev& I, const Smem& S, in
       lfix = A.fix_l || (l <= 0.f && E.gl > 0.f) || (l >= I.l_seg && E.gl < 0.f);
     }
     const bool use_exact = exact && phase == kNewton;
-    r = gn_solve(I, S, N, lfix, E, dl, lane, use_exact, mdth);
+    r = gn_solve(I, S, N, lfix, E, dl, tm, use_exact, mdth);
     if (use_exact && !(r >= 0.0 && isfinite(r))) {
       // exact Hessian not positive definite here: Gauss-Newton matrix instead
-      trace_rec(A, inst, lane, N, it, -2, 0.0, r, E.J, E.J, 0.0, 0.0, (double)E.hll, l, lfix ? 1.0 : 0.0);
+      trace_rec(A, inst, tm.r, N, it, -2, 0.0, r, E.J, E.J, 0.0, 0.0, (double)E.hll, l, lfix ? 1.0 : 0.0);
       st.fallbacks += 1;
       phase = kFallback;
       ev_exact = false;
@@ -931,11 +1101,11 @@ __device__ int step_solve(const GrowArgs& A, const InstDev& I, const Smem& S, in
     if (!isfinite(r) || r < 0.0) {
       // the Gauss-Newton sweep lost its pivots to FP32 range (bending floor
       // against contact stiffness): steepest descent, at most 0.05 rad per joint
-      trace_rec(A, inst, lane, N, it, -3, 0.0, r, E.J, E.S, (double)E.gl, (double)mdth, (double)E.hll, l,
+      trace_rec(A, inst, tm.r, N, it, -3, 0.0, r, E.J, E.S, (double)E.gl, (double)mdth, (double)E.hll, l,
                 lfix ? 1.0 : 0.0);
       float gm = 0.f;
       for (int j = j0; j < j1; ++j) gm = fmaxf(gm, fabsf(S.G[j]));
-      for (int d = 16; d > 0; d >>= 1) gm = fmaxf(gm, __shfl_xor_sync(kFull, gm, d));
+      gm = team_max(gm, tm);
       const float sc = gm > 0.f ? 0.05f / gm : 0.f;
       for (int j = j0; j < j1; ++j) S.DTH[j] = -S.G[j] * sc;
       dl = lfix ? 0.f : -E.gl * sc * I.l_seg * I.l_seg;
@@ -945,10 +1115,10 @@ __device__ int step_solve(const GrowArgs& A, const InstDev& I, const Smem& S, in
       }
       r = 1.0;  // not a Newton step: never taken as converged
       st.fallbacks += 1;
-      __syncwarp();
+      tm.sync();
     }
     if (r <= A.tol) {
-      trace_rec(A, inst, lane, N, it, -1, 1.0, r, E.J, E.J, 0.0, 0.0, 0.0, l + dl, lfix ? 1.0 : 0.0);
+      trace_rec(A, inst, tm.r, N, it, -1, 1.0, r, E.J, E.J, 0.0, 0.0, 0.0, l + dl, lfix ? 1.0 : 0.0);
       for (int j = j0; j < j1; ++j) S.TH[j] += S.DTH[j];
       l = fminf(fmaxf(l + dl, 0.f), I.l_seg);
       status = kOK;
@@ -960,7 +1130,7 @@ __device__ int step_solve(const GrowArgs& A, const InstDev& I, const Smem& S, in
       gd += (double)S.G[j] * (double)S.DTH[j];
       S.TH0[j] = S.TH[j];
     }
-    gd = warp_sum(gd);
+    gd = team_sum(gd, tm);
     l0 = l;
     gl0 = E.gl;
     J0 = E.J;
@@ -974,49 +1144,49 @@ __device__ int step_solve(const GrowArgs& A, const InstDev& I, const Smem& S, in
     l_ev = lt;
     phase = kTrial;
     ev_exact = exact;
-    __syncwarp();
+    tm.sync();
   }
   if (descend) {
     if (status == kOK) {
       bool badl = false;
-      for (int k = lane; k < N; k += 32) badl = badl || !isfinite(S.TH[k]);
-      if (__any_sync(kFull, badl)) status = kNonFinite;
+      for (int k = tm.r; k < N; k += TP) badl = badl || !isfinite(S.TH[k]);
+      if (team_any(badl, tm)) status = kNonFinite;
     }
     st.r = 0.0;
     return status;
   }
   if (it > A.max_iter) it = A.max_iter;
-  __syncwarp();
+  tm.sync();
   st.iters = it;
   st.r = r;
   return status;
 }
 
-template <int KS>
-__device__ void process_instance(const GrowArgs& A, int inst, const Smem& S, int lane) {
+template <int KS, int TP>
+__device__ void process_instance(const GrowArgs& A, int inst, const Smem& S, const Team<TP>& tm) {
   const long long t_start = clock64();
   const InstDev I = A.inst[inst];
   int status = A.status[inst];
   if (status == kBadInput || status == kNonFinite) return;
   int N = A.n_cur[inst];
   if (A.n_steps <= 0 || (A.relax ? N == 0 : N >= I.n_target)) return;
-  for (int k = lane; k < I.n_obs; k += 32) S.obs[k] = A.obs[I.obs_off + k];
-  for (int k = lane; k < I.n_act; k += 32) S.act[k] = A.act[I.act_off + k];
-  for (int k = lane; k < N; k += 32) S.TH[k] = A.theta[I.th_off + k];
+  for (int k = tm.r; k < I.n_obs; k += TP) S.obs[k] = A.obs[I.obs_off + k];
+  for (int k = tm.r; k < I.n_act; k += TP) S.act[k] = A.act[I.act_off + k];
+  for (int k = tm.r; k < N; k += TP) S.TH[k] = A.theta[I.th_off + k];
   float l = A.l_cur[inst];
-  reset_lists(S, I.n_target, lane);
+  reset_lists(S, I.n_target, tm);
   int iters = 0, conv = 0, steps = 0;
   long long rls = 0, evals = 0, linkevals = 0, fallbacks = 0, tests = 0;
   double rmax = 0.0;
   for (int s = 0; s < A.n_steps && (A.relax || N < I.n_target); ++s) {
     if (!A.relax) {
-      if (lane == 0) S.TH[N] = 0.f;  // new link at the tip
+      if (tm.r == 0) S.TH[N] = 0.f;  // new link at the tip
       N += 1;
       l = 0.f;
     }
-    __syncwarp();
+    tm.sync();
     StepStats st{0, 0.0, 0, 0, 0, 0};
-    const int res = step_solve<KS>(A, I, S, N, l, lane, st, inst);
+    const int res = step_solve<KS, TP>(A, I, S, N, l, tm, st, inst);
     iters += st.iters;
     evals += st.evals;
     linkevals += st.linkevals;
@@ -1032,9 +1202,9 @@ __device__ void process_instance(const GrowArgs& A, int inst, const Smem& S, int
     }
     if (status == kNonFinite) break;
   }
-  __syncwarp();
-  for (int k = lane; k < N; k += 32) A.theta[I.th_off + k] = S.TH[k];
-  if (lane == 0) {
+  tm.sync();
+  for (int k = tm.r; k < N; k += TP) A.theta[I.th_off + k] = S.TH[k];
+  if (tm.r == 0) {
     A.n_cur[inst] = N;
     A.l_cur[inst] = l;
     A.status[inst] = status;
@@ -1049,14 +1219,15 @@ __device__ void process_instance(const GrowArgs& A, int inst, const Smem& S, int
     A.cycles[inst] += clock64() - t_start;
     if (!(rmax <= A.resid_max[inst])) A.resid_max[inst] = rmax;
   }
-  __syncwarp();
+  tm.sync();
 }
 
 template <int KS>
 __global__ void __launch_bounds__(32 * kWarpsPerCta, 3) grow_kernel(const GrowArgs A) {
   extern __shared__ float4 smem4[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const Smem S = carve(reinterpret_cast<float*>(smem4) + (size_t)warp * A.warp_floats, A);
+  const Smem S = carve<32>(reinterpret_cast<float*>(smem4) + (size_t)warp * A.warp_floats, A);
+  const Team<32> tm{lane, S.TS};
   const int gw = blockIdx.x * (blockDim.x >> 5) + warp;
   const int nw = gridDim.x * (blockDim.x >> 5);
   for (int round = 0;; ++round) {
@@ -1069,7 +1240,30 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, 3) grow_kernel(const GrowAr
       idx = gw + round * nw;
     }
     if (idx >= A.n_order) break;
-    process_instance<KS>(A, A.order[idx], S, lane);
+    process_instance<KS, 32>(A, A.order[idx], S, tm);
+  }
+}
+
+// Two warps per robot: one robot per 64-thread CTA, the same code with the
+// team operations across the two warps.
+template <int KS>
+__global__ void __launch_bounds__(64, 6) grow_kernel_team(const GrowArgs A) {
+  extern __shared__ float4 smem4[];
+  __shared__ int next;
+  const Smem S = carve<64>(reinterpret_cast<float*>(smem4), A);
+  const Team<64> tm{(int)threadIdx.x, S.TS};
+  for (int round = 0;; ++round) {
+    int idx;
+    if (A.dynamic) {
+      if (tm.r == 0) next = atomicAdd(A.counter, 1);
+      __syncthreads();
+      idx = next;
+      __syncthreads();
+    } else {
+      idx = blockIdx.x + round * gridDim.x;
+    }
+    if (idx >= A.n_order) break;
+    process_instance<KS, 64>(A, A.order[idx], S, tm);
   }
 }
 
@@ -1081,22 +1275,23 @@ __global__ void __launch_bounds__(32) probe_kernel(const GrowArgs A, int inst, i
                                                    int* out_lfix) {
   extern __shared__ float4 smem4[];
   const int lane = threadIdx.x & 31;
-  const Smem S = carve(reinterpret_cast<float*>(smem4), A);
+  const Smem S = carve<32>(reinterpret_cast<float*>(smem4), A);
+  const Team<32> tm{(int)(threadIdx.x & 31), S.TS};
   const InstDev I = A.inst[inst];
   for (int k = lane; k < I.n_obs; k += 32) S.obs[k] = A.obs[I.obs_off + k];
   for (int k = lane; k < I.n_act; k += 32) S.act[k] = A.act[I.act_off + k];
   for (int k = lane; k < N; k += 32) S.TH[k] = theta[k];
-  reset_lists(S, N, lane);
-  EvalOut E = eval<KS>(A, I, S, N, l, lane, A.exact != 0);
+  reset_lists(S, N, tm);
+  EvalOut E = eval<KS, 32>(A, I, S, N, l, tm, A.exact != 0);
   for (int k = lane; k < N; k += 32) out_g[k] = S.G[k];
   __syncwarp();
   const bool lfix = (l <= 0.f && E.gl > 0.f) || (l >= I.l_seg && E.gl < 0.f);
   float dl;
   float mdth;
-  double r = gn_solve(I, S, N, lfix, E, dl, lane, A.exact != 0, mdth);
+  double r = gn_solve(I, S, N, lfix, E, dl, tm, A.exact != 0, mdth);
   if (A.exact != 0 && !(r >= 0.0 && isfinite(r))) {
-    E = eval<KS>(A, I, S, N, l, lane, false);
-    r = gn_solve(I, S, N, lfix, E, dl, lane, false, mdth);
+    E = eval<KS, 32>(A, I, S, N, l, tm, false);
+    r = gn_solve(I, S, N, lfix, E, dl, tm, false, mdth);
   }
   for (int k = lane; k < N; k += 32) out_dx[k] = S.DTH[k];
   if (lane == 0) {
@@ -1134,6 +1329,7 @@ __device__ __forceinline__ float spam_force(const GrowArgs& A, int tid, float e)
 // state (bad input or non-finite; cost and derivatives NaN).
 template <int KS>
 __device__ void grad_instance(const GrowArgs& A, const GradArgs& G, int inst, const Smem& S, int lane) {
+  const Team<32> tm{lane, S.TS};
   const InstDev I = A.inst[inst];
   const int N = A.n_cur[inst];
   const int st = A.status[inst];
@@ -1156,8 +1352,8 @@ __device__ void grad_instance(const GrowArgs& A, const GradArgs& G, int inst, co
   for (int k = lane; k < I.n_act; k += 32) S.act[k] = A.act[I.act_off + k];
   for (int k = lane; k < N; k += 32) S.TH[k] = A.theta[I.th_off + k];
   const float l = A.l_cur[inst];
-  reset_lists(S, N, lane);
-  EvalOut E = eval<KS>(A, I, S, N, l, lane, true);
+  reset_lists(S, N, tm);
+  EvalOut E = eval<KS, 32>(A, I, S, N, l, tm, true);
   const bool lfix = (l <= 0.f && E.gl > 0.f) || (l >= I.l_seg && E.gl < 0.f);
   // tip relative to the base, and dc/dtheta_j = s . (z x (p_N - p_j))
   const int B = (N + 31) >> 5;
@@ -1180,7 +1376,7 @@ __device__ void grad_instance(const GrowArgs& A, const GradArgs& G, int inst, co
   E.gl = -(ux * E.ulx + uy * E.uly);
   __syncwarp();
   float dl, mdth;
-  const double r = gn_solve(I, S, N, lfix, E, dl, lane, true, mdth);
+  const double r = gn_solve(I, S, N, lfix, E, dl, tm, true, mdth);
   const bool ok = r >= 0.0 && isfinite(r);
   for (int a = 0; a < I.n_act; ++a) {
     const float4 ac = S.act[a];
@@ -1221,7 +1417,7 @@ template <int KS>
 __global__ void __launch_bounds__(32) grad_kernel(const GrowArgs A, const GradArgs G) {
   extern __shared__ float4 smem4[];
   const int lane = threadIdx.x & 31;
-  const Smem S = carve(reinterpret_cast<float*>(smem4), A);
+  const Smem S = carve<32>(reinterpret_cast<float*>(smem4), A);
   for (int idx = blockIdx.x; idx < A.n_order; idx += gridDim.x) grad_instance<KS>(A, G, A.order[idx], S, lane);
 }
 
@@ -1230,7 +1426,20 @@ const void* kernel_ptr() {
   return reinterpret_cast<const void*>(&grow_kernel<KS>);
 }
 
-const void* pick(int ks) {
+template <int KS>
+const void* team_kernel_ptr() {
+  return reinterpret_cast<const void*>(&grow_kernel_team<KS>);
+}
+
+const void* pick(int ks, int team) {
+  if (team == 64) {
+    switch (ks) {
+      case 1: return team_kernel_ptr<1>();
+      case 2: return team_kernel_ptr<2>();
+      case 3: return team_kernel_ptr<3>();
+      default: return team_kernel_ptr<4>();
+    }
+  }
   switch (ks) {
     case 1: return kernel_ptr<1>();
     case 2: return kernel_ptr<2>();
@@ -1241,30 +1450,31 @@ const void* pick(int ks) {
 
 }  // namespace
 
-size_t grow_smem_per_warp(int nmax, int omax, int amax) {
+size_t grow_smem_per_warp(int nmax, int omax, int amax, int team) {
   return sizeof(float4) * (size_t)(omax + amax) + sizeof(float) * (16 * (size_t)nmax + 8) +
-         sizeof(int) * 32 * (size_t)kContactQueue + sizeof(float) * 7 * (size_t)nmax +
+         sizeof(int) * (size_t)team * kContactQueue + sizeof(float) * 16 + sizeof(float) * 7 * (size_t)nmax +
          ((sizeof(unsigned short) * (kListCap + 1) * (size_t)nmax + 15) & ~size_t(15));
 }
 
 // The attribute is per kernel and process-wide: batches and servers with
 // different slices share it, so it is only ever raised.
-cudaError_t grow_configure(int ks, size_t smem_per_cta) {
+cudaError_t grow_configure(int ks, size_t smem_per_cta, int team) {
   static std::mutex mu;
-  static std::map<std::pair<int, int>, size_t> set;  // (device, K_s) -> bytes
+  static std::map<std::pair<int, int>, size_t> set;  // (device, K_s + 8 for the team kernel) -> bytes
   int dev = 0;
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lk(mu);
-  size_t& cur = set[{dev, ks}];
+  size_t& cur = set[{dev, ks + (team == 64 ? 8 : 0)}];
   if (smem_per_cta <= cur) return cudaSuccess;
-  const cudaError_t e = cudaFuncSetAttribute(pick(ks), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_per_cta);
+  const cudaError_t e =
+      cudaFuncSetAttribute(pick(ks, team), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_per_cta);
   if (e == cudaSuccess) cur = smem_per_cta;
   return e;
 }
 
-int grow_max_ctas_per_sm(int ks, size_t smem_per_cta, int threads) {
+int grow_max_ctas_per_sm(int ks, size_t smem_per_cta, int threads, int team) {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick(ks), threads, smem_per_cta) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pick(ks, team), threads, smem_per_cta) != cudaSuccess) return 0;
   return n;
 }
 
@@ -1272,10 +1482,17 @@ int grow_max_ctas_per_sm(int ks, size_t smem_per_cta, int threads) {
 // warp slice of smem_warp bytes (a robot's obstacles and link arrays are
 // per warp, so smaller CTAs pack large slices more tightly); ties go to the
 // larger CTA.  Sets the kernel's shared-memory limit for the choice.
-int grow_pick_block(int ks, size_t smem_warp, int* ctas_per_sm) {
+int grow_pick_block(int ks, size_t smem_warp, int* ctas_per_sm, int team) {
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (team == 64) {  // one two-warp team (robot) per CTA
+    int c = 0;
+    if (smem_warp <= (size_t)optin && grow_configure(ks, smem_warp, 64) == cudaSuccess)
+      c = grow_max_ctas_per_sm(ks, smem_warp, 64, 64);
+    if (ctas_per_sm) *ctas_per_sm = c;
+    return c > 0 ? 1 : 0;
+  }
   int best_w = 0, best_c = 0;
   // two-warp CTAs first: at equal resident warps they measured faster than
   // four-warp CTAs on uniform and uneven batches alike
@@ -1295,6 +1512,15 @@ int grow_pick_block(int ks, size_t smem_warp, int* ctas_per_sm) {
 }
 
 cudaError_t launch_grow(const GrowArgs& a, int ks, int grid, int block, size_t smem, cudaStream_t s) {
+  if (a.team == 64) {
+    switch (ks) {
+      case 1: grow_kernel_team<1><<<grid, 64, smem, s>>>(a); break;
+      case 2: grow_kernel_team<2><<<grid, 64, smem, s>>>(a); break;
+      case 3: grow_kernel_team<3><<<grid, 64, smem, s>>>(a); break;
+      default: grow_kernel_team<4><<<grid, 64, smem, s>>>(a); break;
+    }
+    return cudaGetLastError();
+  }
   switch (ks) {
     case 1: grow_kernel<1><<<grid, block, smem, s>>>(a); break;
     case 2: grow_kernel<2><<<grid, block, smem, s>>>(a); break;

@@ -83,6 +83,7 @@ struct GrowArgs {
   int mode;           // 0 equilibrium; 1 Algorithm 1 read literally (frozen actuator force, descent)
   int gd_steps;       // mode 1: descent steps per growth step
   float gd_alpha;     // mode 1: step as a fraction of the free-space Newton step
+  int team;           // threads per robot: 32 (0 reads as 32) or 64
   int relax;          // 1: re-solve the present links without adding one (vine_relax)
   int fix_l;          // 1: hold the distal length fixed while solving
   // diagnostics: per line-search trial records of one robot (off when null)
@@ -160,11 +161,13 @@ cudaError_t launch_synth(int n_targets, const double* target, int n_p, int n_l0,
 void set_last_error(const char* msg, const char* detail = nullptr);
 
 // Growth kernel -- vine_grow.cu
+// team: threads per robot, 32 (one warp; several robots per CTA) or 64 (two
+// warps; one robot per CTA, a.team = 64 selects that kernel)
 cudaError_t launch_grow(const GrowArgs& a, int ks, int grid, int block, size_t smem, cudaStream_t s);
-size_t grow_smem_per_warp(int nmax, int omax, int amax);
-cudaError_t grow_configure(int ks, size_t smem_per_cta);
-int grow_max_ctas_per_sm(int ks, size_t smem_per_cta, int threads);
-int grow_pick_block(int ks, size_t smem_warp, int* ctas_per_sm);  // warps per CTA, 0 if none fits
+size_t grow_smem_per_warp(int nmax, int omax, int amax, int team = 32);
+cudaError_t grow_configure(int ks, size_t smem_per_cta, int team = 32);
+int grow_max_ctas_per_sm(int ks, size_t smem_per_cta, int threads, int team = 32);
+int grow_pick_block(int ks, size_t smem_warp, int* ctas_per_sm, int team = 32);  // robots per CTA, 0 if none fits
 cudaError_t launch_probe(const GrowArgs& a, int ks, int inst, int N, const float* theta, float l, double* J,
                          float* g, float* dx, double* r, int* lfix, size_t smem, cudaStream_t s);
 cudaError_t launch_grad(const GrowArgs& a, const GradArgs& g, int ks, int grid, size_t smem, cudaStream_t s);

@@ -34,7 +34,8 @@ class vine_params(C.Structure):
                 ("pen_frac", C.c_double), ("tol", C.c_double), ("fval_eps", C.c_double),
                 ("armijo_c1", C.c_double), ("max_iter", C.c_int32), ("discs_per_link", C.c_int32),
                 ("max_halvings", C.c_int32), ("mode", C.c_int32), ("gd_alpha", C.c_double),
-                ("gd_steps", C.c_int32), ("exact_hessian", C.c_int32), ("broad_phase", C.c_int32)]
+                ("gd_steps", C.c_int32), ("exact_hessian", C.c_int32), ("broad_phase", C.c_int32),
+                ("threads_per_robot", C.c_int32)]
 
 
 class vine_batch_desc(C.Structure):

@@ -35,6 +35,17 @@ def _oracle(sc, tol=1e-10):
     return oracle.Oracle(sc, oracle.default_params(tol=tol))
 
 
+def _prm(tp):
+    """Library parameters with `tp` threads per robot (32: one warp; 64: a
+    two-warp team)."""
+    p = vine.vine_params_default()
+    p.threads_per_robot = tp
+    return p
+
+
+TEAMS = pytest.mark.parametrize("tp", [32, 64])
+
+
 def test_prologue_tables_match_oracle():
     sc = scenes.design_batch(16)
     b = vine.Batch(sc)
@@ -116,10 +127,11 @@ def _classify(b, st, orc, ost, sc, counts, pairs, idx_gpu=None):
     return out
 
 
-def test_parity_batch_full():
+@TEAMS
+def test_parity_batch_full(tp):
     """64 robots x 20 steps, independent trajectories."""
     sc = scenes.parity_batch()
-    b = vine.Batch(sc)
+    b = vine.Batch(sc, _prm(tp))
     b.simulate()
     st = b.state()
     counts, pairs = b.contacts(64)
@@ -144,12 +156,12 @@ def _to_fp32(ost):
     ost["l"][:] = ost["l"].astype(np.float32)
 
 
-def _stepwise(sc, steps):
+def _stepwise(sc, steps, tp=32):
     """Each step, both sides start from the oracle's previous state (rounded
     to FP32 and loaded into the GPU batch with vine_set_state); returns the
     classification counts over all robot-steps."""
     n = sc["n_links"].size
-    b = vine.Batch(sc)
+    b = vine.Batch(sc, _prm(tp))
     orc = _oracle(sc)
     ost = orc.new_state()
     tally = {"match": 0, "tol": 0, "switch": 0, "flagged": 0}
@@ -176,24 +188,26 @@ def _stepwise(sc, steps):
     return tally
 
 
-def test_parity_batch_stepwise_resynced():
+@TEAMS
+def test_parity_batch_stepwise_resynced(tp):
     """Each step, both sides start from the oracle's previous state; the
     step's result must match unless that step is a snap-through to another
     valid equilibrium."""
     sc = scenes.parity_batch()
-    tally = _stepwise(sc, 20)
+    tally = _stepwise(sc, 20, tp)
     print("stepwise: %s in %d robot-steps" % (tally, 20 * 64))
     assert tally["flagged"] == 0
     assert tally["switch"] <= 0.01 * 20 * 64
 
 
-def test_uneven_stepwise_resynced_parity():
+@TEAMS
+def test_uneven_stepwise_resynced_parity(tp):
     """Uneven robots (40-90 links, 5-200 obstacles, 0-8 actuators), resynced
     every step: over a whole growth the trajectories of two solvers can part
     at a snap-through, but single steps from the same state agree."""
     sc = scenes.uneven_batch(12, n_range=(40, 90))
     steps = int(sc["n_links"].max())
-    tally = _stepwise(sc, steps)
+    tally = _stepwise(sc, steps, tp)
     total = int(sc["n_links"].sum())
     print("uneven stepwise: %s (robot-steps with growth: %d)" % (tally, total))
     assert tally["switch"] <= 0.02 * total
@@ -213,11 +227,12 @@ def test_plain_form_is_bitwise_identical():
     b1.close(); b2.close()
 
 
-def test_design_batch_full_size_sampled():
-    """4096 robots x 100 links in the launch the benchmark times; 12 sampled
-    robots recomputed by the oracle."""
+@TEAMS
+def test_design_batch_full_size_sampled(tp):
+    """4096 robots x 100 links in the launch the benchmark times (one-warp
+    and two-warp teams); 12 sampled robots recomputed by the oracle."""
     sc = scenes.design_batch()
-    b = vine.Batch(sc)
+    b = vine.Batch(sc, _prm(tp))
     b.simulate()
     torch.cuda.synchronize()
     st = b.state()
