@@ -51,7 +51,7 @@ def test_nodes_replay_bitwise_from_their_designs():
     pick = list(rng.choice(deep, min(12, len(deep)), replace=False)) if deep else []
     pick += list(rng.choice(np.arange(1, p.size), 12, replace=False))
     scs = [p.design_scene(int(k)) for k in pick]
-    b = vine.Batch(scenes.concat(scs))
+    b = vine.Batch(scenes.concat(scs), p.params)
     b.simulate()
     st = b.state()
     for j, k in enumerate(pick):
