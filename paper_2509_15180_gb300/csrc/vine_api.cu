@@ -1014,7 +1014,7 @@ vine_status vine_grad(const vine_batch* B, const float* goal_xy, double* cost, d
   const int n = B->n_inst;
   const size_t na = (size_t)B->n_act;
   // one warp per CTA, several CTAs per SM; the robots come longest first
-  const int grid = std::max(1, std::min(n, B->grid * B->wpc));
+  const int grid = std::max(1, std::min(n, B->grid * B->wpc * (B->team / 32)));  // resident warps
   GradArgs g{};
   if (ptrs_are_device) {
     g.goal = goal_xy;
