@@ -417,9 +417,13 @@ def serve_leg(args, vine, scenes):
 def uneven_leg(args, vine, scenes, torch, stream, flush):
     """Uneven persistent batch (links U{30..300}, 0-8 actuators, 5-200
     obstacles): robot-link-steps/s of vine_simulate with the launch
-    configuration picked at creation, then after vine_autotune on a sample."""
+    configuration picked at creation, then after vine_autotune on a sample.
+    Teams of --uneven-threads-per-robot threads (four warps by default: the
+    longest robots set the launch)."""
     sc = scenes.uneven_batch(args.uneven_robots)
-    b = vine.Batch(sc, stream=stream)
+    prm = vine.vine_params_default()
+    prm.threads_per_robot = args.uneven_threads_per_robot
+    b = vine.Batch(sc, prm, stream=stream)
 
     def timed(k):
         b.reset(stream)
@@ -445,6 +449,7 @@ def uneven_leg(args, vine, scenes, torch, stream, flush):
     return {"workload": "uneven batch: %d robots, links U{30..300} of U[1,3] cm, 5-200 obstacles, 0-8 actuators"
                         % args.uneven_robots,
             "robot_link_steps_per_step": scenes.robot_link_steps(sc["n_links"]),
+            "threads_per_robot": args.uneven_threads_per_robot,
             "default": {"value": v0, "ms_per_step": ms0},
             "autotuned": {"value": v1, "ms_per_step": ms1, "warps_per_cta": tune["warps_per_cta"],
                           "list_margin_R": tune["list_margin"], "candidates": tune["candidates"],
@@ -663,8 +668,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--robots", type=int, default=4096, help="robots per GPU (the workload has 4096)")
-    ap.add_argument("--threads-per-robot", type=int, default=64, choices=[32, 64],
-                    help="design-batch legs: one warp (32) or a two-warp team (64) per robot")
+    ap.add_argument("--threads-per-robot", type=int, default=64, choices=[32, 64, 128],
+                    help="design-batch legs: one warp (32) or a team of two (64) or four (128) warps per robot")
     ap.add_argument("--plain-robots", type=int, default=64)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-robots", type=int, default=96)
@@ -674,6 +679,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-overlap", action="store_true")
     ap.add_argument("--uneven-robots", type=int, default=4096)
+    ap.add_argument("--uneven-threads-per-robot", type=int, default=128, choices=[32, 64, 128])
     ap.add_argument("--uneven-sample", type=int, default=2048)
     ap.add_argument("--robust-designs", type=int, default=64)
     ap.add_argument("--robust-perturb", type=int, default=32)

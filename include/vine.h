@@ -94,10 +94,10 @@ typedef enum {
  *   is positive definite, else with the Gauss-Newton matrix (contact second
  *   derivatives dropped); 0 = always Gauss-Newton (default 1).
  * threads_per_robot: 32 = one warp grows a robot (default; several robots
- *   per CTA); 64 = two warps of one CTA share a robot's link loops, which
- *   shortens each robot's evaluation at the cost of fewer robots per SM.
- *   The two agree to rounding (sums over 32 and over 64 threads round
- *   differently), not bitwise.  0 reads as 32.
+ *   per CTA); 64 or 128 = two or four warps of one CTA share a robot's link
+ *   loops, which shortens each robot's evaluation at the cost of fewer
+ *   robots per SM.  Team sizes agree to rounding (sums over different
+ *   thread counts round differently), not bitwise.  0 reads as 32.
  * broad_phase: 1 = each link tests only the obstacles on a list built when
  *   it last moved by more than 0.4 body radii (the result is the same as
  *   with 0, which tests every obstacle at every evaluation; default 1). */

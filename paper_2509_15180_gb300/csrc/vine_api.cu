@@ -297,7 +297,8 @@ vine_status vine_batch_create(const vine_batch_desc* D, const vine_params* P, vo
   if (!(prm.tol > 0.0) || prm.max_iter < 1 || prm.max_halvings < 0 || !(prm.eps_crit > 0.0 && prm.eps_crit < 1.0) ||
       !(prm.R_c > 0.0 && prm.R_act > prm.R_c) || !(prm.m_lo > 0.0 && prm.m_lo < 0.5) || !(prm.pen_frac > 0.0) || !(prm.fval_eps >= 0.0) || !(prm.armijo_c1 > 0.0 && prm.armijo_c1 < 0.5) ||
       (prm.mode != 0 && prm.mode != 1) || (prm.mode == 1 && (prm.gd_steps < 1 || !(prm.gd_alpha > 0.0))) ||
-      (prm.threads_per_robot != 0 && prm.threads_per_robot != 32 && prm.threads_per_robot != 64))
+      (prm.threads_per_robot != 0 && prm.threads_per_robot != 32 && prm.threads_per_robot != 64 &&
+       prm.threads_per_robot != 128))
     return fail(VINE_EINVAL, "vine_batch_create: parameter out of range");
   const int n = D->n_inst;
   if (n <= 0) return fail(VINE_EINVAL, "vine_batch_create: n_inst must be positive");
@@ -574,7 +575,7 @@ vine_status vine_batch_create(const vine_batch_desc* D, const vine_params* P, vo
   B->nmax = (nmax + 31) & ~31;
   B->omax = omax;
   B->amax = amax;
-  B->team = prm.threads_per_robot == 64 ? 64 : 32;
+  B->team = prm.threads_per_robot > 32 ? prm.threads_per_robot : 32;
   B->smem_warp = grow_smem_per_warp(B->nmax, B->omax, B->amax, B->team);
   int dev_id = 0, nsm = 1;
   cudaGetDevice(&dev_id);
@@ -750,7 +751,7 @@ vine_status vine_autotune(vine_batch* B, int32_t sample, void* stream_v, vine_tu
   out->default_ms = -1.0;
   out->sample = ns;
   vine_status rs = VINE_OK;
-  for (int w = B->team == 64 ? 1 : kWarpsPerCta; w >= 1 && rs == VINE_OK; w >>= 1) {
+  for (int w = B->team > 32 ? 1 : kWarpsPerCta; w >= 1 && rs == VINE_OK; w >>= 1) {
     const size_t smem = B->smem_warp * w;
     if (grow_configure(B->ks, smem, B->team) != cudaSuccess) continue;
     const int ctas = grow_max_ctas_per_sm(B->ks, smem, B->team * w, B->team);

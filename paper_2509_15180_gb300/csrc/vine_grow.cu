@@ -92,15 +92,22 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // A team of TP threads owns one robot: one warp (TP = 32, the default), or
-// two warps of one CTA (TP = 64), which split the link loops in half.  The
-// team operations below are the warp's own for TP = 32; for TP = 64 the two
-// warps' partial results meet in shared-memory scratch between CTA barriers.
-// Every branch around them depends only on team-uniform values (reductions,
-// broadcasts, the robot's sizes), so both warps reach every barrier.
+// TP / 32 warps of one CTA (TP = 64 or 128), which split the link loops.
+// The team operations below are the warp's own for TP = 32; for larger
+// teams the warps' partial results meet in shared-memory scratch between CTA
+// barriers and are combined in warp order.  Every branch around them depends
+// only on team-uniform values (reductions, broadcasts, the robot's sizes),
+// so all warps reach every barrier.
+// Scratch layout (floats): FF scan totals [0, 8), suffix totals [8, 12),
+// broadcast [12], sweep results [16, 20), double sums [20, 28), float sums
+// [28, 32), int sums and counts [32, 36), maxima [36, 40), flags [40, 44).
+constexpr int kTeamScratch = 48;
+
 template <int TP>
 struct Team {
   int r;       // rank in the team
   float* scr;  // S.TS
+  static constexpr int W = TP / 32;
   __device__ __forceinline__ int lane() const { return r & 31; }
   __device__ __forceinline__ int warp() const { return r >> 5; }
   __device__ __forceinline__ void sync() const {
@@ -115,13 +122,15 @@ template <int TP>
 __device__ __forceinline__ FF team_excl_scan(FF v, const Team<TP>& t) {
   FF x = warp_excl_scan(v, t.lane());
   if (TP == 32) return x;
-  if (t.r == 31) {
-    const FF inc = ff_add(x, v);  // warp 0's total
-    t.scr[0] = inc.hi;
-    t.scr[1] = inc.lo;
+  if (t.lane() == 31) {
+    const FF inc = ff_add(x, v);  // this warp's total
+    t.scr[2 * t.warp()] = inc.hi;
+    t.scr[2 * t.warp() + 1] = inc.lo;
   }
   t.sync();
-  if (t.warp() == 1) x = ff_add(FF{t.scr[0], t.scr[1]}, x);
+  FF below{0.f, 0.f};
+  for (int w = 0; w < t.warp(); ++w) below = ff_add(below, FF{t.scr[2 * w], t.scr[2 * w + 1]});
+  if (t.warp() > 0) x = ff_add(below, x);
   t.sync();
   return x;
 }
@@ -130,9 +139,11 @@ template <int TP>
 __device__ __forceinline__ float team_excl_suffix(float v, const Team<TP>& t) {
   float x = warp_excl_suffix(v, t.lane());
   if (TP == 32) return x;
-  if (t.r == 32) t.scr[2] = x + v;  // warp 1's total
+  if (t.lane() == 0) t.scr[8 + t.warp()] = x + v;  // this warp's total
   t.sync();
-  if (t.warp() == 0) x += t.scr[2];
+  float above = 0.f;
+  for (int w = Team<TP>::W - 1; w > t.warp(); --w) above += t.scr[8 + w];
+  x += above;
   t.sync();
   return x;
 }
@@ -141,10 +152,11 @@ template <int TP>
 __device__ __forceinline__ double team_sum(double v, const Team<TP>& t) {
   v = warp_sum(v);
   if (TP == 32) return v;
-  double* d = reinterpret_cast<double*>(t.scr + 4);
+  double* d = reinterpret_cast<double*>(t.scr + 20);
   if (t.lane() == 0) d[t.warp()] = v;
   t.sync();
-  const double s = d[0] + d[1];
+  double s = d[0];
+  for (int w = 1; w < Team<TP>::W; ++w) s += d[w];
   t.sync();
   return s;
 }
@@ -154,9 +166,10 @@ __device__ __forceinline__ float team_sum_f(float v, const Team<TP>& t) {
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
   if (TP == 32) return v;
-  if (t.lane() == 0) t.scr[8 + t.warp()] = v;
+  if (t.lane() == 0) t.scr[28 + t.warp()] = v;
   t.sync();
-  const float s = t.scr[8] + t.scr[9];
+  float s = t.scr[28];
+  for (int w = 1; w < Team<TP>::W; ++w) s += t.scr[28 + w];
   t.sync();
   return s;
 }
@@ -166,10 +179,11 @@ __device__ __forceinline__ int team_sum_i(int v, const Team<TP>& t) {
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
   if (TP == 32) return v;
-  int* q = reinterpret_cast<int*>(t.scr + 10);
+  int* q = reinterpret_cast<int*>(t.scr + 32);
   if (t.lane() == 0) q[t.warp()] = v;
   t.sync();
-  const int s = q[0] + q[1];
+  int s = 0;
+  for (int w = 0; w < Team<TP>::W; ++w) s += q[w];
   t.sync();
   return s;
 }
@@ -179,32 +193,34 @@ __device__ __forceinline__ float team_max(float v, const Team<TP>& t) {
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, d));
   if (TP == 32) return v;
-  if (t.lane() == 0) t.scr[12 + t.warp()] = v;
+  if (t.lane() == 0) t.scr[36 + t.warp()] = v;
   t.sync();
-  const float m = fmaxf(t.scr[12], t.scr[13]);
+  float m = t.scr[36];
+  for (int w = 1; w < Team<TP>::W; ++w) m = fmaxf(m, t.scr[36 + w]);
   t.sync();
   return m;
 }
 
 template <int TP>
 __device__ __forceinline__ bool team_any(bool b, const Team<TP>& t) {
-  const bool w = __any_sync(kFull, b);
-  if (TP == 32) return w;
-  int* q = reinterpret_cast<int*>(t.scr + 14);
-  if (t.lane() == 0) q[t.warp()] = w ? 1 : 0;
+  const bool wb = __any_sync(kFull, b);
+  if (TP == 32) return wb;
+  int* q = reinterpret_cast<int*>(t.scr + 40);
+  if (t.lane() == 0) q[t.warp()] = wb ? 1 : 0;
   t.sync();
-  const bool a = (q[0] | q[1]) != 0;
+  int a = 0;
+  for (int w = 0; w < Team<TP>::W; ++w) a |= q[w];
   t.sync();
-  return a;
+  return a != 0;
 }
 
 // value of rank `owner`, for every rank
 template <int TP>
 __device__ __forceinline__ float team_bcast(float v, int owner, const Team<TP>& t) {
   if (TP == 32) return __shfl_sync(kFull, v, owner);
-  if (t.r == owner) t.scr[3] = v;
+  if (t.r == owner) t.scr[12] = v;
   t.sync();
-  const float b = t.scr[3];
+  const float b = t.scr[12];
   t.sync();
   return b;
 }
@@ -218,17 +234,20 @@ __device__ __forceinline__ int team_excl_scan_i(int v, int& total, const Team<TP
     const int o = __shfl_up_sync(kFull, off, d);
     if (t.lane() >= d) off += o;
   }
-  int wt = __shfl_sync(kFull, off, 31);  // the warp's total
+  const int wt = __shfl_sync(kFull, off, 31);  // the warp's total
   off -= v;
   if (TP == 32) {
     total = wt;
     return off;
   }
-  int* q = reinterpret_cast<int*>(t.scr + 10);
+  int* q = reinterpret_cast<int*>(t.scr + 32);
   if (t.lane() == 0) q[t.warp()] = wt;
   t.sync();
-  total = q[0] + q[1];
-  if (t.warp() == 1) off += q[0];
+  total = 0;
+  for (int w = 0; w < Team<TP>::W; ++w) {
+    if (w < t.warp()) off += q[w];
+    total += q[w];
+  }
   t.sync();
   return off;
 }
@@ -240,7 +259,7 @@ struct Smem {
   float *TH, *TH0, *DTH, *LUX, *LUY, *G, *DD, *C0, *C1, *C2, *C3, *C4, *C5, *FX, *FY, *TL;
   float* LX;  // distal-link couplings: g_l contact part, h_ll, q0, q1, q2
   int* Q;     // contact candidates of the link in progress, [kContactQueue][team threads]
-  float* TS;  // team scratch (two-warp teams): 16 floats
+  float* TS;  // team scratch (teams of several warps): kTeamScratch floats
   unsigned short* CL;  // per link: obstacle list near it, [count, index...] x (kListCap + 1)
   float* XB;           // per link: its end points when its list was built, [4]
   float* PB;           // per link: its start point at the current evaluation, [2]
@@ -260,7 +279,7 @@ __device__ __forceinline__ Smem carve(float* base, const GrowArgs& A) {
   s.LX = p + 16 * n;
   s.Q = reinterpret_cast<int*>(p + 16 * n + 8);
   s.TS = p + 16 * n + 8 + TP * kContactQueue;
-  s.XB = s.TS + 16;
+  s.XB = s.TS + kTeamScratch;
   s.PB = s.XB + 4 * n;
   s.RQ = reinterpret_cast<int*>(s.PB + 2 * n);
   s.CL = reinterpret_cast<unsigned short*>(s.RQ + n);
@@ -603,13 +622,16 @@ __device__ void rebuild_lists(const InstDev& I, const Smem& S, int N, int j0, in
         }
       }
       const unsigned bal = __ballot_sync(kFull, near);
-      int before = 0, here = __popc(bal);  // near obstacles of the lower warp, of this chunk
+      int before = 0, here = __popc(bal);  // near obstacles of the lower warps, and of the chunk
       if (TP > 32) {
-        int* q = reinterpret_cast<int*>(tm.scr + 10);
+        int* q = reinterpret_cast<int*>(tm.scr + 32);
         if (lane == 0) q[tm.warp()] = here;
         tm.sync();
-        before = tm.warp() == 1 ? q[0] : 0;
-        here = q[0] + q[1];
+        here = 0;
+        for (int w = 0; w < Team<TP>::W; ++w) {
+          if (w < tm.warp()) before += q[w];
+          here += q[w];
+        }
         tm.sync();
       }
       const int pos = cnt + before + __popc(bal & lt);
@@ -939,16 +961,16 @@ __device__ double gn_solve(const InstDev& I, const Smem& S, int N, bool lfix, co
   }
   if (TP > 32) {
     if (tm.r == 0) {
-      tm.scr[4] = pd ? 1.f : 0.f;
-      tm.scr[5] = rmax;
-      tm.scr[6] = dl;
-      tm.scr[7] = dmax;
+      tm.scr[16] = pd ? 1.f : 0.f;
+      tm.scr[17] = rmax;
+      tm.scr[18] = dl;
+      tm.scr[19] = dmax;
     }
     tm.sync();
-    pd = tm.scr[4] != 0.f;
-    rmax = tm.scr[5];
-    dl = tm.scr[6];
-    dmax = tm.scr[7];
+    pd = tm.scr[16] != 0.f;
+    rmax = tm.scr[17];
+    dl = tm.scr[18];
+    dmax = tm.scr[19];
     tm.sync();
     if (!pd) return -1.0;
   } else {
@@ -1244,14 +1266,14 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta, 3) grow_kernel(const GrowAr
   }
 }
 
-// Two warps per robot: one robot per 64-thread CTA, the same code with the
-// team operations across the two warps.
-template <int KS>
-__global__ void __launch_bounds__(64, 6) grow_kernel_team(const GrowArgs A) {
+// Several warps per robot: one robot per CTA of TP threads, the same code
+// with the team operations across the warps.
+template <int KS, int TP>
+__global__ void __launch_bounds__(TP, 384 / TP) grow_kernel_team(const GrowArgs A) {
   extern __shared__ float4 smem4[];
   __shared__ int next;
-  const Smem S = carve<64>(reinterpret_cast<float*>(smem4), A);
-  const Team<64> tm{(int)threadIdx.x, S.TS};
+  const Smem S = carve<TP>(reinterpret_cast<float*>(smem4), A);
+  const Team<TP> tm{(int)threadIdx.x, S.TS};
   for (int round = 0;; ++round) {
     int idx;
     if (A.dynamic) {
@@ -1263,7 +1285,7 @@ __global__ void __launch_bounds__(64, 6) grow_kernel_team(const GrowArgs A) {
       idx = blockIdx.x + round * gridDim.x;
     }
     if (idx >= A.n_order) break;
-    process_instance<KS, 64>(A, A.order[idx], S, tm);
+    process_instance<KS, TP>(A, A.order[idx], S, tm);
   }
 }
 
@@ -1426,18 +1448,26 @@ const void* kernel_ptr() {
   return reinterpret_cast<const void*>(&grow_kernel<KS>);
 }
 
-template <int KS>
+template <int KS, int TP>
 const void* team_kernel_ptr() {
-  return reinterpret_cast<const void*>(&grow_kernel_team<KS>);
+  return reinterpret_cast<const void*>(&grow_kernel_team<KS, TP>);
 }
 
 const void* pick(int ks, int team) {
   if (team == 64) {
     switch (ks) {
-      case 1: return team_kernel_ptr<1>();
-      case 2: return team_kernel_ptr<2>();
-      case 3: return team_kernel_ptr<3>();
-      default: return team_kernel_ptr<4>();
+      case 1: return team_kernel_ptr<1, 64>();
+      case 2: return team_kernel_ptr<2, 64>();
+      case 3: return team_kernel_ptr<3, 64>();
+      default: return team_kernel_ptr<4, 64>();
+    }
+  }
+  if (team == 128) {
+    switch (ks) {
+      case 1: return team_kernel_ptr<1, 128>();
+      case 2: return team_kernel_ptr<2, 128>();
+      case 3: return team_kernel_ptr<3, 128>();
+      default: return team_kernel_ptr<4, 128>();
     }
   }
   switch (ks) {
@@ -1452,7 +1482,7 @@ const void* pick(int ks, int team) {
 
 size_t grow_smem_per_warp(int nmax, int omax, int amax, int team) {
   return sizeof(float4) * (size_t)(omax + amax) + sizeof(float) * (16 * (size_t)nmax + 8) +
-         sizeof(int) * (size_t)team * kContactQueue + sizeof(float) * 16 + sizeof(float) * 7 * (size_t)nmax +
+         sizeof(int) * (size_t)team * kContactQueue + sizeof(float) * kTeamScratch + sizeof(float) * 7 * (size_t)nmax +
          ((sizeof(unsigned short) * (kListCap + 1) * (size_t)nmax + 15) & ~size_t(15));
 }
 
@@ -1464,7 +1494,7 @@ cudaError_t grow_configure(int ks, size_t smem_per_cta, int team) {
   int dev = 0;
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lk(mu);
-  size_t& cur = set[{dev, ks + (team == 64 ? 8 : 0)}];
+  size_t& cur = set[{dev, ks + 8 * (team / 64)}];
   if (smem_per_cta <= cur) return cudaSuccess;
   const cudaError_t e =
       cudaFuncSetAttribute(pick(ks, team), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_per_cta);
@@ -1486,10 +1516,10 @@ int grow_pick_block(int ks, size_t smem_warp, int* ctas_per_sm, int team) {
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (team == 64) {  // one two-warp team (robot) per CTA
+  if (team > 32) {  // one team (robot) per CTA
     int c = 0;
-    if (smem_warp <= (size_t)optin && grow_configure(ks, smem_warp, 64) == cudaSuccess)
-      c = grow_max_ctas_per_sm(ks, smem_warp, 64, 64);
+    if (smem_warp <= (size_t)optin && grow_configure(ks, smem_warp, team) == cudaSuccess)
+      c = grow_max_ctas_per_sm(ks, smem_warp, team, team);
     if (ctas_per_sm) *ctas_per_sm = c;
     return c > 0 ? 1 : 0;
   }
@@ -1514,10 +1544,19 @@ int grow_pick_block(int ks, size_t smem_warp, int* ctas_per_sm, int team) {
 cudaError_t launch_grow(const GrowArgs& a, int ks, int grid, int block, size_t smem, cudaStream_t s) {
   if (a.team == 64) {
     switch (ks) {
-      case 1: grow_kernel_team<1><<<grid, 64, smem, s>>>(a); break;
-      case 2: grow_kernel_team<2><<<grid, 64, smem, s>>>(a); break;
-      case 3: grow_kernel_team<3><<<grid, 64, smem, s>>>(a); break;
-      default: grow_kernel_team<4><<<grid, 64, smem, s>>>(a); break;
+      case 1: grow_kernel_team<1, 64><<<grid, 64, smem, s>>>(a); break;
+      case 2: grow_kernel_team<2, 64><<<grid, 64, smem, s>>>(a); break;
+      case 3: grow_kernel_team<3, 64><<<grid, 64, smem, s>>>(a); break;
+      default: grow_kernel_team<4, 64><<<grid, 64, smem, s>>>(a); break;
+    }
+    return cudaGetLastError();
+  }
+  if (a.team == 128) {
+    switch (ks) {
+      case 1: grow_kernel_team<1, 128><<<grid, 128, smem, s>>>(a); break;
+      case 2: grow_kernel_team<2, 128><<<grid, 128, smem, s>>>(a); break;
+      case 3: grow_kernel_team<3, 128><<<grid, 128, smem, s>>>(a); break;
+      default: grow_kernel_team<4, 128><<<grid, 128, smem, s>>>(a); break;
     }
     return cudaGetLastError();
   }

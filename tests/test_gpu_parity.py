@@ -36,14 +36,14 @@ def _oracle(sc, tol=1e-10):
 
 
 def _prm(tp):
-    """Library parameters with `tp` threads per robot (32: one warp; 64: a
-    two-warp team)."""
+    """Library parameters with `tp` threads per robot (32: one warp; 64, 128:
+    a team of two or four warps)."""
     p = vine.vine_params_default()
     p.threads_per_robot = tp
     return p
 
 
-TEAMS = pytest.mark.parametrize("tp", [32, 64])
+TEAMS = pytest.mark.parametrize("tp", [32, 64, 128])
 
 
 def test_prologue_tables_match_oracle():
