@@ -280,7 +280,7 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 residual test)", "data": "synthetic",
             "config": {"workload": WORKLOAD if n == 4096 else WORKLOAD.replace("4096", str(n)),
-                       "robots_per_gpu": n, "links": 100, "threads_per_robot": args.threads_per_robot,
+                       "robots_per_gpu": n, "links": 100, "threads_per_robot": b.launch()["threads_per_robot"],
                        "robot_link_steps_per_step": rls_per_step, "l2": "flushed between timed steps (512 MiB write)",
                        "tol": 1e-6},
             "e2e": e2e, "plain": plain, "latency": lat, "roofline": roofline, "cpu_baseline": cpu,
@@ -418,8 +418,8 @@ def uneven_leg(args, vine, scenes, torch, stream, flush):
     """Uneven persistent batch (links U{30..300}, 0-8 actuators, 5-200
     obstacles): robot-link-steps/s of vine_simulate with the launch
     configuration picked at creation, then after vine_autotune on a sample.
-    Teams of --uneven-threads-per-robot threads (four warps by default: the
-    longest robots set the launch)."""
+    Threads per robot from --uneven-threads-per-robot (0: the library's
+    choice by robot length, four warps for these robots)."""
     sc = scenes.uneven_batch(args.uneven_robots)
     prm = vine.vine_params_default()
     prm.threads_per_robot = args.uneven_threads_per_robot
@@ -443,13 +443,14 @@ def uneven_leg(args, vine, scenes, torch, stream, flush):
         return rls / (sum(ms) / 1e3), float(np.mean(ms))
 
     v0, ms0 = timed(2)
+    tpr = b.launch()["threads_per_robot"]
     tune = b.autotune(args.uneven_sample, stream)
     v1, ms1 = timed(2)
     b.close()
     return {"workload": "uneven batch: %d robots, links U{30..300} of U[1,3] cm, 5-200 obstacles, 0-8 actuators"
                         % args.uneven_robots,
             "robot_link_steps_per_step": scenes.robot_link_steps(sc["n_links"]),
-            "threads_per_robot": args.uneven_threads_per_robot,
+            "threads_per_robot": tpr,
             "default": {"value": v0, "ms_per_step": ms0},
             "autotuned": {"value": v1, "ms_per_step": ms1, "warps_per_cta": tune["warps_per_cta"],
                           "list_margin_R": tune["list_margin"], "candidates": tune["candidates"],
@@ -668,8 +669,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--robots", type=int, default=4096, help="robots per GPU (the workload has 4096)")
-    ap.add_argument("--threads-per-robot", type=int, default=64, choices=[32, 64, 128],
-                    help="design-batch legs: one warp (32) or a team of two (64) or four (128) warps per robot")
+    ap.add_argument("--threads-per-robot", type=int, default=0, choices=[0, 32, 64, 128],
+                    help="design-batch legs: threads per robot (0: the library's choice by robot length)")
     ap.add_argument("--plain-robots", type=int, default=64)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-robots", type=int, default=96)
@@ -679,7 +680,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-overlap", action="store_true")
     ap.add_argument("--uneven-robots", type=int, default=4096)
-    ap.add_argument("--uneven-threads-per-robot", type=int, default=128, choices=[32, 64, 128])
+    ap.add_argument("--uneven-threads-per-robot", type=int, default=0, choices=[0, 32, 64, 128])
     ap.add_argument("--uneven-sample", type=int, default=2048)
     ap.add_argument("--robust-designs", type=int, default=64)
     ap.add_argument("--robust-perturb", type=int, default=32)

@@ -93,11 +93,14 @@ typedef enum {
  * exact_hessian: 1 = Newton steps with the exact Hessian of the cost when it
  *   is positive definite, else with the Gauss-Newton matrix (contact second
  *   derivatives dropped); 0 = always Gauss-Newton (default 1).
- * threads_per_robot: 32 = one warp grows a robot (default; several robots
- *   per CTA); 64 or 128 = two or four warps of one CTA share a robot's link
- *   loops, which shortens each robot's evaluation at the cost of fewer
- *   robots per SM.  Team sizes agree to rounding (sums over different
- *   thread counts round differently), not bitwise.  0 reads as 32.
+ * threads_per_robot: 32 = one warp grows a robot (several robots per CTA);
+ *   64 or 128 = two or four warps of one CTA share a robot's link loops,
+ *   which shortens each robot's evaluation at the cost of fewer robots per
+ *   SM.  0 (default) chooses by the batch's longest robot: 32 up to 64
+ *   links, 64 up to 200, else 128 (measured on the design, robustness and
+ *   uneven batches).  Team sizes agree to rounding (sums over different
+ *   thread counts round differently), not bitwise.  The serving loop grows
+ *   one warp per robot.
  * broad_phase: 1 = each link tests only the obstacles on a list built when
  *   it last moved by more than 0.4 body radii (the result is the same as
  *   with 0, which tests every obstacle at every evaluation; default 1). */
@@ -358,6 +361,11 @@ vine_status vine_get_robot_counters(const vine_batch* b, int32_t* steps_converge
 
 /* Number of instances and total link capacity (sum of n_links). */
 vine_status vine_batch_info(const vine_batch* b, int32_t* n_inst, int64_t* total_links);
+
+/* The growth launch chosen at creation (or by vine_autotune): threads per
+ * robot, robots per CTA and CTAs.  Any output may be NULL. */
+vine_status vine_batch_launch(const vine_batch* b, int32_t* threads_per_robot, int32_t* robots_per_cta,
+                              int32_t* grid);
 
 /* Releases the batch (device memory freed after synchronising the device). */
 vine_status vine_batch_destroy(vine_batch* b);

@@ -272,7 +272,7 @@ vine_status vine_params_default(vine_params* p) {
   p->gd_steps = 50;
   p->exact_hessian = 1;
   p->broad_phase = 1;
-  p->threads_per_robot = 32;
+  p->threads_per_robot = 0;
   return VINE_OK;
 }
 
@@ -575,7 +575,10 @@ vine_status vine_batch_create(const vine_batch_desc* D, const vine_params* P, vo
   B->nmax = (nmax + 31) & ~31;
   B->omax = omax;
   B->amax = amax;
-  B->team = prm.threads_per_robot > 32 ? prm.threads_per_robot : 32;
+  if (prm.threads_per_robot == 0)  // by the longest robot: more threads where a robot has more links
+    B->team = B->max_target <= 64 ? 32 : (B->max_target <= 200 ? 64 : 128);
+  else
+    B->team = prm.threads_per_robot;
   B->smem_warp = grow_smem_per_warp(B->nmax, B->omax, B->amax, B->team);
   int dev_id = 0, nsm = 1;
   cudaGetDevice(&dev_id);
@@ -1188,6 +1191,15 @@ vine_status vine_batch_info(const vine_batch* B, int32_t* n_inst, int64_t* total
   if (!B) return fail(VINE_EINVAL, "vine_batch_info: null batch");
   if (n_inst) *n_inst = B->n_inst;
   if (total_links) *total_links = B->total_links;
+  return VINE_OK;
+}
+
+vine_status vine_batch_launch(const vine_batch* B, int32_t* threads_per_robot, int32_t* robots_per_cta,
+                              int32_t* grid) {
+  if (!B) return fail(VINE_EINVAL, "vine_batch_launch: null batch");
+  if (threads_per_robot) *threads_per_robot = B->team;
+  if (robots_per_cta) *robots_per_cta = B->wpc;
+  if (grid) *grid = B->grid;
   return VINE_OK;
 }
 

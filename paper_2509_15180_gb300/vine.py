@@ -88,6 +88,7 @@ _SIG = {
     "vine_get_contacts": [_p, _p, _p, _i32, _i32, _p],
     "vine_get_stats": [_p, _p, _p],
     "vine_batch_info": [_p, _p, _p],
+    "vine_batch_launch": [_p, _p, _p, _p],
     "vine_get_tables": [_p, _p, _p, _p, _p, _p],
     "vine_probe_state": [_p, _i32, _i32, _p, C.c_float, _p, _p, _p, _p, _p],
     "vine_debug_trace": [_p, _i32, _i32],
@@ -238,6 +239,12 @@ class Batch:
 
     def grow_step(self, n_steps: int = 1, stream=None):
         _check(_lib.vine_grow_step(self.h, int(n_steps), _stream(stream)), "vine_grow_step")
+
+    def launch(self) -> dict:
+        """vine_batch_launch: threads per robot, robots per CTA, CTAs."""
+        t, w, g = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(_lib.vine_batch_launch(self.h, C.byref(t), C.byref(w), C.byref(g)), "vine_batch_launch")
+        return dict(threads_per_robot=t.value, robots_per_cta=w.value, grid=g.value)
 
     def relax(self, fix_length: bool = True, stream=None):
         """vine_relax: re-solve at the present links, no link added."""

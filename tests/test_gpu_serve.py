@@ -28,7 +28,9 @@ def _requests(k, replicate=0):
 
 
 def _batch_result(sc):
-    b = vine.Batch(sc)
+    p = vine.vine_params_default()
+    p.threads_per_robot = 32  # the server grows one warp per robot
+    b = vine.Batch(sc, p)
     b.simulate()
     st = b.state()
     b.close()
