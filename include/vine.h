@@ -99,8 +99,8 @@ typedef enum {
  *   SM.  0 (default) chooses by the batch's longest robot: 32 up to 64
  *   links, 64 up to 200, else 128 (measured on the design, robustness and
  *   uneven batches).  Team sizes agree to rounding (sums over different
- *   thread counts round differently), not bitwise.  The serving loop grows
- *   one warp per robot.
+ *   thread counts round differently), not bitwise.  The serving loop takes
+ *   the same rule with its slot capacity in links.
  * broad_phase: 1 = each link tests only the obstacles on a list built when
  *   it last moved by more than 0.4 body radii (the result is the same as
  *   with 0, which tests every obstacle at every evaluation; default 1). */

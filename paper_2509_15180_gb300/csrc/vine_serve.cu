@@ -137,6 +137,7 @@ struct vine_server {
   int device = 0;
   cudaStream_t stream = nullptr;
   int S = 0, nmax = 0, omax = 0, amax = 0, ks = 2, grid = 1, wpc = kWarpsPerCta;
+  int team = 32;  // threads per robot
   size_t smem_warp = 0, stage_bytes = 0;
   char* dmem = nullptr;
   GrowArgs args{};
@@ -325,9 +326,9 @@ cudaError_t launch_lane(vine_server* V, int q, bool* launched) {
   a.n_steps = V->cfg.steps_per_tick;
   a.dynamic = 1;
   if (e == cudaSuccess) e = cudaMemsetAsync(a.counter, 0, sizeof(int), L.st);
-  if (e == cudaSuccess) e = grow_configure(V->ks, V->smem_warp * V->wpc);
+  if (e == cudaSuccess) e = grow_configure(V->ks, V->smem_warp * V->wpc, V->team);
   const int grid = std::max(1, std::min(V->grid, (a.n_order + V->wpc - 1) / V->wpc));
-  if (e == cudaSuccess) e = launch_grow(a, V->ks, grid, 32 * V->wpc, V->smem_warp * V->wpc, L.st);
+  if (e == cudaSuccess) e = launch_grow(a, V->ks, grid, V->team * V->wpc, V->smem_warp * V->wpc, L.st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(L.h_ncur, a.n_cur, sizeof(int) * V->S, cudaMemcpyDeviceToHost, L.st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(L.h_status, a.status, sizeof(int) * V->S, cudaMemcpyDeviceToHost, L.st);
   if (e == cudaSuccess) e = cudaEventRecord(L.ev, L.st);
@@ -550,7 +551,9 @@ vine_status vine_server_create(const vine_params* params, const vine_server_conf
       !(prm.R_c > 0.0 && prm.R_act > prm.R_c) || !(prm.m_lo > 0.0 && prm.m_lo < 0.5) || !(prm.pen_frac > 0.0) ||
       !(prm.fval_eps >= 0.0) || !(prm.armijo_c1 > 0.0 && prm.armijo_c1 < 0.5) || prm.discs_per_link < 1 ||
       prm.discs_per_link > 4 || (prm.mode != 0 && prm.mode != 1) ||
-      (prm.mode == 1 && (prm.gd_steps < 1 || !(prm.gd_alpha > 0.0))))
+      (prm.mode == 1 && (prm.gd_steps < 1 || !(prm.gd_alpha > 0.0))) ||
+      (prm.threads_per_robot != 0 && prm.threads_per_robot != 32 && prm.threads_per_robot != 64 &&
+       prm.threads_per_robot != 128))
     return sfail(VINE_EINVAL, "vine_server_create: parameter out of range");
   vine_server_config c;
   vine_server_config_default(&c);
@@ -692,10 +695,15 @@ vine_status vine_server_create(const vine_params* params, const vine_server_conf
     return sfail(VINE_ECUDA, "vine_server_create: wrinkling table build failed");
   }
   // launch configuration
-  V->smem_warp = grow_smem_per_warp(V->nmax, V->omax, V->amax);
+  // threads per robot as for batches (by the slot capacity in links when 0)
+  if (prm.threads_per_robot == 0)
+    V->team = c.max_links <= 64 ? 32 : (c.max_links <= 200 ? 64 : 128);
+  else
+    V->team = prm.threads_per_robot;
+  V->smem_warp = grow_smem_per_warp(V->nmax, V->omax, V->amax, V->team);
   int nsm = 1, per_sm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, V->device);
-  V->wpc = grow_pick_block(V->ks, V->smem_warp, &per_sm);
+  V->wpc = grow_pick_block(V->ks, V->smem_warp, &per_sm, V->team);
   if (V->wpc == 0 || per_sm == 0) {
     cleanup();
     return sfail(VINE_EINVAL, "vine_server_create: slot capacities too large for shared memory");
@@ -758,6 +766,7 @@ vine_status vine_server_create(const vine_params* params, const vine_server_conf
   a.gd_steps = prm.gd_steps;
   a.gd_alpha = (float)prm.gd_alpha;
   a.list_margin = kListMargin;
+  a.team = V->team;
   a.trace = nullptr;
   a.trace_count = nullptr;
   a.trace_inst = -1;

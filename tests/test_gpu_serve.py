@@ -29,7 +29,7 @@ def _requests(k, replicate=0):
 
 def _batch_result(sc):
     p = vine.vine_params_default()
-    p.threads_per_robot = 32  # the server grows one warp per robot
+    p.threads_per_robot = 32  # the servers below hold at most 64 links per slot: one warp per robot
     b = vine.Batch(sc, p)
     b.simulate()
     st = b.state()
