@@ -419,7 +419,10 @@ vine_status vine_spam_tables_noalloc(const double* l0, int32_t n_tab, const vine
  * n_p n_l0 <= 2^20.  params: sPAM constants and eps_crit (NULL: defaults).
  * Outputs (host): p_index[n_targets], l0_index[n_targets],
  * theta_eq[n_targets], and theta_pairs[n_p][n_l0] (may be NULL).  Host
- * pointers; the stream is synchronised. */
+ * pointers; the stream is synchronised.  The FP64 sPAM tables of a grid of
+ * cell lengths (with its sPAM constants) are kept for later calls on the
+ * same device, up to 8 grids per process; a later call copies them instead
+ * of building them again (bitwise the same tables). */
 typedef struct {
   double R, P_vine, l_seg;
   const double* pressures;

@@ -185,10 +185,21 @@ struct WrinkleEntry {
   float2* utab;  // [kUCells + 1]
   double cst[4];
 };
+// The FP64 sPAM bounds and knots of one synthesis grid of cell lengths
+// (l0_min + k l0_step, k < n_l0), which vine_synthesize would otherwise
+// rebuild on every call; at most kCacheSynth grids.
+constexpr size_t kCacheSynth = 8;
+struct SynthEntry {
+  int dev;
+  double l0_min, l0_step, R_c, R_act, a, m_lo;
+  int n_l0;
+  double* scr;  // [(4 + kKnots) n_l0]
+};
 struct TableCache {
   std::mutex mu;
   std::vector<SpamEntry> spam;
   std::vector<WrinkleEntry> wrinkle;
+  std::vector<SynthEntry> synth;
 };
 TableCache& table_cache() {
   static TableCache* c = new TableCache();  // never destroyed: outlives CUDA teardown at exit
@@ -197,6 +208,13 @@ TableCache& table_cache() {
 const SpamEntry* find_spam(const TableCache& c, int dev, double l0, const vine_params& p) {
   for (const SpamEntry& e : c.spam)
     if (e.dev == dev && e.l0 == l0 && e.R_c == p.R_c && e.R_act == p.R_act && e.a == p.a_spam && e.m_lo == p.m_lo)
+      return &e;
+  return nullptr;
+}
+const SynthEntry* find_synth(const TableCache& c, int dev, const vine_synth_spec& g, const vine_params& p) {
+  for (const SynthEntry& e : c.synth)
+    if (e.dev == dev && e.l0_min == g.l0_min && e.l0_step == g.l0_step && e.n_l0 == g.n_l0 && e.R_c == p.R_c &&
+        e.R_act == p.R_act && e.a == p.a_spam && e.m_lo == p.m_lo)
       return &e;
   return nullptr;
 }
@@ -996,10 +1014,24 @@ vine_status vine_synthesize(const vine_synth_spec* spec, const vine_params* para
   CK(cudaMemcpyAsync(mem + o_l0, l0s.data(), 8 * nl, cudaMemcpyHostToDevice, st));
   GaussLegendre gl;
   gauss_legendre(24, &gl);
+  // the FP64 tables of this grid, if an earlier call built them (the build
+  // is deterministic: the copy is bitwise what a rebuild gives)
+  const size_t scr_bytes = 8 * (4 + (size_t)kKnots) * nl;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  int ready = 0;
+  {
+    TableCache& tc = table_cache();
+    std::lock_guard<std::mutex> lk(tc.mu);
+    if (const SynthEntry* e = find_synth(tc, dev, c, prm)) {
+      CK(cudaMemcpyAsync(mem + o_scr, e->scr, scr_bytes, cudaMemcpyDeviceToDevice, st));
+      ready = 1;
+    }
+  }
   CK(launch_synth(n_targets, (const double*)(mem + o_tg), c.n_p, c.n_l0, (const double*)(mem + o_pr),
                   (const double*)(mem + o_l0), c.R, c.P_vine, c.l_seg, c.tol, prm.R_c, prm.R_act, prm.a_spam, prm.m_lo,
                   prm.eps_crit, gl, (double*)(mem + o_scr), (float4*)(mem + o_hdr), (float2*)(mem + o_tab),
-                  (double*)(mem + o_pair), (int*)(mem + o_pi), (int*)(mem + o_li), (double*)(mem + o_eq), st));
+                  (double*)(mem + o_pair), (int*)(mem + o_pi), (int*)(mem + o_li), (double*)(mem + o_eq), ready, st));
   if (nt) {
     CK(cudaMemcpyAsync(p_index, mem + o_pi, 4 * nt, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(l0_index, mem + o_li, 4 * nt, cudaMemcpyDeviceToHost, st));
@@ -1007,6 +1039,22 @@ vine_status vine_synthesize(const vine_synth_spec* spec, const vine_params* para
   }
   if (theta_pairs) CK(cudaMemcpyAsync(theta_pairs, mem + o_pair, 8 * npl, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
+  if (!ready) {  // keep this grid's tables for later calls
+    TableCache& tc = table_cache();
+    std::lock_guard<std::mutex> lk(tc.mu);
+    if (tc.synth.size() < kCacheSynth && !find_synth(tc, dev, c, prm)) {
+      double* keep = nullptr;
+      if (cudaMalloc((void**)&keep, scr_bytes) == cudaSuccess) {
+        if (cudaMemcpyAsync(keep, mem + o_scr, scr_bytes, cudaMemcpyDeviceToDevice, st) == cudaSuccess &&
+            cudaStreamSynchronize(st) == cudaSuccess)
+          tc.synth.push_back(SynthEntry{dev, c.l0_min, c.l0_step, prm.R_c, prm.R_act, prm.a_spam, prm.m_lo, c.n_l0, keep});
+        else
+          cudaFree(keep);
+      } else {
+        (void)cudaGetLastError();  // no room to keep the tables: not an error of this call
+      }
+    }
+  }
   return VINE_OK;
 }
 

@@ -150,12 +150,14 @@ cudaError_t launch_spam_samples(int n, const double* m, const double* l0, double
 // Actuator design synthesis (vine_synthesize): sPAM tables for the cell
 // lengths l0s[n_l0] (scratch >= (4 + kKnots) n_l0 doubles; hdr / tab as for
 // launch_spam_tables), the free-joint equilibrium of every (pressure, cell
-// length) pair into theta_pair[n_p n_l0], then the choice per target.
+// length) pair into theta_pair[n_p n_l0], then the choice per target.  With
+// tables_ready the scratch already holds the FP64 bounds and knots of these
+// cell lengths (from an earlier call) and the table build is skipped.
 cudaError_t launch_synth(int n_targets, const double* target, int n_p, int n_l0, const double* pressures,
                          const double* l0s, double R, double Pv, double ls, double tol, double R_c, double R_act,
                          double a_spam, double m_lo, double eps_c, const GaussLegendre& gl, double* scratch,
                          float4* hdr, float2* tab, double* theta_pair, int* p_index, int* l0_index,
-                         double* theta_eq, cudaStream_t s);
+                         double* theta_eq, int tables_ready, cudaStream_t s);
 
 // Thread-local message returned by vine_last_error (fixed storage; vine_api.cu).
 void set_last_error(const char* msg, const char* detail = nullptr);

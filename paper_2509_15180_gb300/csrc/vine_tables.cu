@@ -435,8 +435,9 @@ cudaError_t launch_synth(int n_targets, const double* target, int n_p, int n_l0,
                          const double* l0s, double R, double Pv, double ls, double tol, double R_c, double R_act,
                          double a_spam, double m_lo, double eps_c, const GaussLegendre& gl, double* scratch,
                          float4* hdr, float2* tab, double* theta_pair, int* p_index, int* l0_index,
-                         double* theta_eq, cudaStream_t s) {
-  cudaError_t e = launch_spam_tables(l0s, n_l0, R_c, R_act, a_spam, m_lo, gl, hdr, tab, scratch, s);
+                         double* theta_eq, int tables_ready, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  if (!tables_ready) e = launch_spam_tables(l0s, n_l0, R_c, R_act, a_spam, m_lo, gl, hdr, tab, scratch, s);
   if (e != cudaSuccess) return e;
   const double* bounds = scratch;
   const double* fk = scratch + 4 * n_l0;

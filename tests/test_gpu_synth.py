@@ -92,3 +92,21 @@ def test_invalid_specifications_are_rejected():
         vine.synthesize([0.05], R, PV, LS, PRESSURES, 0.0, L0_STEP, N_L0, TOL)
     with pytest.raises(vine.VineError):
         vine.synthesize([0.05], R, PV, LS, PRESSURES, L0_MIN, L0_STEP, 0, TOL)
+
+
+def test_kept_tables_give_bitwise_the_same_synthesis():
+    """The second call on a grid copies the FP64 tables the first one built;
+    pairs and choices are bitwise those of the first call, and another grid
+    (or other sPAM constants) is not served from that grid's tables."""
+    targets = np.linspace(0.002, 0.1, 97)
+    grid = (0.0205, 0.0007, 23)                      # a grid no other test uses
+    a = vine.synthesize(targets, R, PV, LS, PRESSURES, *grid, TOL)
+    b = vine.synthesize(targets, R, PV, LS, PRESSURES, *grid, TOL)
+    for k in ("pairs", "p_index", "l0_index", "theta_eq"):
+        assert np.array_equal(a[k], b[k], equal_nan=(k == "theta_eq")), k
+    p = vine.vine_params_default()
+    p.a_spam *= 2.0
+    c = vine.synthesize(targets, R, PV, LS, PRESSURES, *grid, TOL, params=p)
+    assert not np.array_equal(a["pairs"], c["pairs"])
+    d = vine.synthesize(targets, R, PV, LS, PRESSURES, grid[0], grid[1], grid[2] - 1, TOL)
+    assert np.array_equal(d["pairs"], a["pairs"][:, : grid[2] - 1])
