@@ -43,7 +43,7 @@ class Params(C.Structure):
                 ("tol", C.c_double), ("fval_eps", C.c_double), ("armijo_c1", C.c_double),
                 ("max_iter", C.c_int32), ("discs_per_link", C.c_int32),
                 ("max_halvings", C.c_int32), ("exact_hessian", C.c_int32), ("mode", C.c_int32),
-                ("gd_steps", C.c_int32), ("gd_alpha", C.c_double)]
+                ("gd_steps", C.c_int32), ("gd_alpha", C.c_double), ("tol_link", C.c_double)]
 
 
 class _Batch(C.Structure):

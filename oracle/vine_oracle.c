@@ -54,7 +54,7 @@ typedef struct {
   double a_spam;          /* empirical correction a = 1e-4, Sec. 3.1 */
   double m_lo;            /* lower end of the tabulated m range */
   double pen_frac;        /* contact stiffness: penetration (fraction of R) per unit moment */
-  double tol;             /* convergence: predicted displacement / robot length */
+  double tol;             /* convergence: predicted displacement / robot length ... */
   double fval_eps;        /* cost changes below fval_eps x (sum of |terms|) read as rounding level */
   double armijo_c1;       /* sufficient-decrease constant */
   int32_t max_iter;       /* Newton iterations per growth step */
@@ -64,6 +64,7 @@ typedef struct {
   int32_t mode;           /* 0: equilibrium; 1: Algorithm 1 read literally (frozen actuator force, descent) */
   int32_t gd_steps;       /* mode 1: descent steps per growth step (Algorithm 1: 50) */
   double gd_alpha;        /* mode 1: step as a fraction of the free-space Newton step (see gd_solve) */
+  double tol_link;        /* ... and predicted displacement / link length (when > 0) */
 } orc_params;
 
 void orc_params_default(orc_params* p) {
@@ -73,7 +74,7 @@ void orc_params_default(orc_params* p) {
   p->m_lo = 0.002;
   p->pen_frac = 0.01;
   p->tol = 1e-6;
-  p->fval_eps = 1e-6;
+  p->fval_eps = 1e-13; /* FP64 rounding level of a sum of a few hundred terms */
   p->armijo_c1 = 1e-4;
   p->max_iter = 100;
   p->discs_per_link = 2;
@@ -82,6 +83,7 @@ void orc_params_default(orc_params* p) {
   p->mode = 0;
   p->gd_steps = 50;
   p->gd_alpha = 0.005;
+  p->tol_link = 2.5e-5;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -775,6 +777,9 @@ static int solve_step(const inst_t* I, int N, double* th, double* l, int* iters_
   double r = INFINITY;
   long long evals = 0;
   double Smag = 0.0, Smt = 0.0;
+  /* converged when no link end point moves by more than tol of the robot's
+   * length, nor by more than tol_link link lengths */
+  const double tol_eff = p->tol_link > 0.0 ? fmin(p->tol, p->tol_link / N) : p->tol;
   double J = energy(I, N, th, *l, g, H, &G, &Smag);
   ++evals;
   for (it = 1; it <= p->max_iter; ++it) {
@@ -794,7 +799,7 @@ static int solve_step(const inst_t* I, int N, double* th, double* l, int* iters_
     if (lfix) dx[N] = 0.0;
     r = step_residual(I, N, dx, &G);
     if (!isfinite(r)) { status = ORC_NONFINITE; break; }
-    if (r <= p->tol) {
+    if (r <= tol_eff) {
       for (int k = 0; k < N; ++k) th[k] += dx[k];
       *l = fmin(fmax(*l + dx[N], 0.0), I->l_seg);
       status = ORC_OK;
