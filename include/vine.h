@@ -54,7 +54,10 @@ typedef enum {
 
 typedef enum {
   VINE_INST_OK = 0,        /* every step converged */
-  VINE_INST_MAXITER = 1,   /* some step hit max_iter before the tolerance */
+  VINE_INST_MAXITER = 1,   /* a step did not reach the tolerance (max_iter, or no
+                              acceptable line-search trial); the instance stopped
+                              there: later steps would start from a state that is
+                              not an equilibrium */
   VINE_INST_NONFINITE = 2, /* the state became NaN/Inf; the instance stopped */
   VINE_INST_BADINPUT = 3   /* invalid design or obstacle values; never stepped */
 } vine_inst_status;
@@ -66,9 +69,13 @@ typedef enum {
  * R_c, R_act, a_spam: sPAM constants of Sec. 3.1 / 4.2 (5 mm, 17.18 mm, 1e-4).
  * m_lo: lower end of the contraction parameter range of the force table (0.002).
  * pen_frac: contact stiffness k_c = w_a pi P R^3 / (2 pen_frac R l_seg) (0.01).
- * tol: convergence when the predicted displacement of every link end point
- *   (and l_seg times every joint step) is at most tol times the robot length
- *   N l_seg (1e-6); the test is evaluated in FP64.
+ * tol, tol_link: a growth step has converged when the Newton step predicts
+ *   no displacement of a link end point (nor l_seg times a joint step)
+ *   larger than tol times the robot length N l_seg (1e-6) and no larger
+ *   than tol_link link lengths (default 2.5e-5; <= 0 drops this bound).
+ *   The second bound keeps converged states within 1e-4 link lengths of
+ *   the equilibrium at any chain length.  The displacement sums are
+ *   float-float, the test is decided in FP64.
  * fval_eps, armijo_c1: every step is line-searched on the projected path
  *   (at most max_halvings halvings): accepted when the cost decreases by
  *   armijo_c1 times the predicted decrease (Armijo), or, when the cost change
@@ -122,6 +129,7 @@ typedef struct {
   int32_t exact_hessian;
   int32_t broad_phase;
   int32_t threads_per_robot;
+  double tol_link;
 } vine_params;
 
 /* Batch of independent robot instances, structure-of-arrays with CSR
@@ -342,16 +350,6 @@ vine_status vine_get_tables(const vine_batch* b, int32_t* n_tab, float* hdr, flo
  * predicted-displacement residual.  Does not change the batch state. */
 vine_status vine_probe_state(const vine_batch* b, int32_t inst, int32_t n_links, const float* theta, float l_last,
                              double* cost, float* grad, float* step, double* residual, int32_t* l_fixed);
-
-/* Diagnostics: record every line-search trial of robot `inst` in later
- * growth launches (at most `capacity` records of 13 doubles: links present,
- * iteration, halving (-1 = converged), step fraction, predicted-displacement
- * residual, cost before, cost at the trial, predicted decrease, initial
- * slope, slope at the trial, trial distal length, distal length fixed, 0).
- * inst < 0 switches recording off.  Allocates device memory. */
-vine_status vine_debug_trace(vine_batch* b, int32_t inst, int32_t capacity);
-/* Copies up to `capacity` recorded trials to host `records`; *count = copied. */
-vine_status vine_debug_trace_read(const vine_batch* b, double* records, int32_t capacity, int32_t* count);
 
 /* Per-robot counters since the last reset (host arrays of n; any may be
  * NULL; synchronises the stream): converged growth steps, cost

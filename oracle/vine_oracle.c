@@ -1086,7 +1086,7 @@ int orc_relax(const orc_params* p, const orc_batch* b, const orc_tables* T, int 
 #pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads)
 #endif
   for (int i = 0; i < b->n_inst; ++i) {
-    if (status[i] == ORC_NONFINITE || status[i] == ORC_BADINPUT || N_state[i] < 1) continue;
+    if (status[i] != ORC_OK || N_state[i] < 1) continue;  /* stopped robots stay stopped */
     inst_t I;
     inst_init(&I, p, b, T, i);
     I.fix_l = fix_l ? 1 : 0;
@@ -1132,7 +1132,10 @@ int orc_run(const orc_params* p, const orc_batch* b, const orc_tables* T, int n_
     inst_init(&I, p, b, T, i);
     double* th = theta_state + off[i];
     for (int s = 0; s < n_steps; ++s) {
-      if (status[i] == ORC_NONFINITE || status[i] == ORC_BADINPUT) break;
+      /* a step that did not reach equilibrium (or became non-finite) ends the
+       * robot's growth: the next step would start from a state that is not
+       * an equilibrium of the model */
+      if (status[i] != ORC_OK) break;
       int N = N_state[i];
       if (N >= b->n_links[i]) break;
       th[N] = 0.0;

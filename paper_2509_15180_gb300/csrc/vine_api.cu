@@ -260,7 +260,6 @@ struct vine_batch {
   cudaGraphExec_t graph_exec = nullptr;
   std::vector<int> h_n_links, h_n_obs, h_n_circ;
   std::vector<int> h_order;
-  void* trace_mem = nullptr;
 };
 
 extern "C" {
@@ -291,6 +290,7 @@ vine_status vine_params_default(vine_params* p) {
   p->exact_hessian = 1;
   p->broad_phase = 1;
   p->threads_per_robot = 0;
+  p->tol_link = 2.5e-5;
   return VINE_OK;
 }
 
@@ -653,6 +653,7 @@ vine_status vine_batch_create(const vine_batch_desc* D, const vine_params* P, vo
   a.fval_eps = (float)prm.fval_eps;
   a.c1 = (float)prm.armijo_c1;
   a.tol = prm.tol;
+  a.tol_link = prm.tol_link;
   a.max_iter = prm.max_iter;
   a.max_halv = prm.max_halvings;
   a.exact = prm.exact_hessian;
@@ -1188,40 +1189,6 @@ vine_status vine_probe_state(const vine_batch* B, int32_t inst, int32_t n_links,
   return VINE_OK;
 }
 
-vine_status vine_debug_trace(vine_batch* B, int32_t inst, int32_t capacity) {
-  if (!B) return fail(VINE_EINVAL, "vine_debug_trace: null batch");
-  if (B->trace_mem) cudaFree(B->trace_mem);
-  B->trace_mem = nullptr;
-  B->args.trace = nullptr;
-  B->args.trace_count = nullptr;
-  if (B->graph_exec) {  // the recorded launch carries the old arguments
-    cudaGraphExecDestroy(B->graph_exec);
-    cudaGraphDestroy(B->graph);
-    B->graph_exec = nullptr;
-    B->graph = nullptr;
-  }
-  if (inst < 0 || capacity <= 0) return VINE_OK;
-  CK(cudaMalloc(&B->trace_mem, 256 + sizeof(double) * 13 * (size_t)capacity));
-  CK(cudaMemset(B->trace_mem, 0, 256));
-  B->args.trace_count = (int*)B->trace_mem;
-  B->args.trace = (double*)((char*)B->trace_mem + 256);
-  B->args.trace_inst = inst;
-  B->args.trace_cap = capacity;
-  return VINE_OK;
-}
-
-vine_status vine_debug_trace_read(const vine_batch* B, double* records, int32_t capacity, int32_t* count) {
-  if (!B || !count) return fail(VINE_EINVAL, "vine_debug_trace_read: null argument");
-  *count = 0;
-  if (!B->trace_mem) return VINE_OK;
-  int n = 0;
-  CK(cudaMemcpy(&n, B->args.trace_count, 4, cudaMemcpyDeviceToHost));
-  n = std::min(n, std::min(capacity, B->args.trace_cap));
-  if (n > 0 && records) CK(cudaMemcpy(records, B->args.trace, sizeof(double) * 13 * n, cudaMemcpyDeviceToHost));
-  *count = n;
-  return VINE_OK;
-}
-
 vine_status vine_get_robot_counters(const vine_batch* B, int32_t* steps_converged, int64_t* evaluations,
                                     int64_t* cycles, void* stream_v) {
   if (!B) return fail(VINE_EINVAL, "vine_get_robot_counters: null batch");
@@ -1258,7 +1225,6 @@ vine_status vine_batch_destroy(vine_batch* B) {
   if (B->graph) cudaGraphDestroy(B->graph);
   if (B->cap_stream) cudaStreamDestroy(B->cap_stream);
   if (B->stage) cudaFree(B->stage);
-  if (B->trace_mem) cudaFree(B->trace_mem);
   if (B->dmem) cudaFree(B->dmem);
   delete B;
   return VINE_OK;

@@ -59,6 +59,17 @@ __device__ __forceinline__ FF ff_add(FF a, FF b) {
   return quick_two_sum(t.hi, t.lo);
 }
 
+// exact product of two floats, and a float-float value times a float
+__device__ __forceinline__ FF two_prod(float a, float b) {
+  const float p = a * b;
+  return {p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ FF ff_mul(FF a, float b) {
+  FF p = two_prod(a.hi, b);
+  p.lo = fmaf(a.lo, b, p.lo);
+  return quick_two_sum(p.hi, p.lo);
+}
+
 // exclusive prefix (sum over lanes < lane) of float-float values
 __device__ __forceinline__ FF warp_excl_scan(FF v, int lane) {
   FF x = v;
@@ -99,7 +110,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 // only on team-uniform values (reductions, broadcasts, the robot's sizes),
 // so all warps reach every barrier.
 // Scratch layout (floats): FF scan totals [0, 8), suffix totals [8, 12),
-// broadcast [12], sweep results [16, 20), double sums [20, 28), float sums
+// broadcast [12], sweep results [16, 20), float-float sums [20, 28), float sums
 // [28, 32), int sums and counts [32, 36), maxima [36, 40), flags [40, 44).
 constexpr int kTeamScratch = 48;
 
@@ -148,17 +159,34 @@ __device__ __forceinline__ float team_excl_suffix(float v, const Team<TP>& t) {
   return x;
 }
 
+// float-float sum over the team: butterfly shuffles (every lane ends with
+// the same value: two_sum's error term is exact, hence symmetric), then the
+// warps' sums in warp order
 template <int TP>
-__device__ __forceinline__ double team_sum(double v, const Team<TP>& t) {
-  v = warp_sum(v);
+__device__ __forceinline__ FF team_sum_ff(FF v, const Team<TP>& t) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    const float h = __shfl_xor_sync(kFull, v.hi, d), l = __shfl_xor_sync(kFull, v.lo, d);
+    v = ff_add(v, FF{h, l});
+  }
   if (TP == 32) return v;
-  double* d = reinterpret_cast<double*>(t.scr + 20);
-  if (t.lane() == 0) d[t.warp()] = v;
+  if (t.lane() == 0) {
+    t.scr[20 + 2 * t.warp()] = v.hi;
+    t.scr[21 + 2 * t.warp()] = v.lo;
+  }
   t.sync();
-  double s = d[0];
-  for (int w = 1; w < Team<TP>::W; ++w) s += d[w];
+  FF s{t.scr[20], t.scr[21]};
+  for (int w = 1; w < Team<TP>::W; ++w) s = ff_add(s, FF{t.scr[20 + 2 * w], t.scr[21 + 2 * w]});
   t.sync();
   return s;
+}
+
+// sum over the robot's links of a_j b_j (exact products, float-float sums)
+template <int TP>
+__device__ __forceinline__ FF team_dot(const float* a, const float* b, int j0, int j1, const Team<TP>& t) {
+  FF s{0.f, 0.f};
+  for (int j = j0; j < j1; ++j) s = ff_add(s, two_prod(a[j], b[j]));
+  return team_sum_ff(s, t);
 }
 
 template <int TP>
@@ -539,10 +567,12 @@ __device__ __forceinline__ float disc_pen(const float4 ob, FF x, FF y, float R, 
 }
 
 struct EvalOut {
-  double J, S;  // cost and the sum of the magnitudes of its terms
+  FF J;     // cost (float-float)
+  float S;  // sum of the magnitudes of its terms (scale of the rounding-level test)
   float gl, hll, q0, q1, q2, ulx, uly;
   float kg_wb;  // growth stiffness w_b k_g (scale of the distal-length pivot)
   int tests;    // disc-obstacle pre-tests the warp ran
+  unsigned sig; // signature of the active set: contacts (disc, obstacle) and joints past wrinkling onset
 };
 
 // Every link's obstacle list is marked stale (robot start, or a state the
@@ -686,6 +716,7 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
   const float kap = 2.f * A.w_c * I.kc;
   const float floor_d = 1e-6f * A.w_a * I.PR3;
   int ntest = 0;
+  unsigned sig = 0u;  // order-independent: a sum of per-item codes
   if (A.broad) rebuild_lists<KS, TP>(I, S, N, j0, j1, px, py, tm, A.list_margin, ntest);
   // cost terms summed per lane in float-float (each term is an FP32 value;
   // the sum keeps ~48 bits, far below the rounding-level test on J), their
@@ -742,6 +773,7 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
     Sl += A.w_a * Um;
     S.G[j] = A.w_a * M;
     S.DD[j] = fmaxf(A.w_a * dM, floor_d);
+    if (fabsf(th) > A.theta_c) sig += 0x9e3779b1u * (unsigned)(j + 1);
     // ---- contacts of link j: KS discs x every obstacle
     const float lx = S.LUX[j], ly = S.LUY[j];
     const bool last = (j == N - 1);
@@ -802,6 +834,7 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
         if (pen < kRefinePen * I.R) pen = disc_pen_precise(ob, x, y, I.R, fbx, fby, nx, ny, kinv);
         if (pen > 0.f) {
           pen2 += pen * pen;
+          sig += 0x85ebca6bu * (unsigned)(code + 1) + 0xc2b2ae35u * (unsigned)(j + 1);
           pen1 += pen;
           if (exact) add_contact<true>(S, j, pen, nx, ny, kinv, fr, lx, ly, kap, last, ulx, uly);
           else add_contact<false>(S, j, pen, nx, ny, kinv, fr, lx, ly, kap, last, ulx, uly);
@@ -843,10 +876,10 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
   }
   // ---- reductions
   EvalOut E;
-  const double dlr = (double)I.l_seg - (double)l;
-  const float Ss = team_sum_f(Sl, tm);
-  E.J = team_sum((double)Jl.hi + (double)Jl.lo, tm) + (double)A.w_b * (double)I.kg * dlr * dlr;
-  E.S = (double)Ss + (double)A.w_b * (double)I.kg * dlr * dlr;
+  const float dlr = I.l_seg - l;
+  const float Gt = A.w_b * I.kg * dlr * dlr;  // growth term
+  E.S = team_sum_f(Sl, tm) + Gt;
+  E.J = ff_add(team_sum_ff(Jl, tm), Gt);
   const int owner = (N - 1) / B;
   const float glc = S.LX[0];  // written by the owner thread before the team barrier above
   E.hll = 2.f * A.w_b * I.kg + S.LX[1];
@@ -858,11 +891,17 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
   E.gl = -2.f * A.w_b * I.kg * (I.l_seg - l) - glc;
   E.kg_wb = A.w_b * I.kg;
   E.tests = team_sum_i(ntest, tm) * KS;
+  E.sig = (unsigned)team_sum_i((int)sig, tm);
   tm.sync();
   return E;
 }
 
-// Gauss-Newton step (DTH[0..N), dl) and its predicted displacement / (N l_seg).
+// Gauss-Newton step (DTH[0..N), dl) and its predicted displacement: the
+// largest displacement of a link end point (and l_seg |dtheta_j|), in link
+// lengths (the convergence test of the step).  The displacement sums are
+// float-float beside the FP32 twists (they do not feed back into the step,
+// so they stay off the sweep's dependency chain); per-link FP64 would hold
+// GB300's low-rate FP64 pipe for most of the sweep.
 // Backward sweep: A_j (articulated stiffness of links >= j about p_j) and
 // beta_j; forward sweep: twists V_j and joint steps.  Warp-uniform.
 // With `strict` (exact Hessian) a pivot that is not positive means the matrix
@@ -878,7 +917,7 @@ __device__ double gn_solve(const InstDev& I, const Smem& S, int N, bool lfix, co
   if (strict && !lfix && !(E.hll > 1e-3f * 2.f * E.kg_wb)) return -1.0;
   const float iH = lfix ? 0.f : 1.f / E.hll;
   bool pd = true;
-  float V0 = 0.f, V1 = 0.f, V2 = 0.f, rmax = 0.f, dmax = 0.f;
+  float V0 = 0.f, V1 = 0.f, V2 = 0.f, dmax = 0.f, rmax2 = 0.f;
   dl = 0.f;
   // The sweeps overwrite the stiffness entries they read, so a two-warp
   // team runs them on its first warp alone (the second would lag behind the
@@ -940,11 +979,15 @@ __device__ double gn_solve(const InstDev& I, const Smem& S, int N, bool lfix, co
   } else {
     __syncwarp();
   }
+  // the displacement of link end i+1 is z x sum_{k<=i} W0_k Lu_k, with W0_k
+  // the heading change sum_{j<=k} dtheta_j
+  FF W0{0.f, 0.f}, W1{0.f, 0.f}, W2{0.f, 0.f};
   for (int j = 0; sweeper && pd && j < N; ++j) {
     const float h0 = S.C0[j], h1 = S.C1[j], h2 = S.C2[j], iD = S.C3[j], cc = S.C4[j];
     const float lx = S.LUX[j], ly = S.LUY[j];
     const float dth = -(cc + h0 * V0 + h1 * V1 + h2 * V2) * iD;
     V0 += dth;
+    W0 = ff_add(W0, dth);
     float ex = 0.f, ey = 0.f;
     if (j == N - 1) {
       dl = lfix ? 0.f : -(E.gl + E.q0 * V0 + E.q1 * V1 + E.q2 * V2) * iH;
@@ -953,22 +996,25 @@ __device__ double gn_solve(const InstDev& I, const Smem& S, int N, bool lfix, co
     }
     V1 -= V0 * ly;
     V2 += V0 * lx;
-    const float dx = V1 + ex, dy = V2 + ey;
-    const float v = fmaxf(sqrtf(dx * dx + dy * dy), I.l_seg * fabsf(dth));
-    if (!(v <= rmax)) rmax = v;  // keeps NaN
+    W1 = ff_add(W1, ff_mul(W0, -ly));
+    W2 = ff_add(W2, ff_mul(W0, lx));
+    const FF dx = ff_add(W1, ex), dy = ff_add(W2, ey);
+    const float dt = I.l_seg * dth;
+    const float v2 = fmaxf(dx.hi * dx.hi + dy.hi * dy.hi, dt * dt);
+    if (!(v2 <= rmax2)) rmax2 = v2;  // keeps NaN
     if (!(fabsf(dth) <= dmax)) dmax = fabsf(dth);
     if (tm.r == 0) S.DTH[j] = dth;
   }
   if (TP > 32) {
     if (tm.r == 0) {
       tm.scr[16] = pd ? 1.f : 0.f;
-      tm.scr[17] = rmax;
+      tm.scr[17] = rmax2;
       tm.scr[18] = dl;
       tm.scr[19] = dmax;
     }
     tm.sync();
     pd = tm.scr[16] != 0.f;
-    rmax = tm.scr[17];
+    rmax2 = tm.scr[17];
     dl = tm.scr[18];
     dmax = tm.scr[19];
     tm.sync();
@@ -977,7 +1023,7 @@ __device__ double gn_solve(const InstDev& I, const Smem& S, int N, bool lfix, co
     tm.sync();
   }
   max_dth = dmax;
-  return (double)rmax / ((double)N * (double)I.l_seg);
+  return sqrt((double)rmax2) / (double)I.l_seg;
 }
 
 struct StepStats {
@@ -986,18 +1032,6 @@ struct StepStats {
   long long evals, linkevals, tests;
   int fallbacks;
 };
-
-// Diagnostic record of one line-search trial (only for A.trace_inst).
-__device__ __forceinline__ void trace_rec(const GrowArgs& A, int inst, int rank, int N, int it, int h, double a,
-                                          double r, double J0, double Jt, double dec, double s0, double st, double lt,
-                                          double lfix) {
-  if (A.trace == nullptr || inst != A.trace_inst || rank != 0) return;
-  const int k = atomicAdd(A.trace_count, 1);
-  if (k >= A.trace_cap) return;
-  double* o = A.trace + 13 * (size_t)k;
-  o[0] = N; o[1] = it; o[2] = h; o[3] = a; o[4] = r; o[5] = J0; o[6] = Jt; o[7] = dec; o[8] = s0; o[9] = st;
-  o[10] = lt; o[11] = lfix; o[12] = 0.0;
-}
 
 // One growth step, solved by one of two methods:
 //  * mode 0: to equilibrium from the warm start.  Newton iterations with the
@@ -1021,11 +1055,15 @@ __device__ __forceinline__ void trace_rec(const GrowArgs& A, int inst, int rank,
 // kernel's first stall is instruction fetch).
 template <int KS, int TP>
 __device__ int step_solve(const GrowArgs& A, const InstDev& I, const Smem& S, int N, float& l, const Team<TP>& tm,
-                          StepStats& st, int inst) {
+                          StepStats& st) {
   const int B = (N + TP - 1) / TP;
   const int j0 = min(tm.r * B, N), j1 = min(j0 + B, N);
   const bool exact = A.exact != 0;
   const bool descend = A.mode == 1;
+  // converged when the Newton step moves no link end point by more than
+  // tol N link lengths (tol of the robot's length) nor by more than tol_link
+  // link lengths (the bound that holds at any chain length)
+  const double tol_eff = A.tol_link > 0.0 ? fmin(A.tol * (double)N, A.tol_link) : A.tol * (double)N;
   float a_th = 0.f, a_l = 0.f;
   if (descend) {
     for (int k = tm.r; k < N; k += TP) S.TH0[k] = S.TH[k];
@@ -1039,9 +1077,14 @@ __device__ int step_solve(const GrowArgs& A, const InstDev& I, const Smem& S, in
   float l_ev = l;
   int status = kMaxIter, it = 0, h = 0, k_desc = 0;
   double r = 0.0;
-  double gd = 0.0, J0 = 0.0, S0 = 0.0, slope0 = 0.0;
+  FF J0{0.f, 0.f};
+  float gd = 0.f, S0 = 0.f, slope0 = 0.f;
   float alpha = 1.f, lt = l, l0 = l, gl0 = 0.f, dl = 0.f, mdth = 0.f;
   bool lfix = false;
+  // the last Newton step was small and has been applied; the evaluation at
+  // the point it reached checks the active set against the step's
+  bool checking = false, lfix_conv = false;
+  unsigned sig_conv = 0u;
   // every path below advances it, h or k_desc, all bounded; the cap is a
   // second guarantee that the loop ends
   const long long cap = (long long)(max(A.max_iter, 0) + 1) * (max(A.max_halv, 0) + 3) + max(A.gd_steps, 0) + 4;
@@ -1052,7 +1095,7 @@ __device__ int step_solve(const GrowArgs& A, const InstDev& I, const Smem& S, in
     st.tests += E.tests;
     if (descend) {
       st.iters += 1;
-      if (!isfinite(E.J)) {
+      if (!isfinite(E.J.hi)) {
         status = kNonFinite;
         break;
       }
@@ -1067,17 +1110,29 @@ __device__ int step_solve(const GrowArgs& A, const InstDev& I, const Smem& S, in
       continue;
     }
     if (phase == kTrial) {
-      const double dec = (double)alpha * gd + (double)gl0 * ((double)lt - (double)l0);
-      double sl = 0.0;
-      const bool rounding = fabs(E.J - J0) <= (double)A.fval_eps * fmax(S0, E.S);
-      if (A.trace != nullptr || rounding) {
-        for (int j = j0; j < j1; ++j) sl += (double)S.G[j] * (double)S.DTH[j];
-        sl = team_sum(sl, tm);
-        if (lt > 0.f && lt < I.l_seg) sl += (double)E.gl * (double)dl;
+      // cost change and predicted decrease (float-float difference of the costs)
+      const float dJ = ff_add(E.J, ff_neg(J0)).hi;
+      const float dec = alpha * gd + gl0 * (lt - l0);
+      float sl = 0.f;
+      const bool rounding = fabsf(dJ) <= A.fval_eps * fmaxf(S0, E.S);
+      if (rounding) {
+        const FF d = team_dot(S.G, S.DTH, j0, j1, tm);
+        sl = d.hi + d.lo;
+        if (lt > 0.f && lt < I.l_seg) sl += E.gl * dl;
       }
-      trace_rec(A, inst, tm.r, N, it, h, alpha, r, J0, E.J, dec, slope0, sl, lt, lfix ? 1.0 : 0.0);
-      const bool accepted =
-          E.J <= J0 + (double)A.c1 * dec || (rounding && sl <= (2.0 * (double)A.c1 - 1.0) * slope0);
+      const bool accepted = dJ <= A.c1 * dec || (rounding && sl <= (2.f * A.c1 - 1.f) * slope0);
+      if (accepted) {
+        // a trial so short that no unknown changed (the step below FP32
+        // resolution) is no progress: the iteration would repeat itself
+        bool moved = lt != l0;
+        for (int j = j0; j < j1 && !moved; ++j) moved = S.TH[j] != S.TH0[j];
+        if (!team_any(moved, tm)) {
+          for (int j = j0; j < j1; ++j) S.TH[j] = S.TH0[j];
+          l = l0;
+          tm.sync();
+          break;
+        }
+      }
       if (!accepted) {
         if (h < A.max_halv) {
           alpha *= 0.5f;
@@ -1098,8 +1153,16 @@ __device__ int step_solve(const GrowArgs& A, const InstDev& I, const Smem& S, in
       phase = kNewton;
     }
     if (phase == kNewton) {
+      if (checking) {
+        checking = false;
+        const bool lf = A.fix_l || (l <= 0.f && E.gl > 0.f) || (l >= I.l_seg && E.gl < 0.f);
+        if (E.sig == sig_conv && lf == lfix_conv && isfinite(E.J.hi)) {
+          status = kOK;
+          break;
+        }
+      }
       if (++it > A.max_iter) break;
-      if (!isfinite(E.J)) {
+      if (!isfinite(E.J.hi)) {
         status = kNonFinite;
         break;
       }
@@ -1109,22 +1172,19 @@ __device__ int step_solve(const GrowArgs& A, const InstDev& I, const Smem& S, in
     r = gn_solve(I, S, N, lfix, E, dl, tm, use_exact, mdth);
     if (use_exact && !(r >= 0.0 && isfinite(r))) {
       // exact Hessian not positive definite here: Gauss-Newton matrix instead
-      trace_rec(A, inst, tm.r, N, it, -2, 0.0, r, E.J, E.J, 0.0, 0.0, (double)E.hll, l, lfix ? 1.0 : 0.0);
       st.fallbacks += 1;
       phase = kFallback;
       ev_exact = false;
       l_ev = l;
       continue;
     }
-    if (!isfinite(E.J)) {
+    if (!isfinite(E.J.hi)) {
       status = kNonFinite;
       break;
     }
     if (!isfinite(r) || r < 0.0) {
       // the Gauss-Newton sweep lost its pivots to FP32 range (bending floor
       // against contact stiffness): steepest descent, at most 0.05 rad per joint
-      trace_rec(A, inst, tm.r, N, it, -3, 0.0, r, E.J, E.S, (double)E.gl, (double)mdth, (double)E.hll, l,
-                lfix ? 1.0 : 0.0);
       float gm = 0.f;
       for (int j = j0; j < j1; ++j) gm = fmaxf(gm, fabsf(S.G[j]));
       gm = team_max(gm, tm);
@@ -1135,30 +1195,41 @@ __device__ int step_solve(const GrowArgs& A, const InstDev& I, const Smem& S, in
         status = kNonFinite;
         break;
       }
-      r = 1.0;  // not a Newton step: never taken as converged
+      r = 1e30;  // not a Newton step: never taken as converged
       st.fallbacks += 1;
       tm.sync();
     }
-    if (r <= A.tol) {
-      trace_rec(A, inst, tm.r, N, it, -1, 1.0, r, E.J, E.J, 0.0, 0.0, 0.0, l + dl, lfix ? 1.0 : 0.0);
+    if (r <= tol_eff) {
       for (int j = j0; j < j1; ++j) S.TH[j] += S.DTH[j];
       l = fminf(fmaxf(l + dl, 0.f), I.l_seg);
-      status = kOK;
-      break;
+      // the point the small step reached is evaluated once more: a step that
+      // crosses into a contact (or past the wrinkling onset of a joint) can
+      // leave a long, soft chain far from the equilibrium although the step
+      // itself was small.  Converged when the active set is the one the step
+      // was computed with; else the solve goes on from there.  (The next
+      // Newton step itself is no test: at a near-singular equilibrium its
+      // FP32 value is noise.)
+      sig_conv = E.sig;
+      lfix_conv = lfix;
+      checking = true;
+      phase = kNewton;
+      l_ev = l;
+      ev_exact = exact;
+      tm.sync();
+      continue;
     }
     // line search: first trial at the full step
-    gd = 0.0;
-    for (int j = j0; j < j1; ++j) {
-      gd += (double)S.G[j] * (double)S.DTH[j];
-      S.TH0[j] = S.TH[j];
+    {
+      const FF d = team_dot(S.G, S.DTH, j0, j1, tm);
+      gd = d.hi + d.lo;
     }
-    gd = team_sum(gd, tm);
+    for (int j = j0; j < j1; ++j) S.TH0[j] = S.TH[j];
     l0 = l;
     gl0 = E.gl;
     J0 = E.J;
     S0 = E.S;
     const bool l_moves = !((l0 <= 0.f && dl < 0.f) || (l0 >= I.l_seg && dl > 0.f));
-    slope0 = gd + (l_moves ? (double)gl0 * (double)dl : 0.0);
+    slope0 = gd + (l_moves ? gl0 * dl : 0.f);
     alpha = 1.f;
     h = 0;
     for (int j = j0; j < j1; ++j) S.TH[j] = S.TH0[j] + alpha * S.DTH[j];
@@ -1180,7 +1251,7 @@ __device__ int step_solve(const GrowArgs& A, const InstDev& I, const Smem& S, in
   if (it > A.max_iter) it = A.max_iter;
   tm.sync();
   st.iters = it;
-  st.r = r;
+  st.r = r / (double)N;  // reported relative to the robot length
   return status;
 }
 
@@ -1189,7 +1260,10 @@ __device__ void process_instance(const GrowArgs& A, int inst, const Smem& S, con
   const long long t_start = clock64();
   const InstDev I = A.inst[inst];
   int status = A.status[inst];
-  if (status == kBadInput || status == kNonFinite) return;
+  // a robot whose growth step failed (out of iterations, or non-finite) has
+  // stopped: its later steps would start from a state that is not an
+  // equilibrium of the model
+  if (status != kOK) return;
   int N = A.n_cur[inst];
   if (A.n_steps <= 0 || (A.relax ? N == 0 : N >= I.n_target)) return;
   for (int k = tm.r; k < I.n_obs; k += TP) S.obs[k] = A.obs[I.obs_off + k];
@@ -1208,7 +1282,7 @@ __device__ void process_instance(const GrowArgs& A, int inst, const Smem& S, con
     }
     tm.sync();
     StepStats st{0, 0.0, 0, 0, 0, 0};
-    const int res = step_solve<KS, TP>(A, I, S, N, l, tm, st, inst);
+    const int res = step_solve<KS, TP>(A, I, S, N, l, tm, st);
     iters += st.iters;
     evals += st.evals;
     linkevals += st.linkevals;
@@ -1222,7 +1296,7 @@ __device__ void process_instance(const GrowArgs& A, int inst, const Smem& S, con
     } else if (res > status) {
       status = res;
     }
-    if (status == kNonFinite) break;
+    if (status != kOK) break;
   }
   tm.sync();
   for (int k = tm.r; k < N; k += TP) A.theta[I.th_off + k] = S.TH[k];
@@ -1319,8 +1393,8 @@ __global__ void __launch_bounds__(32) probe_kernel(const GrowArgs A, int inst, i
   if (lane == 0) {
     out_g[N] = E.gl;
     out_dx[N] = dl;
-    *outJ = E.J;
-    *out_r = r;
+    *outJ = (double)E.J.hi + (double)E.J.lo;
+    *out_r = r / (double)N;  // relative to the robot length
     *out_lfix = lfix ? 1 : 0;
   }
 }

@@ -75,7 +75,8 @@ struct GrowArgs {
   float theta_c, inv2thc, inv4thc, eps_c;
   float u_h, u_invh, U_pi, m_pi;
   float fval_eps, c1;
-  double tol;
+  double tol;       // convergence: predicted displacement <= tol N link lengths ...
+  double tol_link;  // ... and <= tol_link link lengths (when > 0)
   int max_iter, max_halv;
   int exact;  // exact Hessian when positive definite (else Gauss-Newton)
   int broad;  // per-link obstacle lists (else every obstacle at every evaluation)
@@ -86,10 +87,6 @@ struct GrowArgs {
   int team;           // threads per robot: 32 (0 reads as 32) or 64
   int relax;          // 1: re-solve the present links without adding one (vine_relax)
   int fix_l;          // 1: hold the distal length fixed while solving
-  // diagnostics: per line-search trial records of one robot (off when null)
-  double* trace;
-  int* trace_count;
-  int trace_inst, trace_cap;
 };
 
 // Descriptor validation and encoding (vine_api.cu): raw device copies of a

@@ -181,7 +181,7 @@ struct vine_server {
 namespace {
 
 bool robot_done(int n_cur, int target, int status) {
-  return n_cur >= target || status == kNonFinite || status == kBadInput;
+  return n_cur >= target || status != kOK;  // a failed step ends the robot's growth
 }
 
 // Admission of one waiting request: slots, tables, upload, validation/encoding.
@@ -758,6 +758,7 @@ vine_status vine_server_create(const vine_params* params, const vine_server_conf
   a.fval_eps = (float)prm.fval_eps;
   a.c1 = (float)prm.armijo_c1;
   a.tol = prm.tol;
+  a.tol_link = prm.tol_link;
   a.max_iter = prm.max_iter;
   a.max_halv = prm.max_halvings;
   a.exact = prm.exact_hessian;
@@ -767,10 +768,6 @@ vine_status vine_server_create(const vine_params* params, const vine_server_conf
   a.gd_alpha = (float)prm.gd_alpha;
   a.list_margin = kListMargin;
   a.team = V->team;
-  a.trace = nullptr;
-  a.trace_count = nullptr;
-  a.trace_inst = -1;
-  a.trace_cap = 0;
   V->d_l0 = (double*)(m + o_l0);
   V->d_scr = scr;
   V->d_stage = m + o_stage;

@@ -35,7 +35,7 @@ class vine_params(C.Structure):
                 ("armijo_c1", C.c_double), ("max_iter", C.c_int32), ("discs_per_link", C.c_int32),
                 ("max_halvings", C.c_int32), ("mode", C.c_int32), ("gd_alpha", C.c_double),
                 ("gd_steps", C.c_int32), ("exact_hessian", C.c_int32), ("broad_phase", C.c_int32),
-                ("threads_per_robot", C.c_int32)]
+                ("threads_per_robot", C.c_int32), ("tol_link", C.c_double)]
 
 
 class vine_batch_desc(C.Structure):
@@ -91,10 +91,8 @@ _SIG = {
     "vine_batch_launch": [_p, _p, _p, _p],
     "vine_get_tables": [_p, _p, _p, _p, _p, _p],
     "vine_probe_state": [_p, _i32, _i32, _p, C.c_float, _p, _p, _p, _p, _p],
-    "vine_debug_trace": [_p, _i32, _i32],
     "vine_get_robot_counters": [_p, _p, _p, _p, _p],
     "vine_spam_tables_noalloc": [_p, _i32, _p, _p, _p, _p],
-    "vine_debug_trace_read": [_p, _p, _i32, _p],
     "vine_set_actuators": [_p, _p, _p, _p, _i32, _p],
     "vine_set_state": [_p, _p, _p, _p, _i32, _p],
     "vine_relax": [_p, _i32, _p],
@@ -386,18 +384,6 @@ class Batch:
         _check(_lib.vine_get_robot_counters(self.h, _ptr(out["conv"]), _ptr(out["evals"]), _ptr(out["cycles"]),
                                             _stream(stream)), "vine_get_robot_counters")
         return out
-
-    def trace(self, inst: int, capacity: int = 4096):
-        """Start recording line-search trials of one robot (vine_debug_trace)."""
-        self._trace_cap = capacity
-        _check(_lib.vine_debug_trace(self.h, int(inst), int(capacity)), "vine_debug_trace")
-
-    def trace_read(self) -> np.ndarray:
-        cap = getattr(self, "_trace_cap", 0)
-        out = np.zeros((max(cap, 1), 13), np.float64)
-        n = C.c_int32()
-        _check(_lib.vine_debug_trace_read(self.h, _ptr(out), int(cap), C.byref(n)), "vine_debug_trace_read")
-        return out[: n.value]
 
     def theta_of(self, st: dict, i: int):
         return st["theta"][self.offsets[i]: self.offsets[i] + st["N"][i]]
