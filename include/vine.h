@@ -224,22 +224,34 @@ vine_status vine_relax(vine_batch* b, int32_t fix_length, void* cuda_stream);
  * longest-first work queue, replayed from a CUDA graph.  Async. */
 vine_status vine_simulate(vine_batch* b, void* cuda_stream);
 
-/* Launch autotuner for uneven batches.  Grows a sample of `sample`
- * instances (0: 4096; spread evenly over the longest-first order) from
- * reset to full length once per candidate configuration -- warps per CTA
- * (4, 2, 1: one robot per warp; fewer warps per CTA pack large per-robot
- * shared-memory slices more tightly) x broad-phase margin (0.5, 1, 2 body
- * radii: list length against rebuild frequency) -- times each launch with
- * CUDA events, and adopts the fastest for later vine_grow_step /
- * vine_simulate calls.  Neither knob changes any result.  Leaves the batch
- * reset.  Synchronises the stream. */
+/* Launch autotuner.  A batch grows in length classes (robots of up to 64
+ * links, 65-200, more: each class one persistent launch of its own team
+ * size, the classes on parallel branches of the CUDA graph, the longest
+ * robots' class first; with threads_per_robot set, one class).  The tuner
+ * grows a sample of every class (`sample` robots in all, 0: 4096; at least
+ * 64 per class; spread over each class's longest-first order) from reset
+ * to full length per candidate and times each launch with CUDA events:
+ *   - per class alone: threads per robot 32 (with 4, 2 or 1 robots per
+ *     CTA), 64 or 128 (warps per robot);
+ *   - all classes together with the chosen teams: the broad-phase margin
+ *     0.5, 1 or 2 body radii (list length against rebuild frequency).
+ * The result is adopted for later vine_grow_step / vine_simulate calls when
+ * the sample grows faster than with the configuration chosen at creation
+ * (timed first).  The margin never changes a result; the team size changes
+ * results at rounding level (sums over other thread counts), each within
+ * the parity bar.  Leaves the batch reset.  Synchronises the stream. */
 typedef struct {
-  int32_t warps_per_cta;   /* chosen */
+  int32_t warps_per_cta;   /* warps per CTA of the first (longest) class */
   float list_margin;       /* chosen, body radii */
-  double best_ms;          /* sample growth time with the chosen configuration */
-  double default_ms;       /* with the configuration chosen at creation (-1 if not tried) */
+  double best_ms;          /* sample growth time with the adopted configuration */
+  double default_ms;       /* with the configuration chosen at creation */
   int32_t candidates;      /* configurations timed */
   int32_t sample;          /* instances grown per candidate */
+  int32_t n_class;         /* length classes */
+  int32_t adopted;         /* 1 if the tuned configuration replaced the default */
+  int32_t class_threads[3];        /* threads per robot per class */
+  int32_t class_robots_per_cta[3]; /* robots per CTA per class */
+  double class_ms[3];      /* best sample time of each class alone */
 } vine_tune_result;
 vine_status vine_autotune(vine_batch* b, int32_t sample, void* cuda_stream, vine_tune_result* out);
 
@@ -360,10 +372,18 @@ vine_status vine_get_robot_counters(const vine_batch* b, int32_t* steps_converge
 /* Number of instances and total link capacity (sum of n_links). */
 vine_status vine_batch_info(const vine_batch* b, int32_t* n_inst, int64_t* total_links);
 
-/* The growth launch chosen at creation (or by vine_autotune): threads per
- * robot, robots per CTA and CTAs.  Any output may be NULL. */
+/* The growth launch of the first (longest robots') length class, chosen at
+ * creation or by vine_autotune: threads per robot, robots per CTA and CTAs.
+ * Any output may be NULL. */
 vine_status vine_batch_launch(const vine_batch* b, int32_t* threads_per_robot, int32_t* robots_per_cta,
                               int32_t* grid);
+
+/* The length classes of the batch's growth launch (see vine_autotune), the
+ * longest robots' first: *n_class (1..3) and per class (arrays of 3, any
+ * may be NULL) threads per robot, robots, robots per CTA, CTAs and the
+ * longest robot's links. */
+vine_status vine_batch_classes(const vine_batch* b, int32_t* n_class, int32_t* threads_per_robot, int32_t* robots,
+                               int32_t* robots_per_cta, int32_t* grid, int32_t* max_links);
 
 /* Releases the batch (device memory freed after synchronising the device). */
 vine_status vine_batch_destroy(vine_batch* b);

@@ -236,6 +236,19 @@ void vine::set_last_error(const char* msg, const char* detail) {
   std::snprintf(g_err, sizeof(g_err), "%s%s", msg, detail ? detail : "");
 }
 
+// One length class of a batch: its robots (a segment of the longest-first
+// order) grow in one persistent launch of their own team size, shared-memory
+// slice and work counter.
+struct LaunchClass {
+  int team = 32;             // threads per robot
+  int wpc = kWarpsPerCta;    // robots (teams) per CTA
+  int grid = 1;
+  int nmax = 32, omax = 1, amax = 1, max_target = 0;
+  size_t smem_warp = 0;      // shared memory per robot slice
+  int off = 0, count = 0;    // segment of the order
+};
+constexpr int kMaxClass = 3;
+
 struct vine_batch {
   int device = 0;
   int n_inst = 0;
@@ -244,12 +257,13 @@ struct vine_batch {
   int n_tab = 0;
   vine_params params{};
   int ks = 2;
-  int wpc = kWarpsPerCta;  // robots (teams) per CTA of the growth launch
-  int team = 32;           // threads per robot
-  int nmax = 32, omax = 1, amax = 1;
-  size_t smem_warp = 0;
-  int grid = 1;
+  int n_class = 1;
+  LaunchClass cls[kMaxClass];  // the longest robots' class first
+  float margin = kListMargin;  // broad-phase margin of the growth launches
+  size_t smem_warp = 0;  // one-warp slice for the batch's largest robot (adjoint, probe)
   int max_target = 0;
+  cudaStream_t aux[kMaxClass - 1] = {};  // the other classes' launch streams
+  cudaEvent_t ev_fork = nullptr, ev_join[kMaxClass - 1] = {};
   void* dmem = nullptr;
   void* stage = nullptr;  // lazily allocated host-output staging
   size_t stage_bytes = 0;
@@ -261,6 +275,55 @@ struct vine_batch {
   std::vector<int> h_n_links, h_n_obs, h_n_circ;
   std::vector<int> h_order;
 };
+
+static void release_launch_streams(vine_batch* B) {
+  for (int c = 0; c < kMaxClass - 1; ++c) {
+    if (B->aux[c]) cudaStreamDestroy(B->aux[c]);
+    if (B->ev_join[c]) cudaEventDestroy(B->ev_join[c]);
+    B->aux[c] = nullptr;
+    B->ev_join[c] = nullptr;
+  }
+  if (B->ev_fork) cudaEventDestroy(B->ev_fork);
+  B->ev_fork = nullptr;
+}
+
+// Growth launch of the classes L[0..nc) over the robots d_order[L[c].off ..
+// + L[c].count): class 0 on stream st, the others on the batch's streams,
+// forked from st and joined back (parallel branches of a captured graph).
+// The longest robots' class is launched first and so takes the SMs first;
+// the other classes' CTAs fill them as its queue drains.
+static cudaError_t launch_classes(vine_batch* B, const LaunchClass* L, int nc, const int* d_order, int n_steps,
+                                  float margin, int relax, int fix_l, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(B->args.counter, 0, sizeof(int) * 4, st);
+  if (e == cudaSuccess && nc > 1) {
+    e = cudaEventRecord(B->ev_fork, st);
+    for (int c = 1; c < nc && e == cudaSuccess; ++c) e = cudaStreamWaitEvent(B->aux[c - 1], B->ev_fork, 0);
+  }
+  for (int c = 0; c < nc && e == cudaSuccess; ++c) {
+    GrowArgs a = B->args;
+    a.order = d_order + L[c].off;
+    a.n_order = L[c].count;
+    a.counter = B->args.counter + c;
+    a.nmax = L[c].nmax;
+    a.omax = L[c].omax;
+    a.amax = L[c].amax;
+    a.warp_floats = (int)(L[c].smem_warp / sizeof(float));
+    a.team = L[c].team;
+    a.n_steps = n_steps;
+    a.dynamic = 1;
+    a.relax = relax;
+    a.fix_l = fix_l;
+    a.list_margin = margin;
+    const cudaStream_t s = c == 0 ? st : B->aux[c - 1];
+    e = grow_configure(B->ks, L[c].smem_warp * L[c].wpc, L[c].team);
+    if (e == cudaSuccess) e = launch_grow(a, B->ks, L[c].grid, L[c].team * L[c].wpc, L[c].smem_warp * L[c].wpc, s);
+    if (e == cudaSuccess && c > 0) {
+      e = cudaEventRecord(B->ev_join[c - 1], s);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(st, B->ev_join[c - 1], 0);
+    }
+  }
+  return e;
+}
 
 extern "C" {
 
@@ -479,6 +542,7 @@ vine_status vine_batch_create(const vine_batch_desc* D, const vine_params* P, vo
   }
   auto cleanup = [&]() {
     cudaFree(mem);
+    release_launch_streams(B);
     delete B;
   };
 #define CKC(call)                                    \
@@ -589,25 +653,61 @@ vine_status vine_batch_create(const vine_batch_desc* D, const vine_params* P, vo
     }
     cudaGetLastError();  // a failed cache copy leaves no sticky error for the caller
   }
-  // ---- launch configuration
-  B->nmax = (nmax + 31) & ~31;
-  B->omax = omax;
-  B->amax = amax;
-  if (prm.threads_per_robot == 0)  // by the longest robot: more threads where a robot has more links
-    B->team = B->max_target <= 64 ? 32 : (B->max_target <= 200 ? 64 : 128);
-  else
-    B->team = prm.threads_per_robot;
-  B->smem_warp = grow_smem_per_warp(B->nmax, B->omax, B->amax, B->team);
+  // ---- launch configuration: length classes (threads per robot by the
+  // robot's length: 32 up to 64 links, 64 up to 200, 128 beyond), or one
+  // class of the caller's team size
   int dev_id = 0, nsm = 1;
   cudaGetDevice(&dev_id);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev_id);
-  int per_sm = 0;
-  B->wpc = grow_pick_block(B->ks, B->smem_warp, &per_sm, B->team);
-  if (B->wpc == 0 || per_sm == 0) {
-    cleanup();
-    return fail(VINE_EINVAL, "vine_batch_create: robot or obstacle set too large for shared memory");
+  {
+    auto team_of = [&](int nl) {
+      if (prm.threads_per_robot != 0) return prm.threads_per_robot;
+      return nl <= 64 ? 32 : (nl <= 200 ? 64 : 128);
+    };
+    const int teams[kMaxClass] = {128, 64, 32};
+    std::vector<int> by_class;
+    by_class.reserve(n);
+    B->n_class = 0;
+    for (int t : teams) {
+      LaunchClass L;
+      L.team = t;
+      L.off = (int)by_class.size();
+      int cn = 1, co = 1, ca = 1;
+      for (int i : B->h_order) {
+        // robots with bad input stop at once: they ride in the last class
+        const int ti = B->h_n_links[i] > 0 ? team_of(B->h_n_links[i]) : -1;
+        if (ti != t && !(ti < 0 && t == 32)) continue;
+        by_class.push_back(i);
+        cn = std::max(cn, B->h_n_links[i]);
+        co = std::max(co, B->h_n_obs[i]);
+        ca = std::max(ca, aptr[i + 1] - aptr[i]);
+      }
+      L.count = (int)by_class.size() - L.off;
+      if (L.count == 0) continue;
+      L.max_target = cn;
+      L.nmax = (cn + 31) & ~31;
+      L.omax = co;
+      L.amax = ca;
+      L.smem_warp = grow_smem_per_warp(L.nmax, L.omax, L.amax, L.team);
+      int per_sm = 0;
+      L.wpc = grow_pick_block(B->ks, L.smem_warp, &per_sm, L.team);
+      if (L.wpc == 0 || per_sm == 0) {
+        cleanup();
+        return fail(VINE_EINVAL, "vine_batch_create: robot or obstacle set too large for shared memory");
+      }
+      L.grid = std::max(1, std::min((L.count + L.wpc - 1) / L.wpc, nsm * per_sm));
+      B->cls[B->n_class++] = L;
+    }
+    B->h_order = by_class;  // class by class, longest first within each
+    CKC(cudaMemcpyAsync(P_(o_ord), B->h_order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+    for (int c = 1; c < B->n_class; ++c) {
+      CKC(cudaStreamCreateWithFlags(&B->aux[c - 1], cudaStreamNonBlocking));
+      CKC(cudaEventCreateWithFlags(&B->ev_join[c - 1], cudaEventDisableTiming));
+    }
+    if (B->n_class > 1) CKC(cudaEventCreateWithFlags(&B->ev_fork, cudaEventDisableTiming));
+    CKC(cudaStreamSynchronize(st));
   }
-  B->grid = std::max(1, std::min((n + B->wpc - 1) / B->wpc, nsm * per_sm));
+  B->smem_warp = grow_smem_per_warp((nmax + 31) & ~31, omax, amax, 32);
 
   GrowArgs& a = B->args;
   a.inst = (const InstDev*)P_(o_inst);
@@ -635,9 +735,9 @@ vine_status vine_batch_create(const vine_batch_desc* D, const vine_params* P, vo
   a.counter = (int*)P_(o_cnt);
   a.dynamic = 1;
   a.n_steps = 0;
-  a.nmax = B->nmax;
-  a.omax = B->omax;
-  a.amax = B->amax;
+  a.nmax = (nmax + 31) & ~31;  // the batch's largest robot (adjoint and probe, one warp)
+  a.omax = omax;
+  a.amax = amax;
   a.warp_floats = (int)(B->smem_warp / sizeof(float));
   a.w_a = (float)prm.w_a;
   a.w_b = (float)prm.w_b;
@@ -658,7 +758,7 @@ vine_status vine_batch_create(const vine_batch_desc* D, const vine_params* P, vo
   a.max_halv = prm.max_halvings;
   a.exact = prm.exact_hessian;
   a.broad = prm.broad_phase;
-  a.team = B->team;
+  a.team = 32;
   a.mode = prm.mode;
   a.gd_steps = prm.gd_steps;
   a.gd_alpha = (float)prm.gd_alpha;
@@ -670,13 +770,8 @@ vine_status vine_batch_create(const vine_batch_desc* D, const vine_params* P, vo
   return VINE_OK;
 }
 
-static vine_status grow_launch(vine_batch* B, int n_steps, cudaStream_t st) {
-  GrowArgs a = B->args;
-  a.n_steps = n_steps;
-  a.dynamic = 1;
-  CK(cudaMemsetAsync(a.counter, 0, sizeof(int), st));
-  CK(grow_configure(B->ks, B->smem_warp * B->wpc, B->team));
-  CK(launch_grow(a, B->ks, B->grid, B->team * B->wpc, B->smem_warp * B->wpc, st));
+static vine_status grow_launch(vine_batch* B, int n_steps, cudaStream_t st, int relax = 0, int fix_l = 0) {
+  CK(launch_classes(B, B->cls, B->n_class, B->args.order, n_steps, B->margin, relax, fix_l, st));
   return VINE_OK;
 }
 
@@ -711,16 +806,7 @@ vine_status vine_grow_step(vine_batch* B, int32_t n_steps, void* stream_v) {
 vine_status vine_relax(vine_batch* B, int32_t fix_length, void* stream_v) {
   if (!B) return fail(VINE_EINVAL, "vine_relax: null batch");
   if (fix_length != 0 && fix_length != 1) return fail(VINE_EINVAL, "vine_relax: fix_length must be 0 or 1");
-  cudaStream_t st = (cudaStream_t)stream_v;
-  GrowArgs a = B->args;
-  a.n_steps = 1;
-  a.dynamic = 1;
-  a.relax = 1;
-  a.fix_l = fix_length;
-  CK(cudaMemsetAsync(a.counter, 0, sizeof(int), st));
-  CK(grow_configure(B->ks, B->smem_warp * B->wpc, B->team));
-  CK(launch_grow(a, B->ks, B->grid, B->team * B->wpc, B->smem_warp * B->wpc, st));
-  return VINE_OK;
+  return grow_launch(B, 1, (cudaStream_t)stream_v, 1, fix_length);
 }
 
 vine_status vine_simulate(vine_batch* B, void* stream_v) {
@@ -747,75 +833,136 @@ vine_status vine_simulate(vine_batch* B, void* stream_v) {
 
 static vine_status ensure_stage(const vine_batch* Bc, size_t bytes);
 
+// A class's launch shape for a given team size (robots per CTA: for one-warp
+// teams the caller's wpc, else one robot per CTA).  False if it does not fit.
+static bool shape_class(const vine_batch* B, LaunchClass& L, int team, int wpc, int nsm) {
+  L.team = team;
+  L.smem_warp = grow_smem_per_warp(L.nmax, L.omax, L.amax, team);
+  L.wpc = team > 32 ? 1 : wpc;
+  const size_t smem = L.smem_warp * L.wpc;
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, B->device);
+  if (smem > (size_t)optin || grow_configure(B->ks, smem, team) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  const int ctas = grow_max_ctas_per_sm(B->ks, smem, team * L.wpc, team);
+  if (ctas <= 0) return false;
+  L.grid = std::max(1, std::min((L.count + L.wpc - 1) / L.wpc, nsm * ctas));
+  return true;
+}
+
 vine_status vine_autotune(vine_batch* B, int32_t sample, void* stream_v, vine_tune_result* out) {
   if (!B || !out) return fail(VINE_EINVAL, "vine_autotune: null argument");
   if (sample < 0) return fail(VINE_EINVAL, "vine_autotune: negative sample size");
   cudaStream_t st = (cudaStream_t)stream_v;
   const int n = B->n_inst;
-  const int ns = std::min(n, sample > 0 ? sample : 4096);
-  // sample spread evenly over the longest-first order (keeps its cost mix),
-  // itself longest first
-  std::vector<int> idx(ns);
-  for (int k = 0; k < ns; ++k) idx[k] = B->h_order[(int64_t)k * n / ns];
-  vine_status s = ensure_stage(B, 4 * (size_t)ns);
+  const int ns_all = std::min(n, sample > 0 ? sample : 4096);
+  int nsm = 1;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, B->device);
+  // per class a sample spread evenly over its longest-first segment (keeps
+  // its cost mix), in proportion to the class's size, at least 64 robots
+  LaunchClass SL[kMaxClass];
+  std::vector<int> idx;
+  for (int c = 0; c < B->n_class; ++c) {
+    const LaunchClass& L = B->cls[c];
+    const int k = std::min(L.count, std::max(std::min(64, L.count), (int)((int64_t)ns_all * L.count / n)));
+    SL[c] = L;
+    SL[c].off = (int)idx.size();
+    SL[c].count = k;
+    for (int q = 0; q < k; ++q) idx.push_back(B->h_order[L.off + (int64_t)q * L.count / k]);
+  }
+  const int ns = (int)idx.size();
+  vine_status s = ensure_stage(B, 4 * (size_t)std::max(ns, 1));
   if (s != VINE_OK) return s;
   int* d_idx = (int*)B->stage;
   CK(cudaMemcpyAsync(d_idx, idx.data(), 4 * (size_t)ns, cudaMemcpyHostToDevice, st));
-  int dev_id = 0, nsm = 1;
-  cudaGetDevice(&dev_id);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev_id);
-  const float margins[3] = {0.5f, kListMargin, 2.0f};
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   std::memset(out, 0, sizeof(*out));
-  out->best_ms = 1e30;
-  out->default_ms = -1.0;
   out->sample = ns;
+  out->n_class = B->n_class;
   vine_status rs = VINE_OK;
-  for (int w = B->team > 32 ? 1 : kWarpsPerCta; w >= 1 && rs == VINE_OK; w >>= 1) {
-    const size_t smem = B->smem_warp * w;
-    if (grow_configure(B->ks, smem, B->team) != cudaSuccess) continue;
-    const int ctas = grow_max_ctas_per_sm(B->ks, smem, B->team * w, B->team);
-    if (ctas <= 0) continue;
-    for (float m : margins) {
-      GrowArgs a = B->args;
-      a.order = d_idx;
-      a.n_order = ns;
-      a.n_steps = B->max_target;
-      a.dynamic = 1;
-      a.list_margin = m;
-      const int grid = std::max(1, std::min((ns + w - 1) / w, nsm * ctas));
-      if ((rs = vine_batch_reset(B, st)) != VINE_OK) break;
-      cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
-      if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-      if (e == cudaSuccess) e = launch_grow(a, B->ks, grid, B->team * w, smem, st);
-      if (e == cudaSuccess) e = cudaEventRecord(e1, st);
-      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-      float ms = 0.f;
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-      if (e != cudaSuccess) {
-        rs = cuda_fail(e, "vine_autotune");
-        break;
+  // grows the sample's classes L[0..nc) from reset; time in ms (< 0: failed)
+  auto timed = [&](const LaunchClass* L, int nc, float margin) -> double {
+    if ((rs = vine_batch_reset(B, st)) != VINE_OK) return -1.0;
+    int mt = 1;
+    for (int c = 0; c < nc; ++c) mt = std::max(mt, L[c].max_target);
+    cudaError_t e = cudaEventRecord(e0, st);
+    if (e == cudaSuccess) e = launch_classes(B, L, nc, d_idx, mt, margin, 0, 0, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      rs = cuda_fail(e, "vine_autotune");
+      return -1.0;
+    }
+    out->candidates += 1;
+    return ms;
+  };
+  // the configuration chosen at creation, all classes together
+  LaunchClass best[kMaxClass];
+  for (int c = 0; c < B->n_class; ++c) {
+    best[c] = SL[c];
+    shape_class(B, best[c], SL[c].team, SL[c].wpc, nsm);
+  }
+  out->default_ms = timed(best, B->n_class, B->margin);
+  // per class: threads per robot (32, 64, 128; one-warp teams also with 4,
+  // 2 or 1 robots per CTA), each class timed alone on its sample
+  for (int c = 0; c < B->n_class && rs == VINE_OK; ++c) {
+    double cbest = 1e30;
+    const int shapes[5][2] = {{32, 4}, {32, 2}, {32, 1}, {64, 1}, {128, 1}};
+    for (const auto& sh : shapes) {
+      LaunchClass L = SL[c];
+      L.off = 0;  // this class alone: its sample segment at the start
+      if (!shape_class(B, L, sh[0], sh[1], nsm)) continue;
+      LaunchClass Lr = L;
+      Lr.off = SL[c].off;
+      const double ms = timed(&Lr, 1, B->margin);
+      if (rs != VINE_OK) break;
+      if (ms >= 0.0 && ms < cbest) {
+        cbest = ms;
+        best[c] = Lr;
       }
-      out->candidates += 1;
-      if (w == B->wpc && m == kListMargin) out->default_ms = ms;
-      if (ms < out->best_ms) {
-        out->best_ms = ms;
-        out->warps_per_cta = w;
-        out->list_margin = m;
-      }
+    }
+    out->class_ms[c] = cbest;
+  }
+  // the broad-phase margin (0.5, 1, 2 body radii) for all classes together
+  double bms = 1e30;
+  float bm = B->margin;
+  const float margins[3] = {0.5f, kListMargin, 2.0f};
+  for (float m : margins) {
+    if (rs != VINE_OK) break;
+    const double ms = timed(best, B->n_class, m);
+    if (ms >= 0.0 && ms < bms) {
+      bms = ms;
+      bm = m;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rs != VINE_OK) return rs;
-  if (out->candidates == 0) return fail(VINE_EINVAL, "vine_autotune: no launch configuration fits");
-  // adopt the fastest (results do not depend on either knob)
-  B->wpc = out->warps_per_cta;
-  const int ctas = grow_max_ctas_per_sm(B->ks, B->smem_warp * B->wpc, B->team * B->wpc, B->team);
-  B->grid = std::max(1, std::min((n + B->wpc - 1) / B->wpc, nsm * std::max(ctas, 1)));
-  B->args.list_margin = out->list_margin;
+  out->best_ms = bms;
+  out->list_margin = bm;
+  const bool adopt = bms < out->default_ms;
+  for (int c = 0; c < B->n_class; ++c) {
+    if (adopt) {
+      LaunchClass L = B->cls[c];
+      shape_class(B, L, best[c].team, best[c].wpc, nsm);  // the full class with the chosen shape
+      B->cls[c] = L;
+    }
+    out->class_threads[c] = B->cls[c].team;
+    out->class_robots_per_cta[c] = B->cls[c].wpc;
+  }
+  if (adopt) B->margin = bm;
+  out->adopted = adopt ? 1 : 0;
+  out->warps_per_cta = B->cls[0].wpc * B->cls[0].team / 32;
+  if (!adopt) {
+    out->best_ms = out->default_ms;
+    out->list_margin = B->margin;
+  }
   if (B->graph_exec) {  // the recorded launch carries the old configuration
     cudaGraphExecDestroy(B->graph_exec);
     cudaGraphDestroy(B->graph);
@@ -832,10 +979,19 @@ vine_status vine_simulate_plain(vine_batch* B, void* stream_v) {
   a.n_steps = B->max_target;
   a.dynamic = 0;
   a.n_order = 1;
-  for (int k = 0; k < B->n_inst; ++k) {
-    a.order = B->args.order + k;
-    CK(grow_configure(B->ks, B->smem_warp, B->team));
-    CK(launch_grow(a, B->ks, 1, B->team, B->smem_warp, st));
+  a.list_margin = B->margin;
+  for (int c = 0; c < B->n_class; ++c) {
+    const LaunchClass& L = B->cls[c];
+    a.nmax = L.nmax;
+    a.omax = L.omax;
+    a.amax = L.amax;
+    a.warp_floats = (int)(L.smem_warp / sizeof(float));
+    a.team = L.team;
+    CK(grow_configure(B->ks, L.smem_warp, L.team));
+    for (int k = L.off; k < L.off + L.count; ++k) {
+      a.order = B->args.order + k;
+      CK(launch_grow(a, B->ks, 1, L.team, L.smem_warp, st));
+    }
   }
   return VINE_OK;
 }
@@ -1067,7 +1223,9 @@ vine_status vine_grad(const vine_batch* B, const float* goal_xy, double* cost, d
   const int n = B->n_inst;
   const size_t na = (size_t)B->n_act;
   // one warp per CTA, several CTAs per SM; the robots come longest first
-  const int grid = std::max(1, std::min(n, B->grid * B->wpc * (B->team / 32)));  // resident warps
+  int nsm = 1;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, B->device);
+  const int grid = std::max(1, std::min(n, 16 * nsm));
   GradArgs g{};
   if (ptrs_are_device) {
     g.goal = goal_xy;
@@ -1212,9 +1370,23 @@ vine_status vine_batch_info(const vine_batch* B, int32_t* n_inst, int64_t* total
 vine_status vine_batch_launch(const vine_batch* B, int32_t* threads_per_robot, int32_t* robots_per_cta,
                               int32_t* grid) {
   if (!B) return fail(VINE_EINVAL, "vine_batch_launch: null batch");
-  if (threads_per_robot) *threads_per_robot = B->team;
-  if (robots_per_cta) *robots_per_cta = B->wpc;
-  if (grid) *grid = B->grid;
+  if (threads_per_robot) *threads_per_robot = B->cls[0].team;
+  if (robots_per_cta) *robots_per_cta = B->cls[0].wpc;
+  if (grid) *grid = B->cls[0].grid;
+  return VINE_OK;
+}
+
+vine_status vine_batch_classes(const vine_batch* B, int32_t* n_class, int32_t* threads_per_robot, int32_t* robots,
+                               int32_t* robots_per_cta, int32_t* grid, int32_t* max_links) {
+  if (!B || !n_class) return fail(VINE_EINVAL, "vine_batch_classes: null argument");
+  *n_class = B->n_class;
+  for (int c = 0; c < B->n_class; ++c) {
+    if (threads_per_robot) threads_per_robot[c] = B->cls[c].team;
+    if (robots) robots[c] = B->cls[c].count;
+    if (robots_per_cta) robots_per_cta[c] = B->cls[c].wpc;
+    if (grid) grid[c] = B->cls[c].grid;
+    if (max_links) max_links[c] = B->cls[c].max_target;
+  }
   return VINE_OK;
 }
 
@@ -1224,6 +1396,7 @@ vine_status vine_batch_destroy(vine_batch* B) {
   if (B->graph_exec) cudaGraphExecDestroy(B->graph_exec);
   if (B->graph) cudaGraphDestroy(B->graph);
   if (B->cap_stream) cudaStreamDestroy(B->cap_stream);
+  release_launch_streams(B);
   if (B->stage) cudaFree(B->stage);
   if (B->dmem) cudaFree(B->dmem);
   delete B;

@@ -73,7 +73,9 @@ class vine_server_stats(C.Structure):
 
 class vine_tune_result(C.Structure):
     _fields_ = [("warps_per_cta", C.c_int32), ("list_margin", C.c_float), ("best_ms", C.c_double),
-                ("default_ms", C.c_double), ("candidates", C.c_int32), ("sample", C.c_int32)]
+                ("default_ms", C.c_double), ("candidates", C.c_int32), ("sample", C.c_int32),
+                ("n_class", C.c_int32), ("adopted", C.c_int32), ("class_threads", C.c_int32 * 3),
+                ("class_robots_per_cta", C.c_int32 * 3), ("class_ms", C.c_double * 3)]
 
 
 _p, _i32, _i64 = C.c_void_p, C.c_int32, C.c_int64
@@ -103,6 +105,7 @@ _SIG = {
     "vine_sst_prune": [_i32, _p, _p, _p, _i32, _p, _p, C.c_float, C.c_float, _p, _p, _i32, _p],
     "vine_sst_select": [_i32, _p, _p, _p, _i32, _p, C.c_float, C.c_float, _p, _i32, _p],
     "vine_autotune": [_p, _i32, _p, _p],
+    "vine_batch_classes": [_p, _p, _p, _p, _p, _p, _p],
     "vine_grad": [_p, _p, _p, _p, _p, _p, _p, _i32, _p],
     "vine_batch_destroy": [_p],
     "vine_server_config_default": [_p],
@@ -256,7 +259,19 @@ class Batch:
         (vine_autotune); leaves the batch reset."""
         r = vine_tune_result()
         _check(_lib.vine_autotune(self.h, int(sample), _stream(stream), C.byref(r)), "vine_autotune")
-        return {k: getattr(r, k) for k, _ in vine_tune_result._fields_}
+        out = {k: getattr(r, k) for k, _ in vine_tune_result._fields_}
+        for k in ("class_threads", "class_robots_per_cta", "class_ms"):
+            out[k] = list(out[k])[: r.n_class]
+        return out
+
+    def classes(self) -> list:
+        """vine_batch_classes: per length class (longest robots first) threads
+        per robot, robots, robots per CTA, CTAs and the longest robot's links."""
+        n = C.c_int32()
+        a = [np.zeros(3, np.int32) for _ in range(5)]
+        _check(_lib.vine_batch_classes(self.h, C.byref(n), *[_ptr(x) for x in a]), "vine_batch_classes")
+        keys = ("threads_per_robot", "robots", "robots_per_cta", "grid", "max_links")
+        return [{k: int(x[c]) for k, x in zip(keys, a)} for c in range(n.value)]
 
     def simulate_plain(self, stream=None):
         _check(_lib.vine_simulate_plain(self.h, _stream(stream)), "vine_simulate_plain")

@@ -190,15 +190,15 @@ def _switches_start_at_snap_throughs(sc, idx, tp, final_state=None, steps=None):
     return first
 
 
-def _check_switches(b, st, sc, cls, idx_gpu=None):
+def _check_switches(b, st, sc, cls, idx_gpu=None, tp=0):
     """Every whole-growth switch of cls starts at a snap-through, and they
-    stay a small fraction of the compared robots."""
+    stay a small fraction of the compared robots.  tp: the threads per robot
+    the batch was created with (0: the length classes)."""
     n = len(cls)
     idx_gpu = list(range(n)) if idx_gpu is None else list(idx_gpu)
     sw = [k for k, c in enumerate(cls) if c == "switch"]
     if not sw:
         return []
-    tp = b.launch()["threads_per_robot"]
     fin = [(b.theta_of(st, idx_gpu[k]), st["l"][idx_gpu[k]]) for k in sw]
     first = _switches_start_at_snap_throughs(sc, sw, tp, final_state=fin)
     # whole growths pass through several snap-throughs each, where FP32
@@ -225,7 +225,7 @@ def test_parity_batch_full(tp):
     assert stats["steps_converged"] == 64 * 20
     assert stats["robot_link_steps"] == scenes.robot_link_steps(sc["n_links"])
     cls = _classify(b, st, orc, ost, sc, counts, pairs)
-    first = _check_switches(b, st, sc, cls)
+    first = _check_switches(b, st, sc, cls, tp=tp)
     print("parity batch: %d match, %d basin switches (parting at steps %s)" % (
         cls.count("match"), cls.count("switch"), first))
     b.close()
@@ -357,7 +357,7 @@ def test_chain_grown_past_256_links(tp):
     orc.run(ost, 320, threads=THREADS)
     assert np.all((st["N"] == 320) | (st["status"] != 0))
     cls = _classify(b, st, orc, ost, sc, counts, pairs)
-    first = _check_switches(b, st, sc, cls)
+    first = _check_switches(b, st, sc, cls, tp=tp)
     print("320-link robots: %d match, %d switches (parting at steps %s), %d flagged" % (
         cls.count("match"), cls.count("switch"), first, cls.count("flagged")))
     assert cls.count("flagged") <= 1
@@ -397,7 +397,7 @@ def test_design_batch_full_size_sampled(tp):
     ost = orc.new_state()
     orc.run(ost, 100, threads=THREADS)
     cls = _classify(b, st, orc, ost, sub, counts, pairs, idx_gpu=idx)
-    first = _check_switches(b, st, sub, cls, idx_gpu=idx)
+    first = _check_switches(b, st, sub, cls, idx_gpu=idx, tp=tp)
     print("design batch sample: %d match, %d basin switches (parting at steps %s), %d flagged" % (
         cls.count("match"), cls.count("switch"), first, cls.count("flagged")))
     assert cls.count("flagged") <= 2
