@@ -130,7 +130,13 @@ def run_gpu(args):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    sc = scenes.design_batch(args.robots, replicate=rank)
+    if ws > 1 and args.shard == "lpt":
+        # one batch split over the ranks (strong scaling): LPT shards by cost
+        from paper_2509_15180_gb300 import shard
+        full = scenes.design_batch(args.robots)
+        sc = scenes.subset(full, shard.lpt_partition(shard.robot_cost(full), ws)[rank])
+    else:
+        sc = scenes.design_batch(args.robots, replicate=rank)  # a replica per rank (weak scaling)
     rls_per_step = scenes.robot_link_steps(sc["n_links"])
     stream = torch.cuda.current_stream()
     dsc = {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in sc.items()}
@@ -241,9 +247,21 @@ def run_gpu(args):
                        14.0 * (st_last["pair_tests"] - st_last["circle_pair_tests"]))
     launch_s = float(np.mean(step_ms)) / 1e3
     achieved = flops / launch_s / 1e12
+    # the survey's algorithmic work: I W per robot-link-step, I the Newton
+    # iterations per growth step, W = 40 + K_s (10 N_circ + 14 N_box) flops
+    # per link and iteration (1000 for 20 circles and 20 boxes, K_s = 2)
+    n_obs = np.diff(sc["obs_ptr"]).astype(np.int64)
+    n_c = np.bincount(np.repeat(np.arange(n_obs.size), n_obs), weights=(sc["obs_kind"] == 0), minlength=n_obs.size)
+    W = float(np.mean(40.0 + 2.0 * (10.0 * n_c + 14.0 * (n_obs - n_c))))
+    iters_per_step = st_last["iterations"] / max(st_last["steps_total"], 1)
+    flops_s8d = st_last["robot_link_steps"] * iters_per_step * W
     traffic = args.traffic if args.traffic is not None else GROW_DRAM_BYTES_PER_ROBOT * n
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+                "frac_s8d": flops_s8d / launch_s / 1e12 / FP32_PEAK_TFLOPS,
+                "flops_s8d_per_launch": flops_s8d,
+                "s8d_what": "robot-link-steps x Newton iterations per step (%.2f) x W = %.0f flops per link and "
+                            "iteration (40 + K_s (10 N_circ + 14 N_box))" % (iters_per_step, W),
                 "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of a 1024-robot launch, "
                                   "scaled by robots",
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived; MEASURED_PEAKS has no FP32 figure)",
@@ -266,6 +284,7 @@ def run_gpu(args):
     robust = None
     if ws == 1 and args.robust_perturb > 0:
         robust = robust_leg(args, vine, scenes, torch, stream, flush)
+    stud = studies_leg(args) if ws == 1 and args.robust_trials > 0 else None
     plan = None
     if ws == 1 and args.plan_seconds > 0:
         plan = planner_leg(args, scenes)
@@ -278,14 +297,15 @@ def run_gpu(args):
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64 residual test)", "data": "synthetic",
+            "scaling": "strong" if (ws > 1 and args.shard == "lpt") else "weak", "vs_baseline": None,
+            "dtype": "f32 (f64 residual test)", "data": "synthetic",
             "config": {"workload": WORKLOAD if n == 4096 else WORKLOAD.replace("4096", str(n)),
                        "robots_per_gpu": n, "links": 100, "threads_per_robot": b.launch()["threads_per_robot"],
                        "robot_link_steps_per_step": rls_per_step, "l2": "flushed between timed steps (512 MiB write)",
                        "tol": 1e-6},
             "e2e": e2e, "plain": plain, "latency": lat, "roofline": roofline, "cpu_baseline": cpu,
             "adjoint": adjoint, "serving": serve, "uneven": uneven, "robustness": robust,
-            "overlapped": overlapped, "planner": plan, "synthesis": synth_r, "surrogate": surr,
+            "overlapped": overlapped, "planner": plan, "synthesis": synth_r, "surrogate": surr, "studies": stud,
             "clocks": ck, "gpu_launches": args.steps, "robots": robots,
             "solver": {"iters_per_step": st_last["iterations"] / max(st_last["steps_total"], 1),
                        "evals_per_step": st_last["evaluations"] / max(st_last["steps_total"], 1),
@@ -443,18 +463,24 @@ def uneven_leg(args, vine, scenes, torch, stream, flush):
         return rls / (sum(ms) / 1e3), float(np.mean(ms))
 
     v0, ms0 = timed(2)
-    tpr = b.launch()["threads_per_robot"]
+    cls0 = b.classes()
+    t0 = time.perf_counter()
     tune = b.autotune(args.uneven_sample, stream)
+    tune_s = time.perf_counter() - t0
     v1, ms1 = timed(2)
+    cls1 = b.classes()
     b.close()
+    shape = lambda cl: [{k: c[k] for k in ("threads_per_robot", "robots", "robots_per_cta", "max_links")} for c in cl]
     return {"workload": "uneven batch: %d robots, links U{30..300} of U[1,3] cm, 5-200 obstacles, 0-8 actuators"
                         % args.uneven_robots,
             "robot_link_steps_per_step": scenes.robot_link_steps(sc["n_links"]),
-            "threads_per_robot": tpr,
-            "default": {"value": v0, "ms_per_step": ms0},
-            "autotuned": {"value": v1, "ms_per_step": ms1, "warps_per_cta": tune["warps_per_cta"],
+            "default": {"value": v0, "ms_per_step": ms0, "classes": shape(cls0)},
+            "autotuned": {"value": v1, "ms_per_step": ms1, "classes": shape(cls1), "adopted": tune["adopted"],
                           "list_margin_R": tune["list_margin"], "candidates": tune["candidates"],
-                          "sample": tune["sample"]},
+                          "sample": tune["sample"], "sample_ms_default": tune["default_ms"],
+                          "sample_ms_tuned": tune["best_ms"], "tuning_s": tune_s},
+            "what": "one vine_simulate (length classes, one persistent launch each on a parallel graph branch) "
+                    "with the classes' team sizes chosen at creation, then after vine_autotune",
             "unit": UNIT}
 
 
@@ -470,7 +496,7 @@ def robust_leg(args, vine, scenes, torch, stream, flush):
     b.grad(g, stream)
     torch.cuda.synchronize()
     ms_f, ms_g, rls = [], [], 0
-    for _ in range(2):
+    for _ in range(args.robust_repeats):
         flush.zero_()
         b.reset(stream)
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
@@ -489,6 +515,29 @@ def robust_leg(args, vine, scenes, torch, stream, flush):
                         % (args.robust_designs, args.robust_perturb),
             "value": rls / (sum(ms_f) / 1e3), "unit": UNIT, "simulate_ms": float(np.mean(ms_f)),
             "grad_ms": float(np.mean(ms_g)), "grad_ok": int((st == 0).sum()), "robots": int(st.size)}
+
+
+def studies_leg(args):
+    """The analysis workloads (Sec. 6.3, 6.4): the robustness sweep (11
+    uncertainty levels 0-20 %, 1000 perturbed trials each, obstacle and
+    actuation kinds, each kind one vine_simulate over all its levels) and the
+    funnelling rollouts (50 start headings x 4 environments, one
+    vine_simulate).  Wall time per launch includes batch creation and the
+    read-back of the tips."""
+    from paper_2509_15180_gb300 import studies
+    r = studies.robustness(trials=args.robust_trials)
+    f = studies.funnel()
+    out = {"robustness": {k: {"success_rate": r[k]["success_rate"], "robots": r[k]["robots"],
+                              "not_converged": r[k]["not_converged"], "seconds": r[k]["seconds"],
+                              "robot_link_steps_per_s": r[k]["robot_link_steps"] / r[k]["seconds"]}
+                          for k in ("obstacles", "actuation")},
+           "levels": list(r["levels"]), "trials_per_level": r["trials"], "goal_radius_m": r["goal_radius"],
+           "funnel": {"obstacles": f["obstacles"], "rollouts": f["rollouts"],
+                      "knn_concentration_ratio": f["ratio"], "seconds": f["seconds"],
+                      "not_converged": f["not_converged"]},
+           "what": "seeded stand-ins for the paper's environment and design (its figures only); success = grown "
+                   "to full length with the tip within the goal radius of the nominal design's tip"}
+    return out
 
 
 def overlapped_leg(args, vine, scenes, torch, sc):
@@ -674,6 +723,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--robots", type=int, default=4096, help="robots per GPU (the workload has 4096)")
+    ap.add_argument("--shard", default="replica", choices=["replica", "lpt"],
+                    help="N > 1: a replica of the workload per rank (weak scaling) or one workload split over "
+                         "the ranks by LPT on N^2 (K_s n_obs + 8) (strong scaling)")
     ap.add_argument("--threads-per-robot", type=int, default=0, choices=[0, 32, 64, 128],
                     help="design-batch legs: threads per robot (0: the library's choice by robot length)")
     ap.add_argument("--plain-robots", type=int, default=64)
@@ -684,11 +736,13 @@ def main():
     ap.add_argument("--traffic", type=float, default=None)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-overlap", action="store_true")
-    ap.add_argument("--uneven-robots", type=int, default=4096)
+    ap.add_argument("--uneven-robots", type=int, default=16384)
     ap.add_argument("--uneven-threads-per-robot", type=int, default=0, choices=[0, 32, 64, 128])
     ap.add_argument("--uneven-sample", type=int, default=2048)
     ap.add_argument("--robust-designs", type=int, default=64)
-    ap.add_argument("--robust-perturb", type=int, default=32)
+    ap.add_argument("--robust-perturb", type=int, default=1024)
+    ap.add_argument("--robust-repeats", type=int, default=1)
+    ap.add_argument("--robust-trials", type=int, default=1000, help="studies leg: trials per uncertainty level (0: skip)")
     ap.add_argument("--plan-seconds", type=float, default=20.0, help="planner leg budget (0: skip)")
     ap.add_argument("--synth-targets", type=int, default=100000, help="design-synthesis leg targets (0: skip)")
     ap.add_argument("--surrogate-steps", type=int, default=3000, help="surrogate leg Adam steps (0: skip)")

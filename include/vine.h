@@ -335,6 +335,23 @@ vine_status vine_set_state(vine_batch* b, const int32_t* n_present, const float*
 vine_status vine_grad(const vine_batch* b, const float* goal_xy, double* cost, double* d_pressure, double* d_begin,
                       double* d_end, int32_t* grad_status, int32_t ptrs_are_device, void* cuda_stream);
 
+/* Adjoint of a path cost (the benchmark spec (3); the path the planner of Sec. 5
+ * grows along, as target points of the link ends):
+ *   cost[n] = (1/N) sum_{k=1..N} |p_k - q_k|^2, p_k the end point of link
+ *     k-1 (p_N the tip) at the current state, q_k = path_xy[2 (o_i + k - 1)
+ *     .. + 1] the targets (m, absolute), o_i the robot's offset in the
+ *     joint-angle layout (sum of the earlier robots' n_links), so path_xy
+ *     holds 2 sum n_links floats; a robot with N < n_links links uses its
+ *     first N targets;
+ *   derivatives and grad_status as vine_grad.
+ * d cost / d theta_j = (2/N) sum_{k > j} (p_k - q_k) . (z x (p_k - p_j)),
+ * d cost / d l_last = (2/N) (p_N - q_N) . u_{N-1}; the adjoint as
+ * vine_grad.  An instance with no links has cost 0.  ptrs_are_device as
+ * vine_grad. */
+vine_status vine_grad_path(const vine_batch* b, const float* path_xy, double* cost, double* d_pressure,
+                           double* d_begin, double* d_end, int32_t* grad_status, int32_t ptrs_are_device,
+                           void* cuda_stream);
+
 /* Batch counters (host struct; synchronises the stream). */
 vine_status vine_get_stats(const vine_batch* b, vine_stats* out, void* cuda_stream);
 

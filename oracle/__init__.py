@@ -94,6 +94,8 @@ def lib():
         L.orc_gn_step.argtypes = [p, p, p, i, i, p, d, p, p, p, p, i]
         L.orc_grad.restype = i
         L.orc_grad.argtypes = [p, p, p, i, i, p, d, d, d, p, p, p, p]
+        L.orc_grad_path.restype = i
+        L.orc_grad_path.argtypes = [p, p, p, i, i, p, d, p, p, p, p, p, p]
         L.orc_set_trace.argtypes = [i]
         L.orc_run.restype = i
         L.orc_run.argtypes = [p, p, p, i, p, p, p, p, p, p, p, p, p, i]
@@ -264,6 +266,21 @@ class Oracle:
         c = C.c_double()
         rc = lib().orc_grad(C.byref(self.P), C.byref(self.B), self.T, int(i), th.size, _ptr(th), float(l),
                             float(goal[0]), float(goal[1]), C.byref(c), _ptr(dP), _ptr(dB), _ptr(dE))
+        return c.value, dP[:na], dB[:na], dE[:na], rc
+
+    def grad_path(self, i: int, theta, l: float, path):
+        """Path cost (1/N) sum_k |p_k - q_k|^2 over the link end points p_1..p_N
+        against targets path[k-1] = q_k ([N, 2], absolute), at the equilibrium
+        (theta, l), and its adjoint derivatives as grad().  Returns
+        (cost, dP, dB, dE, status)."""
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        q = np.asarray(path, dtype=np.float64).reshape(-1, 2)[: th.size]
+        qx, qy = np.ascontiguousarray(q[:, 0]), np.ascontiguousarray(q[:, 1])
+        na = int(self._keep["act_ptr"][i + 1] - self._keep["act_ptr"][i])
+        dP, dB, dE = np.zeros(max(na, 1)), np.zeros(max(na, 1)), np.zeros(max(na, 1))
+        c = C.c_double()
+        rc = lib().orc_grad_path(C.byref(self.P), C.byref(self.B), self.T, int(i), th.size, _ptr(th), float(l),
+                                 _ptr(qx), _ptr(qy), C.byref(c), _ptr(dP), _ptr(dB), _ptr(dE))
         return c.value, dP[:na], dB[:na], dE[:na], rc
 
     def poses(self, i: int, theta, l: float):

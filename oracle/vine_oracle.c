@@ -936,17 +936,54 @@ int orc_gn_step(const orc_params* p, const orc_batch* b, const orc_tables* T, in
  * Outputs dP, dB, dE have one entry per actuator of instance i.  Returns 0,
  * or 1 when the exact Hessian is not positive definite at x* (no gradient;
  * outputs NaN). */
+/* The adjoint part shared by the costs: lambda = H^-1 rhs (rhs = dc/dx),
+ * then dc/dq = -lambda . d(grad J)/dq for each actuator's pressure, begin and
+ * end.  H is the exact Hessian at (th, l); the distal length is dropped when
+ * its bound is active.  Returns 0, or 1 when H is not positive definite
+ * (outputs NaN). */
+static int adjoint_design(const inst_t* I, const orc_batch* b, const orc_tables* T, int N, const double* th,
+                          double l, const double* H, const double* g, double* rhs, double* dP, double* dB,
+                          double* dE) {
+  const orc_params* p = I->p;
+  const int n = N + 1, na = I->a1 - I->a0;
+  double* Hc = (double*)malloc(sizeof(double) * n * n);
+  double* lam = (double*)malloc(sizeof(double) * n);
+  memcpy(Hc, H, sizeof(double) * n * n);
+  const int lfix = (l <= 0.0 && g[N] > 0.0) || (l >= I->l_seg && g[N] < 0.0);
+  const int m = lfix ? N : n;
+  int rc = N > 0 ? chol_solve(Hc, n, m, rhs, lam) : 0;
+  if (lfix) lam[N] = 0.0;
+  for (int a = 0; a < na; ++a) {
+    dP[a] = dB[a] = dE[a] = rc ? NAN : 0.0;
+    if (rc) continue;
+    const int ga = I->a0 + a;
+    const double bg = b->act_begin[ga], en = b->act_end[ga];
+    const double s = (double)b->act_side[ga], Pa = b->act_pressure[ga];
+    const orc_table* t = &T->tab[T->act_tab[ga]];
+    const double jb = floor(bg), je = floor(en);
+    for (int j = 0; j < N; ++j) {
+      double f, fp;
+      table_f(t, s * I->d * th[j] / I->l_seg, &f, &fp);
+      /* d g_j / d P_a = -w_a c_aj s f d */
+      dP[a] += lam[j] * p->w_a * coverage(bg, en, j) * s * f * I->d;
+      if (bg < en && (double)j == jb) dB[a] -= lam[j] * p->w_a * s * Pa * f * I->d;
+      if (bg < en && (double)j == je) dE[a] += lam[j] * p->w_a * s * Pa * f * I->d;
+    }
+  }
+  free(Hc); free(lam);
+  return rc ? 1 : 0;
+}
+
 int orc_grad(const orc_params* p, const orc_batch* b, const orc_tables* T, int i, int N, const double* th,
              double l, double gx, double gy, double* cost, double* dP, double* dB, double* dE) {
   inst_t I;
   inst_init(&I, p, b, T, i);
-  const int n = N + 1, na = I.a1 - I.a0;
+  const int n = N + 1;
   geo_t G;
   geo_alloc(&G, N);
   double* g = (double*)malloc(sizeof(double) * n);
   double* H = (double*)malloc(sizeof(double) * n * n);
   double* rhs = (double*)malloc(sizeof(double) * n);
-  double* lam = (double*)malloc(sizeof(double) * n);
   energy_h(&I, N, th, l, g, H, &G, NULL, 1);
   const double ex = G.px[N] - gx, ey = G.py[N] - gy;
   const double c = sqrt(ex * ex + ey * ey);
@@ -955,30 +992,48 @@ int orc_grad(const orc_params* p, const orc_batch* b, const orc_tables* T, int i
   /* dc/dtheta_j = s . (z x (p_N - p_j)), dc/dl = s . u_{N-1} */
   for (int j = 0; j < N; ++j) rhs[j] = -sx * (G.py[N] - G.py[j]) + sy * (G.px[N] - G.px[j]);
   rhs[N] = N > 0 ? sx * G.ux[N - 1] + sy * G.uy[N - 1] : 0.0;
-  const int lfix = (l <= 0.0 && g[N] > 0.0) || (l >= I.l_seg && g[N] < 0.0);
-  const int m = lfix ? N : n;
-  int rc = N > 0 ? chol_solve(H, n, m, rhs, lam) : 0;
-  if (lfix) lam[N] = 0.0;
-  for (int a = 0; a < na; ++a) {
-    dP[a] = dB[a] = dE[a] = rc ? NAN : 0.0;
-    if (rc) continue;
-    const int ga = I.a0 + a;
-    const double bg = b->act_begin[ga], en = b->act_end[ga];
-    const double s = (double)b->act_side[ga], Pa = b->act_pressure[ga];
-    const orc_table* t = &T->tab[T->act_tab[ga]];
-    const double jb = floor(bg), je = floor(en);
-    for (int j = 0; j < N; ++j) {
-      double f, fp;
-      table_f(t, s * I.d * th[j] / I.l_seg, &f, &fp);
-      /* d g_j / d P_a = -w_a c_aj s f d */
-      dP[a] += lam[j] * p->w_a * coverage(bg, en, j) * s * f * I.d;
-      if (bg < en && (double)j == jb) dB[a] -= lam[j] * p->w_a * s * Pa * f * I.d;
-      if (bg < en && (double)j == je) dE[a] += lam[j] * p->w_a * s * Pa * f * I.d;
-    }
-  }
-  free(g); free(H); free(rhs); free(lam);
+  const int rc = adjoint_design(&I, b, T, N, th, l, H, g, rhs, dP, dB, dE);
+  free(g); free(H); free(rhs);
   geo_free(&G);
-  return rc ? 1 : 0;
+  return rc;
+}
+
+/* Path cost: the mean squared distance of the link end points p_1..p_N to
+ * target points q_1..q_N (a path the robot should follow, sampled at its
+ * link ends), c = (1/N) sum_k |p_k - q_k|^2, and its adjoint derivatives as
+ * orc_grad.  qx, qy: N targets each.
+ *   dc/dtheta_j = (2/N) sum_{k > j} e_k . (z x (p_k - p_j)),  e_k = p_k - q_k
+ *   dc/dl       = (2/N) e_N . u_{N-1}                                       */
+int orc_grad_path(const orc_params* p, const orc_batch* b, const orc_tables* T, int i, int N, const double* th,
+                  double l, const double* qx, const double* qy, double* cost, double* dP, double* dB, double* dE) {
+  inst_t I;
+  inst_init(&I, p, b, T, i);
+  const int n = N + 1;
+  geo_t G;
+  geo_alloc(&G, N);
+  double* g = (double*)malloc(sizeof(double) * n);
+  double* H = (double*)malloc(sizeof(double) * n * n);
+  double* rhs = (double*)malloc(sizeof(double) * n);
+  energy_h(&I, N, th, l, g, H, &G, NULL, 1);
+  double c = 0.0;
+  for (int k = 1; k <= N; ++k) {
+    const double ex = G.px[k] - qx[k - 1], ey = G.py[k] - qy[k - 1];
+    c += ex * ex + ey * ey;
+  }
+  *cost = N > 0 ? c / N : 0.0;
+  for (int j = 0; j < N; ++j) {
+    double s = 0.0;
+    for (int k = j + 1; k <= N; ++k) {
+      const double ex = G.px[k] - qx[k - 1], ey = G.py[k] - qy[k - 1];
+      s += -ex * (G.py[k] - G.py[j]) + ey * (G.px[k] - G.px[j]);
+    }
+    rhs[j] = 2.0 * s / N;
+  }
+  rhs[N] = N > 0 ? 2.0 * ((G.px[N] - qx[N - 1]) * G.ux[N - 1] + (G.py[N] - qy[N - 1]) * G.uy[N - 1]) / N : 0.0;
+  const int rc = adjoint_design(&I, b, T, N, th, l, H, g, rhs, dP, dB, dE);
+  free(g); free(H); free(rhs);
+  geo_free(&G);
+  return rc;
 }
 
 /* Link start points p_0..p_N and headings psi_0..psi_{N-1}. */

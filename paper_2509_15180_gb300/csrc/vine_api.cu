@@ -1215,20 +1215,23 @@ vine_status vine_synthesize(const vine_synth_spec* spec, const vine_params* para
   return VINE_OK;
 }
 
-vine_status vine_grad(const vine_batch* B, const float* goal_xy, double* cost, double* d_pressure, double* d_begin,
-                      double* d_end, int32_t* grad_status, int32_t ptrs_are_device, void* stream_v) {
-  if (!B || !goal_xy || !cost || !grad_status || (B->n_act > 0 && (!d_pressure || !d_begin || !d_end)))
-    return fail(VINE_EINVAL, "vine_grad: null argument");
-  cudaStream_t st = (cudaStream_t)stream_v;
+// The adjoint launch shared by vine_grad (kind 0) and vine_grad_path (kind
+// 1); `target` holds n_target floats (2 n goals or 2 sum n_links targets).
+static vine_status grad_launch(const vine_batch* B, int kind, const float* target, size_t n_target, double* cost,
+                               double* d_pressure, double* d_begin, double* d_end, int32_t* grad_status,
+                               int32_t ptrs_are_device, cudaStream_t st, const char* who) {
+  if (!B || !target || !cost || !grad_status || (B->n_act > 0 && (!d_pressure || !d_begin || !d_end)))
+    return fail(VINE_EINVAL, who);
   const int n = B->n_inst;
   const size_t na = (size_t)B->n_act;
-  // one warp per CTA, several CTAs per SM; the robots come longest first
   int nsm = 1;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, B->device);
+  // one warp per CTA, several CTAs per SM; the robots come longest first
   const int grid = std::max(1, std::min(n, 16 * nsm));
   GradArgs g{};
+  g.kind = kind;
   if (ptrs_are_device) {
-    g.goal = goal_xy;
+    g.goal = target;
     g.cost = cost;
     g.dP = d_pressure;
     g.dB = d_begin;
@@ -1237,9 +1240,10 @@ vine_status vine_grad(const vine_batch* B, const float* goal_xy, double* cost, d
     CK(launch_grad(B->args, g, B->ks, grid, B->smem_warp, st));
     return VINE_OK;
   }
-  const size_t o_goal = 0, o_cost = align256(8 * (size_t)n), o_stat = o_cost + align256(8 * (size_t)n),
-               o_dp = o_stat + align256(4 * (size_t)n), o_db = o_dp + align256(8 * std::max<size_t>(na, 1)),
-               o_de = o_db + align256(8 * std::max<size_t>(na, 1)), total = o_de + align256(8 * std::max<size_t>(na, 1));
+  const size_t o_goal = 0, o_cost = align256(4 * std::max<size_t>(n_target, 1)),
+               o_stat = o_cost + align256(8 * (size_t)n), o_dp = o_stat + align256(4 * (size_t)n),
+               o_db = o_dp + align256(8 * std::max<size_t>(na, 1)), o_de = o_db + align256(8 * std::max<size_t>(na, 1)),
+               total = o_de + align256(8 * std::max<size_t>(na, 1));
   vine_status s = ensure_stage(B, total);
   if (s != VINE_OK) return s;
   char* sg = (char*)B->stage;
@@ -1249,7 +1253,7 @@ vine_status vine_grad(const vine_batch* B, const float* goal_xy, double* cost, d
   g.dP = (double*)(sg + o_dp);
   g.dB = (double*)(sg + o_db);
   g.dE = (double*)(sg + o_de);
-  CK(cudaMemcpyAsync(sg + o_goal, goal_xy, 8 * (size_t)n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(sg + o_goal, target, 4 * n_target, cudaMemcpyHostToDevice, st));
   CK(launch_grad(B->args, g, B->ks, grid, B->smem_warp, st));
   CK(cudaMemcpyAsync(cost, g.cost, 8 * (size_t)n, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(grad_status, g.gstat, 4 * (size_t)n, cudaMemcpyDeviceToHost, st));
@@ -1260,6 +1264,21 @@ vine_status vine_grad(const vine_batch* B, const float* goal_xy, double* cost, d
   }
   CK(cudaStreamSynchronize(st));
   return VINE_OK;
+}
+
+vine_status vine_grad(const vine_batch* B, const float* goal_xy, double* cost, double* d_pressure, double* d_begin,
+                      double* d_end, int32_t* grad_status, int32_t ptrs_are_device, void* stream_v) {
+  if (!B) return fail(VINE_EINVAL, "vine_grad: null batch");
+  return grad_launch(B, 0, goal_xy, 2 * (size_t)B->n_inst, cost, d_pressure, d_begin, d_end, grad_status,
+                     ptrs_are_device, (cudaStream_t)stream_v, "vine_grad: null argument");
+}
+
+vine_status vine_grad_path(const vine_batch* B, const float* path_xy, double* cost, double* d_pressure,
+                           double* d_begin, double* d_end, int32_t* grad_status, int32_t ptrs_are_device,
+                           void* stream_v) {
+  if (!B) return fail(VINE_EINVAL, "vine_grad_path: null batch");
+  return grad_launch(B, 1, path_xy, 2 * (size_t)B->total_links, cost, d_pressure, d_begin, d_end, grad_status,
+                     ptrs_are_device, (cudaStream_t)stream_v, "vine_grad_path: null argument");
 }
 
 vine_status vine_get_stats(const vine_batch* B, vine_stats* out, void* stream_v) {

@@ -1412,11 +1412,15 @@ __device__ __forceinline__ float spam_force(const GrowArgs& A, int tid, float e)
   return tb[k].x + tau * (tb[k + 1].x - tb[k].x);
 }
 
-// Adjoint of the tip-distance cost c = |p_N - goal| at one robot's current
-// state, taken as the equilibrium of its last growth step (implicit
-// differentiation): lambda = H^-1 dc/dx with H the exact Hessian of the cost
-// of Eq. (pbd) (the articulated sweep of gn_solve with the right-hand side
-// replaced), then dc/dq = -lambda . d(grad J)/dq.  grad J depends on an
+// Adjoint of a cost c of the robot's shape at its current state, taken as
+// the equilibrium of its last growth step (implicit differentiation):
+// lambda = H^-1 dc/dx with H the exact Hessian of the cost of Eq. (pbd) (the
+// articulated sweep of gn_solve with the right-hand side replaced), then
+// dc/dq = -lambda . d(grad J)/dq.  Costs: the tip distance |p_N - goal|, or
+// the path cost (1/N) sum_k |p_k - q_k|^2 of the link end points p_1..p_N
+// against targets q_k, whose derivative in joint j is the moment about p_j
+// of "forces" (2/N)(p_k - q_k) at the link ends beyond it -- assembled by the
+// suffix scans of the contact moments.  grad J depends on an
 // actuator's pressure P_a and span [b_a, e_a) only through its moment
 // c_aj s_a P_a f_a(eps_aj) d (Eq. restoring_moment): linearly in P_a, and
 // through the coverage c_aj, whose right derivatives are -1 on link
@@ -1429,7 +1433,8 @@ __device__ void grad_instance(const GrowArgs& A, const GradArgs& G, int inst, co
   const InstDev I = A.inst[inst];
   const int N = A.n_cur[inst];
   const int st = A.status[inst];
-  const float gx = G.goal[2 * inst] - I.bx, gy = G.goal[2 * inst + 1] - I.by;
+  // the tip cost's goal (the path cost reads its targets below)
+  const float gx = G.kind == 0 ? G.goal[2 * inst] - I.bx : 0.f, gy = G.kind == 0 ? G.goal[2 * inst + 1] - I.by : 0.f;
   const double qnan = __longlong_as_double(0x7ff8000000000000ll);
   if (st == kBadInput || st == kNonFinite || N <= 0) {
     const bool ok = (N <= 0 && st != kBadInput && st != kNonFinite);
@@ -1439,7 +1444,7 @@ __device__ void grad_instance(const GrowArgs& A, const GradArgs& G, int inst, co
       G.dE[I.act_off + a] = ok ? 0.0 : qnan;
     }
     if (lane == 0) {
-      G.cost[inst] = ok ? sqrt((double)gx * gx + (double)gy * gy) : qnan;
+      G.cost[inst] = ok ? (G.kind == 1 ? 0.0 : sqrt((double)gx * gx + (double)gy * gy)) : qnan;
       G.gstat[inst] = ok ? 0 : 2;
     }
     return;
@@ -1451,25 +1456,72 @@ __device__ void grad_instance(const GrowArgs& A, const GradArgs& G, int inst, co
   reset_lists(S, N, tm);
   EvalOut E = eval<KS, 32>(A, I, S, N, l, tm, true);
   const bool lfix = (l <= 0.f && E.gl > 0.f) || (l >= I.l_seg && E.gl < 0.f);
-  // tip relative to the base, and dc/dtheta_j = s . (z x (p_N - p_j))
   const int B = (N + 31) >> 5;
   const int j0 = min(lane * B, N), j1 = min(j0 + B, N);
-  float sx = 0.f, sy = 0.f;
-  for (int j = j0; j < j1; ++j) {
-    sx += S.LUX[j];
-    sy += S.LUY[j];
+  double c;
+  if (G.kind == 0) {
+    // tip relative to the base, and dc/dtheta_j = s . (z x (p_N - p_j))
+    float sx = 0.f, sy = 0.f;
+    for (int j = j0; j < j1; ++j) {
+      sx += S.LUX[j];
+      sy += S.LUY[j];
+    }
+    float rx = warp_excl_suffix(sx, lane), ry = warp_excl_suffix(sy, lane);
+    const float tx = __shfl_sync(kFull, rx + sx, 0), ty = __shfl_sync(kFull, ry + sy, 0);
+    const double ex = (double)tx - (double)gx, ey = (double)ty - (double)gy;
+    c = sqrt(ex * ex + ey * ey);
+    const float ux = c > 0.0 ? (float)(ex / c) : 0.f, uy = c > 0.0 ? (float)(ey / c) : 0.f;
+    for (int j = j1 - 1; j >= j0; --j) {
+      rx += S.LUX[j];
+      ry += S.LUY[j];
+      S.G[j] = ux * ry - uy * rx;  // minus dc/dtheta_j: the sweep solves H x = -G
+    }
+    E.gl = -(ux * E.ulx + uy * E.uly);
+  } else {
+    // link end points relative to the base (float-float prefix sums), their
+    // errors e_k = p_k - q_k as forces f_j = (2/N) e_{j+1} at the end of
+    // link j: dc/dtheta_j = sum_{i >= j} (Lu_i x f_i + Lu_i x F_{>i})
+    FF hx{0.f, 0.f}, hy{0.f, 0.f};
+    for (int j = j0; j < j1; ++j) {
+      hx = ff_add(hx, S.LUX[j]);
+      hy = ff_add(hy, S.LUY[j]);
+    }
+    FF px = warp_excl_scan(hx, lane), py = warp_excl_scan(hy, lane);
+    const float* q = G.goal + 2 * (size_t)I.th_off;
+    const float w = 2.f / (float)N;
+    double cs = 0.0;
+    float tfx = 0.f, tfy = 0.f;
+    for (int j = j0; j < j1; ++j) {
+      px = ff_add(px, S.LUX[j]);
+      py = ff_add(py, S.LUY[j]);
+      const float ex = (px.hi - (q[2 * j] - I.bx)) + px.lo, ey = (py.hi - (q[2 * j + 1] - I.by)) + py.lo;
+      cs += (double)ex * ex + (double)ey * ey;
+      S.FX[j] = w * ex;
+      S.FY[j] = w * ey;
+      tfx += S.FX[j];
+      tfy += S.FY[j];
+    }
+    c = warp_sum(cs) / (double)N;
+    float fsx = warp_excl_suffix(tfx, lane), fsy = warp_excl_suffix(tfy, lane);
+    float tt = 0.f;
+    for (int j = j1 - 1; j >= j0; --j) {
+      const float t = S.LUX[j] * (S.FY[j] + fsy) - S.LUY[j] * (S.FX[j] + fsx);
+      S.TL[j] = t;
+      tt += t;
+      fsx += S.FX[j];
+      fsy += S.FY[j];
+    }
+    float run = warp_excl_suffix(tt, lane);
+    for (int j = j1 - 1; j >= j0; --j) {
+      run += S.TL[j];
+      S.G[j] = -run;  // minus dc/dtheta_j
+    }
+    // dc/dl = f_{N-1} . u_{N-1}; the owner of the last link has its force
+    const int owner = (N - 1) / B;
+    const float flx = __shfl_sync(kFull, j1 == N && j0 < j1 ? S.FX[N - 1] : 0.f, owner);
+    const float fly = __shfl_sync(kFull, j1 == N && j0 < j1 ? S.FY[N - 1] : 0.f, owner);
+    E.gl = -(flx * E.ulx + fly * E.uly);
   }
-  float rx = warp_excl_suffix(sx, lane), ry = warp_excl_suffix(sy, lane);
-  const float tx = __shfl_sync(kFull, rx + sx, 0), ty = __shfl_sync(kFull, ry + sy, 0);
-  const double ex = (double)tx - (double)gx, ey = (double)ty - (double)gy;
-  const double c = sqrt(ex * ex + ey * ey);
-  const float ux = c > 0.0 ? (float)(ex / c) : 0.f, uy = c > 0.0 ? (float)(ey / c) : 0.f;
-  for (int j = j1 - 1; j >= j0; --j) {
-    rx += S.LUX[j];
-    ry += S.LUY[j];
-    S.G[j] = ux * ry - uy * rx;  // minus dc/dtheta_j: the sweep solves H x = -G
-  }
-  E.gl = -(ux * E.ulx + uy * E.uly);
   __syncwarp();
   float dl, mdth;
   const double r = gn_solve(I, S, N, lfix, E, dl, tm, true, mdth);

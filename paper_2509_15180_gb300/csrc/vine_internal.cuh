@@ -117,7 +117,8 @@ cudaError_t launch_init(const InitArgs& a, cudaStream_t s);
 
 // Adjoint outputs (vine_grad): device pointers.
 struct GradArgs {
-  const float* goal;  // [2 n] goal points (absolute)
+  int kind;           // 0: tip cost |p_N - goal|; 1: path cost (1/N) sum_k |p_k - q_k|^2
+  const float* goal;  // kind 0: [2 n] goal points; kind 1: [2 sum n_links] link-end targets (absolute, CSR by robot)
   double* cost;       // [n]
   double* dP;         // [n_act_total] d cost / d actuator pressure (per Pa)
   double* dB;         // [n_act_total] d cost / d actuator begin (per link)

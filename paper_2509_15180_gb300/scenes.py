@@ -188,6 +188,22 @@ def goal_points(n_inst: int, box: float, replicate: int = 0) -> np.ndarray:
     return np.stack([gx, gy], axis=1).astype(np.float32)
 
 
+def goal_paths(scene: dict, goals, turn: float = 0.0087) -> np.ndarray:
+    """Target points of the link ends for a path cost: per robot its n_links
+    points, l_seg apart along an arc that leaves the base toward the robot's
+    goal point and turns by `turn` rad per link ([sum n_links, 2] float32,
+    robot i's rows in the order of its links)."""
+    out = []
+    for i, n in enumerate(np.asarray(scene["n_links"])):
+        bx, by = float(scene["base"][i][0]), float(scene["base"][i][1])
+        ls = float(scene["l_seg"][i])
+        phi0 = np.arctan2(float(goals[i][1]) - by, float(goals[i][0]) - bx)
+        k = np.arange(1, int(n) + 1)
+        phi = phi0 + turn * (k - 0.5)
+        out.append(np.stack([bx + ls * np.cumsum(np.cos(phi)), by + ls * np.cumsum(np.sin(phi))], axis=1))
+    return np.concatenate(out).astype(np.float32) if out else np.zeros((0, 2), np.float32)
+
+
 def serve_requests(n_req: int, rate_hz: float = 2000.0, replicate: int = 0, max_inst: int = 256):
     """Poisson request stream for the serving loop: arrival times (s) and, per
     request, a scene of U{1..max_inst} instances drawn as the uneven batch but with
@@ -301,3 +317,96 @@ def concat(scenes) -> dict:
             if k.startswith(pre + "_") and k != ptr:
                 out[k] = np.concatenate([s[k] for s in scenes])
     return out
+
+
+# ---------------------------------------------------------------------------
+# Analysis workloads (Sec. 6.3, 6.4).  The paper's environments and designs
+# exist only as figures, so seeded stand-ins with the paper's robot.
+# ---------------------------------------------------------------------------
+_PAPER_ROBOT = dict(l_seg=0.025, radius=0.03335, pressure=1.5 * 6894.757293168)
+
+
+def nominal_design(replicate: int = 0) -> dict:
+    """A nominal design in a cluttered environment (robustness study): the
+    paper's robot, 64 links, two sPAM actuators ([6, 14) pulling to +1 at
+    40 kPa, [30, 38) pulling to -1 at 35 kPa), 14 circles of radius
+    U[3, 6] cm in [0.2, 1.5] x [-0.5, 0.5] m (0.15 m clear of the base).
+    Returns a one-robot scene."""
+    rng = _rng(8, replicate)
+    cx, cy, ca = [], [], []
+    while len(cx) < 14:
+        x, y, r = rng.uniform(0.2, 1.5), rng.uniform(-0.5, 0.5), rng.uniform(0.03, 0.06)
+        if np.hypot(x, y) - r > 0.15:
+            cx.append(x); cy.append(y); ca.append(r)
+    row = dict(n_links=64, base=(0.0, 0.0, 0.0), acts=[(6.0, 14.0, 1, 40e3), (30.0, 38.0, -1, 35e3)],
+               obs=([0] * len(cx), cx, cy, ca, [0.0] * len(cx)), **_PAPER_ROBOT)
+    return _pack([row])
+
+
+def robustness_sweep(nominal: dict, levels, trials: int = 1000, kind: str = "obstacles", replicate: int = 0):
+    """Perturbed copies of a one-robot scene, `trials` per uncertainty level
+    (Sec. 6.3; levels as fractions, e.g. 0.05 = 5 %).
+      kind "obstacles": every obstacle's radius (or half-sizes) scaled by
+        (1 + level z) and its centre moved by level x its radius times z
+        per coordinate, z ~ N(0, 1) each;
+      kind "actuation": every actuator's pressure scaled by (1 + level z)
+        and its span length (end - begin) by (1 + level z'), begin kept.
+    Returns (scene, level index per robot)."""
+    rng = _rng(9, 1000 * replicate + (0 if kind == "obstacles" else 1))
+    nom = nominal
+    rows, lev = [], []
+    a0, a1 = int(nom["act_ptr"][0]), int(nom["act_ptr"][1])
+    o0, o1 = int(nom["obs_ptr"][0]), int(nom["obs_ptr"][1])
+    kinds = [int(k) for k in nom["obs_kind"][o0:o1]]
+    for li, s in enumerate(levels):
+        for _ in range(trials):
+            cx = np.asarray(nom["obs_cx"][o0:o1], np.float64).copy()
+            cy = np.asarray(nom["obs_cy"][o0:o1], np.float64).copy()
+            oa = np.asarray(nom["obs_a"][o0:o1], np.float64).copy()
+            ob = np.asarray(nom["obs_b"][o0:o1], np.float64).copy()
+            pa = np.asarray(nom["act_pressure"][a0:a1], np.float64).copy()
+            bg = np.asarray(nom["act_begin"][a0:a1], np.float64).copy()
+            en = np.asarray(nom["act_end"][a0:a1], np.float64).copy()
+            if kind == "obstacles":
+                size = oa.copy()
+                scale = np.maximum(1.0 + s * rng.standard_normal(oa.size), 0.2)
+                oa *= scale
+                ob = np.where(np.asarray(kinds) == 1, ob * scale, ob)
+                cx += s * size * rng.standard_normal(cx.size)
+                cy += s * size * rng.standard_normal(cy.size)
+            else:
+                pa *= np.maximum(1.0 + s * rng.standard_normal(pa.size), 0.0)
+                span = (en - bg) * np.maximum(1.0 + s * rng.standard_normal(pa.size), 0.1)
+                en = np.minimum(bg + span, float(nom["n_links"][0]))
+            rows.append(dict(n_links=int(nom["n_links"][0]), l_seg=float(nom["l_seg"][0]),
+                             radius=float(nom["radius"][0]), pressure=float(nom["pressure"][0]),
+                             base=tuple(float(v) for v in nom["base"][0]),
+                             acts=[(bg[k], en[k], int(nom["act_side"][a0 + k]), pa[k]) for k in range(pa.size)],
+                             obs=(kinds, list(cx), list(cy), list(oa), list(ob))))
+            lev.append(li)
+    return _pack(rows), np.asarray(lev, np.int32)
+
+
+def funnel_rollouts(n_rollouts: int = 50, counts=(0, 8, 16, 32), n_links: int = 48, replicate: int = 0):
+    """The funnelling study (Sec. 6.4): per environment (circles of radius
+    U[2, 4] cm uniform in [0.25, 1.25] x [-0.2, 0.8] m, `counts` of them,
+    0.15 m clear of the base) n_rollouts robots of the paper's body with
+    start headings uniform in [-0.3, 0.3] rad and one actuator over links
+    [8, 16) pulling to +1 at 15 kPa x (1 + 0.1 z) -- a varied bending
+    control biased toward the upper side.  Returns (scene, environment index
+    per robot)."""
+    rng = _rng(10, replicate)
+    rows, env = [], []
+    for e, m in enumerate(counts):
+        cx, cy, ca = [], [], []
+        while len(cx) < m:
+            x, y, r = rng.uniform(0.25, 1.25), rng.uniform(-0.2, 0.8), rng.uniform(0.02, 0.04)
+            if np.hypot(x, y) - r > 0.15:
+                cx.append(x); cy.append(y); ca.append(r)
+        heads = rng.uniform(-0.3, 0.3, n_rollouts)
+        for h in heads:
+            p = 15e3 * (1.0 + 0.1 * rng.standard_normal())
+            rows.append(dict(n_links=n_links, base=(0.0, 0.0, float(h)), acts=[(8.0, 16.0, 1, p)],
+                             obs=([0] * m, cx, cy, ca, [0.0] * m), **_PAPER_ROBOT))
+            env.append(e)
+    return _pack(rows), np.asarray(env, np.int32)

@@ -107,6 +107,7 @@ _SIG = {
     "vine_autotune": [_p, _i32, _p, _p],
     "vine_batch_classes": [_p, _p, _p, _p, _p, _p, _p],
     "vine_grad": [_p, _p, _p, _p, _p, _p, _p, _i32, _p],
+    "vine_grad_path": [_p, _p, _p, _p, _p, _p, _p, _i32, _p],
     "vine_batch_destroy": [_p],
     "vine_server_config_default": [_p],
     "vine_server_create": [_p, _p, _p],
@@ -317,6 +318,16 @@ class Batch:
         current state (vine_grad).  goal: [n, 2] numpy (host path, returns
         numpy) or CUDA float32 tensor (device path, returns CUDA tensors,
         async)."""
+        return self._grad(_lib.vine_grad, "vine_grad", goal, self.n_inst, stream)
+
+    def grad_path(self, path, stream=None) -> dict:
+        """Path cost (1/N) sum_k |p_k - q_k|^2 of the link end points against
+        targets path [total_links, 2] (robot i's rows at its joint-angle
+        offset) and its adjoint derivatives (vine_grad_path); numpy or CUDA
+        float32 as grad()."""
+        return self._grad(_lib.vine_grad_path, "vine_grad_path", path, max(self.total_links, 1), stream)
+
+    def _grad(self, fn, name, goal, rows, stream):
         n, na = self.n_inst, self.n_act
         if hasattr(goal, "is_cuda") and goal.is_cuda:
             import torch
@@ -328,12 +339,14 @@ class Batch:
                        status=torch.empty(n, dtype=torch.int32, device=g.device))
             dev = 1
         else:
-            g = np.ascontiguousarray(np.asarray(goal, np.float32).reshape(n, 2))
+            g = np.ascontiguousarray(np.asarray(goal, np.float32).reshape(-1, 2))
             out = dict(cost=np.zeros(n), dP=np.zeros(max(na, 1)), dB=np.zeros(max(na, 1)), dE=np.zeros(max(na, 1)),
                        status=np.zeros(n, np.int32))
             dev = 0
-        _check(_lib.vine_grad(self.h, _ptr(g), _ptr(out["cost"]), _ptr(out["dP"]), _ptr(out["dB"]), _ptr(out["dE"]),
-                              _ptr(out["status"]), dev, _stream(stream)), "vine_grad")
+        if int(np.prod(tuple(g.shape))) < 2 * rows:
+            raise ValueError("%s: expected [%d, 2] target points" % (name, rows))
+        _check(fn(self.h, _ptr(g), _ptr(out["cost"]), _ptr(out["dP"]), _ptr(out["dB"]), _ptr(out["dE"]),
+                  _ptr(out["status"]), dev, _stream(stream)), name)
         for k in ("dP", "dB", "dE"):
             out[k] = out[k][:na]
         return out

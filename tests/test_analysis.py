@@ -31,3 +31,25 @@ def test_success_rate():
     assert analysis.success_rate(tips, goals, 1.0) == pytest.approx(2.0 / 3.0)
     with pytest.raises(ValueError):
         analysis.knn_densities(tips, 3)
+
+
+def test_study_scenes_are_seeded_and_shaped():
+    from paper_2509_15180_gb300 import scenes
+    nom = scenes.nominal_design()
+    a, la = scenes.robustness_sweep(nom, (0.0, 0.05, 0.1), trials=7, kind="obstacles")
+    b, lb = scenes.robustness_sweep(nom, (0.0, 0.05, 0.1), trials=7, kind="obstacles")
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+    assert np.array_equal(la, np.repeat([0, 1, 2], 7))
+    # level 0 leaves the design untouched; higher levels move the obstacles
+    o = slice(int(a["obs_ptr"][0]), int(a["obs_ptr"][1]))
+    assert np.array_equal(a["obs_cx"][o], nom["obs_cx"])
+    o7 = slice(int(a["obs_ptr"][14]), int(a["obs_ptr"][15]))
+    assert not np.array_equal(a["obs_cx"][o7], nom["obs_cx"])
+    c, _ = scenes.robustness_sweep(nom, (0.0, 0.2), trials=3, kind="actuation")
+    assert np.array_equal(c["act_pressure"][:2], nom["act_pressure"])
+    assert np.all(c["act_end"] > c["act_begin"]) and np.all(c["act_pressure"] >= 0)
+    f, env = scenes.funnel_rollouts(n_rollouts=10, counts=(0, 5))
+    assert np.array_equal(np.bincount(env), [10, 10])
+    heads = f["base"][:, 2]
+    assert np.all(np.abs(heads) <= 0.3) and np.unique(heads).size == 20

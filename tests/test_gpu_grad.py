@@ -64,17 +64,24 @@ def _load(b, sc, orc, ost, idx=None, base=None):
     b.set_state(N, th, l)
 
 
-def _compare(sc, orc, ost, goals, g, min_checked, idx=None):
+REL = 1e-2        # per-derivative relative bar
+FLOOR = 1e-3      # absolute floor: this fraction of the largest derivative of its kind in the sample
+COND_MAX = 1e7    # robots whose exact Hessian is worse conditioned are counted, not compared
+
+
+def _compare(sc, orc, ost, goals, g, min_checked, idx=None, kind="tip", paths=None):
     """GPU adjoint against the FP64 oracle's at the same state (the oracle's
     own equilibrium rounded to FP32, loaded with vine_set_state).  Oracle
-    robot j is GPU robot idx[j].  Bar per derivative: 2e-2 of the largest
-    derivative of its kind in the sample, or, for a robot whose Hessian is
-    ill-conditioned, 2e-6 x its condition number of the derivative itself
-    (an FP32 solve of H lambda = c carries a relative error of order
-    cond x 6e-8)."""
+    robot j is GPU robot idx[j].  Bar per derivative: REL of itself plus
+    FLOOR of the largest derivative of its kind (some are ~0: an actuator
+    whose moment barely reaches the cost).  The FP32 Hessian carries
+    relative errors of ~6e-8 per entry, which move lambda = H^-1 c by up to
+    cond x 6e-8: robots whose condition number exceeds COND_MAX are counted
+    and bounded, not compared."""
     idx = np.arange(orc.n) if idx is None else np.asarray(idx)
+    off = np.concatenate([[0], np.cumsum(sc["n_links"])])
     rows = []
-    skipped = 0
+    skipped = ill = 0
     conds = {}
     for j, i in enumerate(idx):
         a0, a1 = int(sc["act_ptr"][i]), int(sc["act_ptr"][i + 1])
@@ -82,12 +89,18 @@ def _compare(sc, orc, ost, goals, g, min_checked, idx=None):
             skipped += 1
             continue
         th, l = orc.theta_of(ost, j), float(ost["l"][j])
-        c, dP, dB, dE, rc = orc.grad(j, th, l, goals[i].astype(np.float64))
+        if kind == "tip":
+            c, dP, dB, dE, rc = orc.grad(j, th, l, goals[i].astype(np.float64))
+        else:
+            c, dP, dB, dE, rc = orc.grad_path(j, th, l, paths[off[i]: off[i + 1]].astype(np.float64))
         if rc != 0:
             skipped += 1
             continue
-        assert abs(g["cost"][i] - c) <= 1e-6 * max(c, 1e-3), (i, g["cost"][i], c)
+        assert abs(g["cost"][i] - c) <= 1e-5 * max(c, 1e-6), (i, g["cost"][i], c)
         conds[i] = _cond(orc, j, th, l)
+        if conds[i] > COND_MAX:
+            ill += 1
+            continue
         for k, v in (("dP", dP), ("dB", dB), ("dE", dE)):
             for a in range(a1 - a0):
                 rows.append((k, i, a, g[k][a0 + a], v[a]))
@@ -97,13 +110,16 @@ def _compare(sc, orc, ost, goals, g, min_checked, idx=None):
         if not sel:
             continue
         scale = max(abs(r[4]) for r in sel)
-        errs = [abs(r[3] - r[4]) / max(2e-2 * scale, 2e-6 * conds[r[1]] * max(abs(r[4]), abs(r[3])))
-                for r in sel]
+        errs = [abs(r[3] - r[4]) / (REL * abs(r[4]) + FLOOR * scale) for r in sel]
         worst[k] = max(errs)
         q = int(np.argmax(errs))
         assert worst[k] < 1.0, (k, worst[k], sel[q], "cond %.3g" % conds[sel[q][1]])
-    print("adjoint parity: %d derivatives, %d robots skipped, worst (fraction of the bar) per kind %s, "
-          "largest condition number %.3g" % (len(rows), skipped, worst, max(conds.values()) if conds else 0.0))
+    cv = np.array(list(conds.values())) if conds else np.zeros(1)
+    print("%s-cost adjoint parity: %d derivatives, %d robots skipped, %d of %d beyond cond %.0e; worst (fraction "
+          "of the bar) %s; condition numbers median %.3g, max compared %.3g" % (
+              kind, len(rows), skipped, ill, len(conds), COND_MAX, worst, float(np.median(cv)),
+              float(cv[cv <= COND_MAX].max()) if np.any(cv <= COND_MAX) else 0.0))
+    assert ill <= 0.25 * max(len(conds), 1)
     assert len(rows) >= min_checked
     return worst
 
@@ -115,6 +131,27 @@ def test_grad_matches_oracle_adjoint_small():
     _load(b, sc, orc, ost)
     g = b.grad(goals)
     _compare(sc, orc, ost, goals, g, 40)
+    b.close()
+
+
+def test_path_grad_matches_oracle_adjoint():
+    """The path cost (1/N) sum_k |p_k - q_k|^2 against the oracle's adjoint,
+    on the small robots and on 150-link robots of the robustness designs."""
+    sc, goals = _scene()
+    paths = scenes.goal_paths(sc, goals)
+    orc, ost = _oracle_equilibria(sc)
+    b = vine.Batch(sc)
+    _load(b, sc, orc, ost)
+    g = b.grad_path(paths)
+    _compare(sc, orc, ost, goals, g, 40, kind="path", paths=paths)
+    b.close()
+    sc, goals = scenes.robustness_batch(n_designs=8, n_perturb=3)
+    paths = scenes.goal_paths(sc, goals)
+    orc, ost = _oracle_equilibria(sc)
+    b = vine.Batch(sc)
+    _load(b, sc, orc, ost)
+    g = b.grad_path(paths)
+    _compare(sc, orc, ost, goals, g, 20, kind="path", paths=paths)
     b.close()
 
 
@@ -199,4 +236,14 @@ def test_autograd_function_chain_rule():
     assert np.allclose(B.grad.cpu().numpy()[ok], (wn * g["dB"])[ok].astype(np.float32), rtol=1e-6, atol=0)
     assert np.allclose(E.grad.cpu().numpy()[ok], (wn * g["dE"])[ok].astype(np.float32), rtol=1e-6, atol=0)
     assert np.allclose(cost.detach().cpu().numpy(), g["cost"], rtol=0, atol=0)
+    # the path cost through the same Function
+    paths = scenes.goal_paths(sc, goals)
+    for t in (P, B, E):
+        t.grad = None
+    cost = VineSim.apply(P, B, E, b, torch.tensor(paths, device=dev), "path")
+    cost.sum().backward()
+    gp = b.grad_path(paths)
+    ok = ~np.isnan(gp["dP"])
+    assert np.allclose(P.grad.cpu().numpy()[ok], gp["dP"][ok].astype(np.float32), rtol=1e-6, atol=0)
+    assert np.allclose(cost.detach().cpu().numpy(), gp["cost"], rtol=0, atol=0)
     b.close()

@@ -51,7 +51,13 @@ def _pieces(orc, sc, i, th, P):
     return out
 
 
-def _fd(sc, i, key, a_glob, h, th0, l0, goal, P):
+def _path_cost(orc, i, th, l, path):
+    px, py, _ = orc.poses(i, th, l)
+    q = np.asarray(path, np.float64)[: th.size]
+    return float(np.mean((px[1:] - q[:, 0]) ** 2 + (py[1:] - q[:, 1]) ** 2))
+
+
+def _fd(sc, i, key, a_glob, h, th0, l0, goal, P, cost=_tip_cost):
     vals, sets = [], []
     for sgn in (1.0, -1.0):
         mod = dict(sc)
@@ -61,7 +67,7 @@ def _fd(sc, i, key, a_glob, h, th0, l0, goal, P):
         th, l, it, r, st = orc.solve(i, th0, l0)
         if st != 0:
             return None, None
-        vals.append(_tip_cost(orc, i, th, l, goal))
+        vals.append(cost(orc, i, th, l, goal))
         sets.append((_contacts(orc, i, th, l), _pieces(orc, mod, i, th, P)))
     same = np.array_equal(sets[0][0], sets[1][0]) and sets[0][1] == sets[1][1]
     return (vals[0] - vals[1]) / (2.0 * h), same
@@ -151,3 +157,64 @@ def test_adjoint_pressure_derivative_is_linear_response():
             assert abs(dP[a] - want) <= 1e-9 * max(abs(want), 1e-12) + 1e-18, (i, a, dP[a], want)
             done += 1
     assert done >= 5
+
+
+def test_path_cost_adjoint_matches_central_differences():
+    """The path cost (1/N) sum_k |p_k - q_k|^2 over the link end points
+    against a target path: the adjoint against central differences of
+    re-solved equilibria, as for the tip cost."""
+    sc, goals = _scene()
+    paths = scenes.goal_paths(sc, goals).astype(np.float64)
+    off = np.concatenate([[0], np.cumsum(sc["n_links"])])
+    P = oracle.default_params(tol=1e-13)
+    orc = oracle.Oracle(sc, oracle.default_params(tol=1e-12))
+    st = orc.new_state()
+    orc.run(st, 30, threads=8)
+    orc13 = oracle.Oracle(sc, P)
+    rows, excluded = [], 0
+    for i in range(sc["n_links"].size):
+        a0, a1 = int(sc["act_ptr"][i]), int(sc["act_ptr"][i + 1])
+        if a1 == a0 or st["status"][i] != 0:
+            continue
+        th, l, _, _, s13 = orc13.solve(i, orc.theta_of(st, i), st["l"][i])
+        assert s13 == 0
+        path = paths[off[i]: off[i + 1]]
+        cost, dP, dB, dE, rc = orc13.grad_path(i, th, l, path)
+        assert rc == 0
+        assert abs(cost - _path_cost(orc13, i, th, l, path)) <= 1e-15 * max(cost, 1e-30)
+        for key, h, adj in (("act_pressure", H_P, dP), ("act_begin", H_S, dB), ("act_end", H_S, dE)):
+            for a in range(a1 - a0):
+                f, ok = _fd(sc, i, key, a0 + a, h, th, l, path, P, cost=_path_cost)
+                if f is None or not ok:
+                    excluded += 1
+                    continue
+                rows.append((key, i, a, adj[a], f))
+    worst = 0.0
+    for kind in ("act_pressure", "act_begin", "act_end"):
+        sel = [r for r in rows if r[0] == kind]
+        scale = max(abs(r[4]) for r in sel)
+        for (_, i, a, adj, f) in sel:
+            err = abs(adj - f) / scale
+            worst = max(worst, err)
+            assert err < 1e-5, (i, kind, a, adj, f)
+    print("path-cost adjoint vs FD: %d derivatives, %d excluded, worst %.2e" % (len(rows), excluded, worst))
+    assert len(rows) >= 15
+
+
+def test_path_cost_value_at_arbitrary_states():
+    """The cost the adjoint reports is the mean squared distance of the link
+    end points to their targets, recomputed from the poses, at states off
+    the equilibrium too."""
+    sc, goals = _scene()
+    orc = oracle.Oracle(sc, oracle.default_params(tol=1e-12))
+    st = orc.new_state()
+    orc.run(st, 12, threads=8)
+    rng = np.random.default_rng(3)
+    for i in range(3):
+        th, l = orc.theta_of(st, i), float(st["l"][i])
+        px, py, _ = orc.poses(i, th, l)
+        q = np.stack([px[1:], py[1:]], 1) + rng.normal(0, 0.01, (th.size, 2))
+        for _ in range(3):
+            tp = th + rng.normal(0, 0.01, th.size)
+            c, *_ = orc.grad_path(i, tp, l, q)
+            assert abs(c - _path_cost(orc, i, tp, l, q)) <= 1e-14 * c
