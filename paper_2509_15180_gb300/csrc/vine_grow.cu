@@ -386,15 +386,15 @@ __device__ __forceinline__ void wrinkle(const GrowArgs& A, float th, float& m, f
 // calling lane; contacts are rare, so the accumulators need no registers).
 // Gauss-Newton part kap w w^T of the link's 3x3 stiffness in twist
 // coordinates about the link start, w = ((x - p) x n, n_x, n_y).  With EXACT
+// (a runtime flag: one copy of the code serves both matrices)
 // also pen times the second derivatives of pen: obstacle curvature
 // -(kap pen kinv) s s^T, s = (n.(x - p), -n_y, n_x) (kinv = 1/distance to the
 // circle centre or box corner, 0 on a box face), and the local part of the
 // load stiffness fr Lu.F on the rotational entry; for the distal link the
 // couplings with its length l.
-template <bool EXACT>
 __device__ __forceinline__ void add_contact(const Smem& S, int j, float pen, float nx, float ny, float kinv,
                                             float fr, float lx, float ly, float kap, bool last, float ulx,
-                                            float uly) {
+                                            float uly, bool EXACT) {
   const float f = kap * pen;
   const float fx = f * nx, fy = f * ny;
   S.FX[j] += fx;
@@ -836,8 +836,7 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
           pen2 += pen * pen;
           sig += 0x85ebca6bu * (unsigned)(code + 1) + 0xc2b2ae35u * (unsigned)(j + 1);
           pen1 += pen;
-          if (exact) add_contact<true>(S, j, pen, nx, ny, kinv, fr, lx, ly, kap, last, ulx, uly);
-          else add_contact<false>(S, j, pen, nx, ny, kinv, fr, lx, ly, kap, last, ulx, uly);
+          add_contact(S, j, pen, nx, ny, kinv, fr, lx, ly, kap, last, ulx, uly, exact);
         }
       }
       qn = 0;
@@ -897,8 +896,8 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
 }
 
 // Gauss-Newton step (DTH[0..N), dl) and its predicted displacement: the
-// largest displacement of a link end point (and l_seg |dtheta_j|), in link
-// lengths (the convergence test of the step).  The displacement sums are
+// square of the largest displacement of a link end point (and of l_seg
+// |dtheta_j|), in link lengths squared (the convergence test of the step).  The displacement sums are
 // float-float beside the FP32 twists (they do not feed back into the step,
 // so they stay off the sweep's dependency chain); per-link FP64 would hold
 // GB300's low-rate FP64 pipe for most of the sweep.
@@ -1023,7 +1022,7 @@ __device__ double gn_solve(const InstDev& I, const Smem& S, int N, bool lfix, co
     tm.sync();
   }
   max_dth = dmax;
-  return sqrt((double)rmax2) / (double)I.l_seg;
+  return (double)(rmax2 / (I.l_seg * I.l_seg));
 }
 
 struct StepStats {
@@ -1064,6 +1063,7 @@ __device__ int step_solve(const GrowArgs& A, const InstDev& I, const Smem& S, in
   // tol N link lengths (tol of the robot's length) nor by more than tol_link
   // link lengths (the bound that holds at any chain length)
   const double tol_eff = A.tol_link > 0.0 ? fmin(A.tol * (double)N, A.tol_link) : A.tol * (double)N;
+  const double tol2 = tol_eff * tol_eff;  // the test compares squared displacements
   float a_th = 0.f, a_l = 0.f;
   if (descend) {
     for (int k = tm.r; k < N; k += TP) S.TH0[k] = S.TH[k];
@@ -1169,7 +1169,7 @@ __device__ int step_solve(const GrowArgs& A, const InstDev& I, const Smem& S, in
       lfix = A.fix_l || (l <= 0.f && E.gl > 0.f) || (l >= I.l_seg && E.gl < 0.f);
     }
     const bool use_exact = exact && phase == kNewton;
-    r = gn_solve(I, S, N, lfix, E, dl, tm, use_exact, mdth);
+    r = gn_solve(I, S, N, lfix, E, dl, tm, use_exact, mdth);  // squared, link lengths
     if (use_exact && !(r >= 0.0 && isfinite(r))) {
       // exact Hessian not positive definite here: Gauss-Newton matrix instead
       st.fallbacks += 1;
@@ -1195,11 +1195,11 @@ __device__ int step_solve(const GrowArgs& A, const InstDev& I, const Smem& S, in
         status = kNonFinite;
         break;
       }
-      r = 1e30;  // not a Newton step: never taken as converged
+      r = 1e60;  // not a Newton step: never taken as converged
       st.fallbacks += 1;
       tm.sync();
     }
-    if (r <= tol_eff) {
+    if (r <= tol2) {
       for (int j = j0; j < j1; ++j) S.TH[j] += S.DTH[j];
       l = fminf(fmaxf(l + dl, 0.f), I.l_seg);
       // the point the small step reached is evaluated once more: a step that
@@ -1251,7 +1251,7 @@ __device__ int step_solve(const GrowArgs& A, const InstDev& I, const Smem& S, in
   if (it > A.max_iter) it = A.max_iter;
   tm.sync();
   st.iters = it;
-  st.r = r / (double)N;  // reported relative to the robot length
+  st.r = (r >= 0.0 ? sqrt(r) : r) / (double)N;  // reported relative to the robot length
   return status;
 }
 
@@ -1394,7 +1394,7 @@ __global__ void __launch_bounds__(32) probe_kernel(const GrowArgs A, int inst, i
     out_g[N] = E.gl;
     out_dx[N] = dl;
     *outJ = (double)E.J.hi + (double)E.J.lo;
-    *out_r = r / (double)N;  // relative to the robot length
+    *out_r = r >= 0.0 ? sqrt(r) / (double)N : r;  // relative to the robot length
     *out_lfix = lfix ? 1 : 0;
   }
 }
