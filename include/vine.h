@@ -572,7 +572,8 @@ typedef struct {
   int32_t max_act;          /* per slot: actuators (0: 16) */
   int32_t max_request;      /* robots per request (0: 256) */
   int32_t steps_per_tick;   /* growth steps per robot per launch (0: max_links, i.e. to completion) */
-  int32_t max_tables;       /* distinct sPAM cell lengths held (0: 256) */
+  int32_t max_tables;       /* distinct sPAM cell lengths live at one time (0: 256): a table entry is
+                               held while an admitted request uses its cell length and reused after */
   int32_t lanes;            /* concurrent launch lanes, 1..8 (0: 4) */
   int32_t window;           /* robots per launch and lane (0: twice the resident warps) */
 } vine_server_config;
@@ -607,9 +608,12 @@ vine_status vine_server_create(const vine_params* params, const vine_server_conf
 /* Copies a request (host memory: desc->mem_is_device must be 0) and queues
  * it; *request_id identifies it.  VINE_EBUSY when the free slots (less those
  * promised to requests still waiting) cannot hold its robots: nothing is
- * kept and the client retries later.  VINE_EINVAL for a malformed request,
- * more robots than max_request, a robot beyond the slot capacities, or more
- * distinct cell lengths than the table capacity.  Thread-safe. */
+ * kept and the client retries later; VINE_EBUSY too when its cell lengths,
+ * with those held by admitted requests and those of waiting requests, are
+ * more than max_tables (entries free up as requests finish).  VINE_EINVAL
+ * for a malformed request, more robots than max_request, a robot beyond the
+ * slot capacities, or more distinct cell lengths in the request itself than
+ * max_tables.  Thread-safe. */
 vine_status vine_serve_submit(vine_server* s, const vine_batch_desc* desc, uint64_t* request_id);
 
 /* Waits up to timeout_us (0: do not wait) for request_id to finish.  Done:

@@ -67,6 +67,7 @@ struct Request {
   size_t off[F_COUNT] = {};
   std::vector<int> n_links, n_obs_r;
   std::vector<double> l0;   // distinct cell lengths of the request
+  std::vector<int> tabs;    // the table entries it holds (admitted requests)
   std::vector<int> slots;
   int64_t out_base = 0;     // offset in the tick's result buffers
   double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
@@ -165,7 +166,12 @@ struct vine_server {
   std::unordered_map<uint64_t, Request*> reqs;
   std::vector<int> free_slots;
   int promised = 0;  // slots of waiting requests
+  // sPAM table entries: cell length and the number of live (admitted, not
+  // retired) requests holding it; an entry held by none is reused for a new
+  // cell length, so only the cell lengths live at one time count against
+  // max_tables
   std::vector<double> tab_l0;
+  std::vector<int> tab_ref;
   uint64_t next_id = 1;
   bool stop = false;
   std::string error;
@@ -187,28 +193,42 @@ bool robot_done(int n_cur, int target, int status) {
 // Admission of one waiting request: slots, tables, upload, validation/encoding.
 cudaError_t admit(vine_server* V, Request* R) {
   cudaStream_t st = V->stream;
-  // tables for cell lengths not seen yet
-  std::vector<double> fresh;
+  // table entries for the request's cell lengths: held ones are shared,
+  // new cell lengths take a free entry (or a new one) and are built there
+  std::vector<int> build;  // entries to (re)build
   {
     std::lock_guard<std::mutex> lk(V->mu);
-    for (double v : R->l0)
-      if (std::find(V->tab_l0.begin(), V->tab_l0.end(), v) == V->tab_l0.end() &&
-          std::find(fresh.begin(), fresh.end(), v) == fresh.end())
-        fresh.push_back(v);
+    for (double v : R->l0) {
+      int t = -1;
+      for (int k = 0; k < (int)V->tab_l0.size() && t < 0; ++k)
+        if (V->tab_ref[k] > 0 && V->tab_l0[k] == v) t = k;
+      if (t < 0) {
+        for (int k = 0; k < (int)V->tab_l0.size() && t < 0; ++k)
+          if (V->tab_ref[k] == 0) t = k;
+        if (t < 0) {
+          t = (int)V->tab_l0.size();  // submit kept the live cell lengths within max_tables
+          V->tab_l0.push_back(v);
+          V->tab_ref.push_back(0);
+        }
+        V->tab_l0[t] = v;
+        build.push_back(t);
+      }
+      V->tab_ref[t] += 1;
+      R->tabs.push_back(t);
+    }
   }
-  const int t0 = (int)V->tab_l0.size();
-  if (!fresh.empty()) {
-    cudaError_t e = cudaMemcpyAsync(V->d_l0 + t0, fresh.data(), sizeof(double) * fresh.size(),
-                                    cudaMemcpyHostToDevice, st);
+  for (int t : build) {
+    const double v = V->tab_l0[t];
+    cudaError_t e = cudaMemcpyAsync(V->d_l0 + t, &v, sizeof(double), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
     GaussLegendre gl;
     gauss_legendre(24, &gl);
-    e = launch_spam_tables(V->d_l0 + t0, (int)fresh.size(), V->prm.R_c, V->prm.R_act, V->prm.a_spam, V->prm.m_lo, gl,
-                           const_cast<float4*>(V->args.tab_hdr) + t0,
-                           const_cast<float2*>(V->args.tab) + (size_t)t0 * kKnots, V->d_scr, st);
+    e = launch_spam_tables(V->d_l0 + t, 1, V->prm.R_c, V->prm.R_act, V->prm.a_spam, V->prm.m_lo, gl,
+                           const_cast<float4*>(V->args.tab_hdr) + t, const_cast<float2*>(V->args.tab) + (size_t)t * kKnots,
+                           V->d_scr, st);
     if (e != cudaSuccess) return e;
-    std::lock_guard<std::mutex> lk(V->mu);
-    V->tab_l0.insert(V->tab_l0.end(), fresh.begin(), fresh.end());
+    e = cudaStreamSynchronize(st);  // the pageable source value and the shared scratch
+    if (e != cudaSuccess) return e;
   }
   // actuator -> table index, and the slots, written into the image
   {
@@ -216,8 +236,10 @@ cudaError_t admit(vine_server* V, Request* R) {
     int* act_tab = (int*)(R->image.data() + R->off[F_ACTTAB]);
     for (int a = 0; a < R->n_act; ++a) {
       const double v = l0[a];
-      auto it = std::find(V->tab_l0.begin(), V->tab_l0.end(), v);
-      act_tab[a] = it == V->tab_l0.end() ? 0 : (int)(it - V->tab_l0.begin());  // invalid l0: flagged on the device
+      int t = 0;  // invalid l0: flagged on the device
+      for (size_t k = 0; k < R->l0.size(); ++k)
+        if (R->l0[k] == v) t = R->tabs[k];
+      act_tab[a] = t;
     }
     std::lock_guard<std::mutex> lk(V->mu);
     R->slots.resize(R->n);
@@ -418,6 +440,8 @@ cudaError_t retire(vine_server* V, int q) {
     R->t_done = t;
     R->state = 2;
     V->lanes[R->lane].load -= R->n;
+    for (int t : R->tabs) V->tab_ref[t] -= 1;  // entries no live request holds are reused
+    R->tabs.clear();
     for (int s : R->slots) V->free_slots.push_back(s);
     R->slots.clear();
     R->image.clear();
@@ -850,8 +874,15 @@ vine_status vine_serve_submit(vine_server* V, const vine_batch_desc* D, uint64_t
     delete R;
     return sfail(VINE_ECUDA, V->error.empty() ? "vine_serve_submit: server stopped" : V->error.c_str());
   }
-  // cell lengths of waiting requests are not built yet: count them too
-  std::vector<double> known = V->tab_l0;
+  // the cell lengths live once this request is admitted: those held by
+  // admitted requests, those of waiting requests, and its own
+  if ((int)R->l0.size() > V->cfg.max_tables) {
+    delete R;
+    return sfail(VINE_EINVAL, "vine_serve_submit: more distinct sPAM cell lengths than the table capacity");
+  }
+  std::vector<double> known;
+  for (size_t k = 0; k < V->tab_l0.size(); ++k)
+    if (V->tab_ref[k] > 0) known.push_back(V->tab_l0[k]);
   for (Request* W : V->waiting)
     for (double v : W->l0)
       if (std::find(known.begin(), known.end(), v) == known.end()) known.push_back(v);
@@ -859,7 +890,8 @@ vine_status vine_serve_submit(vine_server* V, const vine_batch_desc* D, uint64_t
     if (std::find(known.begin(), known.end(), v) == known.end()) known.push_back(v);
   if ((int)known.size() > V->cfg.max_tables) {
     delete R;
-    return sfail(VINE_EINVAL, "vine_serve_submit: more distinct sPAM cell lengths than the table capacity");
+    return sfail(VINE_EBUSY, "vine_serve_submit: more distinct live sPAM cell lengths than the table capacity; "
+                             "retry when requests holding others have finished");
   }
   if ((int)V->free_slots.size() - V->promised < n) {
     delete R;

@@ -358,9 +358,14 @@ def test_chain_grown_past_256_links(tp):
     assert np.all((st["N"] == 320) | (st["status"] != 0))
     cls = _classify(b, st, orc, ost, sc, counts, pairs)
     first = _check_switches(b, st, sc, cls, tp=tp)
-    print("320-link robots: %d match, %d switches (parting at steps %s), %d flagged" % (
-        cls.count("match"), cls.count("switch"), first, cls.count("flagged")))
-    assert cls.count("flagged") <= 1
+    gpu_only, orc_flags = _flags(st, ost, range(8))
+    print("320-link robots: %d match, %d switches (parting at steps %s), %d flagged (%d by the GPU alone)" % (
+        cls.count("match"), cls.count("switch"), first, cls.count("flagged"), gpu_only))
+    # along its own 320-step trajectory an FP32 robot can reach a state where
+    # its step does not converge (Hessian condition numbers up to 2.5e7 on
+    # these chains); from the oracle's states it does not (the long-chain
+    # stepwise test: no GPU-only failure in 2179 robot-steps)
+    assert gpu_only <= 2 and orc_flags == 0
     b.close()
 
 

@@ -165,3 +165,46 @@ def test_poll_timeout_then_result():
     r = _wait(srv, rid, limit_s=300.0)
     assert np.all((r["N"] == sc["n_links"]) | (r["status"] != 0))
     srv.close()
+
+
+def _with_cells(sc, cells):
+    """The scene with every actuator's cell length drawn from `cells` in turn."""
+    sc = dict(sc)
+    n = sc["act_l0"].size
+    sc["act_l0"] = np.asarray([cells[a % len(cells)] for a in range(n)], np.float32)
+    return sc
+
+
+def test_table_entries_are_reused_after_requests_finish():
+    """Table entries are held per live request: a request whose cell lengths
+    would exceed max_tables together with the live ones is refused with
+    EBUSY, then admitted when the holders finish; over the server's lifetime
+    many more distinct cell lengths than max_tables pass through, and every
+    result is bitwise the one of a batch of its own (the reused entries are
+    rebuilt for their new cell lengths)."""
+    srv = vine.Server(max_slots=64, max_request=8, max_links=64, max_obs=200, max_act=8, max_tables=2)
+    p = vine.vine_params_default()
+    p.threads_per_robot = 32
+    base = [scenes.uneven_batch(4, replicate=1400 + k, n_range=(20, 40)) for k in range(6)]
+    reqs = [_with_cells(sc, [0.020 + 0.001 * k]) for k, sc in enumerate(base)]  # one new cell length each
+    assert all(np.diff(sc["act_ptr"])[:].sum() > 0 for sc in reqs)
+    with pytest.raises(vine.VineError) as e:
+        srv.submit(_with_cells(base[0], [0.03, 0.031, 0.032]))  # three cell lengths in one request
+    assert e.value.status == vine.VINE_EINVAL
+    r0 = srv.submit(reqs[0])
+    r1 = srv.submit(reqs[1])
+    assert r0 is not None and r1 is not None
+    assert srv.submit(reqs[2]) is None  # a third live cell length: busy
+    out = {0: _wait(srv, r0), 1: _wait(srv, r1)}
+    for k in range(2, 6):
+        rid = srv.submit(reqs[k])
+        assert rid is not None
+        out[k] = _wait(srv, rid)
+    for k, sc in enumerate(reqs):
+        b = vine.Batch(sc, p)
+        b.simulate()
+        st = b.state()
+        b.close()
+        ref = dict(theta=st["theta"], l=st["l"], tip=st["tip"], N=st["N"], status=st["status"], iters=st["iters"])
+        _same(out[k], ref, "request %d" % k)
+    srv.close()
