@@ -292,6 +292,8 @@ def run_gpu(args):
     surr = surrogate_leg(args) if ws == 1 and args.surrogate_steps > 0 else None
     if rank == 0:
         cpu = cpu_baseline(args, sc) if ws == 1 and not args.no_cpu else None
+        if cpu is not None and args.cpu_other_robots > 0:
+            cpu["other_configs"] = cpu_other_configs(args)
         lat = {"p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
                "what": "latency of one whole-batch simulate call"}
         result = {
@@ -463,6 +465,7 @@ def uneven_leg(args, vine, scenes, torch, stream, flush):
         return rls / (sum(ms) / 1e3), float(np.mean(ms))
 
     v0, ms0 = timed(2)
+    st0 = b.stats(stream)
     cls0 = b.classes()
     t0 = time.perf_counter()
     tune = b.autotune(args.uneven_sample, stream)
@@ -474,7 +477,9 @@ def uneven_leg(args, vine, scenes, torch, stream, flush):
     return {"workload": "uneven batch: %d robots, links U{30..300} of U[1,3] cm, 5-200 obstacles, 0-8 actuators"
                         % args.uneven_robots,
             "robot_link_steps_per_step": scenes.robot_link_steps(sc["n_links"]),
-            "default": {"value": v0, "ms_per_step": ms0, "classes": shape(cls0)},
+            "default": {"value": v0, "ms_per_step": ms0, "classes": shape(cls0),
+                        "iters_per_step": st0["iterations"] / max(st0["steps_total"], 1),
+                        "robots_maxiter": st0["n_maxiter"]},
             "autotuned": {"value": v1, "ms_per_step": ms1, "classes": shape(cls1), "adopted": tune["adopted"],
                           "list_margin_R": tune["list_margin"], "candidates": tune["candidates"],
                           "sample": tune["sample"], "sample_ms_default": tune["default_ms"],
@@ -510,11 +515,13 @@ def robust_leg(args, vine, scenes, torch, stream, flush):
         ms_g.append(e1.elapsed_time(e2))
         rls += b.stats(stream)["robot_link_steps"]
     st = out["status"].cpu().numpy()
+    stats = b.stats(stream)
     b.close()
     return {"workload": "robustness batch: %d designs x %d perturbations, 150 links, 60 obstacles, 2.25 m box"
                         % (args.robust_designs, args.robust_perturb),
             "value": rls / (sum(ms_f) / 1e3), "unit": UNIT, "simulate_ms": float(np.mean(ms_f)),
-            "grad_ms": float(np.mean(ms_g)), "grad_ok": int((st == 0).sum()), "robots": int(st.size)}
+            "grad_ms": float(np.mean(ms_g)), "grad_ok": int((st == 0).sum()), "robots": int(st.size),
+            "iters_per_step": stats["iterations"] / max(stats["steps_total"], 1), "robots_maxiter": stats["n_maxiter"]}
 
 
 def studies_leg(args):
@@ -690,6 +697,32 @@ def cpu_baseline(args, sc, robots=None):
             "sample": "first %d robots of the workload, all 100 growth steps (%.1f s)" % (robots, dt)}
 
 
+def cpu_other_configs(args):
+    """The oracle on seeded subsets of the uneven batch (config 3) and the
+    robustness batch (config 4), robot-link-steps per second of host time:
+    the figures extrapolate to the full batches per robot-link-step."""
+    import oracle
+    from paper_2509_15180_gb300 import scenes
+
+    out = {}
+    cores = os.cpu_count() or 1
+    k = args.cpu_other_robots
+    # the uneven batch's first k robots (robots are drawn one after another);
+    # k robustness designs with one perturbation each
+    subs = (("uneven", scenes.uneven_batch(k), "the uneven batch's first %d robots"),
+            ("robustness", scenes.robustness_batch(n_designs=k, n_perturb=1)[0],
+             "%d robustness designs (150 links, 60 obstacles), one perturbation each"))
+    for name, sub, what in subs:
+        orc = oracle.Oracle(sub)
+        st = orc.new_state()
+        t0 = time.perf_counter()
+        orc.run(st, int(sub["n_links"].max()), threads=cores)
+        dt = time.perf_counter() - t0
+        out[name] = {"value": float(st["rls"].sum()) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+                     "sample": "%s (%.1f s)" % (what % k, dt)}
+    return out
+
+
 def run_reference(args):
     """Reference arm: the oracle on the host cores, same metric and workload."""
     from paper_2509_15180_gb300 import scenes
@@ -732,6 +765,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-robots", type=int, default=96)
     ap.add_argument("--ref-robots", type=int, default=48)
+    ap.add_argument("--cpu-other-robots", type=int, default=24,
+                    help="CPU oracle on this many robots of the uneven and robustness batches (0: skip)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--traffic", type=float, default=None)
     ap.add_argument("--no-serve", action="store_true")
