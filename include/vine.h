@@ -205,7 +205,9 @@ vine_status vine_batch_create(const vine_batch_desc* desc, const vine_params* pa
 vine_status vine_batch_reset(vine_batch* b, void* cuda_stream);
 
 /* Grows every instance by up to n_steps links (capped at its n_links), each
- * step solved to equilibrium, in one persistent launch.  Async. */
+ * step solved to equilibrium, in one persistent launch per length class
+ * (see vine_autotune).  An instance whose step does not converge stops
+ * there (status VINE_INST_MAXITER).  Async. */
 vine_status vine_grow_step(vine_batch* b, int32_t n_steps, void* cuda_stream);
 
 /* Re-solves every instance's equilibrium at its present links without
@@ -215,13 +217,15 @@ vine_status vine_grow_step(vine_batch* b, int32_t n_steps, void* cuda_stream);
  * grow while its actuation changes: the tip-steering of the paper's
  * supplement, where growth is stunted by penalising changes in length and
  * an actuator at the tip is pressurised.  fix_length = 0 leaves it free in
- * [0, l_seg].  Instances with no links, non-finite or bad input are
- * skipped.  Counted in the statistics like a growth step.  (vine_grad
+ * [0, l_seg].  Instances with no links or a status other than OK (a failed
+ * step, non-finite or bad input; vine_batch_reset and vine_set_state
+ * restore it) are skipped.  Counted in the statistics like a growth step.  (vine_grad
  * treats the distal length as free unless it sits at a bound.)  Async. */
 vine_status vine_relax(vine_batch* b, int32_t fix_length, void* cuda_stream);
 
-/* Grows every instance to its n_links: one persistent launch over a
- * longest-first work queue, replayed from a CUDA graph.  Async. */
+/* Grows every instance to its n_links: one persistent launch per length
+ * class over its longest-first work queue (the classes on parallel
+ * branches), replayed from a CUDA graph.  Async. */
 vine_status vine_simulate(vine_batch* b, void* cuda_stream);
 
 /* Launch autotuner.  A batch grows in length classes (robots of up to 64
