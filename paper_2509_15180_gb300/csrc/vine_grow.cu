@@ -110,9 +110,11 @@ __device__ __forceinline__ double warp_sum(double v) {
 // only on team-uniform values (reductions, broadcasts, the robot's sizes),
 // so all warps reach every barrier.
 // Scratch layout (floats): FF scan totals [0, 8), suffix totals [8, 12),
-// broadcast [12], sweep results [16, 20), float-float sums [20, 28), float sums
-// [28, 32), int sums and counts [32, 36), maxima [36, 40), flags [40, 44).
-constexpr int kTeamScratch = 48;
+// broadcasts [12, 14), sweep results [16, 20), float-float sums [20, 28),
+// float sums [28, 32), int sums and counts [32, 36), maxima [36, 40), flags
+// and second int sums [40, 44), second FF scan totals [48, 56), second
+// suffix totals [56, 60).
+constexpr int kTeamScratch = 64;
 
 template <int TP>
 struct Team {
@@ -146,6 +148,49 @@ __device__ __forceinline__ FF team_excl_scan(FF v, const Team<TP>& t) {
   return x;
 }
 
+// two exclusive prefixes at once: the arithmetic of two team_excl_scan
+// calls, interleaved (independent chains), with one pair of barriers
+template <int TP>
+__device__ __forceinline__ void team_excl_scan2(FF& a, FF& b, const Team<TP>& t) {
+  const FF va = a, vb = b;
+  const int lane = t.lane();
+  FF x = a, y = b;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const float xh = __shfl_up_sync(kFull, x.hi, d), xl = __shfl_up_sync(kFull, x.lo, d);
+    const float yh = __shfl_up_sync(kFull, y.hi, d), yl = __shfl_up_sync(kFull, y.lo, d);
+    if (lane >= d) {
+      x = ff_add(FF{xh, xl}, x);
+      y = ff_add(FF{yh, yl}, y);
+    }
+  }
+  {
+    const float xh = __shfl_up_sync(kFull, x.hi, 1), xl = __shfl_up_sync(kFull, x.lo, 1);
+    const float yh = __shfl_up_sync(kFull, y.hi, 1), yl = __shfl_up_sync(kFull, y.lo, 1);
+    a = lane == 0 ? FF{0.f, 0.f} : FF{xh, xl};
+    b = lane == 0 ? FF{0.f, 0.f} : FF{yh, yl};
+  }
+  if (TP == 32) return;
+  if (lane == 31) {
+    const FF ia = ff_add(a, va), ib = ff_add(b, vb);  // the warp's totals
+    t.scr[2 * t.warp()] = ia.hi;
+    t.scr[2 * t.warp() + 1] = ia.lo;
+    t.scr[48 + 2 * t.warp()] = ib.hi;
+    t.scr[49 + 2 * t.warp()] = ib.lo;
+  }
+  t.sync();
+  FF ba{0.f, 0.f}, bb{0.f, 0.f};
+  for (int w = 0; w < t.warp(); ++w) {
+    ba = ff_add(ba, FF{t.scr[2 * w], t.scr[2 * w + 1]});
+    bb = ff_add(bb, FF{t.scr[48 + 2 * w], t.scr[49 + 2 * w]});
+  }
+  if (t.warp() > 0) {
+    a = ff_add(ba, a);
+    b = ff_add(bb, b);
+  }
+  t.sync();
+}
+
 template <int TP>
 __device__ __forceinline__ float team_excl_suffix(float v, const Team<TP>& t) {
   float x = warp_excl_suffix(v, t.lane());
@@ -157,6 +202,42 @@ __device__ __forceinline__ float team_excl_suffix(float v, const Team<TP>& t) {
   x += above;
   t.sync();
   return x;
+}
+
+// two exclusive suffixes at once: the arithmetic of two team_excl_suffix
+// calls, interleaved, with one pair of barriers
+template <int TP>
+__device__ __forceinline__ void team_excl_suffix2(float& a, float& b, const Team<TP>& t) {
+  const float va = a, vb = b;
+  const int lane = t.lane();
+  float x = a, y = b;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const float ox = __shfl_down_sync(kFull, x, d), oy = __shfl_down_sync(kFull, y, d);
+    if (lane + d < 32) {
+      x += ox;
+      y += oy;
+    }
+  }
+  {
+    const float ox = __shfl_down_sync(kFull, x, 1), oy = __shfl_down_sync(kFull, y, 1);
+    a = lane == 31 ? 0.f : ox;
+    b = lane == 31 ? 0.f : oy;
+  }
+  if (TP == 32) return;
+  if (lane == 0) {  // the warp's totals
+    t.scr[8 + t.warp()] = a + va;
+    t.scr[56 + t.warp()] = b + vb;
+  }
+  t.sync();
+  float aa = 0.f, ab = 0.f;
+  for (int w = Team<TP>::W - 1; w > t.warp(); --w) {
+    aa += t.scr[8 + w];
+    ab += t.scr[56 + w];
+  }
+  a += aa;
+  b += ab;
+  t.sync();
 }
 
 // float-float sum over the team: butterfly shuffles (every lane ends with
@@ -251,6 +332,57 @@ __device__ __forceinline__ float team_bcast(float v, int owner, const Team<TP>& 
   const float b = t.scr[12];
   t.sync();
   return b;
+}
+
+// The closing reductions of an evaluation in one team operation: a float
+// sum s, a float-float sum j, two integer sums i0 and i1, and the values bx,
+// by of rank `owner` for every rank.  The arithmetic of team_sum_f,
+// team_sum_ff, team_sum_i and team_bcast, interleaved, with one pair of
+// barriers instead of six.
+template <int TP>
+__device__ __forceinline__ void team_close(float& s, FF& j, int& i0, int& i1, float& bx, float& by, int owner,
+                                           const Team<TP>& t) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    s += __shfl_xor_sync(kFull, s, d);
+    const float h = __shfl_xor_sync(kFull, j.hi, d), l = __shfl_xor_sync(kFull, j.lo, d);
+    j = ff_add(j, FF{h, l});
+    i0 += __shfl_xor_sync(kFull, i0, d);
+    i1 += __shfl_xor_sync(kFull, i1, d);
+  }
+  if (TP == 32) {
+    bx = __shfl_sync(kFull, bx, owner);
+    by = __shfl_sync(kFull, by, owner);
+    return;
+  }
+  int* q = reinterpret_cast<int*>(t.scr + 32);
+  if (t.lane() == 0) {
+    t.scr[28 + t.warp()] = s;
+    t.scr[20 + 2 * t.warp()] = j.hi;
+    t.scr[21 + 2 * t.warp()] = j.lo;
+    q[t.warp()] = i0;
+    q[8 + t.warp()] = i1;
+  }
+  if (t.r == owner) {
+    t.scr[12] = bx;
+    t.scr[13] = by;
+  }
+  t.sync();
+  s = t.scr[28];
+  j = FF{t.scr[20], t.scr[21]};
+  for (int w = 1; w < Team<TP>::W; ++w) {
+    s += t.scr[28 + w];
+    j = ff_add(j, FF{t.scr[20 + 2 * w], t.scr[21 + 2 * w]});
+  }
+  i0 = 0;
+  i1 = 0;
+  for (int w = 0; w < Team<TP>::W; ++w) {
+    i0 += q[w];
+    i1 += q[8 + w];
+  }
+  bx = t.scr[12];
+  by = t.scr[13];
+  t.sync();
 }
 
 // exclusive prefix of integer counts over the ranks, and their total
@@ -711,8 +843,8 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
     sy = ff_add(sy, ly);
   }
   // link start points relative to the base
-  FF px = team_excl_scan(sx, tm);
-  FF py = team_excl_scan(sy, tm);
+  FF px = sx, py = sy;
+  team_excl_scan2(px, py, tm);
   const float kap = 2.f * A.w_c * I.kc;
   const float floor_d = 1e-6f * A.w_a * I.PR3;
   int ntest = 0;
@@ -856,8 +988,8 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
     tfx += S.FX[j];
     tfy += S.FY[j];
   }
-  float fsx = team_excl_suffix(tfx, tm);
-  float fsy = team_excl_suffix(tfy, tm);
+  float fsx = tfx, fsy = tfy;
+  team_excl_suffix2(fsx, fsy, tm);
   float tt = 0.f;
   for (int j = j1 - 1; j >= j0; --j) {
     const float t = S.TL[j] + (S.LUX[j] * fsy - S.LUY[j] * fsx);
@@ -877,20 +1009,22 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
   EvalOut E;
   const float dlr = I.l_seg - l;
   const float Gt = A.w_b * I.kg * dlr * dlr;  // growth term
-  E.S = team_sum_f(Sl, tm) + Gt;
-  E.J = ff_add(team_sum_ff(Jl, tm), Gt);
   const int owner = (N - 1) / B;
+  int nt = ntest, sg = (int)sig;
+  team_close(Sl, Jl, nt, sg, ulx, uly, owner, tm);
+  E.S = Sl + Gt;
+  E.J = ff_add(Jl, Gt);
   const float glc = S.LX[0];  // written by the owner thread before the team barrier above
   E.hll = 2.f * A.w_b * I.kg + S.LX[1];
   E.q0 = S.LX[2];
   E.q1 = S.LX[3];
   E.q2 = S.LX[4];
-  E.ulx = team_bcast(ulx, owner, tm);
-  E.uly = team_bcast(uly, owner, tm);
+  E.ulx = ulx;
+  E.uly = uly;
   E.gl = -2.f * A.w_b * I.kg * (I.l_seg - l) - glc;
   E.kg_wb = A.w_b * I.kg;
-  E.tests = team_sum_i(ntest, tm) * KS;
-  E.sig = (unsigned)team_sum_i((int)sig, tm);
+  E.tests = nt * KS;
+  E.sig = (unsigned)sg;
   tm.sync();
   return E;
 }
