@@ -247,7 +247,7 @@ def run_gpu(args):
                        14.0 * (st_last["pair_tests"] - st_last["circle_pair_tests"]))
     launch_s = float(np.mean(step_ms)) / 1e3
     achieved = flops / launch_s / 1e12
-    # the survey's algorithmic work: I W per robot-link-step, I the Newton
+    # the algorithmic work of the method: I W per robot-link-step, I the Newton
     # iterations per growth step, W = 40 + K_s (10 N_circ + 14 N_box) flops
     # per link and iteration (1000 for 20 circles and 20 boxes, K_s = 2)
     n_obs = np.diff(sc["obs_ptr"]).astype(np.int64)
