@@ -271,33 +271,6 @@ __device__ __forceinline__ FF team_dot(const float* a, const float* b, int j0, i
 }
 
 template <int TP>
-__device__ __forceinline__ float team_sum_f(float v, const Team<TP>& t) {
-#pragma unroll
-  for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
-  if (TP == 32) return v;
-  if (t.lane() == 0) t.scr[28 + t.warp()] = v;
-  t.sync();
-  float s = t.scr[28];
-  for (int w = 1; w < Team<TP>::W; ++w) s += t.scr[28 + w];
-  t.sync();
-  return s;
-}
-
-template <int TP>
-__device__ __forceinline__ int team_sum_i(int v, const Team<TP>& t) {
-#pragma unroll
-  for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(kFull, v, d);
-  if (TP == 32) return v;
-  int* q = reinterpret_cast<int*>(t.scr + 32);
-  if (t.lane() == 0) q[t.warp()] = v;
-  t.sync();
-  int s = 0;
-  for (int w = 0; w < Team<TP>::W; ++w) s += q[w];
-  t.sync();
-  return s;
-}
-
-template <int TP>
 __device__ __forceinline__ float team_max(float v, const Team<TP>& t) {
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) v = fmaxf(v, __shfl_xor_sync(kFull, v, d));
@@ -323,22 +296,11 @@ __device__ __forceinline__ bool team_any(bool b, const Team<TP>& t) {
   return a != 0;
 }
 
-// value of rank `owner`, for every rank
-template <int TP>
-__device__ __forceinline__ float team_bcast(float v, int owner, const Team<TP>& t) {
-  if (TP == 32) return __shfl_sync(kFull, v, owner);
-  if (t.r == owner) t.scr[12] = v;
-  t.sync();
-  const float b = t.scr[12];
-  t.sync();
-  return b;
-}
-
 // The closing reductions of an evaluation in one team operation: a float
 // sum s, a float-float sum j, two integer sums i0 and i1, and the values bx,
-// by of rank `owner` for every rank.  The arithmetic of team_sum_f,
-// team_sum_ff, team_sum_i and team_bcast, interleaved, with one pair of
-// barriers instead of six.
+// by of rank `owner` for every rank.  Each sum is a butterfly over the warp
+// (the float-float one as in team_sum_ff), then the warps' partials in warp
+// order; the four chains are interleaved and share one pair of barriers.
 template <int TP>
 __device__ __forceinline__ void team_close(float& s, FF& j, int& i0, int& i1, float& bx, float& by, int owner,
                                            const Team<TP>& t) {
