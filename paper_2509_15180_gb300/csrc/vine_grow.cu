@@ -70,10 +70,15 @@ __device__ __forceinline__ FF ff_mul(FF a, float b) {
   return quick_two_sum(p.hi, p.lo);
 }
 
+// The shuffle levels of the scans and sums below are kept as loops
+// (`unroll 1`): they are inlined at many call sites, the growth kernel's
+// first stall is instruction fetch, and the rolled form took 10 KB off its
+// text and 7 % off each evaluation, with the same arithmetic.
+
 // exclusive prefix (sum over lanes < lane) of float-float values
 __device__ __forceinline__ FF warp_excl_scan(FF v, int lane) {
   FF x = v;
-#pragma unroll
+#pragma unroll 1
   for (int d = 1; d < 32; d <<= 1) {
     float h = __shfl_up_sync(kFull, x.hi, d);
     float l = __shfl_up_sync(kFull, x.lo, d);
@@ -87,7 +92,7 @@ __device__ __forceinline__ FF warp_excl_scan(FF v, int lane) {
 // exclusive suffix (sum over lanes > lane)
 __device__ __forceinline__ float warp_excl_suffix(float v, int lane) {
   float x = v;
-#pragma unroll
+#pragma unroll 1
   for (int d = 1; d < 32; d <<= 1) {
     float o = __shfl_down_sync(kFull, x, d);
     if (lane + d < 32) x += o;
@@ -155,7 +160,7 @@ __device__ __forceinline__ void team_excl_scan2(FF& a, FF& b, const Team<TP>& t)
   const FF va = a, vb = b;
   const int lane = t.lane();
   FF x = a, y = b;
-#pragma unroll
+#pragma unroll 1
   for (int d = 1; d < 32; d <<= 1) {
     const float xh = __shfl_up_sync(kFull, x.hi, d), xl = __shfl_up_sync(kFull, x.lo, d);
     const float yh = __shfl_up_sync(kFull, y.hi, d), yl = __shfl_up_sync(kFull, y.lo, d);
@@ -211,7 +216,7 @@ __device__ __forceinline__ void team_excl_suffix2(float& a, float& b, const Team
   const float va = a, vb = b;
   const int lane = t.lane();
   float x = a, y = b;
-#pragma unroll
+#pragma unroll 1
   for (int d = 1; d < 32; d <<= 1) {
     const float ox = __shfl_down_sync(kFull, x, d), oy = __shfl_down_sync(kFull, y, d);
     if (lane + d < 32) {
@@ -245,7 +250,7 @@ __device__ __forceinline__ void team_excl_suffix2(float& a, float& b, const Team
 // warps' sums in warp order
 template <int TP>
 __device__ __forceinline__ FF team_sum_ff(FF v, const Team<TP>& t) {
-#pragma unroll
+#pragma unroll 1
   for (int d = 16; d > 0; d >>= 1) {
     const float h = __shfl_xor_sync(kFull, v.hi, d), l = __shfl_xor_sync(kFull, v.lo, d);
     v = ff_add(v, FF{h, l});
@@ -304,7 +309,7 @@ __device__ __forceinline__ bool team_any(bool b, const Team<TP>& t) {
 template <int TP>
 __device__ __forceinline__ void team_close(float& s, FF& j, int& i0, int& i1, float& bx, float& by, int owner,
                                            const Team<TP>& t) {
-#pragma unroll
+#pragma unroll 1
   for (int d = 16; d > 0; d >>= 1) {
     s += __shfl_xor_sync(kFull, s, d);
     const float h = __shfl_xor_sync(kFull, j.hi, d), l = __shfl_xor_sync(kFull, j.lo, d);
