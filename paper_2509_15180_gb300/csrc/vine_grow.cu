@@ -70,10 +70,12 @@ __device__ __forceinline__ FF ff_mul(FF a, float b) {
   return quick_two_sum(p.hi, p.lo);
 }
 
-// The shuffle levels of the scans and sums below are kept as loops
-// (`unroll 1`): they are inlined at many call sites, the growth kernel's
-// first stall is instruction fetch, and the rolled form took 10 KB off its
-// text and 7 % off each evaluation, with the same arithmetic.
+// Loops stay rolled (`unroll 1`) where unrolling buys nothing: the shuffle
+// levels of the scans and sums below (inlined at many call sites) and every
+// loop over a rank's links (1-4 iterations at the team sizes used).  The
+// growth kernel's first stall was instruction fetch; the compiler's
+// unrolling of these loops made up 30 KB of its 105 KB of text, and the
+// rolled form takes 29 % off each evaluation with the same arithmetic.
 
 // exclusive prefix (sum over lanes < lane) of float-float values
 __device__ __forceinline__ FF warp_excl_scan(FF v, int lane) {
@@ -271,6 +273,7 @@ __device__ __forceinline__ FF team_sum_ff(FF v, const Team<TP>& t) {
 template <int TP>
 __device__ __forceinline__ FF team_dot(const float* a, const float* b, int j0, int j1, const Team<TP>& t) {
   FF s{0.f, 0.f};
+  #pragma unroll 1
   for (int j = j0; j < j1; ++j) s = ff_add(s, two_prod(a[j], b[j]));
   return team_sum_ff(s, t);
 }
@@ -678,6 +681,7 @@ struct EvalOut {
 // lists were not built for).
 template <int TP>
 __device__ __forceinline__ void reset_lists(const Smem& S, int n, const Team<TP>& tm) {
+  #pragma unroll 1
   for (int j = tm.r; j < n; j += TP) S.CL[j * (kListCap + 1)] = kListStale;
   tm.sync();
 }
@@ -698,6 +702,7 @@ __device__ void rebuild_lists(const InstDev& I, const Smem& S, int N, int j0, in
   const int lane = tm.lane();
   const float margin = margin_r * I.R, mv = 0.64f * margin * margin;
   int nre = 0;
+  #pragma unroll 1
   for (int j = j0; j < j1; ++j) {
     const float x0 = px.hi, y0 = py.hi;
     px = ff_add(px, S.LUX[j]);
@@ -723,6 +728,7 @@ __device__ void rebuild_lists(const InstDev& I, const Smem& S, int N, int j0, in
   // queue the stale links in link order: exclusive prefix of the lanes' counts
   int total;
   int off = team_excl_scan_i(nre, total, tm);
+  #pragma unroll 1
   for (int j = j0; j < j1 && nre > 0; ++j)
     if (S.CL[j * (kListCap + 1)] == kListStale) S.RQ[off++] = j;
   tm.sync();
@@ -789,10 +795,12 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
   const int j0 = min(tm.r * B, N), j1 = min(j0 + B, N);
   // headings psi_j = psi_b + sum_{i<=j} theta_i
   FF hs{0.f, 0.f};
+  #pragma unroll 1
   for (int j = j0; j < j1; ++j) hs = ff_add(hs, S.TH[j]);
   FF psi = ff_add(team_excl_scan(hs, tm), I.bpsi);
   FF sx{0.f, 0.f}, sy{0.f, 0.f};
   float ulx = 0.f, uly = 0.f;
+  #pragma unroll 1
   for (int j = j0; j < j1; ++j) {
     psi = ff_add(psi, S.TH[j]);
     float sn, cs;
@@ -822,6 +830,7 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
   // magnitudes in FP32 (only a scale for that test): GB300's FP64 rate is low
   FF Jl{0.f, 0.f};
   float Sl = 0.f;
+  #pragma unroll 1
   for (int j = j0; j < j1; ++j) {
     // ---- bending and actuation at joint j (Eq. restoring_moment)
     const float th = S.TH[j];
@@ -951,6 +960,7 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
   // ---- gradient: g_j = w_a M_tot,j - T_j, T_j = moment about p_j of the
   // contact forces on links >= j = sum_{i>=j} (tl_i + Lu_i x F_{>i}).
   float tfx = 0.f, tfy = 0.f;
+  #pragma unroll 1
   for (int j = j0; j < j1; ++j) {
     tfx += S.FX[j];
     tfy += S.FY[j];
@@ -958,6 +968,7 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
   float fsx = tfx, fsy = tfy;
   team_excl_suffix2(fsx, fsy, tm);
   float tt = 0.f;
+  #pragma unroll 1
   for (int j = j1 - 1; j >= j0; --j) {
     const float t = S.TL[j] + (S.LUX[j] * fsy - S.LUY[j] * fsx);
     S.TL[j] = t;
@@ -968,6 +979,7 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
     fsy += S.FY[j];
   }
   float run = team_excl_suffix(tt, tm);
+  #pragma unroll 1
   for (int j = j1 - 1; j >= j0; --j) {
     run += S.TL[j];
     S.G[j] -= run;
@@ -1023,6 +1035,7 @@ __device__ double gn_solve(const InstDev& I, const Smem& S, int N, bool lfix, co
   // team runs them on its first warp alone (the second would lag behind the
   // writes) and takes the results from the scratch.
   const bool sweeper = TP == 32 || tm.warp() == 0;
+  #pragma unroll 1
   for (int j = sweeper ? N - 1 : -1; j >= 0; --j) {
     float c00 = S.C0[j], c01 = S.C1[j], c02 = S.C2[j], c11 = S.C3[j], c12 = S.C4[j], c22 = S.C5[j];
     const float dj = S.DD[j], gj = S.G[j], lx = S.LUX[j], ly = S.LUY[j];
@@ -1082,6 +1095,7 @@ __device__ double gn_solve(const InstDev& I, const Smem& S, int N, bool lfix, co
   // the displacement of link end i+1 is z x sum_{k<=i} W0_k Lu_k, with W0_k
   // the heading change sum_{j<=k} dtheta_j
   FF W0{0.f, 0.f}, W1{0.f, 0.f}, W2{0.f, 0.f};
+  #pragma unroll 1
   for (int j = 0; sweeper && pd && j < N; ++j) {
     const float h0 = S.C0[j], h1 = S.C1[j], h2 = S.C2[j], iD = S.C3[j], cc = S.C4[j];
     const float lx = S.LUX[j], ly = S.LUY[j];
@@ -1226,8 +1240,10 @@ __device__ int step_solve(const GrowArgs& A, const InstDev& I, const Smem& S, in
         // a trial so short that no unknown changed (the step below FP32
         // resolution) is no progress: the iteration would repeat itself
         bool moved = lt != l0;
+        #pragma unroll 1
         for (int j = j0; j < j1 && !moved; ++j) moved = S.TH[j] != S.TH0[j];
         if (!team_any(moved, tm)) {
+          #pragma unroll 1
           for (int j = j0; j < j1; ++j) S.TH[j] = S.TH0[j];
           l = l0;
           tm.sync();
@@ -1238,6 +1254,7 @@ __device__ int step_solve(const GrowArgs& A, const InstDev& I, const Smem& S, in
         if (h < A.max_halv) {
           alpha *= 0.5f;
           ++h;
+          #pragma unroll 1
           for (int j = j0; j < j1; ++j) S.TH[j] = S.TH0[j] + alpha * S.DTH[j];
           lt = fminf(fmaxf(l0 + alpha * dl, 0.f), I.l_seg);
           l_ev = lt;
@@ -1245,6 +1262,7 @@ __device__ int step_solve(const GrowArgs& A, const InstDev& I, const Smem& S, in
           continue;
         }
         // no acceptable trial: the step ends at the last accepted iterate
+        #pragma unroll 1
         for (int j = j0; j < j1; ++j) S.TH[j] = S.TH0[j];
         l = l0;
         tm.sync();
@@ -1287,9 +1305,11 @@ __device__ int step_solve(const GrowArgs& A, const InstDev& I, const Smem& S, in
       // the Gauss-Newton sweep lost its pivots to FP32 range (bending floor
       // against contact stiffness): steepest descent, at most 0.05 rad per joint
       float gm = 0.f;
+      #pragma unroll 1
       for (int j = j0; j < j1; ++j) gm = fmaxf(gm, fabsf(S.G[j]));
       gm = team_max(gm, tm);
       const float sc = gm > 0.f ? 0.05f / gm : 0.f;
+      #pragma unroll 1
       for (int j = j0; j < j1; ++j) S.DTH[j] = -S.G[j] * sc;
       dl = lfix ? 0.f : -E.gl * sc * I.l_seg * I.l_seg;
       if (!(sc > 0.f) || !isfinite(dl)) {
@@ -1301,6 +1321,7 @@ __device__ int step_solve(const GrowArgs& A, const InstDev& I, const Smem& S, in
       tm.sync();
     }
     if (r <= tol2) {
+      #pragma unroll 1
       for (int j = j0; j < j1; ++j) S.TH[j] += S.DTH[j];
       l = fminf(fmaxf(l + dl, 0.f), I.l_seg);
       // the point the small step reached is evaluated once more: a step that
@@ -1324,6 +1345,7 @@ __device__ int step_solve(const GrowArgs& A, const InstDev& I, const Smem& S, in
       const FF d = team_dot(S.G, S.DTH, j0, j1, tm);
       gd = d.hi + d.lo;
     }
+    #pragma unroll 1
     for (int j = j0; j < j1; ++j) S.TH0[j] = S.TH[j];
     l0 = l;
     gl0 = E.gl;
@@ -1333,6 +1355,7 @@ __device__ int step_solve(const GrowArgs& A, const InstDev& I, const Smem& S, in
     slope0 = gd + (l_moves ? gl0 * dl : 0.f);
     alpha = 1.f;
     h = 0;
+    #pragma unroll 1
     for (int j = j0; j < j1; ++j) S.TH[j] = S.TH0[j] + alpha * S.DTH[j];
     lt = fminf(fmaxf(l0 + alpha * dl, 0.f), I.l_seg);
     l_ev = lt;
@@ -1563,6 +1586,7 @@ __device__ void grad_instance(const GrowArgs& A, const GradArgs& G, int inst, co
   if (G.kind == 0) {
     // tip relative to the base, and dc/dtheta_j = s . (z x (p_N - p_j))
     float sx = 0.f, sy = 0.f;
+    #pragma unroll 1
     for (int j = j0; j < j1; ++j) {
       sx += S.LUX[j];
       sy += S.LUY[j];
@@ -1572,6 +1596,7 @@ __device__ void grad_instance(const GrowArgs& A, const GradArgs& G, int inst, co
     const double ex = (double)tx - (double)gx, ey = (double)ty - (double)gy;
     c = sqrt(ex * ex + ey * ey);
     const float ux = c > 0.0 ? (float)(ex / c) : 0.f, uy = c > 0.0 ? (float)(ey / c) : 0.f;
+    #pragma unroll 1
     for (int j = j1 - 1; j >= j0; --j) {
       rx += S.LUX[j];
       ry += S.LUY[j];
@@ -1583,6 +1608,7 @@ __device__ void grad_instance(const GrowArgs& A, const GradArgs& G, int inst, co
     // errors e_k = p_k - q_k as forces f_j = (2/N) e_{j+1} at the end of
     // link j: dc/dtheta_j = sum_{i >= j} (Lu_i x f_i + Lu_i x F_{>i})
     FF hx{0.f, 0.f}, hy{0.f, 0.f};
+    #pragma unroll 1
     for (int j = j0; j < j1; ++j) {
       hx = ff_add(hx, S.LUX[j]);
       hy = ff_add(hy, S.LUY[j]);
@@ -1592,6 +1618,7 @@ __device__ void grad_instance(const GrowArgs& A, const GradArgs& G, int inst, co
     const float w = 2.f / (float)N;
     double cs = 0.0;
     float tfx = 0.f, tfy = 0.f;
+    #pragma unroll 1
     for (int j = j0; j < j1; ++j) {
       px = ff_add(px, S.LUX[j]);
       py = ff_add(py, S.LUY[j]);
@@ -1605,6 +1632,7 @@ __device__ void grad_instance(const GrowArgs& A, const GradArgs& G, int inst, co
     c = warp_sum(cs) / (double)N;
     float fsx = warp_excl_suffix(tfx, lane), fsy = warp_excl_suffix(tfy, lane);
     float tt = 0.f;
+    #pragma unroll 1
     for (int j = j1 - 1; j >= j0; --j) {
       const float t = S.LUX[j] * (S.FY[j] + fsy) - S.LUY[j] * (S.FX[j] + fsx);
       S.TL[j] = t;
@@ -1613,6 +1641,7 @@ __device__ void grad_instance(const GrowArgs& A, const GradArgs& G, int inst, co
       fsy += S.FY[j];
     }
     float run = warp_excl_suffix(tt, lane);
+    #pragma unroll 1
     for (int j = j1 - 1; j >= j0; --j) {
       run += S.TL[j];
       S.G[j] = -run;  // minus dc/dtheta_j
@@ -1635,6 +1664,7 @@ __device__ void grad_instance(const GrowArgs& A, const GradArgs& G, int inst, co
     const float jb = floorf(ac.x), je = floorf(ac.y);
     const bool span = ac.x < ac.y;
     double sP = 0.0, sB = 0.0, sE = 0.0;
+    #pragma unroll 1
     for (int j = j0; j < j1; ++j) {
       const float cov = fminf(ac.y, (float)(j + 1)) - fmaxf(ac.x, (float)j);
       const bool isb = span && (float)j == jb, ise = span && (float)j == je;
@@ -1848,9 +1878,11 @@ __global__ void pose_kernel(const InstDev* inst, int n_inst, const int* sel, con
   const int j0 = min(lane * B, N), j1 = min(j0 + B, N);
   const float* th = theta + I.th_off;
   FF hs{0.f, 0.f};
+  #pragma unroll 1
   for (int j = j0; j < j1; ++j) hs = ff_add(hs, th[j]);
   FF psi0 = ff_add(warp_excl_scan(hs, lane), I.bpsi);
   FF psi = psi0, sx{0.f, 0.f}, sy{0.f, 0.f};
+  #pragma unroll 1
   for (int j = j0; j < j1; ++j) {
     psi = ff_add(psi, th[j]);
     float sn, cs;
@@ -1861,6 +1893,7 @@ __global__ void pose_kernel(const InstDev* inst, int n_inst, const int* sel, con
   }
   FF px = warp_excl_scan(sx, lane), py = warp_excl_scan(sy, lane);
   psi = psi0;
+  #pragma unroll 1
   for (int j = j0; j < j1; ++j) {
     psi = ff_add(psi, th[j]);
     if (out_pose) {
@@ -1875,6 +1908,7 @@ __global__ void pose_kernel(const InstDev* inst, int n_inst, const int* sel, con
     px = ff_add(px, L * (cs - sn * psi.lo));
     py = ff_add(py, L * (sn + cs * psi.lo));
   }
+  #pragma unroll 1
   for (int j = N + lane; j < I.n_target; j += 32) {
     if (out_pose) {
       out_pose[3 * (oo + j) + 0] = 0.f;
@@ -1908,9 +1942,11 @@ __global__ void contacts_kernel(const InstDev* inst, int n_inst, const float4* o
   const float* th = theta + I.th_off;
   const float4* ob = obs + I.obs_off;
   FF hs{0.f, 0.f};
+  #pragma unroll 1
   for (int j = j0; j < j1; ++j) hs = ff_add(hs, th[j]);
   FF psi0 = ff_add(warp_excl_scan(hs, lane), I.bpsi);
   FF psi = psi0, sx{0.f, 0.f}, sy{0.f, 0.f};
+  #pragma unroll 1
   for (int j = j0; j < j1; ++j) {
     psi = ff_add(psi, th[j]);
     float sn, cs;
@@ -1925,6 +1961,7 @@ __global__ void contacts_kernel(const InstDev* inst, int n_inst, const float4* o
     FF px = px0, py = py0;
     psi = psi0;
     int cnt = 0;
+    #pragma unroll 1
     for (int j = j0; j < j1; ++j) {
       psi = ff_add(psi, th[j]);
       float sn, cs;
