@@ -75,7 +75,7 @@ __device__ __forceinline__ FF ff_mul(FF a, float b) {
 // loop over a rank's links (1-4 iterations at the team sizes used).  The
 // growth kernel's first stall was instruction fetch; the compiler's
 // unrolling of these loops made up 30 KB of its 105 KB of text, and the
-// rolled form takes 29 % off each evaluation with the same arithmetic.
+// rolled form takes 28 % off each evaluation with the same arithmetic.
 
 // exclusive prefix (sum over lanes < lane) of float-float values
 __device__ __forceinline__ FF warp_excl_scan(FF v, int lane) {
