@@ -71,11 +71,12 @@ __device__ __forceinline__ FF ff_mul(FF a, float b) {
 }
 
 // Loops stay rolled (`unroll 1`) where unrolling buys nothing: the shuffle
-// levels of the scans and sums below (inlined at many call sites) and every
-// loop over a rank's links (1-4 iterations at the team sizes used).  The
-// growth kernel's first stall was instruction fetch; the compiler's
-// unrolling of these loops made up 30 KB of its 105 KB of text, and the
-// rolled form takes 28 % off each evaluation with the same arithmetic.
+// levels of the scans and sums below (inlined at many call sites), every
+// loop over a rank's links (1-4 iterations at the team sizes used), the
+// per-joint actuator loop, the broad-phase rebuild and the strided copies.
+// The growth kernel's first stall was instruction fetch; the compiler's
+// unrolling of these loops made up 39 KB of its 105 KB of text, and the
+// rolled form takes 36 % off each evaluation with the same arithmetic.
 
 // exclusive prefix (sum over lanes < lane) of float-float values
 __device__ __forceinline__ FF warp_excl_scan(FF v, int lane) {
@@ -734,11 +735,13 @@ __device__ void rebuild_lists(const InstDev& I, const Smem& S, int N, int j0, in
   tm.sync();
   const float Rm = I.R + margin;
   const unsigned lt = (1u << lane) - 1u;
+  #pragma unroll 1
   for (int q = 0; q < total; ++q) {
     const int j = S.RQ[q];
     const float x0 = S.PB[2 * j], y0 = S.PB[2 * j + 1], lx = S.LUX[j], ly = S.LUY[j];
     const int lb = j * (kListCap + 1);
     int cnt = 0;
+    #pragma unroll 1
     for (int o0 = 0; o0 < I.n_obs; o0 += TP) {
       const int o = o0 + tm.r;
       bool near = false;
@@ -838,6 +841,7 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
     wrinkle(A, th, m, dm, u);
     float M = I.PR3 * m, dM = I.PR3 * dm, U = I.PR3 * u;
     float Um = fabsf(U);
+    #pragma unroll 1
     for (int a = 0; a < I.n_act; ++a) {
       const float4 ac = S.act[a];
       const float cov = fminf(ac.y, (float)(j + 1)) - fmaxf(ac.x, (float)j);
@@ -921,7 +925,9 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
     const int lb = j * (kListCap + 1);
     const bool every = !A.broad || S.CL[lb] == kListFull;
     const int cnt = every ? I.n_obs : (int)S.CL[lb];
+    #pragma unroll 1
     for (int q = 0;;) {
+      #pragma unroll 1
       for (; q < cnt && qn <= kContactQueue - KS; ++q) {
         const int o = every ? q : (int)S.CL[lb + 1 + q];
         const float4 ob = S.obs[o];
@@ -929,6 +935,7 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
         for (int k = 0; k < KS; ++k)
           if (contact_candidate(ob, xk[k], yk[k], Rpre)) S.Q[(qn++) * TP + tm.r] = o * KS + k;
       }
+      #pragma unroll 1
       for (int e = 0; e < qn; ++e) {
         const int code = S.Q[e * TP + tm.r];
         const int o = code / KS, k = code - o * KS;
@@ -1181,6 +1188,7 @@ __device__ int step_solve(const GrowArgs& A, const InstDev& I, const Smem& S, in
   const double tol2 = tol_eff * tol_eff;  // the test compares squared displacements
   float a_th = 0.f, a_l = 0.f;
   if (descend) {
+    #pragma unroll 1
     for (int k = tm.r; k < N; k += TP) S.TH0[k] = S.TH[k];
     tm.sync();
     a_th = A.gd_alpha * 2.f * A.theta_c / (A.w_a * I.PR3);
@@ -1214,6 +1222,7 @@ __device__ int step_solve(const GrowArgs& A, const InstDev& I, const Smem& S, in
         status = kNonFinite;
         break;
       }
+      #pragma unroll 1
       for (int k = tm.r; k < N; k += TP) S.TH[k] -= a_th * S.G[k];
       if (!A.fix_l) l = fminf(fmaxf(l - a_l * E.gl, 0.f), I.l_seg);
       l_ev = l;
@@ -1366,6 +1375,7 @@ __device__ int step_solve(const GrowArgs& A, const InstDev& I, const Smem& S, in
   if (descend) {
     if (status == kOK) {
       bool badl = false;
+      #pragma unroll 1
       for (int k = tm.r; k < N; k += TP) badl = badl || !isfinite(S.TH[k]);
       if (team_any(badl, tm)) status = kNonFinite;
     }
@@ -1390,14 +1400,18 @@ __device__ void process_instance(const GrowArgs& A, int inst, const Smem& S, con
   if (status != kOK) return;
   int N = A.n_cur[inst];
   if (A.n_steps <= 0 || (A.relax ? N == 0 : N >= I.n_target)) return;
+  #pragma unroll 1
   for (int k = tm.r; k < I.n_obs; k += TP) S.obs[k] = A.obs[I.obs_off + k];
+  #pragma unroll 1
   for (int k = tm.r; k < I.n_act; k += TP) S.act[k] = A.act[I.act_off + k];
+  #pragma unroll 1
   for (int k = tm.r; k < N; k += TP) S.TH[k] = A.theta[I.th_off + k];
   float l = A.l_cur[inst];
   reset_lists(S, I.n_target, tm);
   int iters = 0, conv = 0, steps = 0;
   long long rls = 0, evals = 0, linkevals = 0, fallbacks = 0, tests = 0;
   double rmax = 0.0;
+  #pragma unroll 1
   for (int s = 0; s < A.n_steps && (A.relax || N < I.n_target); ++s) {
     if (!A.relax) {
       if (tm.r == 0) S.TH[N] = 0.f;  // new link at the tip
@@ -1423,6 +1437,7 @@ __device__ void process_instance(const GrowArgs& A, int inst, const Smem& S, con
     if (status != kOK) break;
   }
   tm.sync();
+  #pragma unroll 1
   for (int k = tm.r; k < N; k += TP) A.theta[I.th_off + k] = S.TH[k];
   if (tm.r == 0) {
     A.n_cur[inst] = N;
