@@ -1173,7 +1173,7 @@ struct StepStats {
 // Written as one loop around a single evaluation: the first evaluation, the
 // Gauss-Newton re-evaluation, every line-search trial and every descent step
 // pass through the same call, so the evaluation's code is inlined once (the
-// kernel's first stall is instruction fetch).
+// kernel's text is what its instruction fetch holds).
 template <int KS, int TP>
 __device__ int step_solve(const GrowArgs& A, const InstDev& I, const Smem& S, int N, float& l, const Team<TP>& tm,
                           StepStats& st) {
