@@ -1030,7 +1030,7 @@ __device__ EvalOut eval(const GrowArgs& A, const InstDev& I, const Smem& S, int 
 // joint) is raised to a small positive floor instead.
 template <int TP>
 __device__ double gn_solve(const InstDev& I, const Smem& S, int N, bool lfix, const EvalOut& E, float& dl,
-                           const Team<TP>& tm, bool strict, float& max_dth) {
+                           const Team<TP>& tm, bool strict, float& max_dth, double tol2 = -1.0) {
   float A00 = 0.f, A01 = 0.f, A02 = 0.f, A11 = 0.f, A12 = 0.f, A22 = 0.f;
   float b0 = 0.f, b1 = 0.f, b2 = 0.f;
   if (strict && !lfix && !(E.hll > 1e-3f * 2.f * E.kg_wb)) return -1.0;
@@ -1101,14 +1101,24 @@ __device__ double gn_solve(const InstDev& I, const Smem& S, int N, bool lfix, co
   }
   // the displacement of link end i+1 is z x sum_{k<=i} W0_k Lu_k, with W0_k
   // the heading change sum_{j<=k} dtheta_j
-  FF W0{0.f, 0.f}, W1{0.f, 0.f}, W2{0.f, 0.f};
+  // The displacement sums run in FP32 beside a running bound on their
+  // rounding error (each rounding adds at most u times the rounded value;
+  // kU = 2u leaves slack for the products and the bound's own rounding).
+  // With tol2 given (the convergence threshold, squared link lengths) and
+  // the bound deciding on which side of it the float-float result lies, the
+  // FP32 value is returned; otherwise the float-float sums are formed from
+  // the stored steps exactly as they always were, so every convergence
+  // decision is the float-float one.
+  constexpr float kU = 1.1920929e-7f;
+  float w0 = 0.f, w1 = 0.f, w2 = 0.f, e0 = 0.f, e1 = 0.f, e2 = 0.f, emax = 0.f, rd2 = 0.f, rt2 = 0.f;
   #pragma unroll 1
   for (int j = 0; sweeper && pd && j < N; ++j) {
     const float h0 = S.C0[j], h1 = S.C1[j], h2 = S.C2[j], iD = S.C3[j], cc = S.C4[j];
     const float lx = S.LUX[j], ly = S.LUY[j];
     const float dth = -(cc + h0 * V0 + h1 * V1 + h2 * V2) * iD;
     V0 += dth;
-    W0 = ff_add(W0, dth);
+    w0 += dth;
+    e0 += kU * fabsf(w0);
     float ex = 0.f, ey = 0.f;
     if (j == N - 1) {
       dl = lfix ? 0.f : -(E.gl + E.q0 * V0 + E.q1 * V1 + E.q2 * V2) * iH;
@@ -1117,14 +1127,51 @@ __device__ double gn_solve(const InstDev& I, const Smem& S, int N, bool lfix, co
     }
     V1 -= V0 * ly;
     V2 += V0 * lx;
-    W1 = ff_add(W1, ff_mul(W0, -ly));
-    W2 = ff_add(W2, ff_mul(W0, lx));
-    const FF dx = ff_add(W1, ex), dy = ff_add(W2, ey);
+    const float p1 = w0 * -ly, p2 = w0 * lx;
+    w1 += p1;
+    w2 += p2;
+    e1 += fabsf(ly) * e0 + kU * (fabsf(p1) + fabsf(w1));
+    e2 += fabsf(lx) * e0 + kU * (fabsf(p2) + fabsf(w2));
+    const float dx = w1 + ex, dy = w2 + ey;
+    emax = fmaxf(emax, e1 + e2 + kU * (fabsf(dx) + fabsf(dy)));
     const float dt = I.l_seg * dth;
-    const float v2 = fmaxf(dx.hi * dx.hi + dy.hi * dy.hi, dt * dt);
-    if (!(v2 <= rmax2)) rmax2 = v2;  // keeps NaN
+    const float v2 = dx * dx + dy * dy, t2 = dt * dt;
+    if (!(v2 <= rd2)) rd2 = v2;  // keeps NaN
+    if (!(t2 <= rt2)) rt2 = t2;
     if (!(fabsf(dth) <= dmax)) dmax = fabsf(dth);
     if (tm.r == 0) S.DTH[j] = dth;
+  }
+  rmax2 = fmaxf(rd2, rt2);
+  if (!(rd2 <= rt2)) rmax2 = rd2;  // keeps NaN
+  bool decided = false;
+  if (tol2 >= 0.0 && sweeper && pd && isfinite(rd2) && isfinite(emax)) {
+    // bounds on the float-float maximum, through the same float division
+    const float s = sqrtf(rd2), E = emax * 1.001f + 1e-30f;
+    const float hi = fmaxf((s + E) * (s + E) * (1.f + 8.f * kU), rt2);
+    const float lo = fmaxf(fmaxf(s - E, 0.f) * fmaxf(s - E, 0.f) * (1.f - 8.f * kU), rt2);
+    const float l2 = I.l_seg * I.l_seg;
+    decided = (double)(hi / l2) <= tol2 || (double)(lo / l2) > tol2;
+  }
+  if (!decided && sweeper && pd) {
+    __syncwarp();
+    FF W0{0.f, 0.f}, W1{0.f, 0.f}, W2{0.f, 0.f};
+    rmax2 = 0.f;
+    #pragma unroll 1
+    for (int j = 0; j < N; ++j) {
+      const float dth = S.DTH[j], lx = S.LUX[j], ly = S.LUY[j];
+      W0 = ff_add(W0, dth);
+      float ex = 0.f, ey = 0.f;
+      if (j == N - 1) {
+        ex = dl * E.ulx;
+        ey = dl * E.uly;
+      }
+      W1 = ff_add(W1, ff_mul(W0, -ly));
+      W2 = ff_add(W2, ff_mul(W0, lx));
+      const FF dx = ff_add(W1, ex), dy = ff_add(W2, ey);
+      const float dt = I.l_seg * dth;
+      const float v2 = fmaxf(dx.hi * dx.hi + dy.hi * dy.hi, dt * dt);
+      if (!(v2 <= rmax2)) rmax2 = v2;  // keeps NaN
+    }
   }
   if (TP > 32) {
     if (tm.r == 0) {
@@ -1297,7 +1344,7 @@ __device__ int step_solve(const GrowArgs& A, const InstDev& I, const Smem& S, in
       lfix = A.fix_l || (l <= 0.f && E.gl > 0.f) || (l >= I.l_seg && E.gl < 0.f);
     }
     const bool use_exact = exact && phase == kNewton;
-    r = gn_solve(I, S, N, lfix, E, dl, tm, use_exact, mdth);  // squared, link lengths
+    r = gn_solve(I, S, N, lfix, E, dl, tm, use_exact, mdth, tol2);  // squared, link lengths
     if (use_exact && !(r >= 0.0 && isfinite(r))) {
       // exact Hessian not positive definite here: Gauss-Newton matrix instead
       st.fallbacks += 1;
