@@ -38,7 +38,7 @@ L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes (read + write) of one growth launch per robot, from an ncu
 # capture of one launch over 1024 robots x 100 links of this workload:
 # designs and obstacles are read once per robot, so traffic scales with robots.
-GROW_DRAM_BYTES_PER_ROBOT = (1.45024e6 + 9.728e3) / 1024
+GROW_DRAM_BYTES_PER_ROBOT = (1.431296e6 + 9.216e3) / 1024
 
 
 def _dist():
