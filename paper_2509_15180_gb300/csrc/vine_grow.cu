@@ -1146,9 +1146,9 @@ __device__ double gn_solve(const InstDev& I, const Smem& S, int N, bool lfix, co
   bool decided = false;
   if (tol2 >= 0.0 && sweeper && pd && isfinite(rd2) && isfinite(emax)) {
     // bounds on the float-float maximum, through the same float division
-    const float s = sqrtf(rd2), E = emax * 1.001f + 1e-30f;
-    const float hi = fmaxf((s + E) * (s + E) * (1.f + 8.f * kU), rt2);
-    const float lo = fmaxf(fmaxf(s - E, 0.f) * fmaxf(s - E, 0.f) * (1.f - 8.f * kU), rt2);
+    const float s = sqrtf(rd2), eb = emax * 1.001f + 1e-30f;
+    const float hi = fmaxf((s + eb) * (s + eb) * (1.f + 8.f * kU), rt2);
+    const float lo = fmaxf(fmaxf(s - eb, 0.f) * fmaxf(s - eb, 0.f) * (1.f - 8.f * kU), rt2);
     const float l2 = I.l_seg * I.l_seg;
     decided = (double)(hi / l2) <= tol2 || (double)(lo / l2) > tol2;
   }
